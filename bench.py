@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Edge-update throughput and latency of the DAMF hot path on one GB300 (or N replicas).
+
+A step is one batch of the workload through the whole hot path: damf_apply_edges
+(adjacency edit, projection, residual CholQR, core SVD, transform update, row rewrite,
+PPR residual fix-up) followed by damf_ppr_refresh (push until every residual <= eps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config C2] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the same
+workload (bounded sample per step) and prints the same metric with "impl": "reference".
+"""
+
+import argparse
+import json
+import os
+import sys
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--oracle-worker" in sys.argv:
+    # the oracle runs single-threaded: pin BLAS pools before numpy loads
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+import subprocess
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge-updates/sec and p50/p99 update latency at d=128, mixed vs plain FP32, same err"
+UNIT = "edge-updates/s"
+
+
+def workload_desc(c):
+    return ("%s: %s Chung-Lu gamma=%.1f n=%d avg_deg=%g; d=%d alpha=%g eps=%g; batches of U[%d,%d] edges, "
+            "%.0f%% node arrivals, %.0f%% deletions" % (c.name, "directed" if c.directed else "undirected", c.gamma,
+                                                       c.n, c.avg_deg, c.d, c.alpha, c.eps, c.k_lo, c.k_hi,
+                                                       100 * c.p_node, 100 * c.p_del))
+
+
+def make_inputs(c, n_batches):
+    from synth import chung_lu_graph, edge_stream
+    ip, ix, w = chung_lu_graph(c.n, c.avg_deg, c.gamma, seed=c.seed, directed=c.directed)
+    st = edge_stream(ip, ix, w, n_batches, c.k_lo, c.k_hi, c.p_node, c.p_del, c.seed + 1,
+                     max_new_degree=c.max_new_degree, directed=c.directed, nodes_per_batch=c.nodes_per_batch)
+    return ip, ix, st
+
+
+# ---------------------------------------------------------------- oracle (CPU) leg
+def oracle_run(c, steps, warmup, time_budget_s):
+    """Times the FP64 oracle (as it stands) on the first warmup+steps batches, stopping
+    early once time_budget_s of timed work is spent.  Returns a dict."""
+    from oracle.damf import DamfOracle
+    from synth import gaussian_test_matrix
+    ip, ix, st = make_inputs(c, warmup + steps)
+    om = gaussian_test_matrix(c.n, 160 if c.d == 128 else ((c.d + 10 + 31) // 32) * 32, seed=c.seed + 2)
+    t0 = time.perf_counter()
+    orc = DamfOracle(ip, ix, c.d, c.alpha, c.eps, n_cap=st.n_final, directed=c.directed, Omega=om)
+    init_s = time.perf_counter() - t0
+    for b in st.batches[:warmup]:
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        orc.ppr_refresh()
+    lat, edges = [], 0
+    t_start = time.perf_counter()
+    for b in st.batches[warmup:warmup + steps]:
+        t = time.perf_counter()
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        orc.ppr_refresh()
+        lat.append(time.perf_counter() - t)
+        edges += b.k
+        if time.perf_counter() - t_start > time_budget_s:
+            break
+    total = time.perf_counter() - t_start
+    return {"value": edges / total, "unit": UNIT, "cores": 1, "kind": "oracle", "batches": len(lat),
+            "edges": edges, "seconds": total, "init_s": init_s,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "sample": "first %d batches of the %s stream after %d warm-up batches (%d edges), FP64 oracle, "
+                      "1 thread" % (len(lat), c.name, warmup, edges)}
+
+
+def oracle_subprocess(c, steps, budget):
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", c.name, "--steps", str(steps),
+           "--budget", str(budget)]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
+    for line in out.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"error": (out.stderr or out.stdout)[-400:]}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args, c, rank, world):
+    import torch
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    K, W, E = args.steps, args.warmup, args.e2e_steps
+    ip, ix, st = make_inputs(c, W + K + E)
+    cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=st.n_final + 16, nnz=len(ix), directed=c.directed,
+                      refold_every=args.refold_every)
+    om = gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
+    t0 = time.perf_counter()
+    g = DamfGraph(ip, ix, cfg, om)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    # device-resident inputs for every step
+    batches = st.batches
+    ks = np.array([b.k for b in batches], np.int64)
+    off = np.concatenate([[0], np.cumsum(ks)])
+    src = torch.from_numpy(np.concatenate([b.src for b in batches])).to(dev)
+    dst = torch.from_numpy(np.concatenate([b.dst for b in batches])).to(dev)
+    opv = torch.from_numpy(np.concatenate([b.op for b in batches])).to(dev)
+    lib, h = g.lib, g.h
+    sp = __import__("ctypes").c_void_p
+    stream = torch.cuda.current_stream()
+    sptr = sp(stream.cuda_stream)
+
+    def step(i):
+        o = int(off[i])
+        st_ = lib.damf_apply_edges(h, sp(src.data_ptr() + 4 * o), sp(dst.data_ptr() + 4 * o), sp(opv.data_ptr() + o),
+                                   int(ks[i]), int(batches[i].new_nodes), sptr)
+        if st_ != 0:
+            raise RuntimeError("apply_edges status %d" % st_)
+        st_ = lib.damf_ppr_refresh(h, sptr)
+        if st_ != 0:
+            raise RuntimeError("ppr_refresh status %d" % st_)
+
+    for i in range(W):
+        step(i)
+    g.check()
+    s0 = g.stats()
+    g.set_timing(True)
+    g.timing()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        evs[0].record(stream)
+        for j in range(K):
+            step(W + j)
+            evs[j + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    g.check()
+    step_ms = np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(K)])
+    elapsed_ms = float(step_ms.sum())
+    stage = g.timing()
+    g.set_timing(False)
+    s1 = g.stats()
+    edges = int(ks[W:W + K].sum())
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = edges * world / (elapsed_ms / 1e3)
+
+    # e2e: host buffers through damf_apply_edges_host, a D2H read of sigma every step
+    sig = torch.empty(c.d, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    e2e_edges, h2d = 0, 0
+    for j in range(E):
+        b = batches[W + K + j]
+        g.apply_edges_host(b.src, b.dst, b.op, b.new_nodes)
+        g.ppr_refresh()
+        sig.copy_(g.embeddings(want=("sigma",))["sigma"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        e2e_edges += b.k
+        h2d += b.k * 9
+    e2e_s = time.perf_counter() - t_e
+    g.check()
+
+    # roofline of the dominant kernel, from live events and device counters
+    d = c.d
+    B = 4 * d
+    pushes = s1["pushes"] - s0["pushes"]
+    push_edges = s1["push_edges"] - s0["push_edges"]
+    push_bytes = pushes * 3 * B + push_edges * (8 + 2 * B)
+    stage_ms = {k: v[0] for k, v in stage.items()}
+    dominant = max(stage_ms, key=stage_ms.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    push_launches = stage["push"][1]
+    push_ms_per = stage_ms["push"] / max(push_launches, 1)
+    achieved = (push_bytes / max(push_launches, 1)) / (push_ms_per * 1e-3) / 1e9 if push_launches else 0.0
+    roof = {"bound": "hbm", "kernel": "k_push", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "bytes_per_launch": push_bytes / max(push_launches, 1), "ms_per_launch": push_ms_per}
+    launches = s1["launches"] - s0["launches"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Chung-Lu graph and edge stream)",
+        "config": {"workload": workload_desc(c), "precision": "fp32", "edges_timed": edges,
+                   "l2": "state %.2f GB (Ub, Vb, Zb, r) > 129 MB L2; no flush" % (4 * st.n_final * d * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU", "refold_every": args.refold_every},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "mean": float(step_ms.mean())},
+        "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / max(E, 1),
+                "d2h_bytes_per_step": 4 * d, "steps": E},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+        "dominant_stage": dominant,
+        "counters": {"pushes": pushes, "push_edges": push_edges, "updates": s1["updates"] - s0["updates"],
+                     "push_rounds": s1["push_rounds"] - s0["push_rounds"],
+                     "touched_rows": s1["touched_rows"] - s0["touched_rows"]},
+        "init_s": init_s,
+        "clocks": clk.summary(),
+    }
+    g.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--config", default="C2")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--refold-every", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--budget", type=float, default=20.0)
+    args = ap.parse_args()
+    from synth import CONFIGS
+    c = CONFIGS[args.config]
+    if args.oracle_worker:
+        print(json.dumps(oracle_run(c, args.steps, 2, args.budget)))
+        return
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # each step a bounded sample: the whole run stays within a few minutes
+        budget = min(120.0, 0.5 * args.steps + 10.0)
+        r = oracle_run(c, args.steps, args.warmup, budget)
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 0,
+                "steps": r["batches"], "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / max(r["batches"], 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Chung-Lu graph and edge stream)",
+                "config": {"workload": workload_desc(c), "precision": "fp64"},
+                "latency_ms": {"p50": r["p50_ms"], "p99": r["p99_ms"]},
+                "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, c, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            r = oracle_subprocess(c, 400, args.cpu_budget)
+            if "value" in r:
+                out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                       "sample": r["sample"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                                       "init_s": r["init_s"]}
+            else:
+                out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": "failed: " + r.get("error", "")}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

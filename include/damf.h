@@ -1,0 +1,218 @@
+/*
+ * damf.h -- C ABI of the DAMF per-update hot path on one GPU (sm_103a).
+ *
+ * DAMF (Dynamic Adjacency Matrix Factorization, arXiv 2306.08967) keeps a rank-d
+ * truncated SVD  A ~ U Sigma V^T  of a graph's adjacency matrix while edges and
+ * nodes change, and a Personalized-PageRank-enhanced context embedding
+ * Z = PPR(U Sigma^{1/2}) (Sec. 4.4, Eq. "ppr").  The library stores U and V as
+ * node-row bases times d x d transforms (U = U_b P_U, V = V_b P_V; the lazy base
+ * space of Sec. 4.1, Eq. "update"), so an update rewrites only the rows the
+ * change touches (Lemma 1) plus four d x d matrices.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked (device) are CUDA device pointers owned by the caller; the
+ *     library reads them during the call's stream work and keeps no reference.
+ *     Pointers marked (host) are ordinary host memory, read before the call returns.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  All work is enqueued asynchronously on it.
+ *   - A returned status covers argument checks made on the host.  Errors found on
+ *     the device (invalid edge ids, capacity exhaustion, a bounded wait that ran
+ *     out, non-finite values) are recorded in a device status word and returned by
+ *     damf_sync_status(); after such an error the context is poisoned and every
+ *     later call returns that status until damf_destroy().
+ *   - Dense arrays are row-major float32 with rows of d entries (16-byte aligned
+ *     when the pointer is 16-byte aligned).  Node ids are int32 in [0, n).
+ *   - One context must be used from one stream at a time.
+ */
+#ifndef DAMF_H_
+#define DAMF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct damf_ctx damf_ctx; /* opaque; owns all device state */
+
+typedef enum {
+  DAMF_OK = 0,
+  DAMF_ERR_INVALID = 1,        /* bad argument or edge event (id out of range, self-loop, op not +-1) */
+  DAMF_ERR_CAPACITY = 2,       /* node or edge capacity exhausted; the update was not applied */
+  DAMF_ERR_CUDA = 3,           /* a CUDA runtime call failed; damf_last_error() has the text */
+  DAMF_ERR_NUMERIC = 4,        /* non-finite value in Sigma, a transform or a residual factor */
+  DAMF_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+  DAMF_ERR_NOT_CONVERGED = 6   /* the PPR push hit max_push_rounds before every residual was <= eps */
+} damf_status;
+
+typedef struct {
+  int32_t n;                /* nodes of the initial graph */
+  int32_t n_capacity;       /* maximum node count (node arrivals append ids n, n+1, ...) */
+  int64_t m_capacity;       /* stored adjacency entries, slack and relocations included
+                               (undirected edges are stored twice; directed graphs keep
+                               an out- and an in-adjacency, each within m_capacity) */
+  int32_t d;                /* rank of the factorisation: 16, 32, 64 or 128 */
+  int32_t directed;         /* 0: undirected (each event touches (u,v) and (v,u)); 1: directed */
+  double alpha;             /* PPR damping factor, 0 < alpha <= 1 (Eq. "ppr") */
+  double eps;               /* PPR tolerance: the push stops when max_j |r[u][j]| <= eps for all u */
+  int32_t refold_every;     /* fold the transforms into the bases every this many updates; 0 = never */
+  int32_t rsvd_oversample;  /* randomized t-SVD: l = round_up(d + rsvd_oversample, 32) test vectors */
+  int32_t rsvd_power_iters; /* randomized t-SVD power iterations q */
+  int32_t max_push_rounds;  /* cap on frontier rounds per damf_ppr_refresh */
+} damf_config;
+
+/* Workspace the library allocates on the device for `cfg` (bytes).  Lets a caller
+ * admit a graph only when it fits in free device memory.  0 for an invalid cfg. */
+size_t damf_bytes_required(const damf_config* cfg);
+
+/* Randomized-t-SVD sample width l for `cfg` (columns of the Omega argument below). */
+int32_t damf_rsvd_width(const damf_config* cfg);
+
+/*
+ * Creates a context and computes the initial state (Appendix A, Algorithm 3):
+ * a rank-d randomized t-SVD A ~ U Sigma V^T (Halko et al., cited at Algorithm 3),
+ * U_b = U, V_b = V, P_U = P_V = I, then the PPR residual r = U_b Sigma^{1/2},
+ * Z_b = 0 and a push to tolerance eps (Algorithm 3, lines 4-5).
+ *   row_ptr (device) int32[n+1], col_idx (device) int32[m]: the initial adjacency in
+ *     CSR; an undirected graph must list both (u,v) and (v,u); no self-loops.
+ *   omega (device) float32[n x l], l = damf_rsvd_width(cfg): standard normal test
+ *     matrix (the caller draws it so that results are reproducible across devices).
+ *   out: receives the context; *out is NULL on failure.
+ * Returns DAMF_ERR_INVALID for a bad cfg, DAMF_ERR_CUDA when allocation fails.
+ * Synchronises `stream` before returning (setup path, not the per-update path).
+ */
+damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx,
+                                int64_t m, const float* omega, void* stream, damf_ctx** out);
+
+/*
+ * Applies one call's edge events (Algorithm 2; Algorithm 1 "UpdateEmbeddingE" with
+ * B C^T = dA, Sec. 4.3, Eqs. "edge_B", "f_edge", "g_edge", "x_edge", "y_edge").
+ *   new_nodes: nodes appended before the edges (ids n .. n+new_nodes-1); a node
+ *     arrival is a zero row and column followed by ordinary edge changes (Sec. 4.2).
+ *   src, dst (device) int32[k], op (device) int8[k]: event i inserts (op = +1) or
+ *     deletes (op = -1) edge (src[i], dst[i]); an undirected event covers both
+ *     directions.  Set semantics: per ordered pair the last event decides whether
+ *     the edge is present; inserting a present edge or deleting an absent one is a
+ *     no-op.
+ * The events are applied as ceil(k/48) consecutive updates of at most 48 events
+ * each (rank r <= 96).  Each update: edits the adjacency; projects dA onto the
+ * bases (W_B = U^T B, W_C = V^T C); re-orthogonalises the residual blocks by
+ * Cholesky of their Gram matrices (Prop. 1 for a block); takes the SVD of the
+ * (d+r) x (d+r) core; folds the rotation into P_U, P_V and their inverses; rewrites
+ * the touched base rows; and updates the PPR residual for the changed signal rows
+ * and the changed out-rows.  The PPR push itself is damf_ppr_refresh().
+ * Device-side validation: ids < n + new_nodes, no self-loop, op = +-1; on failure
+ * nothing is written and the status becomes DAMF_ERR_INVALID.
+ */
+damf_status damf_apply_edges(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,
+                             int32_t k, int32_t new_nodes, void* stream);
+
+/* Same as damf_apply_edges with src, dst, op in (host) memory: the library copies
+ * them to the device on `stream` (k <= 4096). */
+damf_status damf_apply_edges_host(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,
+                                  int32_t k, int32_t new_nodes, void* stream);
+
+/*
+ * Dynamic embedding enhancement (Sec. 4.4; Algorithm 2, last step): frontier push
+ * rounds on the current graph until max_j |r[u][j]| <= eps for every u, keeping the
+ * invariant  Pi X_b = Z_b + Pi r  with Pi = alpha (I - (1-alpha) D^{-1} A)^{-1}, so
+ * that |Z_b - Pi X_b| <= eps elementwise.  One persistent launch; frontier sizes stay
+ * on the device.  DAMF_ERR_NOT_CONVERGED (via damf_sync_status) when
+ * max_push_rounds is reached; DAMF_ERR_TIMEOUT when a grid barrier wait runs out.
+ */
+damf_status damf_ppr_refresh(damf_ctx* ctx, void* stream);
+
+/*
+ * Query (Sec. 4.6, "Query Node's Embedding"): X = U_b P_U Sigma^{1/2},
+ * Y = V_b P_V Sigma^{1/2}, Z = Z_b S0^{-1/2} P_U Sigma^{1/2} (S0 = Sigma at the last
+ * fold; PPR is linear, so the enhanced embedding maps like X).
+ *   rows (device) int32[count] node ids, or NULL for rows 0..count-1.
+ *   X, Y, Z (device) float32[count x d] outputs, sigma (device) float32[d]; any
+ *   output may be NULL.
+ */
+damf_status damf_get_embeddings(damf_ctx* ctx, const int32_t* rows, int32_t count, float* X, float* Y,
+                                float* Z, float* sigma, void* stream);
+
+/*
+ * Copies the base state to caller buffers (device), rows 0..n-1: Ub, Vb, Zb, r are
+ * float32[n x d]; PU, PV float32[d x d] (U = Ub PU, V = Vb PV); sigma, s0 float32[d]
+ * (the PPR signal is X_b = Ub diag(s0)).  Any pointer may be NULL.  For tests,
+ * inspection and checkpointing.
+ */
+damf_status damf_get_state(damf_ctx* ctx, float* Ub, float* Vb, float* Zb, float* r, float* PU, float* PV,
+                           float* sigma, float* s0, void* stream);
+
+/*
+ * Copies the current adjacency into (host) CSR buffers: row_ptr int64[n+1] and
+ * col int32[col_capacity] (row order as stored, not sorted).  outgoing = 1 gives the
+ * out-adjacency A[u][.], 0 the in-adjacency (same as outgoing for undirected graphs).
+ * Blocks on the device.  DAMF_ERR_CAPACITY when col_capacity is too small.
+ */
+damf_status damf_export_adjacency(damf_ctx* ctx, int32_t outgoing, int64_t* row_ptr, int32_t* col,
+                                  int64_t col_capacity);
+
+/*
+ * Touched sets of the most recent update (Lemma 1: the rows of U_b, V_b it rewrote):
+ * S (host) int32[96] sorted source rows, T (host) int32[96] sorted target rows.
+ * Blocks on the device.
+ */
+damf_status damf_get_last_touched(damf_ctx* ctx, int32_t* S, int32_t* nS, int32_t* T, int32_t* nT);
+
+/* Current node count as known to the host (initial n plus all node arrivals). */
+int32_t damf_num_nodes(const damf_ctx* ctx);
+
+typedef struct {
+  int64_t updates;          /* rank-r updates applied (non-empty) */
+  int64_t edges_applied;    /* events passed to damf_apply_edges* */
+  int64_t entries_changed;  /* net adjacency entries changed (set semantics) */
+  int64_t pushes;           /* node pushes (rows moved from r to Z_b) */
+  int64_t push_edges;       /* in-edges traversed by pushes */
+  int64_t push_rounds;      /* frontier rounds */
+  int64_t fixup_edges;      /* adjacency entries gathered by the graph-change fix-up */
+  int64_t touched_rows;     /* sum over updates of |S| + |T| */
+  int64_t folds;            /* refolds of the transforms into the bases */
+  int32_t last_rank;        /* r of the most recent update */
+  int32_t last_status;      /* device status word */
+  int64_t launches;         /* kernels launched by this context so far */
+} damf_stats;
+
+/* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */
+enum {
+  DAMF_STAGE_PREPARE = 0,    /* adjacency edit, set semantics, S, T, N (one CTA) */
+  DAMF_STAGE_FIXUP = 1,      /* PPR residual change of changed out-rows */
+  DAMF_STAGE_GATHER = 2,     /* U[S] = Ub[S] PU, V[T] = Vb[T] PV */
+  DAMF_STAGE_CHOL = 3,       /* residual Grams and Cholesky factors */
+  DAMF_STAGE_CORE = 4,       /* core assembly and one-CTA Jacobi SVD */
+  DAMF_STAGE_TRANSFORMS = 5, /* H, R^{-1} E[d:], K, K^{-1}, transform products */
+  DAMF_STAGE_SCATTER = 6,    /* base-row rewrite and PPR signal change */
+  DAMF_STAGE_PUSH = 7,       /* persistent PPR push */
+  DAMF_STAGE_FOLD = 8,       /* periodic fold of the transforms into the bases */
+  DAMF_NUM_STAGES = 9
+};
+
+/* Enables (1) or disables (0) per-stage timing: CUDA events recorded on the call's
+ * stream around each stage's launches.  Costs a few microseconds of host time per stage. */
+damf_status damf_set_timing(damf_ctx* ctx, int32_t enable);
+
+/* Accumulated device milliseconds and launch counts per stage since the last call
+ * (arrays of DAMF_NUM_STAGES; either may be NULL), then resets them.  Blocks. */
+damf_status damf_get_timing(damf_ctx* ctx, double* ms, int64_t* launches);
+
+/* Copies the device counters (blocking on the context's work). */
+damf_status damf_get_stats(damf_ctx* ctx, damf_stats* out);
+
+/* Reads the device status word (blocking) and returns it. */
+damf_status damf_sync_status(damf_ctx* ctx);
+
+/* Text of the most recent error on this context ("" if none). */
+const char* damf_last_error(const damf_ctx* ctx);
+
+/* Frees all device state.  NULL is ignored. */
+void damf_destroy(damf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAMF_H_ */

@@ -1,0 +1,8 @@
+"""DAMF per-update hot path on one GB300 GPU (sm_103a): C ABI library + thin binding.
+
+The compute runs in libdamf.so (hand-written CUDA, built in-tree by build.py); this
+package only marshals arguments.  Importing it does not load the library; the first
+DamfGraph does, and raises ImportError when the library has not been built.
+"""
+
+from .api import DamfError, DamfGraph, bytes_required, make_config, rsvd_width  # noqa: F401

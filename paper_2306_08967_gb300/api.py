@@ -1,0 +1,190 @@
+"""Python binding of the C ABI (argument marshalling only; every step runs in libdamf.so).
+
+PyTorch provides device memory and streams.  Tensors passed in must be CUDA tensors of
+the stated dtype; numpy arrays are copied to the device first.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Config, Stats, STATUS_NAMES
+
+
+class DamfError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__("%s (%d)%s" % (STATUS_NAMES.get(code, "?"), code, (": " + msg) if msg else ""))
+        self.code = code
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype):
+    if isinstance(x, torch.Tensor):
+        if not x.is_cuda or x.dtype != dtype or not x.is_contiguous():
+            x = x.to(device="cuda", dtype=dtype).contiguous()
+        return x
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def make_config(n, d, alpha, eps, n_capacity=None, m_capacity=None, nnz=0, directed=False, refold_every=0,
+                rsvd_oversample=10, rsvd_power_iters=4, max_push_rounds=100000) -> Config:
+    n_capacity = n if n_capacity is None else n_capacity
+    if m_capacity is None:
+        # initial rows with 25% slack plus room for relocations and growth
+        m_capacity = int(2.0 * nnz) + 64 * n_capacity + 4096
+    return Config(n=n, n_capacity=n_capacity, m_capacity=m_capacity, d=d, directed=int(directed), alpha=alpha,
+                  eps=eps, refold_every=refold_every, rsvd_oversample=rsvd_oversample,
+                  rsvd_power_iters=rsvd_power_iters, max_push_rounds=max_push_rounds)
+
+
+def rsvd_width(cfg: Config) -> int:
+    return int(_lib.load().damf_rsvd_width(ctypes.byref(cfg)))
+
+
+def bytes_required(cfg: Config) -> int:
+    return int(_lib.load().damf_bytes_required(ctypes.byref(cfg)))
+
+
+class DamfGraph:
+    """One graph's DAMF state on the current CUDA device (a damf_ctx)."""
+
+    def __init__(self, indptr, indices, cfg: Config, omega, stream=None):
+        self.lib = _lib.load()
+        self.cfg = cfg
+        self.d = cfg.d
+        ip = _dev(indptr, torch.int32)
+        ix = _dev(indices, torch.int32) if len(indices) else torch.zeros(1, dtype=torch.int32, device="cuda")
+        om = _dev(omega, torch.float32)
+        l = rsvd_width(cfg)
+        if om.shape != (cfg.n, l) and om.numel() < cfg.n * l:
+            raise ValueError("omega must be n x %d" % l)
+        h = ctypes.c_void_p()
+        st = self.lib.damf_init_factorize(ctypes.byref(cfg), ctypes.c_void_p(ip.data_ptr()),
+                                          ctypes.c_void_p(ix.data_ptr()), int(len(indices)),
+                                          ctypes.c_void_p(om.data_ptr()), _stream_ptr(stream), ctypes.byref(h))
+        if st != 0:
+            raise DamfError(st, "init")
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise DamfError(st, self.lib.damf_last_error(self.h).decode())
+
+    @property
+    def n(self) -> int:
+        return int(self.lib.damf_num_nodes(self.h))
+
+    def apply_edges(self, src, dst, op, new_nodes: int = 0, stream=None):
+        """Device-resident events (int32 src/dst, int8 op)."""
+        s, t, o = _dev(src, torch.int32), _dev(dst, torch.int32), _dev(op, torch.int8)
+        self._keep = (s, t, o)  # alive until the stream has consumed them
+        self._check(self.lib.damf_apply_edges(self.h, ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                              ctypes.c_void_p(o.data_ptr()), int(s.numel()), int(new_nodes),
+                                              _stream_ptr(stream)))
+
+    def apply_edges_host(self, src: np.ndarray, dst: np.ndarray, op: np.ndarray, new_nodes: int = 0, stream=None):
+        """Host events: the library copies them to the device on the stream."""
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        t = np.ascontiguousarray(dst, dtype=np.int32)
+        o = np.ascontiguousarray(op, dtype=np.int8)
+        self._check(self.lib.damf_apply_edges_host(self.h, s.ctypes.data_as(ctypes.c_void_p),
+                                                   t.ctypes.data_as(ctypes.c_void_p),
+                                                   o.ctypes.data_as(ctypes.c_void_p), int(s.shape[0]),
+                                                   int(new_nodes), _stream_ptr(stream)))
+
+    def ppr_refresh(self, stream=None):
+        self._check(self.lib.damf_ppr_refresh(self.h, _stream_ptr(stream)))
+
+    def embeddings(self, rows=None, want=("X", "Y", "Z", "sigma"), stream=None):
+        """Returns a dict of CUDA tensors: X, Y, Z (count x d) and sigma (d)."""
+        if rows is None:
+            count, rp = self.n, None
+        else:
+            rows = _dev(rows, torch.int32)
+            count, rp = int(rows.numel()), ctypes.c_void_p(rows.data_ptr())
+        out = {}
+        ptrs = []
+        for name in ("X", "Y", "Z"):
+            if name in want:
+                out[name] = torch.empty((count, self.d), dtype=torch.float32, device="cuda")
+                ptrs.append(ctypes.c_void_p(out[name].data_ptr()))
+            else:
+                ptrs.append(None)
+        if "sigma" in want:
+            out["sigma"] = torch.empty(self.d, dtype=torch.float32, device="cuda")
+            sp = ctypes.c_void_p(out["sigma"].data_ptr())
+        else:
+            sp = None
+        self._check(self.lib.damf_get_embeddings(self.h, rp, count, ptrs[0], ptrs[1], ptrs[2], sp,
+                                                 _stream_ptr(stream)))
+        return out
+
+    def state(self, stream=None) -> dict:
+        """Base state: Ub, Vb, Zb, r (n x d), PU, PV (d x d), sigma, s0 (d) as CUDA tensors."""
+        n, d = self.n, self.d
+        out = {k: torch.empty((n, d), dtype=torch.float32, device="cuda") for k in ("Ub", "Vb", "Zb", "r")}
+        out.update({k: torch.empty((d, d), dtype=torch.float32, device="cuda") for k in ("PU", "PV")})
+        out.update({k: torch.empty(d, dtype=torch.float32, device="cuda") for k in ("sigma", "s0")})
+        ptr = lambda k: ctypes.c_void_p(out[k].data_ptr())
+        self._check(self.lib.damf_get_state(self.h, ptr("Ub"), ptr("Vb"), ptr("Zb"), ptr("r"), ptr("PU"), ptr("PV"),
+                                            ptr("sigma"), ptr("s0"), _stream_ptr(stream)))
+        return out
+
+    def adjacency(self, outgoing: bool = True, capacity: int = None):
+        """Current adjacency as host CSR (row_ptr int64[n+1], col int32[nnz]; rows unsorted)."""
+        capacity = int(self.cfg.m_capacity) if capacity is None else capacity
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        col = np.zeros(max(capacity, 1), dtype=np.int32)
+        self._check(self.lib.damf_export_adjacency(self.h, int(outgoing), rp.ctypes.data_as(ctypes.c_void_p),
+                                                   col.ctypes.data_as(ctypes.c_void_p), capacity))
+        return rp, col[: rp[-1]]
+
+    def last_touched(self):
+        S = np.zeros(96, dtype=np.int32)
+        T = np.zeros(96, dtype=np.int32)
+        ns = ctypes.c_int32()
+        nt = ctypes.c_int32()
+        self._check(self.lib.damf_get_last_touched(self.h, S.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ns),
+                                                   T.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nt)))
+        return S[: ns.value].copy(), T[: nt.value].copy()
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.lib.damf_set_timing(self.h, int(enable)))
+
+    def timing(self) -> dict:
+        """{stage: (device ms, launches)} accumulated since the last call."""
+        ms = np.zeros(len(_lib.STAGES), dtype=np.float64)
+        nl = np.zeros(len(_lib.STAGES), dtype=np.int64)
+        self._check(self.lib.damf_get_timing(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                             nl.ctypes.data_as(ctypes.c_void_p)))
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(_lib.STAGES)}
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self.lib.damf_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def sync_status(self) -> int:
+        return int(self.lib.damf_sync_status(self.h))
+
+    def check(self):
+        self._check(self.sync_status())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.damf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,581 @@
+// C ABI entry points (include/damf.h): context lifetime, per-call orchestration on the
+// caller's stream, and the initial factorisation (Appendix A, Algorithm 3).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "damf_internal.cuh"
+
+namespace damf {
+cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, cudaStream_t s);
+cudaError_t chol_inv_upper2(const float* G, int K, float* R, float* Rinv, DevHeader* h, cudaStream_t s);
+cudaError_t small_mm(const float* A, const float* B, float* C, int K, cudaStream_t s);
+cudaError_t gemm_tall_scaled(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                             const float* ascale, const float* cscale, cudaStream_t s);
+}  // namespace damf
+
+using namespace damf;
+
+struct damf_ctx {
+  Ctx c;
+};
+
+namespace {
+
+constexpr int kHostStageMax = 4096;
+constexpr int kTimerPairs = 16384;
+
+void harvest_timing(Ctx* c) {
+  if (!c->ev || c->ev_used == 0) return;
+  cudaDeviceSynchronize();
+  for (int i = 0; i < c->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) c->stage_ms[c->ev_stage[i]] += ms;
+  }
+  c->ev_used = 0;
+}
+
+// Records a start event for `stage` when timing is on; returns the pair index or -1.
+int timer_begin(Ctx* c, int stage, cudaStream_t s) {
+  if (!c->timing || !c->ev) return -1;
+  if (c->ev_used == kTimerPairs) harvest_timing(c);
+  const int i = c->ev_used++;
+  c->ev_stage[i] = stage;
+  cudaEventRecord(c->ev[2 * i], s);
+  return i;
+}
+
+void timer_end(Ctx* c, int i, int stage, int launches, cudaStream_t s) {
+  c->stage_launches[stage] += launches;
+  if (i >= 0) cudaEventRecord(c->ev[2 * i + 1], s);
+}
+
+#define DAMF_STAGE(stage, nl, call, what)          \
+  do {                                            \
+    const int ti_ = timer_begin(c, stage, s);      \
+    DAMF_CUDA(call, what);                        \
+    timer_end(c, ti_, stage, nl, s);              \
+  } while (0)
+// kernels per update: prepare, fixup, gather, chol, assemble, jacobi, hmat, trans, inverse,
+// products, commit, scatter
+constexpr int kLaunchesPerUpdate = 12;
+// fold: 2 x (gram part + reduce), 2 x (congruence + chol), core, jacobi, hmat, 4 small_mm,
+// finish, 4 tall GEMMs
+constexpr int kLaunchesPerFold = 4 + 4 + 1 + 2 + 4 + 1 + 4;
+
+bool cfg_ok(const damf_config* cfg) {
+  if (!cfg) return false;
+  if (!(cfg->d == 16 || cfg->d == 32 || cfg->d == 64 || cfg->d == 128)) return false;
+  if (cfg->n < 1 || cfg->n_capacity < cfg->n) return false;
+  if (cfg->m_capacity < 1 || cfg->m_capacity > 0x7fffffffll) return false;
+  if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0) || !(cfg->eps > 0.0)) return false;
+  if (cfg->rsvd_oversample < 0 || cfg->rsvd_power_iters < 0 || cfg->max_push_rounds < 1) return false;
+  if (cfg->refold_every < 0) return false;
+  return true;
+}
+
+int width_of(const damf_config* cfg) {
+  int l = cfg->d + cfg->rsvd_oversample;
+  l = (l + 31) / 32 * 32;
+  if (l > 160) l = 160;
+  if (l < cfg->d) l = cfg->d;
+  return l;
+}
+
+long long work_cap_of(const damf_config* cfg) {
+  return (long long)cfg->n_capacity + cfg->m_capacity / kPushChunk + 64;
+}
+
+int gram_parts_of(const damf_config* cfg) {
+  long long p = (cfg->n_capacity + 2047) / 2048;
+  if (p > 1024) p = 1024;
+  if (p < 1) p = 1;
+  return (int)p;
+}
+
+// Sizes of every device allocation, in order (shared by damf_bytes_required and create).
+struct Plan {
+  size_t sz[64];
+  int count;
+};
+
+Plan plan_of(const damf_config* cfg) {
+  Plan p{};
+  const size_t n = (size_t)cfg->n_capacity, d = (size_t)cfg->d, m = (size_t)cfg->m_capacity;
+  const size_t nd = n * d * sizeof(float);
+  const size_t dd = d * d * sizeof(float);
+  size_t* s = p.sz;
+  int k = 0;
+  s[k++] = sizeof(DevHeader);
+  s[k++] = nd; s[k++] = nd; s[k++] = nd; s[k++] = nd;      // Ub Vb Zb r
+  s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;      // PU PV PUi PVi
+  s[k++] = d * sizeof(float); s[k++] = d * sizeof(float);  // sigma s0
+  for (int a = 0; a < (cfg->directed ? 2 : 1); ++a) {
+    s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4; s[k++] = m * 4;  // start len cap col
+  }
+  s[k++] = kMaxR * 4; s[k++] = kMaxR * 4;                   // S T
+  s[k++] = (size_t)kMaxR * kMaxR * 4;                        // N
+  s[k++] = (size_t)kMaxEntries * sizeof(int4);               // edits
+  s[k++] = kMaxR * 4; s[k++] = kMaxR * 4;                    // deg_old deg_new
+  s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // UST VT WCt
+  s[k++] = (size_t)kMaxR * kMaxR * 4; s[k++] = (size_t)kMaxR * kMaxR * 4;                              // RB RC
+  s[k++] = (size_t)kMaxM * kMaxM * 4;                        // M
+  s[k++] = (size_t)kMaxM * d * 4; s[k++] = (size_t)kMaxM * d * 4;  // E H
+  s[k++] = d * 4;                                            // theta
+  s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // YB YC
+  s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;        // KU KV KUi KVi
+  s[k++] = 4 * dd;                                           // tmp
+  s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // cand0 cand1 front
+  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int2);          // work
+  s[k++] = nd;                                               // rho
+  s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // stamp pend pstamp
+  s[k++] = 2 * (size_t)160 * 160 * 4;                        // gram (room for the init width)
+  s[k++] = (size_t)gram_parts_of(cfg) * 160 * 160 * 4;       // gram_part
+  p.count = k;
+  return p;
+}
+
+damf_status fail(Ctx* c, damf_status st, const char* what, cudaError_t e) {
+  if (c) {
+    snprintf(c->errbuf, sizeof(c->errbuf), "%s: %s", what, e == cudaSuccess ? "" : cudaGetErrorString(e));
+    if (st != DAMF_OK && c->sticky == DAMF_OK) c->sticky = st;
+  }
+  return st;
+}
+
+#define DAMF_CUDA(call, what)                                  \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return fail(c, DAMF_ERR_CUDA, what, e_); \
+  } while (0)
+
+void free_all(Ctx* c) {
+  if (c->ev) {
+    for (int i = 0; i < 2 * kTimerPairs; ++i)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    free(c->ev);
+    free(c->ev_stage);
+    c->ev = nullptr;
+  }
+  for (int i = 0; i < c->nallocs; ++i) cudaFree(c->allocs[i]);
+  c->nallocs = 0;
+  if (c->host_stage) cudaFreeHost(c->host_stage);
+  c->host_stage = nullptr;
+}
+
+__global__ void k_init_state(float* Ub, float* r, const float* sigma, float* s0, float* PU, float* PV, float* PUi,
+                             float* PVi, int n, int d) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < (long long)n * d) {
+    const int k = (int)(i % d);
+    r[i] = Ub[i] * sqrtf(fmaxf(sigma[k], 0.0f));
+  }
+  if (i < (long long)d * d) {
+    const float v = (i / d == i % d) ? 1.0f : 0.0f;
+    PU[i] = PV[i] = PUi[i] = PVi[i] = v;
+  }
+  if (i < d) s0[i] = sqrtf(fmaxf(sigma[i], 0.0f));
+}
+
+}  // namespace
+
+namespace damf {
+
+// Randomized t-SVD (Halko et al. 2011, randomized subspace iteration; Algorithm 3 line 1):
+// Q = orth(A Omega); q times: Q' = orth(A^T Q), Q = orth(A Q'); Bt = A^T Q = Q2 R2;
+// R2^T = E Theta H^T (Jacobi);  U = Q E, V = Q2 H.  orth() is CholQR applied twice.
+cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, const float* omega, cudaStream_t s) {
+  const int n = c->n, l = c->l, d = c->d;
+  const size_t nl = (size_t)n * l * sizeof(float);
+  float *Y = nullptr, *Q = nullptr, *Q2 = nullptr, *G = nullptr, *R = nullptr, *Ri = nullptr, *R2 = nullptr,
+        *Rt = nullptr;
+  cudaError_t e;
+  const Adj& out = c->out;
+  const Adj& in = c->cfg.directed ? c->in : c->out;
+  const size_t ll = (size_t)l * l * sizeof(float);
+  if ((e = cudaMalloc(&Y, nl)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&Q, nl)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&Q2, nl)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&G, ll)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&R, ll)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&Ri, ll)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&R2, ll)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&Rt, ll)) != cudaSuccess) goto done;
+  {
+    // orth(X) in place into dst with its triangular factor accumulated in Racc (optional)
+    auto orth = [&](const float* X, float* dst, float* Racc) -> cudaError_t {
+      cudaError_t ee;
+      if ((ee = gram_tall(c, X, l, n, l, G, s)) != cudaSuccess) return ee;
+      if ((ee = chol_inv_upper2(G, l, Racc ? R : nullptr, Ri, c->hdr, s)) != cudaSuccess) return ee;
+      if ((ee = gemm_tall_scaled(X, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
+      if ((ee = gram_tall(c, dst, l, n, l, G, s)) != cudaSuccess) return ee;
+      if ((ee = chol_inv_upper2(G, l, Racc ? Rt : nullptr, Ri, c->hdr, s)) != cudaSuccess) return ee;
+      if ((ee = gemm_tall_scaled(dst, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
+      if (Racc) {  // X = dst (Rt R): R_total = Rt R
+        if ((ee = small_mm(Rt, R, Racc, l, s)) != cudaSuccess) return ee;
+      }
+      return cudaSuccess;
+    };
+    if ((e = spmm(out, n, omega, l, Y, s)) != cudaSuccess) goto done;
+    if ((e = orth(Y, Q, nullptr)) != cudaSuccess) goto done;
+    for (int it = 0; it < c->cfg.rsvd_power_iters; ++it) {
+      if ((e = spmm(in, n, Q, l, Y, s)) != cudaSuccess) goto done;
+      if ((e = orth(Y, Q2, nullptr)) != cudaSuccess) goto done;
+      if ((e = spmm(out, n, Q2, l, Y, s)) != cudaSuccess) goto done;
+      if ((e = orth(Y, Q, nullptr)) != cudaSuccess) goto done;
+    }
+    if ((e = spmm(in, n, Q, l, Y, s)) != cudaSuccess) goto done;  // Bt = A^T Q
+    if ((e = orth(Y, Q2, R2)) != cudaSuccess) goto done;         // Bt = Q2 R2
+    // R2 row-major == (R2^T) column-major: the Jacobi input is R2^T
+    if ((e = jacobi_svd_dense(R2, l, d, c->ws.E, c->ws.H, c->ws.theta, nullptr, c->hdr, s)) != cudaSuccess) goto done;
+    if ((e = gemm_tall_scaled(Q, l, n, c->ws.E, l, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
+    if ((e = gemm_tall_scaled(Q2, l, n, c->ws.H, l, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
+    if ((e = cudaMemcpyAsync(c->sigma, c->ws.theta, sizeof(float) * d, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      goto done;
+    const long long tot = (long long)n * d;
+    k_init_state<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->Ub, c->r, c->sigma, c->s0, c->PU, c->PV, c->PUi,
+                                                                c->PVi, n, d);
+    if ((e = cudaGetLastError()) != cudaSuccess) goto done;
+    e = cudaStreamSynchronize(s);
+  }
+done:
+  cudaStreamSynchronize(s);
+  cudaFree(Y);
+  cudaFree(Q);
+  cudaFree(Q2);
+  cudaFree(G);
+  cudaFree(R);
+  cudaFree(Ri);
+  cudaFree(R2);
+  cudaFree(Rt);
+  return e;
+}
+
+}  // namespace damf
+
+extern "C" {
+
+size_t damf_bytes_required(const damf_config* cfg) {
+  if (!cfg_ok(cfg)) return 0;
+  Plan p = plan_of(cfg);
+  size_t t = 0;
+  for (int i = 0; i < p.count; ++i) t += (p.sz[i] + 255) & ~(size_t)255;
+  return t;
+}
+
+int32_t damf_rsvd_width(const damf_config* cfg) { return cfg_ok(cfg) ? width_of(cfg) : 0; }
+
+damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                const float* omega, void* stream, damf_ctx** out) {
+  if (!out) return DAMF_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg_ok(cfg) || !row_ptr || !omega || m < 0 || (m > 0 && !col_idx)) return DAMF_ERR_INVALID;
+  if (width_of(cfg) < cfg->d + 1 && cfg->rsvd_oversample > 0) return DAMF_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  damf_ctx* x = (damf_ctx*)calloc(1, sizeof(damf_ctx));
+  if (!x) return DAMF_ERR_CUDA;
+  Ctx* c = &x->c;
+  c->cfg = *cfg;
+  c->d = cfg->d;
+  c->n = cfg->n;
+  c->l = width_of(cfg);
+  Plan p = plan_of(cfg);
+  void* ptr[64];
+  for (int i = 0; i < p.count; ++i) {
+    cudaError_t e = cudaMalloc(&ptr[i], p.sz[i]);
+    if (e != cudaSuccess) {
+      free_all(c);
+      free(x);
+      return DAMF_ERR_CUDA;
+    }
+    c->allocs[c->nallocs++] = ptr[i];
+    cudaMemsetAsync(ptr[i], 0, p.sz[i], s);
+  }
+  int k = 0;
+  c->hdr = (DevHeader*)ptr[k++];
+  c->Ub = (float*)ptr[k++]; c->Vb = (float*)ptr[k++]; c->Zb = (float*)ptr[k++]; c->r = (float*)ptr[k++];
+  c->PU = (float*)ptr[k++]; c->PV = (float*)ptr[k++]; c->PUi = (float*)ptr[k++]; c->PVi = (float*)ptr[k++];
+  c->sigma = (float*)ptr[k++]; c->s0 = (float*)ptr[k++];
+  Adj* adjs[2] = {&c->out, &c->in};
+  for (int a = 0; a < (cfg->directed ? 2 : 1); ++a) {
+    adjs[a]->start = (int32_t*)ptr[k++]; adjs[a]->len = (int32_t*)ptr[k++];
+    adjs[a]->cap = (int32_t*)ptr[k++]; adjs[a]->col = (int32_t*)ptr[k++];
+    adjs[a]->m_cap = cfg->m_capacity;
+  }
+  if (!cfg->directed) c->in = c->out;
+  Workspace& w = c->ws;
+  w.S = (int32_t*)ptr[k++]; w.T = (int32_t*)ptr[k++]; w.N = (float*)ptr[k++]; w.edits = (int4*)ptr[k++];
+  w.deg_old = (int32_t*)ptr[k++]; w.deg_new = (int32_t*)ptr[k++];
+  w.UST = (float*)ptr[k++]; w.VT = (float*)ptr[k++]; w.WCt = (float*)ptr[k++];
+  w.RB = (float*)ptr[k++]; w.RC = (float*)ptr[k++]; w.M = (float*)ptr[k++];
+  w.E = (float*)ptr[k++]; w.H = (float*)ptr[k++]; w.theta = (float*)ptr[k++];
+  w.YB = (float*)ptr[k++]; w.YC = (float*)ptr[k++];
+  w.KU = (float*)ptr[k++]; w.KV = (float*)ptr[k++]; w.KUi = (float*)ptr[k++]; w.KVi = (float*)ptr[k++];
+  w.tmp = (float*)ptr[k++];
+  w.cand[0] = (int32_t*)ptr[k++]; w.cand[1] = (int32_t*)ptr[k++]; w.front = (int32_t*)ptr[k++];
+  w.work = (int2*)ptr[k++]; w.work_cap = work_cap_of(cfg);
+  w.rho = (float*)ptr[k++];
+  w.stamp = (uint32_t*)ptr[k++]; w.pend = (int32_t*)ptr[k++]; w.pstamp = (uint32_t*)ptr[k++];
+  w.gram = (float*)ptr[k++]; w.gram_part = (float*)ptr[k++]; w.gram_parts = gram_parts_of(cfg);
+  cudaError_t e;
+  unsigned int one = 1;
+  if ((e = cudaMemcpyAsync(&c->hdr->epoch, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    free_all(c);
+    free(x);
+    return DAMF_ERR_CUDA;
+  }
+  long long tail = 0;
+  e = build_adjacency(c, &c->out, row_ptr, col_idx, m, cfg->n, &tail, 0, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c->hdr->tail_out, &tail, sizeof(tail), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && cfg->directed) {
+    e = build_adjacency(c, &c->in, row_ptr, col_idx, m, cfg->n, &tail, 1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c->hdr->tail_in, &tail, sizeof(tail), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
+  if (e == cudaSuccess) e = launch_push(c, 1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_all(c);
+    free(x);
+    return e == cudaErrorMemoryAllocation ? DAMF_ERR_CAPACITY : DAMF_ERR_CUDA;
+  }
+  int st = 0;
+  cudaMemcpy(&st, &c->hdr->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (st != 0) {
+    free_all(c);
+    free(x);
+    return (damf_status)st;
+  }
+  if (cudaMallocHost(&c->host_stage, sizeof(int32_t) * 3 * kHostStageMax) == cudaSuccess) {
+    if (cudaMalloc(&c->dev_stage, sizeof(int32_t) * 3 * kHostStageMax) == cudaSuccess)
+      c->allocs[c->nallocs++] = c->dev_stage;
+  }
+  *out = x;
+  return DAMF_OK;
+}
+
+damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                             int32_t new_nodes, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (k < 0 || new_nodes < 0 || (k > 0 && (!src || !dst || !op))) return fail(c, DAMF_ERR_INVALID, "arguments", cudaSuccess);
+  if ((long long)c->n + new_nodes > c->cfg.n_capacity) return fail(c, DAMF_ERR_CAPACITY, "node capacity", cudaSuccess);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n_after = c->n + new_nodes;
+  DAMF_CUDA(launch_validate(c, src, dst, op, k, n_after, s), "validate");
+  c->launches += k > 0 ? 1 : 0;
+  c->n = n_after;
+  for (int lo = 0; lo < k; lo += kEdgesPerUpdate) {
+    const int kk = (k - lo) < kEdgesPerUpdate ? (k - lo) : kEdgesPerUpdate;
+    DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_prepare(c, src + lo, dst + lo, op + lo, kk, n_after, s), "prepare");
+    DAMF_STAGE(DAMF_STAGE_FIXUP, 1, launch_fixup(c, s), "fixup");
+    DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
+    DAMF_STAGE(DAMF_STAGE_CHOL, 1, launch_chol(c, s), "chol");
+    DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
+    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 5, launch_transforms(c, s), "transforms");
+    DAMF_STAGE(DAMF_STAGE_SCATTER, 1, launch_scatter(c, s), "scatter");
+    c->launches += kLaunchesPerUpdate;
+    if (c->cfg.refold_every > 0 && ++c->updates_since_fold >= c->cfg.refold_every) {
+      DAMF_STAGE(DAMF_STAGE_FOLD, kLaunchesPerFold, launch_fold(c, s), "fold");
+      c->launches += kLaunchesPerFold;
+      c->updates_since_fold = 0;
+      c->check_all_next = 1;
+    }
+  }
+  return DAMF_OK;
+}
+
+damf_status damf_apply_edges_host(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                                  int32_t new_nodes, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (k < 0 || k > kHostStageMax || (k > 0 && (!src || !dst || !op)) || !c->host_stage || !c->dev_stage)
+    return fail(c, DAMF_ERR_INVALID, "arguments", cudaSuccess);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the previous call's copy out of the staging buffer must be complete before reuse
+  DAMF_CUDA(cudaStreamSynchronize(s), "stage sync");
+  memcpy(c->host_stage, src, sizeof(int32_t) * k);
+  memcpy(c->host_stage + kHostStageMax, dst, sizeof(int32_t) * k);
+  memcpy((int8_t*)(c->host_stage + 2 * kHostStageMax), op, (size_t)k);
+  if (k > 0) {
+    DAMF_CUDA(cudaMemcpyAsync(c->dev_stage, c->host_stage, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s), "h2d");
+    DAMF_CUDA(cudaMemcpyAsync(c->dev_stage + kHostStageMax, c->host_stage + kHostStageMax, sizeof(int32_t) * k,
+                              cudaMemcpyHostToDevice, s),
+              "h2d");
+    DAMF_CUDA(cudaMemcpyAsync(c->dev_stage + 2 * kHostStageMax, c->host_stage + 2 * kHostStageMax, (size_t)k,
+                              cudaMemcpyHostToDevice, s),
+              "h2d");
+  }
+  return damf_apply_edges(x, c->dev_stage, c->dev_stage + kHostStageMax, (const int8_t*)(c->dev_stage + 2 * kHostStageMax),
+                          k, new_nodes, stream);
+}
+
+damf_status damf_ppr_refresh(damf_ctx* x, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  cudaStream_t s = (cudaStream_t)stream;
+  DAMF_STAGE(DAMF_STAGE_PUSH, 1, launch_push(c, c->check_all_next, s), "push");
+  c->launches += 1;
+  c->check_all_next = 0;
+  return DAMF_OK;
+}
+
+damf_status damf_get_embeddings(damf_ctx* x, const int32_t* rows, int32_t count, float* X, float* Y, float* Z,
+                                float* sigma, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (count < 0 || (!rows && count > c->n)) return fail(c, DAMF_ERR_INVALID, "count", cudaSuccess);
+  DAMF_CUDA(launch_query(c, rows, count, X, Y, Z, sigma, (cudaStream_t)stream), "query");
+  return DAMF_OK;
+}
+
+int32_t damf_num_nodes(const damf_ctx* x) { return x ? x->c.n : 0; }
+
+damf_status damf_set_timing(damf_ctx* x, int32_t enable) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (enable && !c->ev) {
+    c->ev = (cudaEvent_t*)calloc(2 * kTimerPairs, sizeof(cudaEvent_t));
+    c->ev_stage = (int*)calloc(kTimerPairs, sizeof(int));
+    if (!c->ev || !c->ev_stage) return fail(c, DAMF_ERR_CAPACITY, "timing", cudaSuccess);
+    for (int i = 0; i < 2 * kTimerPairs; ++i) DAMF_CUDA(cudaEventCreate(&c->ev[i]), "timing");
+  }
+  if (!enable) harvest_timing(c);
+  c->timing = enable ? 1 : 0;
+  return DAMF_OK;
+}
+
+damf_status damf_get_timing(damf_ctx* x, double* ms, int64_t* launches) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  harvest_timing(c);
+  for (int k = 0; k < DAMF_NUM_STAGES; ++k) {
+    if (ms) ms[k] = c->stage_ms[k];
+    if (launches) launches[k] = c->stage_launches[k];
+    c->stage_ms[k] = 0.0;
+    c->stage_launches[k] = 0;
+  }
+  return DAMF_OK;
+}
+
+damf_status damf_get_state(damf_ctx* x, float* Ub, float* Vb, float* Zb, float* r, float* PU, float* PV,
+                           float* sigma, float* s0, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nd = (size_t)c->n * c->d * sizeof(float), dd = (size_t)c->d * c->d * sizeof(float);
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (Ub) DAMF_CUDA(cudaMemcpyAsync(Ub, c->Ub, nd, k, s), "state");
+  if (Vb) DAMF_CUDA(cudaMemcpyAsync(Vb, c->Vb, nd, k, s), "state");
+  if (Zb) DAMF_CUDA(cudaMemcpyAsync(Zb, c->Zb, nd, k, s), "state");
+  if (r) DAMF_CUDA(cudaMemcpyAsync(r, c->r, nd, k, s), "state");
+  if (PU) DAMF_CUDA(cudaMemcpyAsync(PU, c->PU, dd, k, s), "state");
+  if (PV) DAMF_CUDA(cudaMemcpyAsync(PV, c->PV, dd, k, s), "state");
+  if (sigma) DAMF_CUDA(cudaMemcpyAsync(sigma, c->sigma, c->d * sizeof(float), k, s), "state");
+  if (s0) DAMF_CUDA(cudaMemcpyAsync(s0, c->s0, c->d * sizeof(float), k, s), "state");
+  return DAMF_OK;
+}
+
+damf_status damf_export_adjacency(damf_ctx* x, int32_t outgoing, int64_t* row_ptr, int32_t* col,
+                                  int64_t col_capacity) {
+  if (!x || !row_ptr || (!col && col_capacity > 0)) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  const Adj& a = (outgoing || !c->cfg.directed) ? c->out : c->in;
+  DAMF_CUDA(cudaDeviceSynchronize(), "export");
+  long long tails[2];
+  DAMF_CUDA(cudaMemcpy(tails, &c->hdr->tail_out, sizeof(tails), cudaMemcpyDeviceToHost), "export");
+  const long long tail = (outgoing || !c->cfg.directed) ? tails[0] : tails[1];
+  const int n = c->n;
+  int32_t* st = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* ln = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(tail > 0 ? tail : 1));
+  damf_status ret = DAMF_OK;
+  if (!st || !ln || !cl) {
+    ret = DAMF_ERR_CAPACITY;
+  } else if (cudaMemcpy(st, a.start, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+             cudaMemcpy(ln, a.len, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+             (tail > 0 && cudaMemcpy(cl, a.col, sizeof(int32_t) * (size_t)tail, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    ret = DAMF_ERR_CUDA;
+  } else {
+    long long pos = 0;
+    for (int u = 0; u < n && ret == DAMF_OK; ++u) {
+      row_ptr[u] = pos;
+      if (pos + ln[u] > col_capacity) {
+        ret = DAMF_ERR_CAPACITY;
+        break;
+      }
+      memcpy(col + pos, cl + st[u], sizeof(int32_t) * (size_t)ln[u]);
+      pos += ln[u];
+    }
+    if (ret == DAMF_OK) row_ptr[n] = pos;
+  }
+  free(st);
+  free(ln);
+  free(cl);
+  return ret;
+}
+
+damf_status damf_get_last_touched(damf_ctx* x, int32_t* S, int32_t* nS, int32_t* T, int32_t* nT) {
+  if (!x || !S || !nS || !T || !nT) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  DAMF_CUDA(cudaDeviceSynchronize(), "touched");
+  int sz[2];
+  DAMF_CUDA(cudaMemcpy(sz, &c->hdr->nS, sizeof(sz), cudaMemcpyDeviceToHost), "touched");
+  *nS = sz[0];
+  *nT = sz[1];
+  if (sz[0] > 0) DAMF_CUDA(cudaMemcpy(S, c->ws.S, sizeof(int32_t) * sz[0], cudaMemcpyDeviceToHost), "touched");
+  if (sz[1] > 0) DAMF_CUDA(cudaMemcpy(T, c->ws.T, sizeof(int32_t) * sz[1], cudaMemcpyDeviceToHost), "touched");
+  return DAMF_OK;
+}
+
+damf_status damf_get_stats(damf_ctx* x, damf_stats* o) {
+  if (!x || !o) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  DevHeader h;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, c->hdr, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(c, DAMF_ERR_CUDA, "stats", e);
+  o->updates = h.updates;
+  o->edges_applied = h.edges_applied;
+  o->entries_changed = h.entries_changed;
+  o->pushes = h.pushes;
+  o->push_edges = h.push_edges;
+  o->push_rounds = h.push_rounds;
+  o->fixup_edges = h.fixup_edges;
+  o->touched_rows = h.touched_rows;
+  o->folds = h.folds;
+  o->last_rank = h.last_rank;
+  o->last_status = h.status;
+  o->launches = c->launches;
+  return DAMF_OK;
+}
+
+damf_status damf_sync_status(damf_ctx* x) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  int st = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, &c->hdr->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(c, DAMF_ERR_CUDA, "sync", e);
+  if (st != 0 && c->sticky == 0) {
+    c->sticky = st;
+    snprintf(c->errbuf, sizeof(c->errbuf), "device status %d", st);
+  }
+  return (damf_status)(c->sticky ? c->sticky : st);
+}
+
+const char* damf_last_error(const damf_ctx* x) { return x ? x->c.errbuf : "null context"; }
+
+void damf_destroy(damf_ctx* x) {
+  if (!x) return;
+  cudaDeviceSynchronize();
+  free_all(&x->c);
+  free(x);
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device data layout (one context, all in HBM):
+//   Ub, Vb      float [n_cap x d]   node-row bases; U = Ub PU, V = Vb PV
+//   Zb, r       float [n_cap x d]   PPR state in base space (signal Xb = Ub diag(s0))
+//   PU, PV, PUi, PVi  float [d x d] accumulated transforms and their inverses
+//   sigma, s0   float [d]           singular values; s0 = sqrt(sigma) at the last fold
+//   out / in    slack adjacency: start/len/cap int32 [n_cap], col int32 [m_cap]
+//   workspace   the small per-update matrices (rank r <= kMaxR), push lists, rho
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "damf.h"
+
+namespace damf {
+
+constexpr int kMaxR = 96;                 // maximum rank of one update
+constexpr int kEdgesPerUpdate = 48;       // events per update (undirected: 2 entries each)
+constexpr int kMaxEntries = 2 * kEdgesPerUpdate;
+constexpr int kMaxD = 128;
+constexpr int kMaxM = kMaxD + kMaxR;      // 224: largest core
+constexpr int kPushChunk = 8;             // in-edges per push work item
+constexpr long long kSpinLimit = 1ll << 26;  // iterations of a bounded wait (with nanosleep)
+
+// Grid barrier state for persistent cooperative kernels.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Device header: status word, counters, per-update sizes.
+struct DevHeader {
+  int status;            // first device error (damf_status), 0 = ok
+  int nS, nT;            // touched sets of the current update
+  int nedit;             // net entries changed by the current update
+  int nrowS;             // distinct source rows edited (== nS)
+  int rankB, rankC;      // pivots kept by the residual Cholesky factors
+  int pending;           // rows queued for the next push (signal or graph changed)
+  int check_all;         // next push starts from every node
+  unsigned int epoch;    // stamp generation for push dedupe
+  long long tail_out, tail_in;   // adjacency bump allocators
+  // counters (damf_stats)
+  long long updates, edges_applied, entries_changed, pushes, push_edges, push_rounds, fixup_edges,
+      touched_rows, folds;
+  int last_rank;
+  int pad;
+  // push control (parity-indexed, see ppr.cu)
+  int cand_count[2];
+  int front_count[2];
+  int work_count[2];
+  GridBar bar;
+};
+
+struct Adj {
+  int32_t* start;
+  int32_t* len;
+  int32_t* cap;
+  int32_t* col;
+  long long m_cap;
+};
+
+struct Workspace {
+  int32_t* S;        // [kMaxR]
+  int32_t* T;        // [kMaxR]
+  float* N;          // [kMaxR x kMaxR] net change, rows S, cols T
+  int4* edits;       // [kMaxEntries] (u, v, delta, s_index)
+  int32_t* deg_old;  // [kMaxR] out-degree of S rows before/after
+  int32_t* deg_new;
+  float* UST;        // [kMaxR x d] rows U[S] = Ub[S] PU
+  float* VT;         // [kMaxR x d] rows V[T] = Vb[T] PV
+  float* WCt;        // [kMaxR x d] N V[T]  (= W_C^T)
+  float* RB;         // [kMaxR x kMaxR] upper Cholesky factor (dropped rows zero)
+  float* RC;
+  float* M;          // [kMaxM x kMaxM] core, column-major with leading dimension m
+  float* E;          // [kMaxM x d] left singular vectors (column k = k-th largest)
+  float* H;          // [kMaxM x d]
+  float* theta;      // [d]
+  float* YB;         // [kMaxR x d]  R_B^{-1} E[d:]
+  float* YC;         // [kMaxR x d]  R_C^{-1} H[d:]
+  float* KU;         // [d x d]
+  float* KV;
+  float* KUi;
+  float* KVi;
+  float* tmp;        // [4 x d x d] scratch for products
+  // push
+  int32_t* cand[2];  // [n_cap]
+  int32_t* front;    // [n_cap]
+  int2* work;        // [work_cap]
+  long long work_cap;
+  float* rho;        // [n_cap x d]
+  uint32_t* stamp;   // [n_cap]
+  int32_t* pend;     // [n_cap] rows queued for the next push
+  uint32_t* pstamp;  // [n_cap]
+  // fold
+  float* gram;       // [2 x d x d] reduced Grams
+  float* gram_part;  // [gram_parts x d x d]
+  int gram_parts;
+};
+
+struct Ctx {
+  damf_config cfg;
+  int d;
+  int n;           // host-tracked node count
+  int l;           // randomized t-SVD width
+  DevHeader* hdr;
+  float *Ub, *Vb, *Zb, *r;
+  float *PU, *PV, *PUi, *PVi, *sigma, *s0;
+  Adj out, in;
+  Workspace ws;
+  int push_blocks;       // persistent push grid size
+  int updates_since_fold;
+  int32_t* host_stage;   // pinned staging for damf_apply_edges_host
+  int32_t* dev_stage;    // device copy of staged events
+  char errbuf[256];
+  int sticky;            // host-side poisoned status
+  int check_all_next;    // next push starts from every row (after a fold)
+  long long launches;    // kernels this context has launched (host count)
+  // per-stage timing (api.cu)
+  int timing;
+  cudaEvent_t* ev;       // 2 * kTimerPairs events
+  int* ev_stage;         // stage of each pair
+  int ev_used;
+  double stage_ms[DAMF_NUM_STAGES];
+  long long stage_launches[DAMF_NUM_STAGES];
+  void* allocs[64];
+  int nallocs;
+};
+
+// ---- small device helpers ----
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void set_status(DevHeader* h, int code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+// Bounded sense-free grid barrier: every block must call it the same number of times.
+// Returns false (and records DAMF_ERR_TIMEOUT) when a wait runs out.
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigned int nblocks) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = &bar->gen;
+    unsigned int gen = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == gen) {
+        if (++it > kSpinLimit) {
+          ok = 0;
+          set_status(h, DAMF_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// ---- launchers implemented in the .cu files ----
+cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
+                            cudaStream_t s);
+cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
+                           cudaStream_t s);
+cudaError_t launch_fixup(Ctx* c, cudaStream_t s);
+cudaError_t launch_gather(Ctx* c, cudaStream_t s);
+cudaError_t launch_chol(Ctx* c, cudaStream_t s);
+cudaError_t launch_core(Ctx* c, cudaStream_t s);
+cudaError_t launch_transforms(Ctx* c, cudaStream_t s);
+cudaError_t launch_scatter(Ctx* c, cudaStream_t s);
+cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s);
+cudaError_t launch_fold(Ctx* c, cudaStream_t s);
+cudaError_t launch_query(Ctx* c, const int32_t* rows, int count, float* X, float* Y, float* Z, float* sigma,
+                         cudaStream_t s);
+cudaError_t build_adjacency(Ctx* c, Adj* a, const int32_t* row_ptr, const int32_t* col_idx, int64_t m, int n,
+                            long long* tail_dev, int transpose, cudaStream_t s);
+cudaError_t init_factorize(Ctx* c, const int32_t* row_ptr, const int32_t* col_idx, int64_t m, const float* omega,
+                           cudaStream_t s);
+
+// dense helpers (dense.cu)
+// C[rows x N] (+)= A[rows x K] * B[K x N]; A row i taken from A + idx[i]*lda when idx != nullptr.
+cudaError_t gemm_rowgather(const float* A, int lda, const int32_t* idx, const int* rows_dev, int rows_max,
+                           const float* B, int K, int N, float* C, int ldc, int accumulate, cudaStream_t s);
+// tall-skinny C[n x N] = A[n x K] B[K x N] (K, N <= 160, multiples of 16)
+cudaError_t gemm_tall(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                      cudaStream_t s);
+// partial Grams of A[n x K]: out[K x K] = A^T A (uses ws.gram_part)
+cudaError_t gram_tall(Ctx* c, const float* A, int lda, long long n, int K, float* out, cudaStream_t s);
+// one-CTA Cholesky (lower, G = L L^T) and inverse of L^T; out Linvt[K x K] with A * Linvt orthonormal
+cudaError_t chol_inv_upper(const float* G, int K, float* Rinv, DevHeader* h, cudaStream_t s);
+// dense one-CTA one-sided Jacobi SVD of an m x m column-major matrix: top-d (E, theta, H)
+cudaError_t jacobi_svd_dense(const float* Min, int m, int d, float* E, float* H, float* theta, float* work_M,
+                             DevHeader* h, cudaStream_t s);
+
+}  // namespace damf

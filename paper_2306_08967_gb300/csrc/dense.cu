@@ -1,0 +1,260 @@
+// Dense building blocks on n x d (tall-skinny) arrays: GEMM with a small right factor,
+// Gram matrices, Cholesky with triangular inverse, and the adjacency SpMM.  Used by the
+// randomized t-SVD initialisation (Appendix A, Algorithm 3; Halko et al.), the query
+// (Sec. 4.6) and the periodic fold of the transforms into the bases.
+#include "damf_internal.cuh"
+
+namespace damf {
+
+// C[n x N] = A[n x K] B[K x N]; 64-row tiles, 16 x 16 threads, each a 4 x (N/16) micro-tile.
+// Optional per-column scalings: A's column k by ascale[k] (before), C's column j by cscale[j].
+template <int K, int N>
+__global__ void __launch_bounds__(256) k_gemm_tall(const float* __restrict__ A, int lda, long long n,
+                                                   const float* __restrict__ B, float* __restrict__ C, int ldc,
+                                                   const float* __restrict__ ascale, const float* __restrict__ cscale) {
+  extern __shared__ float smem[];
+  float* Bs = smem;             // K x N
+  float* As = smem + K * N;     // 64 x (K + 1)
+  constexpr int CN = N / 16;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int i = threadIdx.x; i < K * N; i += 256) Bs[i] = B[i];
+  for (long long r0 = (long long)blockIdx.x * 64; r0 < n; r0 += (long long)gridDim.x * 64) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * K; i += 256) {
+      const int rr = i / K, k = i % K;
+      float v = 0.f;
+      if (r0 + rr < n) {
+        v = A[(r0 + rr) * lda + k];
+        if (ascale) v *= ascale[k];
+      }
+      As[rr * (K + 1) + k] = v;
+    }
+    __syncthreads();
+    float acc[4][CN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < CN; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      float av[4], bv[CN];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[(ty + 16 * a) * (K + 1) + k];
+#pragma unroll
+      for (int b = 0; b < CN; ++b) bv[b] = Bs[k * N + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < CN; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const long long row = r0 + ty + 16 * a;
+      if (row >= n) continue;
+#pragma unroll
+      for (int b = 0; b < CN; ++b) {
+        const int col = tx + 16 * b;
+        C[row * ldc + col] = cscale ? acc[a][b] * cscale[col] : acc[a][b];
+      }
+    }
+  }
+}
+
+template <int K, int N>
+static cudaError_t gemm_tall_kn(const float* A, int lda, long long n, const float* B, float* C, int ldc,
+                                const float* as, const float* cs, cudaStream_t s) {
+  const size_t sm = (size_t)(K * N + 64 * (K + 1)) * sizeof(float);
+  cudaFuncSetAttribute(k_gemm_tall<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  long long tiles = (n + 63) / 64;
+  int grid = (int)(tiles < 152 * 8 ? tiles : 152 * 8);
+  if (grid < 1) grid = 1;
+  k_gemm_tall<K, N><<<grid, 256, sm, s>>>(A, lda, n, B, C, ldc, as, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tall_scaled(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                             const float* ascale, const float* cscale, cudaStream_t s) {
+#define DAMF_GT(KK, NN) \
+  if (K == KK && N == NN) return gemm_tall_kn<KK, NN>(A, lda, n, B, C, ldc, ascale, cscale, s);
+  DAMF_GT(16, 16) DAMF_GT(32, 32) DAMF_GT(64, 64) DAMF_GT(96, 96) DAMF_GT(128, 128) DAMF_GT(160, 160)
+  DAMF_GT(32, 16) DAMF_GT(64, 32) DAMF_GT(96, 64) DAMF_GT(160, 128)
+#undef DAMF_GT
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t gemm_tall(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                      cudaStream_t s) {
+  return gemm_tall_scaled(A, lda, n, B, K, N, C, ldc, nullptr, nullptr, s);
+}
+
+// Partial Grams: block b accumulates rows [b*rows_per, (b+1)*rows_per) into part[b] (K x K).
+template <int K>
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A, int lda, long long n,
+                                                   long long rows_per, float* part) {
+  constexpr int CK = K / 16;
+  __shared__ float tile[32][K + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[CK][CK];
+#pragma unroll
+  for (int a = 0; a < CK; ++a)
+#pragma unroll
+    for (int b = 0; b < CK; ++b) acc[a][b] = 0.f;
+  const long long r_begin = blockIdx.x * rows_per;
+  const long long r_end = min(n, r_begin + rows_per);
+  for (long long r0 = r_begin; r0 < r_end; r0 += 32) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * K; i += 256) {
+      const int rr = i / K, k = i % K;
+      tile[rr][k] = (r0 + rr < r_end) ? A[(r0 + rr) * lda + k] : 0.0f;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < 32; ++rr) {
+      float x[CK], y[CK];
+#pragma unroll
+      for (int a = 0; a < CK; ++a) x[a] = tile[rr][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < CK; ++b) y[b] = tile[rr][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < CK; ++a)
+#pragma unroll
+        for (int b = 0; b < CK; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+    }
+  }
+  float* out = part + (size_t)blockIdx.x * K * K;
+#pragma unroll
+  for (int a = 0; a < CK; ++a)
+#pragma unroll
+    for (int b = 0; b < CK; ++b) out[(ty + 16 * a) * K + tx + 16 * b] = acc[a][b];
+}
+
+__global__ void k_gram_reduce(const float* part, int parts, int KK, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= KK) return;
+  double s = 0.0;
+  for (int p = 0; p < parts; ++p) s += (double)part[(size_t)p * KK + i];
+  out[i] = (float)s;
+}
+
+cudaError_t gram_tall(Ctx* c, const float* A, int lda, long long n, int K, float* out, cudaStream_t s) {
+  int parts = c->ws.gram_parts;
+  long long rows_per = (n + parts - 1) / parts;
+  rows_per = ((rows_per + 31) / 32) * 32;
+  if (rows_per < 32) rows_per = 32;
+  parts = (int)((n + rows_per - 1) / rows_per);
+  if (parts < 1) parts = 1;
+  switch (K) {
+    case 16: k_gram_part<16><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    case 32: k_gram_part<32><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    case 64: k_gram_part<64><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    case 96: k_gram_part<96><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    case 128: k_gram_part<128><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    case 160: k_gram_part<160><<<parts, 256, 0, s>>>(A, lda, n, rows_per, c->ws.gram_part); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gram_reduce<<<(K * K + 255) / 256, 256, 0, s>>>(c->ws.gram_part, parts, K * K, out);
+  return cudaGetLastError();
+}
+
+// One CTA: G (K x K, symmetric positive definite) = R^T R with R upper; writes R and R^{-1}.
+__global__ void __launch_bounds__(1024) k_chol_inv(const float* __restrict__ G, int K, float* Rout, float* Rinv,
+                                                   DevHeader* h) {
+  extern __shared__ float smem[];
+  float* R = smem;          // K x K
+  float* X = smem + K * K;  // K x K
+  __shared__ float piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < K * K; i += nt) R[i] = G[i];
+  __syncthreads();
+  for (int j = 0; j < K; ++j) {
+    if (tid == 0) {
+      const float p = R[j * K + j];
+      piv = p > 0.f ? sqrtf(p) : 0.0f;
+      if (!(p > 0.f)) set_status(h, DAMF_ERR_NUMERIC);
+    }
+    __syncthreads();
+    const float ip = piv > 0.f ? 1.0f / piv : 0.0f;
+    for (int l = j + tid; l < K; l += nt) R[j * K + l] = (l == j) ? piv : R[j * K + l] * ip;
+    __syncthreads();
+    const int rem = K - j - 1;
+    for (int i = tid; i < rem * rem; i += nt) {
+      const int a = j + 1 + i / rem, b = j + 1 + i % rem;
+      R[a * K + b] -= R[j * K + a] * R[j * K + b];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < K * K; i += nt) {
+    const int a = i / K, b = i % K;
+    if (b < a) R[i] = 0.0f;
+    X[i] = (a == b) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  // back substitution R X = I, column-parallel
+  for (int j = K - 1; j >= 0; --j) {
+    for (int col = tid; col < K; col += nt) {
+      float s = X[j * K + col];
+      for (int l = j + 1; l < K; ++l) s = fmaf(-R[j * K + l], X[l * K + col], s);
+      const float p = R[j * K + j];
+      X[j * K + col] = p > 0.f ? s / p : 0.0f;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < K * K; i += nt) {
+    if (Rout) Rout[i] = R[i];
+    Rinv[i] = X[i];
+  }
+}
+
+cudaError_t chol_inv_upper2(const float* G, int K, float* R, float* Rinv, DevHeader* h, cudaStream_t s) {
+  const size_t sm = (size_t)2 * K * K * sizeof(float);
+  cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_chol_inv<<<1, 1024, sm, s>>>(G, K, R, Rinv, h);
+  return cudaGetLastError();
+}
+
+cudaError_t chol_inv_upper(const float* G, int K, float* Rinv, DevHeader* h, cudaStream_t s) {
+  return chol_inv_upper2(G, K, nullptr, Rinv, h, s);
+}
+
+// Y[u] = sum_{v in row u} X[v] over an adjacency (warp per row, float4 columns).
+__global__ void k_spmm(Adj a, int n, const float* __restrict__ X, int l, float* Y) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= n) return;
+  const int u = (int)wid;
+  const int st = a.start[u], ln = a.len[u];
+  const int nq = l / 4;
+  for (int c = lane; c < nq; c += 32) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < ln; ++j) {
+      const int v = __ldg(a.col + st + j);
+      const float4 x = __ldg(reinterpret_cast<const float4*>(X + (size_t)v * l) + c);
+      acc.x += x.x, acc.y += x.y, acc.z += x.z, acc.w += x.w;
+    }
+    reinterpret_cast<float4*>(Y + (size_t)u * l)[c] = acc;
+  }
+}
+
+cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, cudaStream_t s) {
+  const long long threads = (long long)n * 32;
+  k_spmm<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, n, X, l, Y);
+  return cudaGetLastError();
+}
+
+// small K x K product C = A B (one CTA)
+__global__ void k_small_mm(const float* A, const float* B, float* C, int K) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < K * K; o += gridDim.x * blockDim.x) {
+    const int i = o / K, j = o % K;
+    float s = 0.f;
+    for (int k = 0; k < K; ++k) s = fmaf(A[i * K + k], B[k * K + j], s);
+    C[o] = s;
+  }
+}
+
+cudaError_t small_mm(const float* A, const float* B, float* C, int K, cudaStream_t s) {
+  k_small_mm<<<(K * K + 255) / 256, 256, 0, s>>>(A, B, C, K);
+  return cudaGetLastError();
+}
+
+}  // namespace damf

@@ -1,0 +1,456 @@
+// Graph store and per-update sparse change.
+//
+//  * slack adjacency: each row owns [start, start+cap) of col[], holds len entries;
+//    a row that overflows is relocated to the bump tail with doubled capacity.
+//  * k_prepare (one CTA per update): set semantics of the events (last event per
+//    ordered pair decides; delta = final - initial membership), the touched sets
+//    S (rows with a changed entry) and T (columns), the net-change matrix
+//    N[a][b] = dA[S_a][T_b] so that dA = I_S N I_T^T (Sec. 4.3, Eq. "edge_B" summed
+//    over the update), and the adjacency edit.  Capacity is checked before any write.
+//  * k_fixup: the PPR residual change for changed out-rows.  With P = D^{-1} A and
+//    Pi^{-1} = (I - (1-alpha) P) / alpha, the residual r = X_b - Pi^{-1} Z_b changes by
+//    ((1-alpha)/alpha) (P' - P) Z_b; only rows u in S change (Sec. 4.4, Step 4).
+#include <algorithm>
+#include <vector>
+
+#include "damf_internal.cuh"
+
+namespace damf {
+
+__global__ void k_validate(DevHeader* h, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
+                           int n_after) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  int u = src[i], v = dst[i], o = op[i];
+  bool bad = u < 0 || v < 0 || u >= n_after || v >= n_after || u == v || (o != 1 && o != -1);
+  if (bad) set_status(h, DAMF_ERR_INVALID);
+  if (i == 0) atomicAdd((unsigned long long*)&h->edges_applied, (unsigned long long)k);
+}
+
+cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
+                            cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_validate<<<(k + 255) / 256, 256, 0, s>>>(c->hdr, src, dst, op, k, n_after);
+  return cudaGetLastError();
+}
+
+// Warp searches row u for v; returns the position or -1.
+__device__ __forceinline__ int row_find(const Adj& a, int u, int v) {
+  const int lane = threadIdx.x & 31;
+  const int st = a.start[u], ln = a.len[u];
+  for (int base = 0; base < ln; base += 32) {
+    int j = base + lane;
+    unsigned hit = __ballot_sync(0xffffffffu, j < ln && a.col[st + j] == v);
+    if (hit) return base + __ffs(hit) - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int grown_cap(int cap, int need) {
+  int c = max(2 * cap, need + 4);
+  return (c + 3) & ~3;
+}
+
+// Edits the rows listed in rows[0..nrows) of adjacency a; entries (row, col, delta) of
+// row q are ent[first[q] .. first[q+1]).  One warp per row.  Relocation space was
+// reserved by the caller at reloc_base[q] (or -1 when the row fits).
+__device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* first, const int3* ent,
+                                const long long* reloc_base, const int* reloc_cap, int* deg_new) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < nrows; q += nw) {
+    const int u = rows[q];
+    if (reloc_base[q] >= 0) {  // move the row to its new home first
+      const int st = a.start[u], ln = a.len[u];
+      const long long nb = reloc_base[q];
+      for (int j = lane; j < ln; j += 32) a.col[nb + j] = a.col[st + j];
+      __syncwarp();
+      if (lane == 0) {
+        a.start[u] = (int)nb;
+        a.cap[u] = reloc_cap[q];
+      }
+      __syncwarp();
+    }
+    // deletions first, so the row never holds more than max(len, new len) entries
+    for (int e = first[q]; e < first[q + 1]; ++e) {
+      const int3 x = ent[e];
+      if (x.z >= 0) continue;
+      const int pos = row_find(a, u, x.y);
+      if (lane == 0 && pos >= 0) {
+        const int st = a.start[u], ln = a.len[u];
+        a.col[st + pos] = a.col[st + ln - 1];
+        a.len[u] = ln - 1;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      for (int e = first[q]; e < first[q + 1]; ++e) {
+        const int3 x = ent[e];
+        if (x.z <= 0) continue;
+        const int st = a.start[u], ln = a.len[u];
+        a.col[st + ln] = x.y;
+        a.len[u] = ln + 1;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && deg_new) deg_new[q] = a.len[u];
+  }
+}
+
+template <int DIRECTED>
+__global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, Workspace ws, const int32_t* src,
+                                                 const int32_t* dst, const int8_t* op, int k) {
+  __shared__ unsigned long long key[kMaxEntries];
+  __shared__ int evt[kMaxEntries];
+  __shared__ int eop[kMaxEntries];
+  __shared__ unsigned long long skey[kMaxEntries];
+  __shared__ int sop[kMaxEntries];
+  __shared__ int sdelta[kMaxEntries];
+  __shared__ int3 ed[kMaxEntries];     // compacted edits, key order (u, v, delta)
+  __shared__ int3 edT[kMaxEntries];    // directed: (v, u, delta) in (v, u) order
+  __shared__ int ne, nedit, nS, nT, nTrow, fail;
+  __shared__ int Srow[kMaxR + 1], Sfirst[kMaxR + 1];
+  __shared__ int Tcol[kMaxR + 1], Tfirst[kMaxR + 1];
+  __shared__ long long relocS[kMaxR], relocT[kMaxR];
+  __shared__ int rcapS[kMaxR], rcapT[kMaxR];
+  const int tid = threadIdx.x;
+  if (h->status != 0) {
+    if (tid == 0) h->nS = h->nT = h->nedit = 0;
+    return;
+  }
+  if (tid == 0) {
+    ne = DIRECTED ? k : 2 * k;
+    fail = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += blockDim.x) {
+    const unsigned int u = (unsigned int)src[i], v = (unsigned int)dst[i];
+    key[DIRECTED ? i : 2 * i] = ((unsigned long long)u << 32) | v;
+    evt[DIRECTED ? i : 2 * i] = i;
+    eop[DIRECTED ? i : 2 * i] = op[i];
+    if (!DIRECTED) {
+      key[2 * i + 1] = ((unsigned long long)v << 32) | u;
+      evt[2 * i + 1] = i;
+      eop[2 * i + 1] = op[i];
+    }
+  }
+  __syncthreads();
+  // sort entries by (key, event index): rank by counting
+  for (int i = tid; i < ne; i += blockDim.x) {
+    int rk = 0;
+    const unsigned long long ki = key[i];
+    const int ti = evt[i];
+    for (int j = 0; j < ne; ++j) {
+      const unsigned long long kj = key[j];
+      rk += (kj < ki) || (kj == ki && evt[j] < ti);
+    }
+    skey[rk] = ki;
+    sop[rk] = eop[i];
+  }
+  __syncthreads();
+  // last event per ordered pair decides; membership lookup (one warp per pair)
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < ne; i += nw) {
+      const bool last = (i == ne - 1) || (skey[i + 1] != skey[i]);
+      int dl = 0;
+      if (last) {
+        const int u = (int)(skey[i] >> 32), v = (int)(skey[i] & 0xffffffffu);
+        const int initial = row_find(out, u, v) >= 0 ? 1 : 0;
+        const int fin = sop[i] > 0 ? 1 : 0;
+        dl = fin - initial;
+      }
+      if (lane == 0) sdelta[i] = dl;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {  // compaction and S (edits are in (u, v) order)
+    int m = 0, s = 0;
+    for (int i = 0; i < ne; ++i) {
+      if (sdelta[i] == 0) continue;
+      const int u = (int)(skey[i] >> 32), v = (int)(skey[i] & 0xffffffffu);
+      if (s == 0 || Srow[s - 1] != u) {
+        Srow[s] = u;
+        Sfirst[s] = m;
+        ++s;
+      }
+      ed[m++] = make_int3(u, v, sdelta[i]);
+    }
+    Sfirst[s] = m;
+    nedit = m;
+    nS = s;
+  }
+  __syncthreads();
+  // T: sorted unique columns; edT = edits ordered by (v, u)
+  for (int i = tid; i < nedit; i += blockDim.x) {
+    int rk = 0;
+    const int3 x = ed[i];
+    for (int j = 0; j < nedit; ++j) {
+      const int3 y = ed[j];
+      rk += (y.y < x.y) || (y.y == x.y && y.x < x.x);
+    }
+    edT[rk] = make_int3(x.y, x.x, x.z);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int i = 0; i < nedit; ++i) {
+      if (t == 0 || Tcol[t - 1] != edT[i].x) {
+        Tcol[t] = edT[i].x;
+        Tfirst[t] = i;
+        ++t;
+      }
+    }
+    Tfirst[t] = nedit;
+    nT = t;
+    nTrow = t;
+  }
+  __syncthreads();
+  // capacity check (before any write)
+  if (tid == 0) {
+    long long need = 0;
+    for (int q = 0; q < nS; ++q) {
+      const int u = Srow[q];
+      int ins = 0, del = 0;
+      for (int e = Sfirst[q]; e < Sfirst[q + 1]; ++e) (ed[e].z > 0 ? ins : del)++;
+      const int nl = out.len[u] - del + ins;
+      relocS[q] = -1;
+      if (nl > out.cap[u]) {
+        rcapS[q] = grown_cap(out.cap[u], nl);
+        relocS[q] = h->tail_out + need;
+        need += rcapS[q];
+      }
+    }
+    if (h->tail_out + need > out.m_cap) fail = 1;
+    if (DIRECTED) {
+      long long needT = 0;
+      for (int q = 0; q < nTrow; ++q) {
+        const int v = Tcol[q];
+        int ins = 0, del = 0;
+        for (int e = Tfirst[q]; e < Tfirst[q + 1]; ++e) (edT[e].z > 0 ? ins : del)++;
+        const int nl = in.len[v] - del + ins;
+        relocT[q] = -1;
+        if (nl > in.cap[v]) {
+          rcapT[q] = grown_cap(in.cap[v], nl);
+          relocT[q] = h->tail_in + needT;
+          needT += rcapT[q];
+        }
+      }
+      if (h->tail_in + needT > in.m_cap) fail = 1;
+      if (!fail) h->tail_in += needT;
+    }
+    if (fail) {
+      set_status(h, DAMF_ERR_CAPACITY);
+    } else {
+      h->tail_out += need;
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    if (tid == 0) h->nS = h->nT = h->nedit = 0;
+    return;
+  }
+  // write the sets, N and the degrees before the edit
+  for (int i = tid; i < nS; i += blockDim.x) {
+    ws.S[i] = Srow[i];
+    ws.deg_old[i] = out.len[Srow[i]];
+  }
+  for (int i = tid; i < nT; i += blockDim.x) ws.T[i] = Tcol[i];
+  for (int i = tid; i < nS * nT; i += blockDim.x) ws.N[i] = 0.0f;
+  __syncthreads();
+  for (int e = tid; e < nedit; e += blockDim.x) {
+    const int3 x = ed[e];
+    int a = 0;
+    while (Srow[a] != x.x) ++a;
+    int b = 0;
+    while (Tcol[b] != x.y) ++b;
+    ws.N[a * nT + b] = (float)x.z;
+    ws.edits[e] = make_int4(x.x, x.y, x.z, a);
+  }
+  __syncthreads();
+  apply_row_edits(out, Srow, nS, Sfirst, ed, relocS, rcapS, ws.deg_new);
+  if (DIRECTED) {
+    __syncthreads();
+    apply_row_edits(in, Tcol, nTrow, Tfirst, edT, relocT, rcapT, nullptr);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    h->nS = nS;
+    h->nT = nT;
+    h->nedit = nedit;
+    if (nedit > 0) {
+      h->updates += 1;
+      h->entries_changed += nedit;
+      h->touched_rows += nS + nT;
+      h->last_rank = nS;
+    }
+  }
+  // rows whose residual changes (signal delta and fix-up) are queued for the next push
+  for (int i = tid; i < nS; i += blockDim.x) {
+    const int u = Srow[i];
+    if (atomicExch(&ws.pstamp[u], h->epoch) != h->epoch) {
+      const int p = atomicAdd(&h->pending, 1);
+      ws.pend[p] = u;
+    }
+  }
+}
+
+cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int,
+                           cudaStream_t s) {
+  if (c->cfg.directed)
+    k_prepare<1><<<1, 512, 0, s>>>(c->hdr, c->out, c->in, c->ws, src, dst, op, k);
+  else
+    k_prepare<0><<<1, 512, 0, s>>>(c->hdr, c->out, c->out, c->ws, src, dst, op, k);
+  return cudaGetLastError();
+}
+
+// ---- graph-change fix-up of the PPR residual (one CTA per changed out-row) ----
+// r[u] += (a - b) sum_{v in N'(u)} Zb[v] + b (sum_{added} Zb[v] - sum_{removed} Zb[v])
+// with a = c/deg'(u) (0 if deg' = 0), b = c/deg(u) (0 if deg = 0), c = (1-alpha)/alpha:
+// this equals c (mean_{N'(u)} Zb - mean_{N(u)} Zb) because N(u) = N'(u) - added + removed.
+template <int D>
+__global__ void __launch_bounds__(256) k_fixup(DevHeader* h, Adj out, Workspace ws, const float* __restrict__ Zb,
+                                               float* r, float c_alpha) {
+  constexpr int LPR = D / 4;          // lanes per row (float4 each)
+  constexpr int RPW = 32 / LPR;       // rows per warp step
+  __shared__ float4 part[8][32];
+  const int a_idx = blockIdx.x;
+  if (h->status != 0 || a_idx >= h->nS) return;
+  const int u = ws.S[a_idx];
+  const int dold = ws.deg_old[a_idx], dnew = ws.deg_new[a_idx];
+  const float ca = dnew > 0 ? c_alpha / (float)dnew : 0.0f;
+  const float cb = dold > 0 ? c_alpha / (float)dold : 0.0f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / LPR, q = lane % LPR;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int st = out.start[u], ln = out.len[u];
+  for (int j = warp * RPW + sub; j < ln; j += 8 * RPW) {
+    const int v = out.col[st + j];
+    const float4 z = reinterpret_cast<const float4*>(Zb + (size_t)v * D)[q];
+    const float w = ca - cb;
+    acc.x += w * z.x, acc.y += w * z.y, acc.z += w * z.z, acc.w += w * z.w;
+  }
+  const int nedit = h->nedit;
+  for (int e = warp * RPW + sub; e < nedit; e += 8 * RPW) {
+    const int4 x = ws.edits[e];
+    if (x.x != u) continue;
+    const float4 z = reinterpret_cast<const float4*>(Zb + (size_t)x.y * D)[q];
+    const float w = x.z > 0 ? cb : -cb;
+    acc.x += w * z.x, acc.y += w * z.y, acc.z += w * z.z, acc.w += w * z.w;
+  }
+  // reduce the RPW sub-rows of the warp, then the 8 warps
+#pragma unroll
+  for (int o = LPR; o < 32; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && lane < LPR) {
+    float4 s = part[0][lane];
+    for (int w = 1; w < 8; ++w) {
+      const float4 t = part[w][lane];
+      s.x += t.x, s.y += t.y, s.z += t.z, s.w += t.w;
+    }
+    float4* ru = reinterpret_cast<float4*>(r + (size_t)u * D) + lane;
+    float4 cur = *ru;
+    cur.x += s.x, cur.y += s.y, cur.z += s.z, cur.w += s.w;
+    *ru = cur;
+  }
+  if (threadIdx.x == 0) atomicAdd((unsigned long long*)&h->fixup_edges, (unsigned long long)(ln + nedit));
+}
+
+cudaError_t launch_fixup(Ctx* c, cudaStream_t s) {
+  const float ca = (float)((1.0 - c->cfg.alpha) / c->cfg.alpha);
+  switch (c->d) {
+    case 16: k_fixup<16><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    case 32: k_fixup<32><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    case 64: k_fixup<64><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    default: k_fixup<128><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---- adjacency construction from a caller CSR ----
+__global__ void k_row_len(const int32_t* row_ptr, int n, int32_t* len, int32_t* cap) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int l = row_ptr[u + 1] - row_ptr[u];
+  len[u] = l;
+  int c = l + max(4, l >> 2);
+  cap[u] = (c + 3) & ~3;
+}
+
+__global__ void k_copy_rows(const int32_t* row_ptr, const int32_t* col_idx, int n, const int32_t* start,
+                            int32_t* col) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int b = row_ptr[warp], e = row_ptr[warp + 1], st = start[warp];
+  for (int j = b + lane; j < e; j += 32) col[st + (j - b)] = col_idx[j];
+}
+
+__global__ void k_in_count(const int32_t* col_idx, long long m, int32_t* cnt) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < m) atomicAdd(&cnt[col_idx[i]], 1);
+}
+
+__global__ void k_in_fill(const int32_t* row_ptr, const int32_t* col_idx, int n, const int32_t* start, int32_t* fillpos,
+                          int32_t* col) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  for (int j = row_ptr[warp] + lane; j < row_ptr[warp + 1]; j += 32) {
+    const int v = col_idx[j];
+    const int p = atomicAdd(&fillpos[v], 1);
+    col[start[v] + p] = warp;
+  }
+}
+
+__global__ void k_cap_from_len(const int32_t* len, int n, int32_t* cap) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int l = len[u];
+  int c = l + max(4, l >> 2);
+  cap[u] = (c + 3) & ~3;
+}
+
+cudaError_t build_adjacency(Ctx* c, Adj* a, const int32_t* row_ptr, const int32_t* col_idx, int64_t m, int n,
+                            long long* tail_host, int transpose, cudaStream_t s) {
+  cudaError_t e;
+  const int nb = (n + 255) / 256;
+  if (!transpose) {
+    k_row_len<<<nb, 256, 0, s>>>(row_ptr, n, a->len, a->cap);
+  } else {
+    cudaMemsetAsync(a->len, 0, sizeof(int32_t) * (size_t)n, s);
+    if (m > 0) k_in_count<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(col_idx, m, a->len);
+    k_cap_from_len<<<nb, 256, 0, s>>>(a->len, n, a->cap);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // exclusive scan of the capacities on the host (setup path)
+  std::vector<int32_t> cap(n), start(n);
+  if ((e = cudaMemcpyAsync(cap.data(), a->cap, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  long long acc = 0;
+  for (int u = 0; u < n; ++u) {
+    start[u] = (int32_t)acc;
+    acc += cap[u];
+  }
+  if (acc > a->m_cap || acc > 0x7fffffffll) return cudaErrorMemoryAllocation;
+  *tail_host = acc;
+  if ((e = cudaMemcpyAsync(a->start, start.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  const int wb = (int)(((long long)n * 32 + 255) / 256);
+  if (!transpose) {
+    k_copy_rows<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, a->col);
+  } else {
+    int32_t* fillpos = c->ws.cand[1];  // n_cap ints of scratch, unused until the first push
+    cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * (size_t)n, s);
+    k_in_fill<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, fillpos, a->col);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace damf

@@ -1,0 +1,180 @@
+// Dynamic embedding enhancement (Sec. 4.4; Step 4 of Sec. 4.5): PPR push rounds.
+//
+// State (Zb, r) keeps  Pi X_b = Zb + Pi r  with P = D^{-1} A, Pi = alpha (I - (1-alpha) P)^{-1}.
+// Because Pi = alpha I + (1-alpha) Pi P, pushing node u moves alpha r[u] into Zb[u] and
+// adds (1-alpha) A[w][u] / deg(w) * r[u] to r[w] for every in-neighbour w of u.
+// Rounds: the frontier is {u : max_j |r[u][j]| > eps} among the candidates (rows whose
+// residual may have crossed eps).  When no row exceeds eps, |Zb - Pi X_b| <= eps
+// elementwise since Pi is row-substochastic.
+//
+// One persistent cooperative launch runs all rounds; two bounded grid barriers per round:
+//   phase A: candidates -> frontier rows; rho[pos] = r[u], r[u] = 0, Zb[u] += alpha rho,
+//            and the in-edges of u cut into work items of kPushChunk edges;
+//   phase B: each work item adds coef * rho to r[w] with float4 atomics (L2); a row whose
+//            new value crosses eps is queued once per round (stamp) as a candidate.
+// Counters are indexed by round parity so each is reset by one block between its uses.
+#include "damf_internal.cuh"
+
+namespace damf {
+
+__device__ __forceinline__ float4 f4_ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+
+template <int D>
+__global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
+                                              float* Zb, float* r, int n, float alpha, float eps, int max_rounds,
+                                              int check_all) {
+  constexpr int LPR = D / 4;      // lanes per row
+  constexpr int RPW = 32 / LPR;   // rows per warp
+  const unsigned nblocks = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPR, q = lane % LPR;
+  const unsigned sub_mask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (sub * LPR));
+  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned epoch0 = h->epoch;
+  const float beta = 1.0f - alpha;
+  long long my_pushes = 0, my_edges = 0;
+  const int ncand0 = check_all ? n : h->pending;
+  int round = 0;
+  for (;; ++round) {
+    const int P = round & 1;
+    if (round >= max_rounds) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, DAMF_ERR_NOT_CONVERGED);
+      break;
+    }
+    // ---- phase A: frontier ----
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      h->front_count[P ^ 1] = 0;
+      h->work_count[P ^ 1] = 0;
+    }
+    const int ncand = round == 0 ? ncand0 : __ldcg(&h->cand_count[P]);
+    const int32_t* cand = round == 0 ? (check_all ? nullptr : ws.pend) : ws.cand[P];
+    for (long long base = gwarp * RPW; base < ncand; base += nwarps * RPW) {
+      const long long ci = base + sub;
+      const bool valid = ci < ncand;
+      const int u = valid ? (cand ? __ldcg(cand + ci) : (int)ci) : 0;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+      float mx = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const bool push = valid && mx > eps;
+      const unsigned bal = __ballot_sync(0xffffffffu, push && q == 0);
+      int basepos = 0;
+      if (lane == 0 && bal) basepos = atomicAdd(&h->front_count[P], __popc(bal));
+      basepos = __shfl_sync(0xffffffffu, basepos, 0);
+      if (push) {
+        const int pos = basepos + __popc(bal & ((1u << (sub * LPR)) - 1u));
+        __stcg(reinterpret_cast<float4*>(ws.rho + (size_t)pos * D) + q, v);
+        __stcg(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(0.f, 0.f, 0.f, 0.f));
+        float4 z = f4_ldcg(Zb + (size_t)u * D + 4 * q);
+        z.x = fmaf(alpha, v.x, z.x);
+        z.y = fmaf(alpha, v.y, z.y);
+        z.z = fmaf(alpha, v.z, z.z);
+        z.w = fmaf(alpha, v.w, z.w);
+        __stcg(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q, z);
+        if (q == 0) {
+          __stcg(ws.front + pos, u);
+          const int deg = in.len[u];
+          const int nch = (deg + kPushChunk - 1) / kPushChunk;
+          if (nch > 0) {
+            const int wpos = atomicAdd(&h->work_count[P], nch);
+            for (int c2 = 0; c2 < nch; ++c2) __stcg(&ws.work[wpos + c2], make_int2(pos, c2));
+          }
+          my_pushes += 1;
+          my_edges += deg;
+        }
+      }
+    }
+    if (!grid_barrier(&h->bar, h, nblocks)) return;
+    const int nfront = __ldcg(&h->front_count[P]);
+    if (nfront == 0) break;
+    // ---- phase B: scatter (1-alpha) rho / deg(w) to in-neighbours ----
+    if (blockIdx.x == 0 && threadIdx.x == 0) h->cand_count[P] = 0;
+    const int nwork = __ldcg(&h->work_count[P]);
+    const unsigned tag = epoch0 + (unsigned)round + 1u;
+    for (long long it = gwarp * RPW + sub; it - sub < nwork; it += nwarps * RPW) {
+      const bool valid = it < nwork;
+      int2 wi = make_int2(0, 0);
+      if (valid) wi = __ldcg(&ws.work[it]);
+      const int u = valid ? __ldcg(ws.front + wi.x) : 0;
+      const int st = valid ? in.start[u] : 0;
+      const int deg = valid ? in.len[u] : 0;
+      const int e0 = wi.y * kPushChunk;
+      const int e1 = valid ? min(e0 + kPushChunk, deg) : e0;
+      float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
+      for (int e = e0; e < kPushChunk + e0; ++e) {
+        const bool act = e < e1;
+        int w = 0;
+        bool crossed = false;
+        if (act) {
+          w = __ldg(in.col + st + e);
+          const float coef = beta / (float)__ldg(outdeg + w);
+          const float4 add = make_float4(coef * rv.x, coef * rv.y, coef * rv.z, coef * rv.w);
+          const float4 old = atomicAdd(reinterpret_cast<float4*>(r + (size_t)w * D) + q, add);
+          const float nx = old.x + add.x, ny = old.y + add.y, nz = old.z + add.z, nw2 = old.w + add.w;
+          crossed = fmaxf(fmaxf(fabsf(nx), fabsf(ny)), fmaxf(fabsf(nz), fabsf(nw2))) > eps;
+        }
+        const unsigned cb = __ballot_sync(0xffffffffu, crossed) & sub_mask;
+        if (act && q == 0 && cb) {
+          if (atomicExch(&ws.stamp[w], tag) != tag) {
+            const int p = atomicAdd(&h->cand_count[P ^ 1], 1);
+            __stcg(ws.cand[P ^ 1] + p, w);
+          }
+        }
+      }
+    }
+    if (!grid_barrier(&h->bar, h, nblocks)) return;
+  }
+  // counters and bookkeeping (block 0 after the last barrier; everyone has left the loop)
+  for (int o = 16; o > 0; o >>= 1) {
+    my_pushes += __shfl_xor_sync(0xffffffffu, my_pushes, o);
+    my_edges += __shfl_xor_sync(0xffffffffu, my_edges, o);
+  }
+  if (lane == 0 && (my_pushes || my_edges)) {
+    atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)my_pushes);
+    atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)my_edges);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    h->push_rounds += round;
+    h->pending = 0;
+    h->check_all = 0;
+    h->epoch = epoch0 + (unsigned)round + 2u;
+  }
+}
+
+template <int D>
+static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
+  if (c->push_blocks == 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D>, 256, 0);
+    c->push_blocks = sms * (per_sm < 1 ? 1 : per_sm);
+  }
+  cudaError_t e = cudaMemsetAsync(&c->hdr->cand_count[0], 0, 6 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  DevHeader* h = c->hdr;
+  Adj in = c->cfg.directed ? c->in : c->out;
+  const int32_t* outdeg = c->out.len;
+  Workspace ws = c->ws;
+  float* Zb = c->Zb;
+  float* r = c->r;
+  int n = c->n;
+  float alpha = (float)c->cfg.alpha, eps = (float)c->cfg.eps;
+  int max_rounds = c->cfg.max_push_rounds;
+  void* args[] = {&h, &in, &outdeg, &ws, &Zb, &r, &n, &alpha, &eps, &max_rounds, &check_all};
+  return cudaLaunchCooperativeKernel((void*)k_push<D>, dim3(c->push_blocks), dim3(256), args, 0, s);
+}
+
+cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s) {
+  switch (c->d) {
+    case 16: return push_impl<16>(c, check_all, s);
+    case 32: return push_impl<32>(c, check_all, s);
+    case 64: return push_impl<64>(c, check_all, s);
+    default: return push_impl<128>(c, check_all, s);
+  }
+}
+
+}  // namespace damf

@@ -1,0 +1,485 @@
+// The factor update for one batch of net changes dA = I_S N I_T^T (Sec. 4.3, Thm 2),
+// in U-form: U = Ub PU, V = Vb PV, Sigma kept separately (X = U Sigma^{1/2}).
+//
+// Choice of factors: B = I_S (orthonormal columns, one per touched source row) and
+// C = I_T N^T, so that B C^T = dA and r = |S|.  Then
+//   Step 1 (orthogonalisation, Alg. 1):  W_B = U^T B = U[S]^T,  W_C = V^T C = (N V[T])^T,
+//          residual Grams  G_B = B^T B - W_B^T W_B = I - U[S] U[S]^T,
+//                          G_C = N N^T - (N V[T]) (N V[T])^T        (Prop. 1 for a block),
+//          R_B, R_C upper Cholesky factors (pivots below a tolerance are dropped: the
+//          residual column is dependent, e.g. rank(N) < |S| when events share endpoints).
+//   Step 2 (rediagonalisation):  M = [[Sigma, 0], [0, 0]] + [W_B; R_B] [W_C; R_C]^T,
+//          top-d SVD  M = E Theta H^T  (Eq. "svd_small_edge"; jacobi.cu).
+//   Step 3 (space projection):   Y_B = R_B^{-1} E[d:],  K_U = E[:d] - W_B Y_B,
+//          PU <- PU K_U, PUi <- K_U^{-1} PUi, Ub[S] += Y_B PUi   (Eqs. "f_edge", "x_edge",
+//          "update" with the Sigma^{1/2} scalings moved to query time), same for V with
+//          Y_C = R_C^{-1} H[d:], K_V = H[:d] - W_C Y_C, Vb[T] += (N^T Y_C) PVi;  Sigma <- Theta.
+//   Step 4 input: r[S] += (Ub[S] change) diag(s0), the change of the PPR signal Ub diag(s0).
+#include "damf_internal.cuh"
+
+namespace damf {
+
+constexpr float kPivotTol = 1e-5f;   // relative Cholesky pivot tolerance (FP32)
+
+// ---- a2: gather U[S] = Ub[S] PU and V[T] = Vb[T] PV (16 rows per CTA) ----
+template <int D>
+__global__ void __launch_bounds__(256) k_gather(DevHeader* h, Workspace ws, const float* __restrict__ Ub,
+                                                const float* __restrict__ Vb, const float* __restrict__ PU,
+                                                const float* __restrict__ PV) {
+  extern __shared__ float smem[];
+  float* P = smem;               // D x D
+  float* A = smem + D * D;       // 16 x D
+  if (h->status != 0) return;
+  const int side = blockIdx.y;
+  const int nrows = side == 0 ? h->nS : h->nT;
+  const int r0 = blockIdx.x * 16;
+  if (r0 >= nrows) return;
+  const int32_t* idx = side == 0 ? ws.S : ws.T;
+  const float* base = side == 0 ? Ub : Vb;
+  const float* Pm = side == 0 ? PU : PV;
+  float* outp = side == 0 ? ws.UST : ws.VT;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < D * D / 4; i += 256) reinterpret_cast<float4*>(P)[i] = reinterpret_cast<const float4*>(Pm)[i];
+  for (int i = tid; i < 16 * D / 4; i += 256) {
+    const int rr = i / (D / 4), q = i % (D / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 + rr < nrows) v = reinterpret_cast<const float4*>(base + (size_t)idx[r0 + rr] * D)[q];
+    reinterpret_cast<float4*>(A)[i] = v;
+  }
+  __syncthreads();
+  for (int o = tid; o < 16 * D; o += 256) {
+    const int rr = o / D, j = o % D;
+    if (r0 + rr >= nrows) continue;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < D; ++k) s = fmaf(A[rr * D + k], P[k * D + j], s);
+    outp[(r0 + rr) * D + j] = s;
+  }
+}
+
+// ---- a3: W_C^T = N V[T], residual Grams, semi-definite Cholesky (one CTA) ----
+template <int D>
+__global__ void __launch_bounds__(1024) k_chol(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* GB = smem;                      // kMaxR x kMaxR
+  float* GC = GB + kMaxR * kMaxR;
+  float* US = GC + kMaxR * kMaxR;        // nS x D
+  float* WC = US + kMaxR * D;            // nS x D
+  __shared__ float pivB, pivC;
+  __shared__ int keptB, keptC;
+  __shared__ float scaleB, scaleC;
+  if (h->status != 0) return;
+  const int nS = h->nS, nT = h->nT;
+  if (nS == 0) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < nS * D; i += nt) US[i] = ws.UST[i];
+  for (int i = tid; i < nS * D; i += nt) {
+    const int a = i / D, j = i % D;
+    float s = 0.f;
+    for (int b = 0; b < nT; ++b) s = fmaf(ws.N[a * nT + b], ws.VT[b * D + j], s);
+    WC[i] = s;
+    ws.WCt[i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < nS * nS; i += nt) {
+    const int a = i / nS, b = i % nS;
+    if (b < a) continue;
+    float gb = (a == b) ? 1.0f : 0.0f, gc = 0.f;
+    for (int t = 0; t < nT; ++t) gc = fmaf(ws.N[a * nT + t], ws.N[b * nT + t], gc);
+    float sb = 0.f, sc = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+      sb = fmaf(US[a * D + k], US[b * D + k], sb);
+      sc = fmaf(WC[a * D + k], WC[b * D + k], sc);
+    }
+    gb -= sb;
+    gc -= sc;
+    GB[a * kMaxR + b] = GB[b * kMaxR + a] = gb;
+    GC[a * kMaxR + b] = GC[b * kMaxR + a] = gc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float mb = 1.0f, mc = 1.0f;
+    for (int a = 0; a < nS; ++a) {
+      mb = fmaxf(mb, GB[a * kMaxR + a]);
+      mc = fmaxf(mc, GC[a * kMaxR + a]);
+    }
+    scaleB = mb * kPivotTol;
+    scaleC = mc * kPivotTol;
+    keptB = keptC = 0;
+  }
+  __syncthreads();
+  // right-looking Cholesky G = R^T R (R upper); rows with a pivot <= tol are zero
+  for (int j = 0; j < nS; ++j) {
+    if (tid == 0) {
+      const float pb = GB[j * kMaxR + j], pc = GC[j * kMaxR + j];
+      pivB = pb > scaleB ? sqrtf(pb) : 0.0f;
+      pivC = pc > scaleC ? sqrtf(pc) : 0.0f;
+      keptB += pivB > 0.f;
+      keptC += pivC > 0.f;
+    }
+    __syncthreads();
+    const float ib = pivB > 0.f ? 1.0f / pivB : 0.0f, ic = pivC > 0.f ? 1.0f / pivC : 0.0f;
+    // row j of R
+    for (int l = j + tid; l < nS; l += nt) {
+      GB[j * kMaxR + l] = (l == j) ? pivB : GB[j * kMaxR + l] * ib;
+      GC[j * kMaxR + l] = (l == j) ? pivC : GC[j * kMaxR + l] * ic;
+    }
+    __syncthreads();
+    const int rem = nS - j - 1;
+    for (int i = tid; i < rem * rem; i += nt) {
+      const int a = j + 1 + i / rem, b = j + 1 + i % rem;
+      if (b < a) continue;
+      const float vb = GB[a * kMaxR + b] - GB[j * kMaxR + a] * GB[j * kMaxR + b];
+      const float vc = GC[a * kMaxR + b] - GC[j * kMaxR + a] * GC[j * kMaxR + b];
+      GB[a * kMaxR + b] = vb;
+      GC[a * kMaxR + b] = vc;
+      GB[b * kMaxR + a] = vb;
+      GC[b * kMaxR + a] = vc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nS * nS; i += nt) {
+    const int a = i / nS, b = i % nS;
+    ws.RB[a * kMaxR + b] = b >= a ? GB[a * kMaxR + b] : 0.0f;
+    ws.RC[a * kMaxR + b] = b >= a ? GC[a * kMaxR + b] : 0.0f;
+  }
+  if (tid == 0) {
+    h->rankB = keptB;
+    h->rankC = keptC;
+  }
+}
+
+// ---- core assembly: M = diag(sigma, 0) + L R^T, column-major with ld = m ----
+template <int D>
+__global__ void __launch_bounds__(256) k_assemble(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
+  if (h->status != 0) return;
+  const int nS = h->nS;
+  if (nS == 0) return;
+  const int m = D + nS;
+  const int j = blockIdx.x;  // column
+  if (j >= m) return;
+  __shared__ float Rj[kMaxR];
+  for (int a = threadIdx.x; a < nS; a += blockDim.x)
+    Rj[a] = j < D ? ws.WCt[a * D + j] : ws.RC[(j - D) * kMaxR + a];
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    float s = (i == j && i < D) ? sigma[i] : 0.0f;
+    if (i < D) {
+      for (int a = 0; a < nS; ++a) s = fmaf(ws.UST[a * D + i], Rj[a], s);
+    } else {
+      const float* rb = ws.RB + (i - D) * kMaxR;
+      for (int a = 0; a < nS; ++a) s = fmaf(rb[a], Rj[a], s);
+    }
+    ws.M[(size_t)j * m + i] = s;
+  }
+}
+
+// ---- H = M^T E Theta^{-1} (top-d right singular vectors) ----
+template <int D>
+__global__ void __launch_bounds__(128) k_hmat(DevHeader* h, Workspace ws) {
+  if (h->status != 0) return;
+  const int nS = h->nS;
+  if (nS == 0) return;
+  const int m = D + nS;
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  __shared__ float Mj[kMaxM];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) Mj[i] = ws.M[(size_t)j * m + i];
+  __syncthreads();
+  for (int k = threadIdx.x; k < D; k += blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < m; ++i) s = fmaf(Mj[i], ws.E[i * D + k], s);
+    const float t = ws.theta[k];
+    ws.H[j * D + k] = t > 0.f ? s / t : 0.0f;
+  }
+}
+
+// ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
+template <int D>
+__global__ void __launch_bounds__(1024) k_trans(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* R = smem;                    // kMaxR x kMaxR
+  float* Y = R + kMaxR * kMaxR;       // nS x D
+  if (h->status != 0) return;
+  const int nS = h->nS;
+  if (nS == 0) return;
+  const int side = blockIdx.x;
+  const float* Rg = side == 0 ? ws.RB : ws.RC;
+  const float* Eg = side == 0 ? ws.E : ws.H;     // (D + nS) x D row-major
+  const float* Wt = side == 0 ? ws.UST : ws.WCt;  // nS x D  (W^T)
+  float* Yg = side == 0 ? ws.YB : ws.YC;
+  float* K = side == 0 ? ws.KU : ws.KV;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < nS * nS; i += blockDim.x) {
+    const int a = i / nS, b = i % nS;
+    R[a * kMaxR + b] = Rg[a * kMaxR + b];
+  }
+  for (int i = tid; i < nS * D; i += blockDim.x) Y[i] = Eg[D * D + i];
+  __syncthreads();
+  // back substitution, 8 threads per column
+  const int col = tid >> 3, sub = tid & 7;
+  for (int j = nS - 1; j >= 0; --j) {
+    float s = 0.f;
+    if (col < D)
+      for (int l = j + 1 + sub; l < nS; l += 8) s = fmaf(R[j * kMaxR + l], Y[l * D + col], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (col < D && sub == 0) {
+      const float p = R[j * kMaxR + j];
+      Y[j * D + col] = p > 0.f ? (Y[j * D + col] - s) / p : 0.0f;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nS * D; i += blockDim.x) Yg[i] = Y[i];
+  for (int o = tid; o < D * D; o += blockDim.x) {
+    const int i = o / D, k = o % D;
+    float s = Eg[i * D + k];
+    for (int a = 0; a < nS; ++a) s = fmaf(-Wt[a * D + i], Y[a * D + k], s);
+    K[o] = s;
+  }
+}
+
+// ---- Gauss-Jordan inverse with partial pivoting (block 0: K_U, block 1: K_V) ----
+template <int D>
+__global__ void __launch_bounds__(1024) k_inverse(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* Aug = smem;   // D x 2D
+  __shared__ int piv_row;
+  __shared__ float piv_val;
+  __shared__ float colv[D];
+  if (h->status != 0 || h->nS == 0) return;
+  const float* K = blockIdx.x == 0 ? ws.KU : ws.KV;
+  float* Ki = blockIdx.x == 0 ? ws.KUi : ws.KVi;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int o = tid; o < D * 2 * D; o += nt) {
+    const int i = o / (2 * D), j = o % (2 * D);
+    Aug[o] = j < D ? K[i * D + j] : (j - D == i ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  for (int p = 0; p < D; ++p) {
+    if (tid < 32) {  // pivot search in column p, rows p..D-1
+      float best = -1.f;
+      int br = p;
+      for (int i = p + tid; i < D; i += 32) {
+        const float a = fabsf(Aug[i * 2 * D + p]);
+        if (a > best) best = a, br = i;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && orr < br)) best = ob, br = orr;
+      }
+      if (tid == 0) {
+        piv_row = br;
+        piv_val = Aug[br * 2 * D + p];
+      }
+    }
+    __syncthreads();
+    if (!(fabsf(piv_val) > 1e-30f)) {
+      if (tid == 0) set_status(h, DAMF_ERR_NUMERIC);
+      return;
+    }
+    const int pr = piv_row;
+    const float inv = 1.0f / piv_val;
+    for (int j = tid; j < 2 * D; j += nt) {  // swap rows p, pr and scale the pivot row
+      const float a = Aug[p * 2 * D + j], b = Aug[pr * 2 * D + j];
+      Aug[pr * 2 * D + j] = a;
+      Aug[p * 2 * D + j] = b * inv;
+    }
+    __syncthreads();
+    for (int i = tid; i < D; i += nt) colv[i] = Aug[i * 2 * D + p];
+    __syncthreads();
+    for (int o = tid; o < D * 2 * D; o += nt) {
+      const int i = o / (2 * D), j = o % (2 * D);
+      if (i == p) continue;
+      Aug[o] = fmaf(-colv[i], Aug[p * 2 * D + j], Aug[o]);
+    }
+    __syncthreads();
+  }
+  for (int o = tid; o < D * D; o += nt) {
+    const int i = o / D, j = o % D;
+    Ki[o] = Aug[i * 2 * D + D + j];
+  }
+}
+
+// ---- d x d products into tmp: PU K_U, K_U^{-1} PUi, PV K_V, K_V^{-1} PVi ----
+template <int D>
+__global__ void __launch_bounds__(256) k_products(DevHeader* h, Workspace ws, const float* __restrict__ PU,
+                                                  const float* __restrict__ PUi, const float* __restrict__ PV,
+                                                  const float* __restrict__ PVi) {
+  constexpr int TS = D < 32 ? D : 32;
+  constexpr int NT = D / TS;
+  __shared__ float As[TS][D + 1];
+  __shared__ float Bs[D][TS + 1];
+  if (h->status != 0 || h->nS == 0) return;
+  const int prod = blockIdx.x / (NT * NT), tile = blockIdx.x % (NT * NT);
+  const int ti = tile / NT, tj = tile % NT;
+  const float *A, *B;
+  switch (prod) {
+    case 0: A = PU, B = ws.KU; break;
+    case 1: A = ws.KUi, B = PUi; break;
+    case 2: A = PV, B = ws.KV; break;
+    default: A = ws.KVi, B = PVi; break;
+  }
+  float* C = ws.tmp + (size_t)prod * D * D;
+  for (int o = threadIdx.x; o < TS * D; o += blockDim.x) {
+    const int i = o / D, k = o % D;
+    As[i][k] = A[(ti * TS + i) * D + k];
+  }
+  for (int o = threadIdx.x; o < D * TS; o += blockDim.x) {
+    const int k = o / TS, j = o % TS;
+    Bs[k][j] = B[k * D + tj * TS + j];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < TS * TS; o += blockDim.x) {
+    const int i = o / TS, j = o % TS;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < D; ++k) s = fmaf(As[i][k], Bs[k][j], s);
+    C[(ti * TS + i) * D + tj * TS + j] = s;
+  }
+}
+
+// ---- commit the new transforms and Sigma; non-finite check ----
+template <int D>
+__global__ void __launch_bounds__(256) k_commit(DevHeader* h, Workspace ws, float* PU, float* PUi, float* PV,
+                                                float* PVi, float* sigma) {
+  __shared__ int bad;
+  if (h->status != 0 || h->nS == 0) return;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  float* dst[4] = {PU, PUi, PV, PVi};
+  const int part = blockIdx.x;  // one block per matrix
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
+    const float v = ws.tmp[(size_t)part * D * D + o];
+    if (!isfinite(v)) bad = 1;
+  }
+  if (part == 0)
+    for (int k = threadIdx.x; k < D; k += blockDim.x)
+      if (!isfinite(ws.theta[k])) bad = 1;
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) set_status(h, DAMF_ERR_NUMERIC);
+    return;
+  }
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) dst[part][o] = ws.tmp[(size_t)part * D * D + o];
+  if (part == 0)
+    for (int k = threadIdx.x; k < D; k += blockDim.x) sigma[k] = ws.theta[k];
+}
+
+// ---- a6: Ub[S] += Y_B PUi,  Vb[T] += (N^T Y_C) PVi,  r[S] += (Ub[S] change) diag(s0) ----
+template <int D>
+__global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, float* Ub, float* Vb, float* r,
+                                                 const float* __restrict__ PUi, const float* __restrict__ PVi,
+                                                 const float* __restrict__ s0) {
+  extern __shared__ float smem[];
+  float* P = smem;             // D x D
+  float* A = smem + D * D;     // 16 x D
+  if (h->status != 0) return;
+  const int nS = h->nS, nT = h->nT;
+  if (nS == 0) return;
+  const int side = blockIdx.y;
+  const int nrows = side == 0 ? nS : nT;
+  const int r0 = blockIdx.x * 16;
+  if (r0 >= nrows) return;
+  const float* Pm = side == 0 ? PUi : PVi;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < D * D / 4; i += 256) reinterpret_cast<float4*>(P)[i] = reinterpret_cast<const float4*>(Pm)[i];
+  for (int o = tid; o < 16 * D; o += 256) {
+    const int rr = o / D, k = o % D;
+    float v = 0.f;
+    if (r0 + rr < nrows) {
+      if (side == 0) {
+        v = ws.YB[(r0 + rr) * D + k];
+      } else {
+        const int b = r0 + rr;
+        for (int a = 0; a < nS; ++a) v = fmaf(ws.N[a * nT + b], ws.YC[a * D + k], v);
+      }
+    }
+    A[o] = v;
+  }
+  __syncthreads();
+  for (int o = tid; o < 16 * D; o += 256) {
+    const int rr = o / D, j = o % D;
+    if (r0 + rr >= nrows) continue;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < D; ++k) s = fmaf(A[rr * D + k], P[k * D + j], s);
+    if (side == 0) {
+      const size_t row = (size_t)ws.S[r0 + rr] * D;
+      Ub[row + j] += s;
+      r[row + j] += s * s0[j];
+    } else {
+      Vb[(size_t)ws.T[r0 + rr] * D + j] += s;
+    }
+  }
+}
+
+template <int D>
+static cudaError_t gather_impl(Ctx* c, cudaStream_t s) {
+  const size_t sm = (size_t)(D * D + 16 * D) * sizeof(float);
+  cudaFuncSetAttribute(k_gather<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gather<D><<<dim3(kMaxR / 16, 2), 256, sm, s>>>(c->hdr, c->ws, c->Ub, c->Vb, c->PU, c->PV);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t chol_impl(Ctx* c, cudaStream_t s) {
+  const size_t sm = (size_t)(2 * kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
+  cudaFuncSetAttribute(k_chol<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_chol<D><<<1, 1024, sm, s>>>(c->hdr, c->ws);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
+  cudaError_t e;
+  k_hmat<D><<<kMaxM, 128, 0, s>>>(c->hdr, c->ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t sm = (size_t)(kMaxR * kMaxR + kMaxR * D) * sizeof(float);
+  cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_trans<D><<<2, 1024, sm, s>>>(c->hdr, c->ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smi = (size_t)(D * 2 * D) * sizeof(float);
+  cudaFuncSetAttribute(k_inverse<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+  k_inverse<D><<<2, 1024, smi, s>>>(c->hdr, c->ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  constexpr int TS = D < 32 ? D : 32;
+  constexpr int NT = D / TS;
+  k_products<D><<<4 * NT * NT, 256, 0, s>>>(c->hdr, c->ws, c->PU, c->PUi, c->PV, c->PVi);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_commit<D><<<4, 256, 0, s>>>(c->hdr, c->ws, c->PU, c->PUi, c->PV, c->PVi, c->sigma);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t scatter_impl(Ctx* c, cudaStream_t s) {
+  const size_t sm = (size_t)(D * D + 16 * D) * sizeof(float);
+  cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scatter<D><<<dim3(kMaxR / 16, 2), 256, sm, s>>>(c->hdr, c->ws, c->Ub, c->Vb, c->r, c->PUi, c->PVi, c->s0);
+  return cudaGetLastError();
+}
+
+#define DAMF_DISPATCH_D(fn, ...)                    \
+  switch (c->d) {                                   \
+    case 16: return fn<16>(__VA_ARGS__);            \
+    case 32: return fn<32>(__VA_ARGS__);            \
+    case 64: return fn<64>(__VA_ARGS__);            \
+    default: return fn<128>(__VA_ARGS__);           \
+  }
+
+cudaError_t launch_gather(Ctx* c, cudaStream_t s) { DAMF_DISPATCH_D(gather_impl, c, s) }
+cudaError_t launch_chol(Ctx* c, cudaStream_t s) { DAMF_DISPATCH_D(chol_impl, c, s) }
+cudaError_t launch_transforms(Ctx* c, cudaStream_t s) { DAMF_DISPATCH_D(trans_impl, c, s) }
+cudaError_t launch_scatter(Ctx* c, cudaStream_t s) { DAMF_DISPATCH_D(scatter_impl, c, s) }
+
+template <int D>
+static cudaError_t assemble_impl(Ctx* c, cudaStream_t s) {
+  k_assemble<D><<<kMaxM, 256, 0, s>>>(c->hdr, c->ws, c->sigma);
+  return cudaGetLastError();
+}
+cudaError_t launch_assemble(Ctx* c, cudaStream_t s) { DAMF_DISPATCH_D(assemble_impl, c, s) }
+
+}  // namespace damf

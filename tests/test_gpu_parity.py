@@ -1,0 +1,212 @@
+"""CUDA path (through the C ABI) against the FP64 oracle and the paper's definitions.
+
+Tolerances (FP32 device arithmetic, derived in the design doc):
+  * integer work (adjacency, touched sets S/T): bit-exact
+  * one update vs the brute-force t-SVD of (previous product + dA) (Theorem 2):
+    sigma rel 2e-4, X Y^T rel Frobenius 2e-4
+  * PPR: |Zb - Pi Xb|_max <= eps (1 + 1e-3) + 2e-6 |Xb|_max  (push bound plus FP32 rounding)
+  * whole-stream runs vs the FP64 oracle: sigma rel 1e-3, X Y^T rel Frobenius 1e-3
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.ppr import ppr_matrix_dense
+from oracle.tsvd import brute_force_update
+from synth import CONFIGS, chung_lu_graph, edge_stream
+from tests.gpu_util import dense_adj, gpu_xy, make_pair, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0xDA3F0000 + 200
+
+
+def _events(rng, n, k, p_del=0.25):
+    src, dst, op = [], [], []
+    while len(src) < k:
+        u, v = rng.integers(0, n, 2)
+        if u != v:
+            src.append(u), dst.append(v), op.append(-1 if rng.random() < p_del else 1)
+    return np.array(src, np.int32), np.array(dst, np.int32), np.array(op, np.int8)
+
+
+@pytest.mark.parametrize("d,n", [(16, 1500), (64, 3000)])
+def test_init_matches_oracle(d, n):
+    g, orc, _ = make_pair(n, 10.0, 2.5, d, 0.15, 1e-4, SEED + d, propagate=False)
+    X, Y, s = gpu_xy(g)
+    np.testing.assert_allclose(s, orc.sigma, rtol=1e-3)
+    assert rel_fro(X @ Y.T, orc.X() @ orc.Y().T) < 1e-3
+    U = X / np.sqrt(s)
+    assert np.abs(U.T @ U - np.eye(d)).max() < 1e-4
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_each_update_equals_bruteforce_tsvd(directed):
+    rng = np.random.default_rng(7)
+    n, d = 400, 16
+    g, _, (ip, ix, _) = make_pair(n, 8.0, 2.5, d, 0.15, 1e-4, SEED + 3, directed=directed, oracle=False)
+    checked = 0
+    for step in range(30):
+        X1, Y1, _ = gpu_xy(g)
+        rp0, col0 = g.adjacency()
+        nn = 1 if step % 7 == 3 else 0
+        src, dst, op = _events(rng, g.n + nn, int(rng.integers(1, 40)))
+        if nn:
+            src[0], dst[0], op[0] = g.n, int(rng.integers(0, g.n)), 1
+        g.apply_edges(src, dst, op, new_nodes=nn)
+        g.check()
+        n1 = g.n
+        rp1, col1 = g.adjacency()
+        dA = dense_adj(rp1, col1, n1)
+        A0 = np.zeros((n1, n1))
+        A0[: n1 - nn, : n1 - nn] = dense_adj(rp0, col0, n1 - nn)
+        dA -= A0
+        Xp = np.vstack([X1, np.zeros((nn, d))])
+        Yp = np.vstack([Y1, np.zeros((nn, d))])
+        target = Xp @ Yp.T + dA
+        sv = np.linalg.svd(target, compute_uv=False)
+        if (sv[d - 1] - sv[d]) / sv[0] < 1e-3:
+            continue
+        X2, Y2, s2 = brute_force_update(Xp, Yp, dA, d)
+        Xg, Yg, sg = gpu_xy(g)
+        np.testing.assert_allclose(sg, s2, rtol=2e-4)
+        assert rel_fro(Xg @ Yg.T, X2 @ Y2.T) < 2e-4
+        checked += 1
+    assert checked >= 15
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_adjacency_and_touched_sets_bit_exact(directed):
+    from oracle.graph import DynGraph
+    rng = np.random.default_rng(9)
+    n, d = 600, 16
+    g, _, (ip, ix, _) = make_pair(n, 6.0, 2.3, d, 0.15, 1e-4, SEED + 5, directed=directed, oracle=False)
+    og = DynGraph(ip, ix, n + 64, directed=directed)
+    for step in range(40):
+        k = int(rng.integers(1, 49))
+        src, dst, op = _events(rng, n, k, p_del=0.4)
+        if step % 5 == 0:    # repeat events inside one update: the last one decides
+            src[-1], dst[-1], op[-1] = src[0], dst[0], -op[0]
+        g.apply_edges(src, dst, op)
+        ch = og.apply(src, dst, op)
+        S, T = g.last_touched()
+        if ch.empty:
+            assert len(S) == 0 and len(T) == 0
+        else:
+            assert S.tolist() == ch.S.tolist() and T.tolist() == ch.T.tolist()
+    g.check()
+    for outgoing in (True, False):
+        rp, col = g.adjacency(outgoing)
+        adj = og.out if outgoing else og.inn
+        for u in range(n):
+            assert sorted(col[rp[u]:rp[u + 1]].tolist()) == sorted(adj.row(u).tolist()), u
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_ppr_within_eps_of_exact(directed):
+    rng = np.random.default_rng(11)
+    n, d, alpha, eps = 500, 16, 0.15, 1e-5
+    g, _, _ = make_pair(n, 8.0, 2.5, d, alpha, eps, SEED + 7, directed=directed, oracle=False)
+    for step in range(6):
+        if step:
+            src, dst, op = _events(rng, n, 20)
+            g.apply_edges(src, dst, op)
+            g.ppr_refresh()
+        g.check()
+        st = g.state()
+        Xb = (st["Ub"] * st["s0"]).double().cpu().numpy()
+        Zb = st["Zb"].double().cpu().numpy()
+        r = st["r"].double().cpu().numpy()
+        rp, col = g.adjacency()
+        A = dense_adj(rp, col, g.n)
+        exact = ppr_matrix_dense(A, alpha) @ Xb
+        assert np.abs(r).max() <= eps
+        assert np.abs(Zb - exact).max() <= eps * (1 + 1e-3) + 2e-6 * np.abs(Xb).max()
+    g.close()
+
+
+def test_alpha_one_gives_z_equal_x():
+    # the paper's ablation: alpha = 1 means Z = X
+    g, _, _ = make_pair(300, 8.0, 2.5, 16, 1.0, 1e-6, SEED + 9, oracle=False)
+    g.apply_edges(np.array([1, 2], np.int32), np.array([5, 9], np.int32), np.array([1, 1], np.int8))
+    g.ppr_refresh()
+    e = g.embeddings()
+    np.testing.assert_allclose(e["Z"].cpu().numpy(), e["X"].cpu().numpy(), atol=2e-6)
+    g.close()
+
+
+def test_c1_stream_against_oracle():
+    c = CONFIGS["C1"]
+    ip, ix, w = chung_lu_graph(c.n, c.avg_deg, c.gamma, seed=c.seed)
+    stream = edge_stream(ip, ix, w, c.n_batches, c.k_lo, c.k_hi, c.p_node, c.p_del, c.seed + 1,
+                         max_new_degree=c.max_new_degree, nodes_per_batch=c.nodes_per_batch)
+    from oracle.damf import DamfOracle
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=stream.n_final, nnz=len(ix))
+    om = gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
+    g = DamfGraph(ip, ix, cfg, om)
+    orc = DamfOracle(ip, ix, c.d, c.alpha, c.eps, n_cap=stream.n_final, Omega=om)
+    for b in stream.batches:
+        g.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        g.ppr_refresh()
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        orc.ppr_refresh()
+    g.check()
+    Xg, Yg, sg = gpu_xy(g)
+    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
+    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    # Z is PPR(X); columns of X, Y, Z carry a common sign (or rotation within a repeated
+    # singular value), so compare the invariant product Z Y^T = PPR(X Y^T)
+    Zg = g.embeddings()["Z"].double().cpu().numpy()
+    assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
+    g.close()
+
+
+def test_edge_cases():
+    from paper_2306_08967_gb300 import DamfError
+    g, _, _ = make_pair(200, 6.0, 2.5, 16, 0.2, 1e-4, SEED + 11, n_extra=4, oracle=False)
+    s0 = gpu_xy(g)[2]
+    g.apply_edges(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8))   # empty call
+    rp, col = g.adjacency()
+    u = 0
+    v = int(col[rp[0]])
+    g.apply_edges(np.array([u], np.int32), np.array([v], np.int32), np.array([1], np.int8))  # existing edge
+    g.check()
+    np.testing.assert_array_equal(gpu_xy(g)[2], s0)
+    g.apply_edges(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8), new_nodes=1)  # lone node
+    assert g.n == 201
+    # 130 events: three consecutive updates in one call
+    rng = np.random.default_rng(3)
+    src, dst, op = _events(rng, 201, 130)
+    g.apply_edges(src, dst, op)
+    g.ppr_refresh()
+    g.check()
+    with pytest.raises(DamfError):
+        g.apply_edges(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8), new_nodes=10)
+    g.close()
+    # device-side validation: a self-loop poisons the context, nothing is written
+    g, _, _ = make_pair(200, 6.0, 2.5, 16, 0.2, 1e-4, SEED + 13, oracle=False)
+    g.apply_edges(np.array([3], np.int32), np.array([3], np.int32), np.array([1], np.int8))
+    assert g.sync_status() == 1
+    g.close()
+    # adjacency capacity exhaustion is reported before any write
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    ip, ix, _ = chung_lu_graph(200, 6.0, 2.5, seed=SEED + 15)
+    cfg = make_config(200, 16, 0.2, 1e-4, nnz=len(ix), m_capacity=int(len(ix) * 1.3) + 1200)
+    g = DamfGraph(ip, ix, cfg, gaussian_test_matrix(200, rsvd_width(cfg), SEED + 17))
+    status = 0
+    for i in range(200):
+        src = np.arange(0, 40, dtype=np.int32) + (i % 4) * 40
+        dst = (src + 1 + i) % 200
+        g.apply_edges(src.astype(np.int32), dst.astype(np.int32), np.ones(40, np.int8))
+        status = g.sync_status()
+        if status:
+            break
+    assert status == 2
+    g.close()
