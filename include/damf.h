@@ -124,6 +124,19 @@ damf_status damf_apply_edges_host(damf_ctx* ctx, const int32_t* src, const int32
 damf_status damf_ppr_refresh(damf_ctx* ctx, void* stream);
 
 /*
+ * Ordering of the push.  damf_ppr_refresh runs the push on a stream the context owns,
+ * after all work enqueued on `stream` before the call; the next damf_apply_edges on
+ * `stream` overlaps its read-only part (net change, projection, residual factors, core
+ * SVD, transform update) with that push and waits for it before editing the adjacency
+ * and the PPR state.  damf_get_embeddings and damf_get_state wait for it as well.
+ * damf_join makes `stream` wait for the most recent push (e.g. before the caller reads
+ * results produced by it through other means); damf_record_event records a caller's
+ * cudaEvent_t (passed as void*) on the push stream after the most recent push.
+ */
+damf_status damf_join(damf_ctx* ctx, void* stream);
+damf_status damf_record_event(damf_ctx* ctx, void* event);
+
+/*
  * Query (Sec. 4.6, "Query Node's Embedding"): X = U_b P_U Sigma^{1/2},
  * Y = V_b P_V Sigma^{1/2}, Z = Z_b S0^{-1/2} P_U Sigma^{1/2} (S0 = Sigma at the last
  * fold; PPR is linear, so the enhanced embedding maps like X).
@@ -175,6 +188,8 @@ typedef struct {
   int32_t last_rank;        /* r of the most recent update */
   int32_t last_status;      /* device status word */
   int64_t launches;         /* kernels launched by this context so far */
+  int32_t last_sweeps;      /* Jacobi sweeps of the most recent update's core SVD */
+  int32_t reserved;
 } damf_stats;
 
 /* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */

@@ -21,7 +21,8 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("updates", c_i64), ("edges_applied", c_i64), ("entries_changed", c_i64), ("pushes", c_i64),
                 ("push_edges", c_i64), ("push_rounds", c_i64), ("fixup_edges", c_i64), ("touched_rows", c_i64),
-                ("folds", c_i64), ("last_rank", c_i32), ("last_status", c_i32), ("launches", c_i64)]
+                ("folds", c_i64), ("last_rank", c_i32), ("last_status", c_i32), ("launches", c_i64),
+                ("last_sweeps", c_i32), ("reserved", c_i32)]
 
 
 # every symbol include/damf.h declares, with its ctypes signature
@@ -32,6 +33,8 @@ SIGNATURES = {
     "damf_apply_edges": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_ppr_refresh": (c_i32, [c_vp, c_vp]),
+    "damf_join": (c_i32, [c_vp, c_vp]),
+    "damf_record_event": (c_i32, [c_vp, c_vp]),
     "damf_get_embeddings": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "damf_num_nodes": (c_i32, [c_vp]),
     "damf_set_timing": (c_i32, [c_vp, c_i32]),

@@ -103,6 +103,14 @@ class DamfGraph:
     def ppr_refresh(self, stream=None):
         self._check(self.lib.damf_ppr_refresh(self.h, _stream_ptr(stream)))
 
+    def join(self, stream=None):
+        """Makes the stream wait for the most recent PPR push."""
+        self._check(self.lib.damf_join(self.h, _stream_ptr(stream)))
+
+    def record_event(self, event):
+        """Records a torch.cuda.Event on the push stream after the most recent push."""
+        self._check(self.lib.damf_record_event(self.h, ctypes.c_void_p(event.cuda_event)))
+
     def embeddings(self, rows=None, want=("X", "Y", "Z", "sigma"), stream=None):
         """Returns a dict of CUDA tensors: X, Y, Z (count x d) and sigma (d)."""
         if rows is None:

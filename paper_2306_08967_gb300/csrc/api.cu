@@ -56,9 +56,9 @@ void timer_end(Ctx* c, int i, int stage, int launches, cudaStream_t s) {
     DAMF_CUDA(call, what);                        \
     timer_end(c, ti_, stage, nl, s);              \
   } while (0)
-// kernels per update: prepare, fixup, gather, chol, assemble, jacobi, hmat, trans, inverse,
-// products, commit, scatter
-constexpr int kLaunchesPerUpdate = 12;
+// kernels per update: prepare, gather, wct, chol, assemble, jacobi, hmat, trans, inverse,
+// products, commit, edit, fixup, scatter
+constexpr int kLaunchesPerUpdate = 14;
 // fold: 2 x (gram part + reduce), 2 x (congruence + chol), core, jacobi, hmat, 4 small_mm,
 // finish, 4 tall GEMMs
 constexpr int kLaunchesPerFold = 4 + 4 + 1 + 2 + 4 + 1 + 4;
@@ -83,7 +83,7 @@ int width_of(const damf_config* cfg) {
 }
 
 long long work_cap_of(const damf_config* cfg) {
-  return (long long)cfg->n_capacity + cfg->m_capacity / kPushChunk + 64;
+  return (long long)cfg->n_capacity + cfg->m_capacity / 4 + 64;   // items hold >= 4 in-edges
 }
 
 int gram_parts_of(const damf_config* cfg) {
@@ -116,6 +116,10 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = kMaxR * 4; s[k++] = kMaxR * 4;                   // S T
   s[k++] = (size_t)kMaxR * kMaxR * 4;                        // N
   s[k++] = (size_t)kMaxEntries * sizeof(int4);               // edits
+  s[k++] = (size_t)kMaxEntries * sizeof(int4);               // editsT
+  s[k++] = (kMaxR + 1) * 4; s[k++] = (kMaxR + 1) * 4;        // Sfirst Tfirst
+  s[k++] = kMaxR * 8; s[k++] = kMaxR * 8;                    // relocS relocT
+  s[k++] = kMaxR * 4; s[k++] = kMaxR * 4;                    // rcapS rcapT
   s[k++] = kMaxR * 4; s[k++] = kMaxR * 4;                    // deg_old deg_new
   s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // UST VT WCt
   s[k++] = (size_t)kMaxR * kMaxR * 4; s[k++] = (size_t)kMaxR * kMaxR * 4;                              // RB RC
@@ -150,6 +154,11 @@ damf_status fail(Ctx* c, damf_status st, const char* what, cudaError_t e) {
   } while (0)
 
 void free_all(Ctx* c) {
+  if (c->push_stream) cudaStreamDestroy(c->push_stream);
+  if (c->ev_caller) cudaEventDestroy(c->ev_caller);
+  if (c->ev_push) cudaEventDestroy(c->ev_push);
+  c->push_stream = nullptr;
+  c->ev_caller = c->ev_push = nullptr;
   if (c->ev) {
     for (int i = 0; i < 2 * kTimerPairs; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -305,6 +314,9 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   if (!cfg->directed) c->in = c->out;
   Workspace& w = c->ws;
   w.S = (int32_t*)ptr[k++]; w.T = (int32_t*)ptr[k++]; w.N = (float*)ptr[k++]; w.edits = (int4*)ptr[k++];
+  w.editsT = (int4*)ptr[k++]; w.Sfirst = (int32_t*)ptr[k++]; w.Tfirst = (int32_t*)ptr[k++];
+  w.relocS = (long long*)ptr[k++]; w.relocT = (long long*)ptr[k++];
+  w.rcapS = (int32_t*)ptr[k++]; w.rcapT = (int32_t*)ptr[k++];
   w.deg_old = (int32_t*)ptr[k++]; w.deg_new = (int32_t*)ptr[k++];
   w.UST = (float*)ptr[k++]; w.VT = (float*)ptr[k++]; w.WCt = (float*)ptr[k++];
   w.RB = (float*)ptr[k++]; w.RC = (float*)ptr[k++]; w.M = (float*)ptr[k++];
@@ -332,8 +344,12 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
     e = build_adjacency(c, &c->in, row_ptr, col_idx, m, cfg->n, &tail, 1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&c->hdr->tail_in, &tail, sizeof(tail), cudaMemcpyHostToDevice, s);
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->push_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_caller, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
   if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
   if (e == cudaSuccess) e = launch_push(c, 1, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_push, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_all(c);
@@ -369,12 +385,18 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
   c->n = n_after;
   for (int lo = 0; lo < k; lo += kEdgesPerUpdate) {
     const int kk = (k - lo) < kEdgesPerUpdate ? (k - lo) : kEdgesPerUpdate;
+    // read-only part: net change, projection, residual factors, core SVD, transforms.
+    // It runs on the caller's stream while the previous push may still run on the
+    // push stream (both only read the adjacency).
     DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_prepare(c, src + lo, dst + lo, op + lo, kk, n_after, s), "prepare");
-    DAMF_STAGE(DAMF_STAGE_FIXUP, 1, launch_fixup(c, s), "fixup");
     DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
-    DAMF_STAGE(DAMF_STAGE_CHOL, 1, launch_chol(c, s), "chol");
+    DAMF_STAGE(DAMF_STAGE_CHOL, 2, launch_chol(c, s), "chol");
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
     DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 5, launch_transforms(c, s), "transforms");
+    // writes to the adjacency, Zb and r follow the push
+    DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_push, 0), "join push");
+    DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_edit(c, s), "edit");
+    DAMF_STAGE(DAMF_STAGE_FIXUP, 1, launch_fixup(c, s), "fixup");
     DAMF_STAGE(DAMF_STAGE_SCATTER, 1, launch_scatter(c, s), "scatter");
     c->launches += kLaunchesPerUpdate;
     if (c->cfg.refold_every > 0 && ++c->updates_since_fold >= c->cfg.refold_every) {
@@ -417,10 +439,27 @@ damf_status damf_ppr_refresh(damf_ctx* x, void* stream) {
   if (!x) return DAMF_ERR_INVALID;
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
-  cudaStream_t s = (cudaStream_t)stream;
+  DAMF_CUDA(cudaEventRecord(c->ev_caller, (cudaStream_t)stream), "record");
+  cudaStream_t s = c->push_stream;
+  DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_caller, 0), "push wait");
   DAMF_STAGE(DAMF_STAGE_PUSH, 1, launch_push(c, c->check_all_next, s), "push");
+  DAMF_CUDA(cudaEventRecord(c->ev_push, s), "record");
   c->launches += 1;
   c->check_all_next = 0;
+  return DAMF_OK;
+}
+
+damf_status damf_join(damf_ctx* x, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join");
+  return DAMF_OK;
+}
+
+damf_status damf_record_event(damf_ctx* x, void* event) {
+  if (!x || !event) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  DAMF_CUDA(cudaEventRecord((cudaEvent_t)event, c->push_stream), "record");
   return DAMF_OK;
 }
 
@@ -430,6 +469,7 @@ damf_status damf_get_embeddings(damf_ctx* x, const int32_t* rows, int32_t count,
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
   if (count < 0 || (!rows && count > c->n)) return fail(c, DAMF_ERR_INVALID, "count", cudaSuccess);
+  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
   DAMF_CUDA(launch_query(c, rows, count, X, Y, Z, sigma, (cudaStream_t)stream), "query");
   return DAMF_OK;
 }
@@ -470,6 +510,7 @@ damf_status damf_get_state(damf_ctx* x, float* Ub, float* Vb, float* Zb, float* 
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nd = (size_t)c->n * c->d * sizeof(float), dd = (size_t)c->d * c->d * sizeof(float);
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_push, 0), "join push");
   if (Ub) DAMF_CUDA(cudaMemcpyAsync(Ub, c->Ub, nd, k, s), "state");
   if (Vb) DAMF_CUDA(cudaMemcpyAsync(Vb, c->Vb, nd, k, s), "state");
   if (Zb) DAMF_CUDA(cudaMemcpyAsync(Zb, c->Zb, nd, k, s), "state");
@@ -552,6 +593,7 @@ damf_status damf_get_stats(damf_ctx* x, damf_stats* o) {
   o->last_rank = h.last_rank;
   o->last_status = h.status;
   o->launches = c->launches;
+  o->last_sweeps = h.last_sweeps;
   return DAMF_OK;
 }
 

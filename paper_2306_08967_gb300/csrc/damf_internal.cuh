@@ -21,7 +21,7 @@ constexpr int kEdgesPerUpdate = 48;       // events per update (undirected: 2 en
 constexpr int kMaxEntries = 2 * kEdgesPerUpdate;
 constexpr int kMaxD = 128;
 constexpr int kMaxM = kMaxD + kMaxR;      // 224: largest core
-constexpr int kPushChunk = 8;             // in-edges per push work item
+constexpr int kChainThreads = 512;        // one-CTA chain kernels: leave room beside a push
 constexpr long long kSpinLimit = 1ll << 26;  // iterations of a bounded wait (with nanosleep)
 
 // Grid barrier state for persistent cooperative kernels.
@@ -45,7 +45,7 @@ struct DevHeader {
   long long updates, edges_applied, entries_changed, pushes, push_edges, push_rounds, fixup_edges,
       touched_rows, folds;
   int last_rank;
-  int pad;
+  int last_sweeps;       // Jacobi sweeps of the most recent update
   // push control (parity-indexed, see ppr.cu)
   int cand_count[2];
   int front_count[2];
@@ -65,7 +65,14 @@ struct Workspace {
   int32_t* S;        // [kMaxR]
   int32_t* T;        // [kMaxR]
   float* N;          // [kMaxR x kMaxR] net change, rows S, cols T
-  int4* edits;       // [kMaxEntries] (u, v, delta, s_index)
+  int4* edits;       // [kMaxEntries] (u, v, delta, s_index), (u, v) order
+  int4* editsT;      // [kMaxEntries] (v, u, delta, -), (v, u) order (directed in-adjacency)
+  int32_t* Sfirst;   // [kMaxR + 1] edits of row S[q]: edits[Sfirst[q] .. Sfirst[q+1])
+  int32_t* Tfirst;   // [kMaxR + 1] editsT of row T[q]
+  long long* relocS; // [kMaxR] new start of a relocated out-row (-1: fits)
+  long long* relocT; // [kMaxR]
+  int32_t* rcapS;    // [kMaxR] its new capacity
+  int32_t* rcapT;
   int32_t* deg_old;  // [kMaxR] out-degree of S rows before/after
   int32_t* deg_new;
   float* UST;        // [kMaxR x d] rows U[S] = Ub[S] PU
@@ -116,6 +123,10 @@ struct Ctx {
   char errbuf[256];
   int sticky;            // host-side poisoned status
   int check_all_next;    // next push starts from every row (after a fold)
+  // the PPR push runs on its own stream so the next update's factor chain overlaps it
+  cudaStream_t push_stream;
+  cudaEvent_t ev_caller;  // caller-stream work a push must follow
+  cudaEvent_t ev_push;    // the most recent push
   long long launches;    // kernels this context has launched (host count)
   // per-stage timing (api.cu)
   int timing;
@@ -173,6 +184,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigne
 }
 
 // ---- launchers implemented in the .cu files ----
+cudaError_t launch_edit(Ctx* c, cudaStream_t s);
 cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
                             cudaStream_t s);
 cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,

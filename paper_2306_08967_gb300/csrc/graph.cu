@@ -54,7 +54,7 @@ __device__ __forceinline__ int grown_cap(int cap, int need) {
 // Edits the rows listed in rows[0..nrows) of adjacency a; entries (row, col, delta) of
 // row q are ent[first[q] .. first[q+1]).  One warp per row.  Relocation space was
 // reserved by the caller at reloc_base[q] (or -1 when the row fits).
-__device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* first, const int3* ent,
+__device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* first, const int4* ent,
                                 const long long* reloc_base, const int* reloc_cap, int* deg_new) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int q = warp; q < nrows; q += nw) {
@@ -72,7 +72,7 @@ __device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* fi
     }
     // deletions first, so the row never holds more than max(len, new len) entries
     for (int e = first[q]; e < first[q + 1]; ++e) {
-      const int3 x = ent[e];
+      const int4 x = ent[e];
       if (x.z >= 0) continue;
       const int pos = row_find(a, u, x.y);
       if (lane == 0 && pos >= 0) {
@@ -84,7 +84,7 @@ __device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* fi
     }
     if (lane == 0) {
       for (int e = first[q]; e < first[q + 1]; ++e) {
-        const int3 x = ent[e];
+        const int4 x = ent[e];
         if (x.z <= 0) continue;
         const int st = a.start[u], ln = a.len[u];
         a.col[st + ln] = x.y;
@@ -205,43 +205,47 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     nTrow = t;
   }
   __syncthreads();
-  // capacity check (before any write)
+  // capacity check (before any write): one thread per touched row, then a prefix sum
+  // of the relocation sizes (thread 0, shared memory only)
+  for (int q = tid; q < nS; q += blockDim.x) {
+    const int u = Srow[q];
+    int ins = 0, del = 0;
+    for (int e = Sfirst[q]; e < Sfirst[q + 1]; ++e) (ed[e].z > 0 ? ins : del)++;
+    const int nl = out.len[u] - del + ins;
+    rcapS[q] = nl > out.cap[u] ? grown_cap(out.cap[u], nl) : 0;
+  }
+  if (DIRECTED) {
+    for (int q = tid; q < nTrow; q += blockDim.x) {
+      const int v = Tcol[q];
+      int ins = 0, del = 0;
+      for (int e = Tfirst[q]; e < Tfirst[q + 1]; ++e) (edT[e].z > 0 ? ins : del)++;
+      const int nl = in.len[v] - del + ins;
+      rcapT[q] = nl > in.cap[v] ? grown_cap(in.cap[v], nl) : 0;
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
     long long need = 0;
+    const long long t0 = h->tail_out;
     for (int q = 0; q < nS; ++q) {
-      const int u = Srow[q];
-      int ins = 0, del = 0;
-      for (int e = Sfirst[q]; e < Sfirst[q + 1]; ++e) (ed[e].z > 0 ? ins : del)++;
-      const int nl = out.len[u] - del + ins;
-      relocS[q] = -1;
-      if (nl > out.cap[u]) {
-        rcapS[q] = grown_cap(out.cap[u], nl);
-        relocS[q] = h->tail_out + need;
-        need += rcapS[q];
-      }
+      relocS[q] = rcapS[q] ? t0 + need : -1;
+      need += rcapS[q];
     }
-    if (h->tail_out + need > out.m_cap) fail = 1;
+    if (t0 + need > out.m_cap) fail = 1;
+    long long needT = 0;
     if (DIRECTED) {
-      long long needT = 0;
+      const long long t1 = h->tail_in;
       for (int q = 0; q < nTrow; ++q) {
-        const int v = Tcol[q];
-        int ins = 0, del = 0;
-        for (int e = Tfirst[q]; e < Tfirst[q + 1]; ++e) (edT[e].z > 0 ? ins : del)++;
-        const int nl = in.len[v] - del + ins;
-        relocT[q] = -1;
-        if (nl > in.cap[v]) {
-          rcapT[q] = grown_cap(in.cap[v], nl);
-          relocT[q] = h->tail_in + needT;
-          needT += rcapT[q];
-        }
+        relocT[q] = rcapT[q] ? t1 + needT : -1;
+        needT += rcapT[q];
       }
-      if (h->tail_in + needT > in.m_cap) fail = 1;
-      if (!fail) h->tail_in += needT;
+      if (t1 + needT > in.m_cap) fail = 1;
     }
     if (fail) {
       set_status(h, DAMF_ERR_CAPACITY);
     } else {
-      h->tail_out += need;
+      h->tail_out = t0 + need;
+      if (DIRECTED) h->tail_in += needT;
     }
   }
   __syncthreads();
@@ -249,12 +253,23 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     if (tid == 0) h->nS = h->nT = h->nedit = 0;
     return;
   }
-  // write the sets, N and the degrees before the edit
+  // write the sets, N, the edit lists and the relocation plan; the adjacency itself is
+  // edited later by k_edit (a PPR push may still be reading it)
   for (int i = tid; i < nS; i += blockDim.x) {
     ws.S[i] = Srow[i];
     ws.deg_old[i] = out.len[Srow[i]];
+    ws.relocS[i] = relocS[i];
+    ws.rcapS[i] = rcapS[i];
   }
-  for (int i = tid; i < nT; i += blockDim.x) ws.T[i] = Tcol[i];
+  for (int i = tid; i <= nS; i += blockDim.x) ws.Sfirst[i] = Sfirst[i];
+  for (int i = tid; i < nT; i += blockDim.x) {
+    ws.T[i] = Tcol[i];
+    if (DIRECTED) {
+      ws.relocT[i] = relocT[i];
+      ws.rcapT[i] = rcapT[i];
+    }
+  }
+  for (int i = tid; i <= nT; i += blockDim.x) ws.Tfirst[i] = Tfirst[i];
   for (int i = tid; i < nS * nT; i += blockDim.x) ws.N[i] = 0.0f;
   __syncthreads();
   for (int e = tid; e < nedit; e += blockDim.x) {
@@ -265,33 +280,51 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     while (Tcol[b] != x.y) ++b;
     ws.N[a * nT + b] = (float)x.z;
     ws.edits[e] = make_int4(x.x, x.y, x.z, a);
+    if (DIRECTED) ws.editsT[e] = make_int4(edT[e].x, edT[e].y, edT[e].z, 0);
   }
-  __syncthreads();
-  apply_row_edits(out, Srow, nS, Sfirst, ed, relocS, rcapS, ws.deg_new);
-  if (DIRECTED) {
-    __syncthreads();
-    apply_row_edits(in, Tcol, nTrow, Tfirst, edT, relocT, rcapT, nullptr);
-  }
-  __syncthreads();
   if (tid == 0) {
     h->nS = nS;
     h->nT = nT;
     h->nedit = nedit;
-    if (nedit > 0) {
-      h->updates += 1;
-      h->entries_changed += nedit;
-      h->touched_rows += nS + nT;
-      h->last_rank = nS;
-    }
+  }
+}
+
+// Applies the planned adjacency edit of the current update (after any push that reads
+// the adjacency has finished), records the new out-degrees, queues the rows whose PPR
+// residual changes for the next push, and counts the update.
+template <int DIRECTED>
+__global__ void __launch_bounds__(512) k_edit(DevHeader* h, Adj out, Adj in, Workspace ws) {
+  if (h->status != 0) return;
+  const int nS = h->nS, nT = h->nT, nedit = h->nedit;
+  if (nedit == 0) return;
+  const int tid = threadIdx.x;
+  apply_row_edits(out, ws.S, nS, ws.Sfirst, ws.edits, ws.relocS, ws.rcapS, ws.deg_new);
+  if (DIRECTED) {
+    __syncthreads();
+    apply_row_edits(in, ws.T, nT, ws.Tfirst, ws.editsT, ws.relocT, ws.rcapT, nullptr);
+  }
+  if (tid == 0) {
+    h->updates += 1;
+    h->entries_changed += nedit;
+    h->touched_rows += nS + nT;
+    h->last_rank = nS;
   }
   // rows whose residual changes (signal delta and fix-up) are queued for the next push
   for (int i = tid; i < nS; i += blockDim.x) {
-    const int u = Srow[i];
+    const int u = ws.S[i];
     if (atomicExch(&ws.pstamp[u], h->epoch) != h->epoch) {
       const int p = atomicAdd(&h->pending, 1);
       ws.pend[p] = u;
     }
   }
+}
+
+cudaError_t launch_edit(Ctx* c, cudaStream_t s) {
+  if (c->cfg.directed)
+    k_edit<1><<<1, 512, 0, s>>>(c->hdr, c->out, c->in, c->ws);
+  else
+    k_edit<0><<<1, 512, 0, s>>>(c->hdr, c->out, c->out, c->ws);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int,

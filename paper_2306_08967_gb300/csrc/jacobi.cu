@@ -6,95 +6,212 @@
 // warp holds a column in m/32 registers per lane.  Each sweep visits every column pair
 // once in round-robin order (m/2 disjoint pairs per round, one warp per pair); a pair
 // is rotated when |a_p . a_q| > tol |a_p| |a_q|, which makes the two columns
-// orthogonal.  At convergence the columns are U Theta; the top-d by norm give E and
+// orthogonal.  A warp works on 4 pairs at once (8 lanes per pair, float4 accesses), which
+// shares the reduction and the rotation arithmetic of a pair across 4 pairs; the kernel
+// is bound by instruction issue.  Squared column norms are cached in shared memory and updated by each
+// rotation (|a_p'|^2 = |a_p|^2 - t g, |a_q'|^2 = |a_q|^2 + t g), so a pair costs one
+// warp reduction; they are recomputed exactly at the start of every sweep.
+// Only pairs with at least one column among the current top-d (by norm) are rotated:
+// when the top columns are mutually orthogonal and orthogonal to all others,
+// A^T A is block diagonal, so M^T M J_top = J_top Theta_top^2 and the top columns are
+// exactly the top-d singular vectors (given theta_d > every other column norm).  The
+// discarded block's internal structure, which holds the slowest-converging clustered
+// singular values, is never resolved; this cuts the sweep count roughly in half.  The
+// premise is checked at convergence (Gershgorin bound on the discarded block's Gram
+// against the smallest top norm^2); when the gap is too small to certify it the kernel
+// continues with sweeps over every pair.  At convergence the columns are U Theta; the top-d by norm give E and
 // Theta, and the right vectors follow as H = M^T E Theta^{-1} (update.cu, k_hmat).
 #include "damf_internal.cuh"
 
 namespace damf {
 
-constexpr int kMaxEP = kMaxM / 32;  // column elements per lane (7)
+constexpr int kMaxEP = kMaxM / 32;  // column elements per lane of a warp (7)
+constexpr int kMaxC = kMaxM / 32;   // float4 chunks per lane of an 8-lane group (7)
+constexpr int kJacobiThreads = 256;
+// A pair is rotated while |a_p . a_q| > tol |a_p| |a_q|; FP32 dot products of length <= 224
+// carry relative noise of a few 1e-7, so the tolerance sits a little above that floor.
+constexpr float kJacobiTol = 1e-6f;
+// sweeps restricted to pairs touching the top-d set before falling back to every pair
+constexpr int kTopOnlySweeps = 6;
 
+// Circle-method pairing: in round t (0 <= t < mp-1) pair k is (mp-1, t) for k = 0 and
+// ((t+k) mod (mp-1), (t-k) mod (mp-1)) otherwise; every column appears once per round.
+// Both arguments of the modulo lie in [0, 2(mp-1)), so one conditional subtraction does.
 __device__ __forceinline__ void round_robin_pair(int mp, int round, int k, int& p, int& q) {
   const int L = mp - 1;
   if (k == 0) {
     p = L;
     q = round;
   } else {
-    p = (round + k) % L;
-    q = (round - k + L) % L;
+    p = round + k;
+    p -= p >= L ? L : 0;
+    q = round - k + L;
+    q -= q >= L ? L : 0;
   }
 }
 
 template <int D>
-__global__ void __launch_bounds__(1024, 1) k_jacobi(DevHeader* h, const float* __restrict__ Min, int m_host, int use_hdr,
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const float* __restrict__ Min, int m_host, int use_hdr,
                                                     float* E, float* theta, float tol, int max_sweeps) {
   extern __shared__ float A[];
-  __shared__ float nrm[kMaxM];
+  __shared__ float nrm[kMaxM];   // squared column norms, refreshed every sweep
+  __shared__ unsigned char top[kMaxM];
   __shared__ int rot_flag;
   if (h->status != 0) return;
   const int m = use_hdr ? D + h->nS : m_host;
   if (use_hdr && h->nS == 0) return;
   const int mp = (m + 31) & ~31;
   const int ep = mp / 32;
+  const int nc = mp / 32;   // float4 chunks per lane of an 8-lane group, per column
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int grp = lane >> 3, gl = lane & 7;
   for (int o = tid; o < mp * mp; o += blockDim.x) {
     const int j = o / mp, i = o % mp;
     A[o] = (i < m && j < m) ? Min[(size_t)j * m + i] : 0.0f;
   }
   __syncthreads();
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  const float tol2 = tol * tol;
+  __shared__ int full_mode;    // 0: only pairs touching the top-d set; 1: every pair
+  __shared__ float gersh, topmin, bsum, bmax;
+  if (tid == 0) full_mode = 0;
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int j = warp; j < mp; j += nw) {
+      float s2 = 0.f;
+      for (int e = 0; e < ep; ++e) {
+        const float v = A[j * mp + lane + 32 * e];
+        s2 = fmaf(v, v, s2);
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
     if (tid == 0) rot_flag = 0;
     __syncthreads();
+    // the D columns of largest norm are the current "top" set
+    for (int j = warp; j < mp; j += nw) {
+      const float nj = nrm[j];
+      int rk = 0;
+      for (int i = lane; i < mp; i += 32) {
+        const float ni = nrm[i];
+        rk += (ni > nj) || (ni == nj && i < j);
+      }
+      for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
+      if (lane == 0) top[j] = rk < D ? 1 : 0;
+    }
+    __syncthreads();
+    const bool full = full_mode != 0;
     for (int round = 0; round < mp - 1; ++round) {
-      for (int k = warp; k < mp / 2; k += nw) {
-        int p, q;
-        round_robin_pair(mp, round, k, p, q);
-        float* ap = A + p * mp;
-        float* aq = A + q * mp;
-        float x[kMaxEP], y[kMaxEP];
-        float aa = 0.f, bb = 0.f, gg = 0.f;
+      // 4 pairs per warp, 8 lanes per pair; lane gl of a group holds rows 4 (gl + 8 c) .. +3
+      for (int kb = warp * 4; kb < mp / 2; kb += nw * 4) {
+        const int k = kb + grp;
+        int p = 0, q = 0;
+        if (k < mp / 2) round_robin_pair(mp, round, k, p, q);
+        const float aa = nrm[p], bb = nrm[q];
+        const bool act = k < mp / 2 && (full || (top[p] | top[q])) && aa > 1e-30f && bb > 1e-30f;
+        float4* ap = reinterpret_cast<float4*>(A + p * mp);
+        float4* aq = reinterpret_cast<float4*>(A + q * mp);
+        float4 x[kMaxC], y[kMaxC];
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;   // four short dependent chains
 #pragma unroll
-        for (int e = 0; e < kMaxEP; ++e) {
-          if (e < ep) {
-            x[e] = ap[lane + 32 * e];
-            y[e] = aq[lane + 32 * e];
-            aa = fmaf(x[e], x[e], aa);
-            bb = fmaf(y[e], y[e], bb);
-            gg = fmaf(x[e], y[e], gg);
+        for (int c = 0; c < kMaxC; ++c) {
+          if (c < nc && act) {
+            x[c] = ap[gl + 8 * c];
+            y[c] = aq[gl + 8 * c];
+            g0 = fmaf(x[c].x, y[c].x, g0);
+            g1 = fmaf(x[c].y, y[c].y, g1);
+            g2 = fmaf(x[c].z, y[c].z, g2);
+            g3 = fmaf(x[c].w, y[c].w, g3);
           }
         }
-        aa = warp_sum(aa);
-        bb = warp_sum(bb);
-        gg = warp_sum(gg);
-        if (aa > 1e-30f && bb > 1e-30f && fabsf(gg) > tol * sqrtf(aa) * sqrtf(bb)) {
-          const float zeta = (bb - aa) / (2.0f * gg);
-          const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + hypotf(1.0f, zeta));
-          const float c = rsqrtf(1.0f + t * t);
-          const float s = c * t;
+        float gg = (g0 + g1) + (g2 + g3);
+        gg += __shfl_xor_sync(0xffffffffu, gg, 1);
+        gg += __shfl_xor_sync(0xffffffffu, gg, 2);
+        gg += __shfl_xor_sync(0xffffffffu, gg, 4);
+        if (act && gg * gg > tol2 * aa * bb) {
+          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g): the smaller
+          // root of t^2 + 2 zeta t - 1 = 0, so the rotated columns are orthogonal
+          const float zeta = __fdividef(bb - aa, 2.0f * gg);
+          const float az = fabsf(zeta);
+          const float ta = az < 1e15f ? __frcp_rn(az + __fsqrt_rn(fmaf(az, az, 1.0f))) : __fdividef(0.5f, az);
+          const float t = copysignf(ta, zeta);
+          const float cs = rsqrtf(fmaf(t, t, 1.0f));
+          const float sn = cs * t;
 #pragma unroll
-          for (int e = 0; e < kMaxEP; ++e) {
-            if (e < ep) {
-              ap[lane + 32 * e] = c * x[e] - s * y[e];
-              aq[lane + 32 * e] = s * x[e] + c * y[e];
+          for (int c = 0; c < kMaxC; ++c) {
+            if (c < nc) {
+              ap[gl + 8 * c] = make_float4(cs * x[c].x - sn * y[c].x, cs * x[c].y - sn * y[c].y,
+                                           cs * x[c].z - sn * y[c].z, cs * x[c].w - sn * y[c].w);
+              aq[gl + 8 * c] = make_float4(sn * x[c].x + cs * y[c].x, sn * x[c].y + cs * y[c].y,
+                                           sn * x[c].z + cs * y[c].z, sn * x[c].w + cs * y[c].w);
             }
           }
-          if (lane == 0) rot_flag = 1;
+          if (gl == 0) {
+            nrm[p] = fmaxf(aa - t * gg, 0.0f);
+            nrm[q] = bb + t * gg;
+            rot_flag = 1;
+          }
         }
       }
       __syncthreads();
     }
-    if (rot_flag == 0) break;
+    if (!full && sweep + 1 >= kTopOnlySweeps && rot_flag != 0) {
+      // the top set keeps changing (singular values straddling the cut are too close):
+      // resolve every pair from here on
+      if (tid == 0) full_mode = 1;
+    }
+    if (rot_flag == 0) {
+      if (full) break;
+      // top-only convergence is exact when every eigenvalue of the discarded block's
+      // Gram is below the smallest top norm^2; Gershgorin row sums bound those
+      // eigenvalues.  Otherwise fall back to rotating every pair.
+      if (tid == 0) {
+        gersh = 0.f;
+        topmin = 3.0e38f;
+        bsum = 0.f;
+        bmax = 0.f;
+      }
+      __syncthreads();
+      // cheap bound first: row sums of |G_bot| <= max_j |a_j| * sum_i |a_i| (Cauchy-Schwarz)
+      for (int j = tid; j < m; j += blockDim.x) {
+        if (top[j]) {
+          atomicMin((int*)&topmin, __float_as_int(nrm[j]));
+        } else {
+          const float nj = sqrtf(nrm[j]);
+          atomicAdd(&bsum, nj);
+          atomicMax((int*)&bmax, __float_as_int(nj));
+        }
+      }
+      __syncthreads();
+      if (bmax * bsum < 0.98f * topmin) break;
+      // exact Gershgorin row sums of the discarded block's Gram
+      for (int j = warp; j < m; j += nw) {
+        if (top[j]) continue;
+        float row = 0.f;
+        for (int i = 0; i < m; ++i) {
+          if (top[i]) continue;
+          float dv = 0.f;
+          for (int e = 0; e < ep; ++e) dv = fmaf(A[j * mp + lane + 32 * e], A[i * mp + lane + 32 * e], dv);
+          row += fabsf(warp_sum(dv));
+        }
+        if (lane == 0) atomicMax((int*)&gersh, __float_as_int(row));
+      }
+      __syncthreads();
+      if (gersh < 0.98f * topmin) break;
+      if (tid == 0) full_mode = 1;
+    }
     __syncthreads();
   }
-  // column norms, then order by decreasing norm (ties by index)
+  if (tid == 0 && use_hdr) h->last_sweeps = sweep + 1;
+  // exact column norms, then order by decreasing norm (ties by index)
   for (int j = warp; j < mp; j += nw) {
-    float s = 0.f;
+    float s2 = 0.f;
     for (int e = 0; e < ep; ++e) {
       const float v = A[j * mp + lane + 32 * e];
-      s = fmaf(v, v, s);
+      s2 = fmaf(v, v, s2);
     }
-    s = warp_sum(s);
-    if (lane == 0) nrm[j] = (j < m) ? sqrtf(s) : -1.0f;
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[j] = (j < m) ? sqrtf(s2) : -1.0f;
   }
   __syncthreads();
   for (int j = warp; j < m; j += nw) {
@@ -118,7 +235,7 @@ template <int D>
 static cudaError_t core_impl(Ctx* c, cudaStream_t s) {
   const size_t sm = (size_t)kMaxM * kMaxM * sizeof(float);
   cudaFuncSetAttribute(k_jacobi<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_jacobi<D><<<1, 1024, sm, s>>>(c->hdr, c->ws.M, 0, 1, c->ws.E, c->ws.theta, 2e-6f, 30);
+  k_jacobi<D><<<1, kJacobiThreads, sm, s>>>(c->hdr, c->ws.M, 0, 1, c->ws.E, c->ws.theta, kJacobiTol, 20);
   return cudaGetLastError();
 }
 
@@ -155,7 +272,7 @@ static cudaError_t dense_impl(const float* Min, int m, float* E, float* H, float
                               cudaStream_t s) {
   const size_t sm = (size_t)kMaxM * kMaxM * sizeof(float);
   cudaFuncSetAttribute(k_jacobi<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_jacobi<D><<<1, 1024, sm, s>>>(h, Min, m, 0, E, theta, 2e-6f, 40);
+  k_jacobi<D><<<1, kJacobiThreads, sm, s>>>(h, Min, m, 0, E, theta, kJacobiTol, 30);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_hmat_dense<D><<<m, 128, 0, s>>>(h, Min, m, E, theta, H);

@@ -9,22 +9,34 @@
 //
 // One persistent cooperative launch runs all rounds; two bounded grid barriers per round:
 //   phase A: candidates -> frontier rows; rho[pos] = r[u], r[u] = 0, Zb[u] += alpha rho,
-//            and the in-edges of u cut into work items of kPushChunk edges;
-//   phase B: each work item adds coef * rho to r[w] with float4 atomics (L2); a row whose
-//            new value crosses eps is queued once per round (stamp) as a candidate.
+//            and the in-edges of u cut into work items (one in-edge per lane of a row group);
+//   phase B: each work item adds coef * rho to r[w] with float4 atomics (L2), all of an
+//            item's atomics in flight at once; a row whose new value crosses eps is
+//            queued once per round (stamp) as a candidate.
 // Counters are indexed by round parity so each is reset by one block between its uses.
 #include "damf_internal.cuh"
 
 namespace damf {
 
+constexpr int kPushBlocksPerSM = 2;
+
 __device__ __forceinline__ float4 f4_ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+
+// in-edges per work item: one per lane of a row group, at most 8
+template <int D>
+struct PushShape {
+  static constexpr int LPR = D / 4;                 // lanes per row (float4 each)
+  static constexpr int RPW = 32 / LPR;              // row groups per warp
+  static constexpr int CH = LPR < 8 ? LPR : 8;      // in-edges per work item
+};
 
 template <int D>
 __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
                                               float* Zb, float* r, int n, float alpha, float eps, int max_rounds,
                                               int check_all) {
-  constexpr int LPR = D / 4;      // lanes per row
-  constexpr int RPW = 32 / LPR;   // rows per warp
+  constexpr int LPR = PushShape<D>::LPR;
+  constexpr int RPW = PushShape<D>::RPW;
+  constexpr int CH = PushShape<D>::CH;
   const unsigned nblocks = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR, q = lane % LPR;
@@ -73,17 +85,17 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
         z.z = fmaf(alpha, v.z, z.z);
         z.w = fmaf(alpha, v.w, z.w);
         __stcg(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q, z);
+        const int deg = in.len[u];
+        const int nch = (deg + CH - 1) / CH;
+        int wpos = 0;
         if (q == 0) {
           __stcg(ws.front + pos, u);
-          const int deg = in.len[u];
-          const int nch = (deg + kPushChunk - 1) / kPushChunk;
-          if (nch > 0) {
-            const int wpos = atomicAdd(&h->work_count[P], nch);
-            for (int c2 = 0; c2 < nch; ++c2) __stcg(&ws.work[wpos + c2], make_int2(pos, c2));
-          }
+          if (nch > 0) wpos = atomicAdd(&h->work_count[P], nch);
           my_pushes += 1;
           my_edges += deg;
         }
+        wpos = __shfl_sync(sub_mask, wpos, sub * LPR);
+        for (int c2 = q; c2 < nch; c2 += LPR) __stcg(&ws.work[wpos + c2], make_int2(pos, c2));
       }
     }
     if (!grid_barrier(&h->bar, h, nblocks)) return;
@@ -100,28 +112,41 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
       const int u = valid ? __ldcg(ws.front + wi.x) : 0;
       const int st = valid ? in.start[u] : 0;
       const int deg = valid ? in.len[u] : 0;
-      const int e0 = wi.y * kPushChunk;
-      const int e1 = valid ? min(e0 + kPushChunk, deg) : e0;
+      const int e0 = wi.y * CH;
+      const int ne = valid ? min(CH, deg - e0) : 0;
+      // lane q < ne of the row group owns in-edge e0 + q
+      int w_own = 0;
+      float c_own = 0.f;
+      if (q < ne) {
+        w_own = __ldg(in.col + st + e0 + q);
+        c_own = beta / (float)__ldg(outdeg + w_own);
+      }
       float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
-      for (int e = e0; e < kPushChunk + e0; ++e) {
-        const bool act = e < e1;
-        int w = 0;
-        bool crossed = false;
-        if (act) {
-          w = __ldg(in.col + st + e);
-          const float coef = beta / (float)__ldg(outdeg + w);
+      // issue every atomic of the item before looking at any result
+      float4 nv[CH];
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        const int w = __shfl_sync(0xffffffffu, w_own, sub * LPR + e);
+        const float coef = __shfl_sync(0xffffffffu, c_own, sub * LPR + e);
+        nv[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < ne) {
           const float4 add = make_float4(coef * rv.x, coef * rv.y, coef * rv.z, coef * rv.w);
           const float4 old = atomicAdd(reinterpret_cast<float4*>(r + (size_t)w * D) + q, add);
-          const float nx = old.x + add.x, ny = old.y + add.y, nz = old.z + add.z, nw2 = old.w + add.w;
-          crossed = fmaxf(fmaxf(fabsf(nx), fabsf(ny)), fmaxf(fabsf(nz), fabsf(nw2))) > eps;
+          nv[e] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
         }
-        const unsigned cb = __ballot_sync(0xffffffffu, crossed) & sub_mask;
-        if (act && q == 0 && cb) {
-          if (atomicExch(&ws.stamp[w], tag) != tag) {
-            const int p = atomicAdd(&h->cand_count[P ^ 1], 1);
-            __stcg(ws.cand[P ^ 1] + p, w);
-          }
+      }
+      unsigned crossed_bits = 0;
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        const bool cr = fmaxf(fmaxf(fabsf(nv[e].x), fabsf(nv[e].y)), fmaxf(fabsf(nv[e].z), fabsf(nv[e].w))) > eps;
+        if (__ballot_sync(0xffffffffu, cr) & sub_mask) crossed_bits |= 1u << e;
+      }
+      // lane q handles the stamp of its own edge
+      if (q < ne && ((crossed_bits >> q) & 1u)) {
+        if (atomicExch(&ws.stamp[w_own], tag) != tag) {
+          const int p = atomicAdd(&h->cand_count[P ^ 1], 1);
+          __stcg(ws.cand[P ^ 1] + p, w_own);
         }
       }
     }
@@ -147,10 +172,14 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
 template <int D>
 static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   if (c->push_blocks == 0) {
+    // two CTAs per SM: leaves registers, threads and shared memory on every SM for the
+    // one-CTA kernels of the next update's factor chain, which overlap the push
+    cudaFuncSetAttribute(k_push<D>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D>, 256, 0);
+    if (per_sm > kPushBlocksPerSM) per_sm = kPushBlocksPerSM;
     c->push_blocks = sms * (per_sm < 1 ? 1 : per_sm);
   }
   cudaError_t e = cudaMemsetAsync(&c->hdr->cand_count[0], 0, 6 * sizeof(int), s);

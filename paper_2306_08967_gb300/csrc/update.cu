@@ -57,14 +57,41 @@ __global__ void __launch_bounds__(256) k_gather(DevHeader* h, Workspace ws, cons
   }
 }
 
-// ---- a3: W_C^T = N V[T], residual Grams, semi-definite Cholesky (one CTA) ----
+// ---- a2 (second half): W_C^T = N V[T]  (16 rows per CTA) ----
 template <int D>
-__global__ void __launch_bounds__(1024) k_chol(DevHeader* h, Workspace ws) {
+__global__ void __launch_bounds__(256) k_wct(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* Vs = smem;                 // nT x D
+  float* Ns = smem + kMaxR * D;     // 16 x nT
+  if (h->status != 0) return;
+  const int nS = h->nS, nT = h->nT;
+  const int r0 = blockIdx.x * 16;
+  if (r0 >= nS) return;
+  for (int i = threadIdx.x; i < nT * D / 4; i += blockDim.x)
+    reinterpret_cast<float4*>(Vs)[i] = reinterpret_cast<const float4*>(ws.VT)[i];
+  for (int i = threadIdx.x; i < 16 * nT; i += blockDim.x) {
+    const int rr = i / nT, b = i % nT;
+    Ns[i] = (r0 + rr < nS) ? ws.N[(r0 + rr) * nT + b] : 0.0f;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 16 * D; o += blockDim.x) {
+    const int rr = o / D, j = o % D;
+    if (r0 + rr >= nS) continue;
+    float s = 0.f;
+    for (int b = 0; b < nT; ++b) s = fmaf(Ns[rr * nT + b], Vs[b * D + j], s);
+    ws.WCt[(r0 + rr) * D + j] = s;
+  }
+}
+
+// ---- a3: residual Grams and semi-definite Cholesky (one CTA) ----
+template <int D>
+__global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace ws) {
   extern __shared__ float smem[];
   float* GB = smem;                      // kMaxR x kMaxR
   float* GC = GB + kMaxR * kMaxR;
   float* US = GC + kMaxR * kMaxR;        // nS x D
   float* WC = US + kMaxR * D;            // nS x D
+  float* Ns = WC + kMaxR * D;            // nS x nT
   __shared__ float pivB, pivC;
   __shared__ int keptB, keptC;
   __shared__ float scaleB, scaleC;
@@ -72,20 +99,17 @@ __global__ void __launch_bounds__(1024) k_chol(DevHeader* h, Workspace ws) {
   const int nS = h->nS, nT = h->nT;
   if (nS == 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < nS * D; i += nt) US[i] = ws.UST[i];
-  for (int i = tid; i < nS * D; i += nt) {
-    const int a = i / D, j = i % D;
-    float s = 0.f;
-    for (int b = 0; b < nT; ++b) s = fmaf(ws.N[a * nT + b], ws.VT[b * D + j], s);
-    WC[i] = s;
-    ws.WCt[i] = s;
+  for (int i = tid; i < nS * D / 4; i += nt) {
+    reinterpret_cast<float4*>(US)[i] = reinterpret_cast<const float4*>(ws.UST)[i];
+    reinterpret_cast<float4*>(WC)[i] = reinterpret_cast<const float4*>(ws.WCt)[i];
   }
+  for (int i = tid; i < nS * nT; i += nt) Ns[i] = ws.N[i];
   __syncthreads();
   for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
     if (b < a) continue;
     float gb = (a == b) ? 1.0f : 0.0f, gc = 0.f;
-    for (int t = 0; t < nT; ++t) gc = fmaf(ws.N[a * nT + t], ws.N[b * nT + t], gc);
+    for (int t = 0; t < nT; ++t) gc = fmaf(Ns[a * nT + t], Ns[b * nT + t], gc);
     float sb = 0.f, sc = 0.f;
 #pragma unroll 4
     for (int k = 0; k < D; ++k) {
@@ -197,10 +221,11 @@ __global__ void __launch_bounds__(128) k_hmat(DevHeader* h, Workspace ws) {
 
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
 template <int D>
-__global__ void __launch_bounds__(1024) k_trans(DevHeader* h, Workspace ws) {
+__global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace ws) {
   extern __shared__ float smem[];
   float* R = smem;                    // kMaxR x kMaxR
   float* Y = R + kMaxR * kMaxR;       // nS x D
+  float* Wts = Y + kMaxR * D;         // nS x D
   if (h->status != 0) return;
   const int nS = h->nS;
   if (nS == 0) return;
@@ -215,20 +240,26 @@ __global__ void __launch_bounds__(1024) k_trans(DevHeader* h, Workspace ws) {
     const int a = i / nS, b = i % nS;
     R[a * kMaxR + b] = Rg[a * kMaxR + b];
   }
-  for (int i = tid; i < nS * D; i += blockDim.x) Y[i] = Eg[D * D + i];
+  for (int i = tid; i < nS * D; i += blockDim.x) {
+    Y[i] = Eg[D * D + i];
+    Wts[i] = Wt[i];
+  }
   __syncthreads();
   // back substitution, 8 threads per column
-  const int col = tid >> 3, sub = tid & 7;
+  const int sub = tid & 7;
   for (int j = nS - 1; j >= 0; --j) {
-    float s = 0.f;
-    if (col < D)
-      for (int l = j + 1 + sub; l < nS; l += 8) s = fmaf(R[j * kMaxR + l], Y[l * D + col], s);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    if (col < D && sub == 0) {
-      const float p = R[j * kMaxR + j];
-      Y[j * D + col] = p > 0.f ? (Y[j * D + col] - s) / p : 0.0f;
+    for (int col0 = 0; col0 < D; col0 += blockDim.x >> 3) {
+      const int col = col0 + (tid >> 3);
+      float s = 0.f;
+      if (col < D)
+        for (int l = j + 1 + sub; l < nS; l += 8) s = fmaf(R[j * kMaxR + l], Y[l * D + col], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (col < D && sub == 0) {
+        const float p = R[j * kMaxR + j];
+        Y[j * D + col] = p > 0.f ? (Y[j * D + col] - s) / p : 0.0f;
+      }
     }
     __syncthreads();
   }
@@ -236,14 +267,14 @@ __global__ void __launch_bounds__(1024) k_trans(DevHeader* h, Workspace ws) {
   for (int o = tid; o < D * D; o += blockDim.x) {
     const int i = o / D, k = o % D;
     float s = Eg[i * D + k];
-    for (int a = 0; a < nS; ++a) s = fmaf(-Wt[a * D + i], Y[a * D + k], s);
+    for (int a = 0; a < nS; ++a) s = fmaf(-Wts[a * D + i], Y[a * D + k], s);
     K[o] = s;
   }
 }
 
 // ---- Gauss-Jordan inverse with partial pivoting (block 0: K_U, block 1: K_V) ----
 template <int D>
-__global__ void __launch_bounds__(1024) k_inverse(DevHeader* h, Workspace ws) {
+__global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspace ws) {
   extern __shared__ float smem[];
   float* Aug = smem;   // D x 2D
   __shared__ int piv_row;
@@ -291,10 +322,14 @@ __global__ void __launch_bounds__(1024) k_inverse(DevHeader* h, Workspace ws) {
     __syncthreads();
     for (int i = tid; i < D; i += nt) colv[i] = Aug[i * 2 * D + p];
     __syncthreads();
-    for (int o = tid; o < D * 2 * D; o += nt) {
-      const int i = o / (2 * D), j = o % (2 * D);
+    // columns < p of the left half are already unit vectors, so the live window is
+    // [p, 2D) (with row pivoting the right half's live columns are not contiguous);
+    // one warp per row, lanes across columns
+    for (int i = tid >> 5; i < D; i += nt >> 5) {
       if (i == p) continue;
-      Aug[o] = fmaf(-colv[i], Aug[p * 2 * D + j], Aug[o]);
+      const float f = colv[i];
+      for (int j = p + (tid & 31); j < 2 * D; j += 32)
+        Aug[i * 2 * D + j] = fmaf(-f, Aug[p * 2 * D + j], Aug[i * 2 * D + j]);
     }
     __syncthreads();
   }
@@ -427,9 +462,14 @@ static cudaError_t gather_impl(Ctx* c, cudaStream_t s) {
 
 template <int D>
 static cudaError_t chol_impl(Ctx* c, cudaStream_t s) {
-  const size_t sm = (size_t)(2 * kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
+  const size_t smw = (size_t)(kMaxR * D + 16 * kMaxR) * sizeof(float);
+  cudaFuncSetAttribute(k_wct<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+  k_wct<D><<<kMaxR / 16, 256, smw, s>>>(c->hdr, c->ws);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t sm = (size_t)(3 * kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_chol<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_chol<D><<<1, 1024, sm, s>>>(c->hdr, c->ws);
+  k_chol<D><<<1, kChainThreads, sm, s>>>(c->hdr, c->ws);
   return cudaGetLastError();
 }
 
@@ -438,13 +478,13 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
   cudaError_t e;
   k_hmat<D><<<kMaxM, 128, 0, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t sm = (size_t)(kMaxR * kMaxR + kMaxR * D) * sizeof(float);
+  const size_t sm = (size_t)(kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_trans<D><<<2, 1024, sm, s>>>(c->hdr, c->ws);
+  k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smi = (size_t)(D * 2 * D) * sizeof(float);
   cudaFuncSetAttribute(k_inverse<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
-  k_inverse<D><<<2, 1024, smi, s>>>(c->hdr, c->ws);
+  k_inverse<D><<<2, kChainThreads, smi, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   constexpr int TS = D < 32 ? D : 32;
   constexpr int NT = D / TS;
