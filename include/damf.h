@@ -172,6 +172,24 @@ damf_status damf_export_adjacency(damf_ctx* ctx, int32_t outgoing, int64_t* row_
  */
 damf_status damf_get_last_touched(damf_ctx* ctx, int32_t* S, int32_t* nS, int32_t* T, int32_t* nT);
 
+/*
+ * Step 2 of an update on its own (Sec. 4.5 "Rediagonalization", Eq. "svd_small_edge"):
+ * the top-d SVD  E Theta H^T  of the (d + r) x (d + r) core
+ *     M = [[diag(sigma), 0], [0, 0]] + L R^T,
+ * computed by the kernels of the update path (one-CTA one-sided Jacobi).  No context.
+ *   sigma (device) float32[d]; L, R (device) float32[(d+r) x r] row-major (L = [W_B; R_B],
+ *   R = [W_C; R_C] in the paper's notation); d in {16, 32, 64, 128}, 1 <= r <= 96.
+ *   E, H (device) float32[(d+r) x d] row-major: column k is the k-th left / right
+ *   singular vector (non-increasing singular values); theta (device) float32[d].
+ *   workspace (device): at least damf_core_svd_workspace_size(d, r) bytes, 256-byte
+ *   aligned, owned by the caller; it holds a status word and a copy of M.
+ * DAMF_ERR_INVALID for bad sizes or NULL pointers, DAMF_ERR_CAPACITY for a short
+ * workspace.  Asynchronous on `stream`.
+ */
+size_t damf_core_svd_workspace_size(int32_t d, int32_t r);
+damf_status damf_core_svd(const float* sigma, const float* L, const float* R, int32_t d, int32_t r, float* E,
+                          float* H, float* theta, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Current node count as known to the host (initial n plus all node arrivals). */
 int32_t damf_num_nodes(const damf_ctx* ctx);
 

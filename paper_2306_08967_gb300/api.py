@@ -53,6 +53,27 @@ def bytes_required(cfg: Config) -> int:
     return int(_lib.load().damf_bytes_required(ctypes.byref(cfg)))
 
 
+def core_svd(sigma, L, R, stream=None):
+    """Top-d SVD of diag(sigma, 0) + L R^T through damf_core_svd (Step 2 of an update).
+    Returns (E, H, theta) CUDA tensors."""
+    lib = _lib.load()
+    sigma, L, R = _dev(sigma, torch.float32), _dev(L, torch.float32), _dev(R, torch.float32)
+    d, r = int(sigma.numel()), int(L.shape[1])
+    m = d + r
+    E = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    H = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    th = torch.empty(d, dtype=torch.float32, device="cuda")
+    nbytes = int(lib.damf_core_svd_workspace_size(d, r))
+    if nbytes == 0:
+        raise DamfError(1, "core_svd sizes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = lib.damf_core_svd(p(sigma), p(L), p(R), d, r, p(E), p(H), p(th), p(ws), nbytes, _stream_ptr(stream))
+    if st != 0:
+        raise DamfError(st, "core_svd")
+    return E, H, th
+
+
 class DamfGraph:
     """One graph's DAMF state on the current CUDA device (a damf_ctx)."""
 

@@ -210,3 +210,27 @@ def test_edge_cases():
             break
     assert status == 2
     g.close()
+
+
+@pytest.mark.parametrize("d,r", [(16, 5), (64, 40), (128, 96)])
+def test_core_svd_against_numpy(d, r):
+    # Step 2 alone: the top-d SVD of diag(sigma, 0) + L R^T for random cores shaped like
+    # the update's (W blocks small, R blocks O(1))
+    from paper_2306_08967_gb300 import core_svd
+    rng = np.random.default_rng(d + r)
+    sigma = np.sort(rng.uniform(2.0, 40.0, d))[::-1]
+    L = np.vstack([0.05 * rng.standard_normal((d, r)), np.triu(rng.standard_normal((r, r))) + np.eye(r)])
+    R = np.vstack([0.05 * rng.standard_normal((d, r)), np.triu(rng.standard_normal((r, r))) + np.eye(r)])
+    M = np.zeros((d + r, d + r))
+    M[:d, :d] = np.diag(sigma)
+    M += L @ R.T
+    U, s, Vt = np.linalg.svd(M)
+    E, H, th = core_svd(sigma.astype(np.float32), L.astype(np.float32), R.astype(np.float32))
+    E, H, th = E.double().cpu().numpy(), H.double().cpu().numpy(), th.double().cpu().numpy()
+    np.testing.assert_allclose(th, s[:d], rtol=1e-4, atol=1e-5 * s[0])
+    top = (U[:, :d] * s[:d]) @ Vt[:d]
+    assert rel_fro((E * th) @ H.T, top) < 1e-4
+    # E comes from orthogonalised columns (Jacobi tolerance 1e-6); H = M^T E Theta^{-1}
+    # inherits FP32 rounding amplified by sigma_1 / sigma_d (20 here) and sqrt(d + r)
+    assert np.abs(E.T @ E - np.eye(d)).max() < 2e-5
+    assert np.abs(H.T @ H - np.eye(d)).max() < 5e-4
