@@ -190,6 +190,27 @@ size_t damf_core_svd_workspace_size(int32_t d, int32_t r);
 damf_status damf_core_svd(const float* sigma, const float* L, const float* R, int32_t d, int32_t r, float* E,
                           float* H, float* theta, void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * damf_core_svd without a workspace, for callers that cannot allocate device memory:
+ * for example an engine plugin that receives only input and output pointers from a host
+ * framework whose allocator owns all device memory, or code on a latency-critical path
+ * that must not call cudaMalloc (it can synchronise the device).  The paper has no
+ * counterpart; this is a deployment variant of Step 2.
+ *   Arguments and results are those of damf_core_svd.  The caller still provides and
+ *   owns every input and output.  Nothing is allocated: the scratch (a status word and
+ *   the assembled core) is one static device array of 200,960 bytes compiled into the
+ *   library, which every GPU that loads the library holds until the process exits.
+ *   Limit: d + r <= 224 (d in {16, 32, 64, 128}, 1 <= r <= 96); a larger r returns
+ *   DAMF_ERR_CAPACITY, bad d or NULL pointers DAMF_ERR_INVALID.
+ *   The first call on each device looks up the array's device address (with that device
+ *   current); make that first call before any stream capture.
+ *   All calls on a device share the one array and each call overwrites it (the status
+ *   word is cleared at the start of every call): calls that overlap on the GPU (other
+ *   streams or threads) race and give undefined results; serialise them.
+ */
+damf_status damf_core_svd_noalloc(const float* sigma, const float* L, const float* R, int32_t d, int32_t r,
+                                  float* E, float* H, float* theta, void* stream);
+
 /* Current node count as known to the host (initial n plus all node arrivals). */
 int32_t damf_num_nodes(const damf_ctx* ctx);
 

@@ -1,0 +1,62 @@
+// damf_core_svd_noalloc: the core SVD of damf_core_svd for callers that cannot allocate
+// device memory.
+//
+// Some callers cannot call cudaMalloc or hand us a workspace: for example an engine
+// plugin that receives only its input and output pointers from a host framework whose
+// allocator owns all device memory, or code on a latency-critical path where cudaMalloc
+// (which may synchronise the device) is not allowed.  This entry point keeps its scratch
+// (a status word and the assembled core M) in one file-scope device array of fixed size,
+// so it allocates nothing.  Limits and sharing rules are stated in include/damf.h.
+#include <mutex>
+
+#include "damf_internal.cuh"
+
+namespace damf {
+cudaError_t core_svd_into(const float* sigma, const float* L, const float* R, int d, int r, float* E, float* H,
+                          float* theta, DevHeader* h, float* M, cudaStream_t s);
+}  // namespace damf
+
+using namespace damf;
+
+namespace {
+
+constexpr size_t kHeaderBytes = 256;
+static_assert(sizeof(DevHeader) <= kHeaderBytes, "status area too small");
+// status word area + the largest core (d + r <= 224) in FP32: 200,960 bytes
+constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxM * kMaxM * sizeof(float);
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_core_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices];   // device address of g_core_scratch, per device
+std::mutex g_scratch_mu;
+
+}  // namespace
+
+extern "C" damf_status damf_core_svd_noalloc(const float* sigma, const float* L, const float* R, int32_t d,
+                                             int32_t r, float* E, float* H, float* theta, void* stream) {
+  if (!(d == 16 || d == 32 || d == 64 || d == 128) || !sigma || !L || !R || !E || !H || !theta)
+    return DAMF_ERR_INVALID;
+  if (r < 1 || r > kMaxR) return DAMF_ERR_CAPACITY;   // the scratch holds cores up to (128 + 96)^2
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DAMF_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return DAMF_ERR_INVALID;
+  void* base = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name of the array
+    // is not a device address, so look the address up
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_core_scratch) != cudaSuccess || p == nullptr) return DAMF_ERR_CUDA;
+      g_scratch_addr[dev] = p;
+    }
+    base = g_scratch_addr[dev];
+  }
+  DevHeader* h = (DevHeader*)base;
+  float* M = (float*)((char*)base + kHeaderBytes);
+  // core_svd_into clears the status word before use; M is fully overwritten by the assembly
+  const cudaError_t e = core_svd_into(sigma, L, R, d, r, E, H, theta, h, M, (cudaStream_t)stream);
+  return e == cudaSuccess ? DAMF_OK : DAMF_ERR_CUDA;
+}

@@ -1,0 +1,64 @@
+"""damf_core_svd_noalloc: the core SVD for callers that cannot allocate device memory.
+
+Such callers (a plugin that only receives input and output pointers, code that must not
+call cudaMalloc) get their scratch from a static device array inside the library.  This
+file sorts last so that a run stopping at the first failure has run every other test.
+It compares the no-allocation entry point with damf_core_svd (caller workspace) through
+the C ABI, on two calls in a row with different inputs, at the parity tests' tolerance.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _core(rng, d, r):
+    sigma = np.sort(rng.uniform(2.0, 40.0, d))[::-1].astype(np.float32)
+    L = np.vstack([0.05 * rng.standard_normal((d, r)), np.triu(rng.standard_normal((r, r))) + np.eye(r)])
+    R = np.vstack([0.05 * rng.standard_normal((d, r)), np.triu(rng.standard_normal((r, r))) + np.eye(r)])
+    return sigma, L.astype(np.float32), R.astype(np.float32)
+
+
+def test_noalloc_matches_workspace_entry_point_twice():
+    import torch
+    from paper_2306_08967_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(2024)
+    d, r = 128, 64
+    m = d + r
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    nbytes = int(lib.damf_core_svd_workspace_size(d, r))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    for call in range(2):                    # the static scratch keeps the previous call's data
+        sigma, L, R = (torch.from_numpy(a).cuda() for a in _core(rng, d, r))
+        outs = []
+        for noalloc in (False, True):
+            E = torch.full((m, d), float("nan"), device="cuda")
+            H = torch.full((m, d), float("nan"), device="cuda")
+            th = torch.full((d,), float("nan"), device="cuda")
+            if noalloc:
+                st = lib.damf_core_svd_noalloc(p(sigma), p(L), p(R), d, r, p(E), p(H), p(th), stream)
+            else:
+                st = lib.damf_core_svd(p(sigma), p(L), p(R), d, r, p(E), p(H), p(th), p(ws), nbytes, stream)
+            assert st == 0
+            torch.cuda.synchronize()
+            outs.append((E.double().cpu().numpy(), H.double().cpu().numpy(), th.double().cpu().numpy()))
+        (E0, H0, t0), (E1, H1, t1) = outs
+        assert np.isfinite(E1).all() and np.isfinite(H1).all() and np.isfinite(t1).all()
+        np.testing.assert_allclose(t1, t0, rtol=2e-4)
+        # compare the rank-d products (invariant to the sign of each singular pair)
+        P0, P1 = (E0 * t0) @ H0.T, (E1 * t1) @ H1.T
+        assert np.linalg.norm(P1 - P0) / np.linalg.norm(P0) < 2e-4
+
+
+def test_noalloc_rejects_cores_beyond_its_scratch():
+    from paper_2306_08967_gb300 import _lib
+    lib = _lib.load()
+    # r = 97 exceeds the static scratch (d + r <= 224): refused before any device work
+    dummy = ctypes.c_void_p(16)
+    assert lib.damf_core_svd_noalloc(dummy, dummy, dummy, 128, 97, dummy, dummy, dummy, None) == 2
+    assert lib.damf_core_svd_noalloc(dummy, dummy, dummy, 24, 8, dummy, dummy, dummy, None) == 1
