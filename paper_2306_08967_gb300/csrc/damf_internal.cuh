@@ -94,7 +94,7 @@ struct Workspace {
   // push
   int32_t* cand[2];  // [n_cap]
   int32_t* front;    // [n_cap]
-  int2* work;        // [work_cap]
+  int4* work;        // [work_cap] (rho slot, first in-edge, in-edge count, -)
   long long work_cap;
   float* rho;        // [n_cap x d]
   uint32_t* stamp;   // [n_cap]
@@ -173,7 +173,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigne
           set_status(h, DAMF_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(32);
+        if (it > 4096) __nanosleep(64);   // short phases finish within the first spins
       }
     }
     __threadfence();

@@ -65,37 +65,55 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
       const long long ci = base + sub;
       const bool valid = ci < ncand;
       const int u = valid ? (cand ? __ldcg(cand + ci) : (int)ci) : 0;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+      // everything that depends only on u is requested at once
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f), z = v;
+      int st = 0, deg = 0;
+      if (valid) {
+        v = f4_ldcg(r + (size_t)u * D + 4 * q);
+        z = f4_ldcg(Zb + (size_t)u * D + 4 * q);
+        st = in.start[u];
+        deg = in.len[u];
+      }
       float mx = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
 #pragma unroll
       for (int o = 1; o < LPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       const bool push = valid && mx > eps;
+      const int nch = push ? (deg + CH - 1) / CH : 0;
+      // warp-aggregated slots: one frontier row per pushing group, nch work items each
       const unsigned bal = __ballot_sync(0xffffffffu, push && q == 0);
-      int basepos = 0;
-      if (lane == 0 && bal) basepos = atomicAdd(&h->front_count[P], __popc(bal));
+      int wsum = (q == 0) ? nch : 0, wpre = wsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {   // inclusive prefix sum over the warp
+        const int t = __shfl_up_sync(0xffffffffu, wpre, o);
+        if (lane >= o) wpre += t;
+      }
+      const int wtot = __shfl_sync(0xffffffffu, wpre, 31);
+      int basepos = 0, wbase = 0;
+      if (lane == 0 && bal) {
+        basepos = atomicAdd(&h->front_count[P], __popc(bal));
+        if (wtot) wbase = atomicAdd(&h->work_count[P], wtot);
+      }
       basepos = __shfl_sync(0xffffffffu, basepos, 0);
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      const int wmine = __shfl_sync(0xffffffffu, wpre - wsum, sub * LPR);   // exclusive prefix of my group
       if (push) {
         const int pos = basepos + __popc(bal & ((1u << (sub * LPR)) - 1u));
         __stcg(reinterpret_cast<float4*>(ws.rho + (size_t)pos * D) + q, v);
         __stcg(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(0.f, 0.f, 0.f, 0.f));
-        float4 z = f4_ldcg(Zb + (size_t)u * D + 4 * q);
         z.x = fmaf(alpha, v.x, z.x);
         z.y = fmaf(alpha, v.y, z.y);
         z.z = fmaf(alpha, v.z, z.z);
         z.w = fmaf(alpha, v.w, z.w);
         __stcg(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q, z);
-        const int deg = in.len[u];
-        const int nch = (deg + CH - 1) / CH;
-        int wpos = 0;
+        // work item: (rho slot, first in-edge, number of in-edges)
+        for (int c2 = q; c2 < nch; c2 += LPR) {
+          const int e0 = c2 * CH;
+          __stcg(&ws.work[wbase + wmine + c2], make_int4(pos, st + e0, min(CH, deg - e0), 0));
+        }
         if (q == 0) {
-          __stcg(ws.front + pos, u);
-          if (nch > 0) wpos = atomicAdd(&h->work_count[P], nch);
           my_pushes += 1;
           my_edges += deg;
         }
-        wpos = __shfl_sync(sub_mask, wpos, sub * LPR);
-        for (int c2 = q; c2 < nch; c2 += LPR) __stcg(&ws.work[wpos + c2], make_int2(pos, c2));
       }
     }
     if (!grid_barrier(&h->bar, h, nblocks)) return;
@@ -107,22 +125,16 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
     const unsigned tag = epoch0 + (unsigned)round + 1u;
     for (long long it = gwarp * RPW + sub; it - sub < nwork; it += nwarps * RPW) {
       const bool valid = it < nwork;
-      int2 wi = make_int2(0, 0);
+      int4 wi = make_int4(0, 0, 0, 0);
       if (valid) wi = __ldcg(&ws.work[it]);
-      const int u = valid ? __ldcg(ws.front + wi.x) : 0;
-      const int st = valid ? in.start[u] : 0;
-      const int deg = valid ? in.len[u] : 0;
-      const int e0 = wi.y * CH;
-      const int ne = valid ? min(CH, deg - e0) : 0;
-      // lane q < ne of the row group owns in-edge e0 + q
+      const int ne = wi.z;
+      // lane q < ne of the row group owns in-edge wi.y + q; rho is requested alongside
       int w_own = 0;
-      float c_own = 0.f;
-      if (q < ne) {
-        w_own = __ldg(in.col + st + e0 + q);
-        c_own = beta / (float)__ldg(outdeg + w_own);
-      }
+      if (q < ne) w_own = __ldg(in.col + wi.y + q);
       float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
+      float c_own = 0.f;
+      if (q < ne) c_own = beta / (float)__ldg(outdeg + w_own);
       // issue every atomic of the item before looking at any result
       float4 nv[CH];
 #pragma unroll

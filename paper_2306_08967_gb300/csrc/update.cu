@@ -273,28 +273,33 @@ __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace
 }
 
 // ---- Gauss-Jordan inverse with partial pivoting (block 0: K_U, block 1: K_V) ----
+// [K | I] in shared memory with a padded row stride (2D + 1: column reads are free of
+// bank conflicts); each warp owns rows, each lane columns; the pivot row's live window
+// [p, 2D) is read once per step into registers.
 template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspace ws) {
+  constexpr int LD = 2 * D + 1;
+  constexpr int CPL = (2 * D + 31) / 32;   // columns per lane
   extern __shared__ float smem[];
-  float* Aug = smem;   // D x 2D
+  float* Aug = smem;   // D x LD
   __shared__ int piv_row;
   __shared__ float piv_val;
   __shared__ float colv[D];
   if (h->status != 0 || h->nS == 0) return;
   const float* K = blockIdx.x == 0 ? ws.KU : ws.KV;
   float* Ki = blockIdx.x == 0 ? ws.KUi : ws.KVi;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int o = tid; o < D * 2 * D; o += nt) {
     const int i = o / (2 * D), j = o % (2 * D);
-    Aug[o] = j < D ? K[i * D + j] : (j - D == i ? 1.0f : 0.0f);
+    Aug[i * LD + j] = j < D ? K[i * D + j] : (j - D == i ? 1.0f : 0.0f);
   }
   __syncthreads();
   for (int p = 0; p < D; ++p) {
-    if (tid < 32) {  // pivot search in column p, rows p..D-1
+    if (warp == 0) {  // pivot search in column p, rows p..D-1
       float best = -1.f;
       int br = p;
-      for (int i = p + tid; i < D; i += 32) {
-        const float a = fabsf(Aug[i * 2 * D + p]);
+      for (int i = p + lane; i < D; i += 32) {
+        const float a = fabsf(Aug[i * LD + p]);
         if (a > best) best = a, br = i;
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -302,9 +307,9 @@ __global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspa
         const int orr = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && orr < br)) best = ob, br = orr;
       }
-      if (tid == 0) {
+      if (lane == 0) {
         piv_row = br;
-        piv_val = Aug[br * 2 * D + p];
+        piv_val = Aug[br * LD + p];
       }
     }
     __syncthreads();
@@ -314,28 +319,34 @@ __global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspa
     }
     const int pr = piv_row;
     const float inv = 1.0f / piv_val;
-    for (int j = tid; j < 2 * D; j += nt) {  // swap rows p, pr and scale the pivot row
-      const float a = Aug[p * 2 * D + j], b = Aug[pr * 2 * D + j];
-      Aug[pr * 2 * D + j] = a;
-      Aug[p * 2 * D + j] = b * inv;
+    for (int j = p + tid; j < 2 * D; j += nt) {  // swap rows p, pr and scale the pivot row
+      const float a = Aug[p * LD + j], b = Aug[pr * LD + j];
+      Aug[pr * LD + j] = a;
+      Aug[p * LD + j] = b * inv;
     }
     __syncthreads();
-    for (int i = tid; i < D; i += nt) colv[i] = Aug[i * 2 * D + p];
+    for (int i = tid; i < D; i += nt) colv[i] = Aug[i * LD + p];
+    float pv[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int j = p + lane + 32 * c;
+      pv[c] = j < 2 * D ? Aug[p * LD + j] : 0.0f;
+    }
     __syncthreads();
-    // columns < p of the left half are already unit vectors, so the live window is
-    // [p, 2D) (with row pivoting the right half's live columns are not contiguous);
-    // one warp per row, lanes across columns
-    for (int i = tid >> 5; i < D; i += nt >> 5) {
+    for (int i = warp; i < D; i += nw) {
       if (i == p) continue;
       const float f = colv[i];
-      for (int j = p + (tid & 31); j < 2 * D; j += 32)
-        Aug[i * 2 * D + j] = fmaf(-f, Aug[p * 2 * D + j], Aug[i * 2 * D + j]);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = p + lane + 32 * c;
+        if (j < 2 * D) Aug[i * LD + j] = fmaf(-f, pv[c], Aug[i * LD + j]);
+      }
     }
     __syncthreads();
   }
   for (int o = tid; o < D * D; o += nt) {
     const int i = o / D, j = o % D;
-    Ki[o] = Aug[i * 2 * D + D + j];
+    Ki[o] = Aug[i * LD + D + j];
   }
 }
 
@@ -482,7 +493,7 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smi = (size_t)(D * 2 * D) * sizeof(float);
+  const size_t smi = (size_t)(D * (2 * D + 1)) * sizeof(float);
   cudaFuncSetAttribute(k_inverse<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
   k_inverse<D><<<2, kChainThreads, smi, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
