@@ -153,7 +153,7 @@ def run_ours(args, c, rank, world):
     K, W, E = args.steps, args.warmup, args.e2e_steps
     ip, ix, st = make_inputs(c, W + K + E)
     cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=st.n_final + 16, nnz=len(ix), directed=c.directed,
-                      refold_every=args.refold_every)
+                      refold_every=args.refold_every, precision=args.precision)
     om = gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
     t0 = time.perf_counter()
     g = DamfGraph(ip, ix, cfg, om)
@@ -231,8 +231,17 @@ def run_ours(args, c, rank, world):
         torch.cuda.current_stream().synchronize()
         e2e_edges += b.k
         h2d += b.k * 9
-    e2e_s = time.perf_counter() - t_e
+    e2e_s = max(time.perf_counter() - t_e, 1e-9)
     g.check()
+
+    # error of the run: drift of the effective bases from orthonormality (U = Ub PU)
+    stt = g.state()
+    U = stt["Ub"].double() @ stt["PU"].double()
+    V = stt["Vb"].double() @ stt["PV"].double()
+    eye = torch.eye(c.d, dtype=torch.float64, device=dev)
+    err = {"U_orth_max": float((U.T @ U - eye).abs().max()), "V_orth_max": float((V.T @ V - eye).abs().max())}
+    sigma_final = stt["sigma"].double().cpu().numpy()
+    del U, V, stt
 
     # roofline of the dominant kernel, from live events and device counters
     d = c.d
@@ -260,7 +269,7 @@ def run_ours(args, c, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded Chung-Lu graph and edge stream)",
-        "config": {"workload": workload_desc(c), "precision": "fp32", "edges_timed": edges,
+        "config": {"workload": workload_desc(c), "precision": args.precision, "edges_timed": edges,
                    "l2": "state %.2f GB (Ub, Vb, Zb, r) > 129 MB L2; no flush" % (4 * st.n_final * d * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU", "refold_every": args.refold_every},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -279,6 +288,8 @@ def run_ours(args, c, rank, world):
                      "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"]},
         "init_s": init_s,
         "clocks": clk.summary(),
+        "err": err,
+        "_sigma": sigma_final.tolist(),
     }
     g.close()
     return out
@@ -293,6 +304,9 @@ def main():
     ap.add_argument("--config", default="C2")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refold-every", type=int, default=256)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--no-compare-precision", dest="compare_precision", action="store_false",
+                    help="skip timing the other precision build of the path on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--oracle-worker", action="store_true")
@@ -326,6 +340,22 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, c, rank, world)
+    sig_a = np.array(out.pop("_sigma"))
+    if args.compare_precision:
+        import copy
+        a2 = copy.copy(args)
+        a2.precision = "fp32" if args.precision == "mixed" else "mixed"
+        a2.e2e_steps = 0
+        o2 = run_ours(a2, c, rank, world)
+        sig_b = np.array(o2.pop("_sigma"))
+        out["precision_compare"] = {
+            args.precision: {"value": out["value"], "ms_per_step": out["ms_per_step"], "err": out["err"],
+                             "fold_ms": out["stage_ms"].get("fold")},
+            a2.precision: {"value": o2["value"], "ms_per_step": o2["ms_per_step"], "err": o2["err"],
+                           "fold_ms": o2["stage_ms"].get("fold")},
+            "sigma_max_rel_diff": float(np.max(np.abs(sig_a - sig_b) / np.abs(sig_b))),
+            "note": "same workload and stream; err = max |U^T U - I|, |V^T V - I| of the effective bases "
+                    "after the run; mixed runs the fold's n x d by d x d GEMMs on tcgen05 (TF32, 3-term split)"}
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             r = oracle_subprocess(c, 400, args.cpu_budget)

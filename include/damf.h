@@ -60,6 +60,10 @@ typedef struct {
   int32_t rsvd_oversample;  /* randomized t-SVD: l = round_up(d + rsvd_oversample, 32) test vectors */
   int32_t rsvd_power_iters; /* randomized t-SVD power iterations q */
   int32_t max_push_rounds;  /* cap on frontier rounds per damf_ppr_refresh */
+  int32_t precision;        /* 0: plain FP32 (SIMT for every kernel); 1: mixed, the n x d by d x d
+                               GEMMs of the fold, the initialisation and the full query run on
+                               the tensor cores (tcgen05, TF32 with a three-term split that keeps
+                               FP32 accuracy); the small dense factor update is FP32 in both */
 } damf_config;
 
 /* Workspace the library allocates on the device for `cfg` (bytes).  Lets a caller

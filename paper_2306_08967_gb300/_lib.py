@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "DAMF_OK", 1: "DAMF_ERR_INVALID", 2: "DAMF_ERR_CAPACITY", 3: 
 class Config(ctypes.Structure):
     _fields_ = [("n", c_i32), ("n_capacity", c_i32), ("m_capacity", c_i64), ("d", c_i32), ("directed", c_i32),
                 ("alpha", c_f64), ("eps", c_f64), ("refold_every", c_i32), ("rsvd_oversample", c_i32),
-                ("rsvd_power_iters", c_i32), ("max_push_rounds", c_i32)]
+                ("rsvd_power_iters", c_i32), ("max_push_rounds", c_i32), ("precision", c_i32)]
 
 
 class Stats(ctypes.Structure):

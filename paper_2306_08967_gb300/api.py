@@ -35,14 +35,16 @@ def _dev(x, dtype):
 
 
 def make_config(n, d, alpha, eps, n_capacity=None, m_capacity=None, nnz=0, directed=False, refold_every=0,
-                rsvd_oversample=10, rsvd_power_iters=4, max_push_rounds=100000) -> Config:
+                rsvd_oversample=10, rsvd_power_iters=4, max_push_rounds=100000, precision="mixed") -> Config:
+    """precision: "fp32" (SIMT everywhere) or "mixed" (tensor-core GEMMs for the fold, init, query)."""
     n_capacity = n if n_capacity is None else n_capacity
     if m_capacity is None:
         # initial rows with 25% slack plus room for relocations and growth
         m_capacity = int(2.0 * nnz) + 64 * n_capacity + 4096
     return Config(n=n, n_capacity=n_capacity, m_capacity=m_capacity, d=d, directed=int(directed), alpha=alpha,
                   eps=eps, refold_every=refold_every, rsvd_oversample=rsvd_oversample,
-                  rsvd_power_iters=rsvd_power_iters, max_push_rounds=max_push_rounds)
+                  rsvd_power_iters=rsvd_power_iters, max_push_rounds=max_push_rounds,
+                  precision={"fp32": 0, "mixed": 1}[precision])
 
 
 def rsvd_width(cfg: Config) -> int:

@@ -56,9 +56,9 @@ void timer_end(Ctx* c, int i, int stage, int launches, cudaStream_t s) {
     DAMF_CUDA(call, what);                        \
     timer_end(c, ti_, stage, nl, s);              \
   } while (0)
-// kernels per update: prepare, gather, wct, chol, assemble, jacobi, hmat, trans, inverse,
-// products, commit, edit, fixup, scatter
-constexpr int kLaunchesPerUpdate = 14;
+// kernels per update: prepare, gather, wct, chol, assemble, jacobi, hmat, ns_gram, ns_apply,
+// trans, inverse, products, commit, edit, fixup, scatter
+constexpr int kLaunchesPerUpdate = 16;
 // fold: 2 x (gram part + reduce), 2 x (congruence + chol), core, jacobi, hmat, 4 small_mm,
 // finish, 4 tall GEMMs
 constexpr int kLaunchesPerFold = 4 + 4 + 1 + 2 + 4 + 1 + 4;
@@ -71,6 +71,7 @@ bool cfg_ok(const damf_config* cfg) {
   if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0) || !(cfg->eps > 0.0)) return false;
   if (cfg->rsvd_oversample < 0 || cfg->rsvd_power_iters < 0 || cfg->max_push_rounds < 1) return false;
   if (cfg->refold_every < 0) return false;
+  if (cfg->precision != 0 && cfg->precision != 1) return false;
   return true;
 }
 
@@ -216,10 +217,10 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
       cudaError_t ee;
       if ((ee = gram_tall(c, X, l, n, l, G, s)) != cudaSuccess) return ee;
       if ((ee = chol_inv_upper2(G, l, Racc ? R : nullptr, Ri, c->hdr, s)) != cudaSuccess) return ee;
-      if ((ee = gemm_tall_scaled(X, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
+      if ((ee = gemm_ctx(c, X, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
       if ((ee = gram_tall(c, dst, l, n, l, G, s)) != cudaSuccess) return ee;
       if ((ee = chol_inv_upper2(G, l, Racc ? Rt : nullptr, Ri, c->hdr, s)) != cudaSuccess) return ee;
-      if ((ee = gemm_tall_scaled(dst, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
+      if ((ee = gemm_ctx(c, dst, l, n, Ri, l, l, dst, l, nullptr, nullptr, s)) != cudaSuccess) return ee;
       if (Racc) {  // X = dst (Rt R): R_total = Rt R
         if ((ee = small_mm(Rt, R, Racc, l, s)) != cudaSuccess) return ee;
       }
@@ -237,8 +238,8 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
     if ((e = orth(Y, Q2, R2)) != cudaSuccess) goto done;         // Bt = Q2 R2
     // R2 row-major == (R2^T) column-major: the Jacobi input is R2^T
     if ((e = jacobi_svd_dense(R2, l, d, c->ws.E, c->ws.H, c->ws.theta, nullptr, c->hdr, s)) != cudaSuccess) goto done;
-    if ((e = gemm_tall_scaled(Q, l, n, c->ws.E, l, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
-    if ((e = gemm_tall_scaled(Q2, l, n, c->ws.H, l, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
+    if ((e = gemm_ctx(c, Q, l, n, c->ws.E, l, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
+    if ((e = gemm_ctx(c, Q2, l, n, c->ws.H, l, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
     if ((e = cudaMemcpyAsync(c->sigma, c->ws.theta, sizeof(float) * d, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       goto done;
     const long long tot = (long long)n * d;
@@ -392,7 +393,7 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
     DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
     DAMF_STAGE(DAMF_STAGE_CHOL, 2, launch_chol(c, s), "chol");
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
-    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 5, launch_transforms(c, s), "transforms");
+    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 7, launch_transforms(c, s), "transforms");
     // writes to the adjacency, Zb and r follow the push
     DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_push, 0), "join push");
     DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_edit(c, s), "edit");

@@ -208,6 +208,9 @@ cudaError_t init_factorize(Ctx* c, const int32_t* row_ptr, const int32_t* col_id
 // C[rows x N] (+)= A[rows x K] * B[K x N]; A row i taken from A + idx[i]*lda when idx != nullptr.
 cudaError_t gemm_rowgather(const float* A, int lda, const int32_t* idx, const int* rows_dev, int rows_max,
                            const float* B, int K, int N, float* C, int ldc, int accumulate, cudaStream_t s);
+// n x K by K x N product for a context (tensor cores in mixed precision where covered)
+cudaError_t gemm_ctx(Ctx* c, const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                     const float* ascale, const float* cscale, cudaStream_t s);
 // tall-skinny C[n x N] = A[n x K] B[K x N] (K, N <= 160, multiples of 16)
 cudaError_t gemm_tall(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
                       cudaStream_t s);

@@ -3,6 +3,7 @@
 // randomized t-SVD initialisation (Appendix A, Algorithm 3; Halko et al.), the query
 // (Sec. 4.6) and the periodic fold of the transforms into the bases.
 #include "damf_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace damf {
 
@@ -72,6 +73,34 @@ static cudaError_t gemm_tall_kn(const float* A, int lda, long long n, const floa
   return cudaGetLastError();
 }
 
+template <int K, int N>
+static cudaError_t gemm_tc_kn(const float* A, int lda, long long n, const float* B, float* C, int ldc,
+                              const float* as, const float* cs, int* err, cudaStream_t s) {
+  const size_t sm = tc::smem_bytes<K, N>();
+  cudaFuncSetAttribute(tc::k_gemm_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (n + tc::kTileM - 1) / tc::kTileM;
+  int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
+  if (grid < 1) grid = 1;
+  tc::k_gemm_tc<K, N><<<grid, tc::kThreads, sm, s>>>(A, lda, n, B, C, ldc, as, cs, err);
+  return cudaGetLastError();
+}
+
+// Tensor-core version (kind::tf32, three-term split) of gemm_tall_scaled; `err` receives 1
+// if a bounded wait for the tensor core ran out.
+cudaError_t gemm_tall_tc(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                         const float* ascale, const float* cscale, int* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+#define DAMF_GTC(KK, NN) \
+  if (K == KK && N == NN) return gemm_tc_kn<KK, NN>(A, lda, n, B, C, ldc, ascale, cscale, err, s);
+  DAMF_GTC(32, 32) DAMF_GTC(64, 64) DAMF_GTC(96, 96) DAMF_GTC(128, 128) DAMF_GTC(160, 160)
+  DAMF_GTC(32, 16) DAMF_GTC(64, 32) DAMF_GTC(96, 64) DAMF_GTC(160, 128)
+#undef DAMF_GTC
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t gemm_tall_scaled(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
                              const float* ascale, const float* cscale, cudaStream_t s) {
 #define DAMF_GT(KK, NN) \
@@ -80,6 +109,18 @@ cudaError_t gemm_tall_scaled(const float* A, int lda, long long n, const float* 
   DAMF_GT(32, 16) DAMF_GT(64, 32) DAMF_GT(96, 64) DAMF_GT(160, 128)
 #undef DAMF_GT
   return cudaErrorInvalidValue;
+}
+
+// n x K by K x N product for a context: tensor cores in mixed precision when the shape is
+// covered (K a multiple of 32), otherwise the FP32 SIMT kernel.
+cudaError_t gemm_ctx(Ctx* c, const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
+                     const float* ascale, const float* cscale, cudaStream_t s) {
+  if (c->cfg.precision == 1 && K % tc::kChunkK == 0) {
+    const cudaError_t e = gemm_tall_tc(A, lda, n, B, K, N, C, ldc, ascale, cscale, &c->hdr->status, s);
+    if (e != cudaErrorInvalidValue) return e;
+    cudaGetLastError();
+  }
+  return gemm_tall_scaled(A, lda, n, B, K, N, C, ldc, ascale, cscale, s);
 }
 
 cudaError_t gemm_tall(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,

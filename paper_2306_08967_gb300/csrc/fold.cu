@@ -73,7 +73,7 @@ static cudaError_t query_rows_impl(const int32_t* rows, int count, int n, DevHea
 
 static cudaError_t query_one(Ctx* c, const int32_t* rows, int count, const float* base, const float* P,
                              const float* pre, const float* post, float* out, cudaStream_t s) {
-  if (!rows) return gemm_tall_scaled(base, c->d, count, P, c->d, c->d, out, c->d, pre, post, s);
+  if (!rows) return gemm_ctx(c, base, c->d, count, P, c->d, c->d, out, c->d, pre, post, s);
   switch (c->d) {
     case 16: return query_rows_impl<16>(rows, count, c->n, c->hdr, base, P, pre, post, out, s);
     case 32: return query_rows_impl<32>(rows, count, c->n, c->hdr, base, P, pre, post, out, s);
@@ -181,10 +181,10 @@ cudaError_t launch_fold(Ctx* c, cudaStream_t s) {
   k_fold_finish<<<1, 1024, 0, s>>>(TU, T2, c->s0, c->sigma, c->ws.theta, c->PU, c->PUi, c->PV, c->PVi, d, c->hdr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // in-place re-basing of the four n x d arrays
-  if ((e = gemm_tall_scaled(c->Ub, d, c->n, TU, d, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) return e;
-  if ((e = gemm_tall_scaled(c->Vb, d, c->n, TV, d, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) return e;
-  if ((e = gemm_tall_scaled(c->Zb, d, c->n, T2, d, d, c->Zb, d, nullptr, nullptr, s)) != cudaSuccess) return e;
-  if ((e = gemm_tall_scaled(c->r, d, c->n, T2, d, d, c->r, d, nullptr, nullptr, s)) != cudaSuccess) return e;
+  if ((e = gemm_ctx(c, c->Ub, d, c->n, TU, d, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) return e;
+  if ((e = gemm_ctx(c, c->Vb, d, c->n, TV, d, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) return e;
+  if ((e = gemm_ctx(c, c->Zb, d, c->n, T2, d, d, c->Zb, d, nullptr, nullptr, s)) != cudaSuccess) return e;
+  if ((e = gemm_ctx(c, c->r, d, c->n, T2, d, d, c->r, d, nullptr, nullptr, s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

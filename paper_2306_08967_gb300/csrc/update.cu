@@ -219,6 +219,75 @@ __global__ void __launch_bounds__(128) k_hmat(DevHeader* h, Workspace ws) {
   }
 }
 
+// ---- one Newton-Schulz step on E and H: X <- X (3 I - X^T X) / 2 ----
+// E's columns are orthonormal to the Jacobi tolerance; H = M^T E Theta^{-1} inherits that
+// error amplified by the spread of the singular values.  One step of the iteration for the
+// orthonormal polar factor squares the orthonormality error of both, so the updated bases
+// stay orthonormal to FP32 level between folds.
+// (a) G = X^T X over the m rows: 32 x 32 output tiles, blockIdx.z selects E or H
+template <int D>
+__global__ void __launch_bounds__(256) k_ns_gram(DevHeader* h, Workspace ws) {
+  __shared__ float xa[32][33], xb[32][33];
+  if (h->status != 0 || h->nS == 0) return;
+  const int m = D + h->nS;
+  const float* X = blockIdx.z == 0 ? ws.E : ws.H;
+  float* G = ws.tmp + (size_t)blockIdx.z * D * D;
+  const int ta = blockIdx.x * 32, tb = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int r0 = 0; r0 < m; r0 += 32) {
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int row = r0 + i;
+      xa[i][tx] = (row < m && ta + tx < D) ? X[row * D + ta + tx] : 0.0f;
+      xb[i][tx] = (row < m && tb + tx < D) ? X[row * D + tb + tx] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = 0; i < 32; ++i) {
+      const float b = xb[i][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(xa[i][ty + 8 * q], b, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = ta + ty + 8 * q, b = tb + tx;
+    if (a < D && b < D) G[a * D + b] = acc[q];
+  }
+}
+
+// (b) X <- X (1.5 I - 0.5 G), 16 rows per CTA, blockIdx.y selects E or H (rows are owned by
+// one CTA, so the update is in place)
+template <int D>
+__global__ void __launch_bounds__(256) k_ns_apply(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* Gs = smem;            // D x D: 1.5 I - 0.5 G
+  float* Xs = smem + D * D;    // 16 x D
+  if (h->status != 0 || h->nS == 0) return;
+  const int m = D + h->nS;
+  const int r0 = blockIdx.x * 16;
+  if (r0 >= m) return;
+  float* X = blockIdx.y == 0 ? ws.E : ws.H;
+  const float* G = ws.tmp + (size_t)blockIdx.y * D * D;
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
+    const int a = i / D, b = i % D;
+    Gs[i] = (a == b ? 1.5f : 0.0f) - 0.5f * G[i];
+  }
+  for (int i = threadIdx.x; i < 16 * D; i += blockDim.x) {
+    const int rr = i / D;
+    Xs[i] = (r0 + rr < m) ? X[(r0 + rr) * D + i % D] : 0.0f;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 16 * D; o += blockDim.x) {
+    const int rr = o / D, j = o % D;
+    if (r0 + rr >= m) continue;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < D; ++k) s = fmaf(Xs[rr * D + k], Gs[k * D + j], s);
+    X[(r0 + rr) * D + j] = s;
+  }
+}
+
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
 template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace ws) {
@@ -489,6 +558,15 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
   cudaError_t e;
   k_hmat<D><<<kMaxM, 128, 0, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    constexpr int GT = (D + 31) / 32;
+    k_ns_gram<D><<<dim3(GT, GT, 2), 256, 0, s>>>(c->hdr, c->ws);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t sma = (size_t)(D * D + 16 * D) * sizeof(float);
+    cudaFuncSetAttribute(k_ns_apply<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
+    k_ns_apply<D><<<dim3(kMaxM / 16, 2), 256, sma, s>>>(c->hdr, c->ws);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const size_t sm = (size_t)(kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);

@@ -234,3 +234,54 @@ def test_core_svd_against_numpy(d, r):
     # inherits FP32 rounding amplified by sigma_1 / sigma_d (20 here) and sqrt(d + r)
     assert np.abs(E.T @ E - np.eye(d)).max() < 2e-5
     assert np.abs(H.T @ H - np.eye(d)).max() < 5e-4
+
+
+def _run_stream(precision, refold_every, n_batches=30, d=32, seed=SEED + 21):
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    ip, ix, w = chung_lu_graph(1500, 10.0, 2.5, seed=seed)
+    st = edge_stream(ip, ix, w, n_batches, 1, 40, 0.05, 0.1, seed + 1)
+    cfg = make_config(1500, d, 0.15, 1e-5, n_capacity=st.n_final, nnz=len(ix), refold_every=refold_every,
+                      precision=precision)
+    g = DamfGraph(ip, ix, cfg, gaussian_test_matrix(1500, rsvd_width(cfg), seed + 2))
+    for b in st.batches:
+        g.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        g.ppr_refresh()
+    g.check()
+    X, Y, s = gpu_xy(g)
+    Z = g.embeddings()["Z"].double().cpu().numpy()
+    folds = g.stats()["folds"]
+    g.close()
+    return X, Y, Z, s, folds, (ip, ix, st)
+
+
+def test_fold_preserves_the_factorisation():
+    # the periodic fold re-bases U_b, V_b and resets P to I; U Sigma V^T must not change
+    X0, Y0, Z0, s0, f0, _ = _run_stream("fp32", 0)
+    X1, Y1, Z1, s1, f1, (ip, ix, st) = _run_stream("fp32", 4)
+    assert f0 == 0 and f1 >= 7
+    np.testing.assert_allclose(s1, s0, rtol=2e-5)
+    assert rel_fro(X1 @ Y1.T, X0 @ Y0.T) < 2e-5
+    assert rel_fro(Z1 @ Y1.T, Z0 @ Y0.T) < 1e-3      # both within eps of PPR of the same X
+    # and against the FP64 oracle on the same stream
+    from oracle.damf import DamfOracle
+    from synth import gaussian_test_matrix
+    from paper_2306_08967_gb300 import make_config, rsvd_width
+    cfg = make_config(1500, 32, 0.15, 1e-5)
+    orc = DamfOracle(ip, ix, 32, 0.15, 1e-5, n_cap=st.n_final, Omega=gaussian_test_matrix(1500, rsvd_width(cfg), SEED + 23),
+                     propagate=False)
+    for b in st.batches:
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+    np.testing.assert_allclose(s1, orc.sigma, rtol=1e-3)
+    assert rel_fro(X1 @ Y1.T, orc.X() @ orc.Y().T) < 1e-3
+
+
+def test_mixed_precision_matches_plain_fp32():
+    # tensor-core GEMMs (TF32 with a three-term split) in the fold, init and query give
+    # the FP32 results within FP32-level differences
+    Xm, Ym, Zm, sm, fm, _ = _run_stream("mixed", 4)
+    Xp, Yp, Zp, sp, fp, _ = _run_stream("fp32", 4)
+    assert fm == fp and fm >= 7
+    np.testing.assert_allclose(sm, sp, rtol=2e-5)
+    assert rel_fro(Xm @ Ym.T, Xp @ Yp.T) < 2e-5
+    assert rel_fro(Zm @ Ym.T, Zp @ Yp.T) < 1e-3
