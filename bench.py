@@ -285,7 +285,10 @@ def run_ours(args, c, rank, world):
         "dominant_stage": dominant,
         "counters": {"pushes": pushes, "push_edges": push_edges, "updates": s1["updates"] - s0["updates"],
                      "push_rounds": s1["push_rounds"] - s0["push_rounds"],
-                     "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"]},
+                     "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"],
+                     "jacobi_sweeps": s1["jacobi_sweeps"] - s0["jacobi_sweeps"],
+                     "jacobi_full": s1["jacobi_full"] - s0["jacobi_full"],
+                     "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"]},
         "init_s": init_s,
         "clocks": clk.summary(),
         "err": err,

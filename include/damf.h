@@ -233,6 +233,9 @@ typedef struct {
   int64_t launches;         /* kernels launched by this context so far */
   int32_t last_sweeps;      /* Jacobi sweeps of the most recent update's core SVD */
   int32_t reserved;
+  int64_t jacobi_sweeps;    /* Jacobi sweeps over all updates */
+  int64_t jacobi_full;      /* updates whose core needed sweeps over every pair */
+  int64_t jacobi_gersh;     /* updates that needed the exact Gershgorin gap check */
 } damf_stats;
 
 /* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */

@@ -595,6 +595,9 @@ damf_status damf_get_stats(damf_ctx* x, damf_stats* o) {
   o->last_status = h.status;
   o->launches = c->launches;
   o->last_sweeps = h.last_sweeps;
+  o->jacobi_sweeps = h.jacobi_sweeps;
+  o->jacobi_full = h.jacobi_full;
+  o->jacobi_gersh = h.jacobi_gersh;
   return DAMF_OK;
 }
 

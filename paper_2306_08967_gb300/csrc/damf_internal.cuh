@@ -46,6 +46,7 @@ struct DevHeader {
       touched_rows, folds;
   int last_rank;
   int last_sweeps;       // Jacobi sweeps of the most recent update
+  long long jacobi_sweeps, jacobi_full, jacobi_gersh;   // totals: sweeps, full-mode fallbacks, exact Gershgorin checks
   // push control (parity-indexed, see ppr.cu)
   int cand_count[2];
   int front_count[2];

@@ -25,9 +25,8 @@
 
 namespace damf {
 
-constexpr int kMaxEP = kMaxM / 32;  // column elements per lane of a warp (7)
 constexpr int kMaxC = kMaxM / 32;   // float4 chunks per lane of an 8-lane group (7)
-constexpr int kJacobiThreads = 256;
+constexpr int kJacobiThreads = 768;   // 96 pairs in flight: one pass per round for d + r <= 192
 // A pair is rotated while |a_p . a_q| > tol |a_p| |a_q|; FP32 dot products of length <= 224
 // carry relative noise of a few 1e-7, so the tolerance sits a little above that floor.
 constexpr float kJacobiTol = 1e-6f;
@@ -51,7 +50,7 @@ __device__ __forceinline__ void round_robin_pair(int mp, int round, int k, int& 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const float* __restrict__ Min, int m_host, int use_hdr,
+__global__ void __launch_bounds__(kJacobiThreads, 2) k_jacobi(DevHeader* h, const float* __restrict__ Min, int m_host, int use_hdr,
                                                     float* E, float* theta, float tol, int max_sweeps) {
   extern __shared__ float A[];
   __shared__ float nrm[kMaxM];   // squared column norms, refreshed every sweep
@@ -111,20 +110,19 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const f
         const bool act = k < mp / 2 && (full || (top[p] | top[q])) && aa > 1e-30f && bb > 1e-30f;
         float4* ap = reinterpret_cast<float4*>(A + p * mp);
         float4* aq = reinterpret_cast<float4*>(A + q * mp);
-        float4 x[kMaxC], y[kMaxC];
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;   // four short dependent chains
+        // pass 1: dot product (columns are read again for the rotation, keeping the
+        // register footprint small enough for 768 threads beside a push)
+        float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < kMaxC; ++c) {
           if (c < nc && act) {
-            x[c] = ap[gl + 8 * c];
-            y[c] = aq[gl + 8 * c];
-            g0 = fmaf(x[c].x, y[c].x, g0);
-            g1 = fmaf(x[c].y, y[c].y, g1);
-            g2 = fmaf(x[c].z, y[c].z, g2);
-            g3 = fmaf(x[c].w, y[c].w, g3);
+            const float4 x = ap[gl + 8 * c];
+            const float4 y = aq[gl + 8 * c];
+            g01 = __ffma2_rn(make_float2(x.x, x.y), make_float2(y.x, y.y), g01);
+            g23 = __ffma2_rn(make_float2(x.z, x.w), make_float2(y.z, y.w), g23);
           }
         }
-        float gg = (g0 + g1) + (g2 + g3);
+        float gg = (g01.x + g01.y) + (g23.x + g23.y);
         gg += __shfl_xor_sync(0xffffffffu, gg, 1);
         gg += __shfl_xor_sync(0xffffffffu, gg, 2);
         gg += __shfl_xor_sync(0xffffffffu, gg, 4);
@@ -137,13 +135,21 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const f
           const float t = copysignf(ta, zeta);
           const float cs = rsqrtf(fmaf(t, t, 1.0f));
           const float sn = cs * t;
+          const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ms2 = make_float2(-sn, -sn);
+          // pass 2: rotate
 #pragma unroll
           for (int c = 0; c < kMaxC; ++c) {
             if (c < nc) {
-              ap[gl + 8 * c] = make_float4(cs * x[c].x - sn * y[c].x, cs * x[c].y - sn * y[c].y,
-                                           cs * x[c].z - sn * y[c].z, cs * x[c].w - sn * y[c].w);
-              aq[gl + 8 * c] = make_float4(sn * x[c].x + cs * y[c].x, sn * x[c].y + cs * y[c].y,
-                                           sn * x[c].z + cs * y[c].z, sn * x[c].w + cs * y[c].w);
+              const float4 x = ap[gl + 8 * c];
+              const float4 y = aq[gl + 8 * c];
+              const float2 xl = make_float2(x.x, x.y), xh = make_float2(x.z, x.w);
+              const float2 yl = make_float2(y.x, y.y), yh = make_float2(y.z, y.w);
+              const float2 pl = __ffma2_rn(c2, xl, __fmul2_rn(ms2, yl));
+              const float2 ph = __ffma2_rn(c2, xh, __fmul2_rn(ms2, yh));
+              const float2 ql = __ffma2_rn(s2, xl, __fmul2_rn(c2, yl));
+              const float2 qh = __ffma2_rn(s2, xh, __fmul2_rn(c2, yh));
+              ap[gl + 8 * c] = make_float4(pl.x, pl.y, ph.x, ph.y);
+              aq[gl + 8 * c] = make_float4(ql.x, ql.y, qh.x, qh.y);
             }
           }
           if (gl == 0) {
@@ -158,7 +164,10 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const f
     if (!full && sweep + 1 >= kTopOnlySweeps && rot_flag != 0) {
       // the top set keeps changing (singular values straddling the cut are too close):
       // resolve every pair from here on
-      if (tid == 0) full_mode = 1;
+      if (tid == 0) {
+        full_mode = 1;
+        if (use_hdr) h->jacobi_full += 1;
+      }
     }
     if (rot_flag == 0) {
       if (full) break;
@@ -184,6 +193,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const f
       }
       __syncthreads();
       if (bmax * bsum < 0.98f * topmin) break;
+      if (tid == 0 && use_hdr) h->jacobi_gersh += 1;
       // exact Gershgorin row sums of the discarded block's Gram
       for (int j = warp; j < m; j += nw) {
         if (top[j]) continue;
@@ -198,11 +208,17 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(DevHeader* h, const f
       }
       __syncthreads();
       if (gersh < 0.98f * topmin) break;
-      if (tid == 0) full_mode = 1;
+      if (tid == 0) {
+        full_mode = 1;
+        if (use_hdr) h->jacobi_full += 1;
+      }
     }
     __syncthreads();
   }
-  if (tid == 0 && use_hdr) h->last_sweeps = sweep + 1;
+  if (tid == 0 && use_hdr) {
+    h->last_sweeps = sweep + 1;
+    h->jacobi_sweeps += sweep + 1;
+  }
   // exact column norms, then order by decreasing norm (ties by index)
   for (int j = warp; j < mp; j += nw) {
     float s2 = 0.f;

@@ -14,10 +14,15 @@
 //            item's atomics in flight at once; a row whose new value crosses eps is
 //            queued once per round (stamp) as a candidate.
 // Counters are indexed by round parity so each is reset by one block between its uses.
+#include <stdlib.h>
+
 #include "damf_internal.cuh"
 
 namespace damf {
 
+// CTAs of the push per SM: leaves registers, threads and shared memory on every SM for
+// the one-CTA kernels of the next update's factor chain (overridable for tuning with the
+// environment variable DAMF_PUSH_CTAS_PER_SM).
 constexpr int kPushBlocksPerSM = 2;
 
 __device__ __forceinline__ float4 f4_ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
@@ -191,7 +196,12 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D>, 256, 0);
-    if (per_sm > kPushBlocksPerSM) per_sm = kPushBlocksPerSM;
+    int cap = kPushBlocksPerSM;
+    if (const char* ev = getenv("DAMF_PUSH_CTAS_PER_SM")) {
+      const int v = atoi(ev);
+      if (v >= 1 && v <= 8) cap = v;
+    }
+    if (per_sm > cap) per_sm = cap;
     c->push_blocks = sms * (per_sm < 1 ? 1 : per_sm);
   }
   cudaError_t e = cudaMemsetAsync(&c->hdr->cand_count[0], 0, 6 * sizeof(int), s);
