@@ -288,7 +288,9 @@ def run_ours(args, c, rank, world):
                      "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"],
                      "jacobi_sweeps": s1["jacobi_sweeps"] - s0["jacobi_sweeps"],
                      "jacobi_full": s1["jacobi_full"] - s0["jacobi_full"],
-                     "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"]},
+                     "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"],
+                     "push_phase_ms": {k: (s1["push_ns"][i] - s0["push_ns"][i]) / 1e6 for i, k in
+                                       enumerate(["A", "barrier_A", "B", "barrier_B"])}},
         "init_s": init_s,
         "clocks": clk.summary(),
         "err": err,

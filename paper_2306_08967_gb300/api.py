@@ -201,7 +201,9 @@ class DamfGraph:
     def stats(self) -> dict:
         st = Stats()
         self._check(self.lib.damf_get_stats(self.h, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in Stats._fields_}
+        out = {k: getattr(st, k) for k, _ in Stats._fields_}
+        out["push_ns"] = list(out["push_ns"])
+        return out
 
     def sync_status(self) -> int:
         return int(self.lib.damf_sync_status(self.h))

@@ -598,6 +598,7 @@ damf_status damf_get_stats(damf_ctx* x, damf_stats* o) {
   o->jacobi_sweeps = h.jacobi_sweeps;
   o->jacobi_full = h.jacobi_full;
   o->jacobi_gersh = h.jacobi_gersh;
+  for (int i = 0; i < 4; ++i) o->push_ns[i] = (int64_t)h.push_ns[i];
   return DAMF_OK;
 }
 

@@ -46,7 +46,8 @@ struct DevHeader {
       touched_rows, folds;
   int last_rank;
   int last_sweeps;       // Jacobi sweeps of the most recent update
-  long long jacobi_sweeps, jacobi_full, jacobi_gersh;   // totals: sweeps, full-mode fallbacks, exact Gershgorin checks
+  long long jacobi_sweeps, jacobi_full, jacobi_gersh;
+  unsigned long long push_ns[4];   // block 0: phase A, barrier, phase B, barrier (nanoseconds)   // totals: sweeps, full-mode fallbacks, exact Gershgorin checks
   // push control (parity-indexed, see ppr.cu)
   int cand_count[2];
   int front_count[2];

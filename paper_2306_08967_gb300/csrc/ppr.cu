@@ -25,6 +25,19 @@ namespace damf {
 // environment variable DAMF_PUSH_CTAS_PER_SM).
 constexpr int kPushBlocksPerSM = 2;
 
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// adds the time since the last mark to slot i and sets a new mark
+__device__ __forceinline__ void time_mark(unsigned long long* s_t, int i) {
+  const unsigned long long t = gtimer();
+  s_t[i] += t - s_t[4];
+  s_t[4] = t;
+}
+
 __device__ __forceinline__ float4 f4_ldcg(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
 
 // in-edges per work item: one per lane of a row group, at most 8
@@ -35,8 +48,10 @@ struct PushShape {
   static constexpr int CH = LPR < 8 ? LPR : 8;      // in-edges per work item
 };
 
+// 64 registers at most (min. 4 CTAs' worth per SM): two push CTAs (32k registers) then leave room
+// on every SM for the 768-thread core SVD CTA of the next update, which runs beside the push
 template <int D>
-__global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
+__global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
                                               float* Zb, float* r, int n, float alpha, float eps, int max_rounds,
                                               int check_all) {
   constexpr int LPR = PushShape<D>::LPR;
@@ -53,7 +68,13 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
   long long my_pushes = 0, my_edges = 0;
   const int ncand0 = check_all ? n : h->pending;
   int round = 0;
+  // block 0's view of where the time goes (ns): phase A, barrier after A, phase B, barrier after B;
+  // [4] is the last time mark. Kept in shared memory, where it costs no registers.
+  __shared__ unsigned long long s_t[5];
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  if (timer) s_t[0] = s_t[1] = s_t[2] = s_t[3] = 0ull;
   for (;; ++round) {
+    if (timer) s_t[4] = gtimer();
     const int P = round & 1;
     if (round >= max_rounds) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, DAMF_ERR_NOT_CONVERGED);
@@ -121,7 +142,9 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
         }
       }
     }
+    if (timer) time_mark(s_t, 0);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
+    if (timer) time_mark(s_t, 1);
     const int nfront = __ldcg(&h->front_count[P]);
     if (nfront == 0) break;
     // ---- phase B: scatter (1-alpha) rho / deg(w) to in-neighbours ----
@@ -167,8 +190,12 @@ __global__ void __launch_bounds__(256) k_push(DevHeader* h, Adj in, const int32_
         }
       }
     }
+    if (timer) time_mark(s_t, 2);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
+    if (timer) time_mark(s_t, 3);
   }
+  if (timer)
+    for (int i = 0; i < 4; ++i) h->push_ns[i] += s_t[i];
   // counters and bookkeeping (block 0 after the last barrier; everyone has left the loop)
   for (int o = 16; o > 0; o >>= 1) {
     my_pushes += __shfl_xor_sync(0xffffffffu, my_pushes, o);
