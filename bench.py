@@ -290,7 +290,7 @@ def run_ours(args, c, rank, world):
                      "jacobi_full": s1["jacobi_full"] - s0["jacobi_full"],
                      "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"],
                      "push_phase_ms": {k: (s1["push_ns"][i] - s0["push_ns"][i]) / 1e6 for i, k in
-                                       enumerate(["A", "barrier_A", "B", "barrier_B"])}},
+                                       enumerate(["deferred_items", "candidates", "barrier"])}},
         "init_s": init_s,
         "clocks": clk.summary(),
         "err": err,

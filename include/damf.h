@@ -236,7 +236,7 @@ typedef struct {
   int64_t jacobi_sweeps;    /* Jacobi sweeps over all updates */
   int64_t jacobi_full;      /* updates whose core needed sweeps over every pair */
   int64_t jacobi_gersh;     /* updates that needed the exact Gershgorin gap check */
-  int64_t push_ns[4];       /* push time seen by one CTA: phase A, barrier after A, phase B, barrier after B */
+  int64_t push_ns[4];       /* push time seen by one CTA (ns): deferred work items, candidate rows, grid barrier, unused */
 } damf_stats;
 
 /* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */

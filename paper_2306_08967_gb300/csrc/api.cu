@@ -130,9 +130,10 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // YB YC
   s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;        // KU KV KUi KVi
   s[k++] = 4 * dd;                                           // tmp
-  s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // cand0 cand1 front
-  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // work
-  s[k++] = nd;                                               // rho
+  s[k++] = n * 4; s[k++] = n * 4;                            // cand0 cand1
+  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // work0
+  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // work1
+  s[k++] = nd; s[k++] = nd;                                  // rho0 rho1
   s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // stamp pend pstamp
   s[k++] = 2 * (size_t)160 * 160 * 4;                        // gram (room for the init width)
   s[k++] = (size_t)gram_parts_of(cfg) * 160 * 160 * 4;       // gram_part
@@ -325,9 +326,9 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   w.YB = (float*)ptr[k++]; w.YC = (float*)ptr[k++];
   w.KU = (float*)ptr[k++]; w.KV = (float*)ptr[k++]; w.KUi = (float*)ptr[k++]; w.KVi = (float*)ptr[k++];
   w.tmp = (float*)ptr[k++];
-  w.cand[0] = (int32_t*)ptr[k++]; w.cand[1] = (int32_t*)ptr[k++]; w.front = (int32_t*)ptr[k++];
-  w.work = (int4*)ptr[k++]; w.work_cap = work_cap_of(cfg);
-  w.rho = (float*)ptr[k++];
+  w.cand[0] = (int32_t*)ptr[k++]; w.cand[1] = (int32_t*)ptr[k++];
+  w.work[0] = (int4*)ptr[k++]; w.work[1] = (int4*)ptr[k++]; w.work_cap = work_cap_of(cfg);
+  w.rho[0] = (float*)ptr[k++]; w.rho[1] = (float*)ptr[k++];
   w.stamp = (uint32_t*)ptr[k++]; w.pend = (int32_t*)ptr[k++]; w.pstamp = (uint32_t*)ptr[k++];
   w.gram = (float*)ptr[k++]; w.gram_part = (float*)ptr[k++]; w.gram_parts = gram_parts_of(cfg);
   cudaError_t e;

@@ -47,11 +47,12 @@ struct DevHeader {
   int last_rank;
   int last_sweeps;       // Jacobi sweeps of the most recent update
   long long jacobi_sweeps, jacobi_full, jacobi_gersh;
-  unsigned long long push_ns[4];   // block 0: phase A, barrier, phase B, barrier (nanoseconds)   // totals: sweeps, full-mode fallbacks, exact Gershgorin checks
-  // push control (parity-indexed, see ppr.cu)
-  int cand_count[2];
-  int front_count[2];
-  int work_count[2];
+  unsigned long long push_ns[4];   // block 0 of the push: deferred items, candidates, barrier, - (ns)
+  // push control, indexed by round mod 3 (see ppr.cu): rows queued for a round, rho slots and
+  // deferred work items written for it
+  int cand_count[3];
+  int front_count[3];
+  int work_count[3];
   GridBar bar;
 };
 
@@ -94,11 +95,10 @@ struct Workspace {
   float* KVi;
   float* tmp;        // [4 x d x d] scratch for products
   // push
-  int32_t* cand[2];  // [n_cap]
-  int32_t* front;    // [n_cap]
-  int4* work;        // [work_cap] (rho slot, first in-edge, in-edge count, -)
+  int32_t* cand[2];  // [n_cap] rows queued for the next round (by round parity)
+  int4* work[2];     // [work_cap] deferred items (rho slot, first in-edge, in-edge count, -)
   long long work_cap;
-  float* rho;        // [n_cap x d]
+  float* rho[2];     // [n_cap x d] residuals of the deferred (high in-degree) pushes
   uint32_t* stamp;   // [n_cap]
   int32_t* pend;     // [n_cap] rows queued for the next push
   uint32_t* pstamp;  // [n_cap]
