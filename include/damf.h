@@ -64,6 +64,10 @@ typedef struct {
                                GEMMs of the fold, the initialisation and the full query run on
                                the tensor cores (tcgen05, TF32 with a three-term split that keeps
                                FP32 accuracy); the small dense factor update is FP32 in both */
+  int32_t threshold;        /* push threshold: 0 absolute, the push stops when max_j |r[u][j]| <= eps
+                               for all u (then |Z_b - Pi X_b| <= eps elementwise); 1 degree-scaled,
+                               max_j |r[u][j]| <= eps * max(deg(u), 1) with deg the out-degree (the
+                               c of the push cost in Sec. 4.5; |Z_b - Pi X_b| <= eps Pi deg) */
 } damf_config;
 
 /* Workspace the library allocates on the device for `cfg` (bytes).  Lets a caller
@@ -150,6 +154,37 @@ damf_status damf_record_event(damf_ctx* ctx, void* event);
  */
 damf_status damf_get_embeddings(damf_ctx* ctx, const int32_t* rows, int32_t count, float* X, float* Y,
                                 float* Z, float* sigma, void* stream);
+
+/*
+ * Link-prediction scores (Sec. 5, "Link Prediction", and the appendix "Additional Details of
+ * Link Prediction"): the score of the pair (u, v) is the inner product of u's context vector
+ * with v's content vector, Z[u] . Y[v] (context = 0, the PPR-enhanced context) or X[u] . Y[v]
+ * (context = 1), with X, Y, Z as in damf_get_embeddings. symmetric = 1 scores an undirected
+ * pair as the larger of score(u, v) and score(v, u); 0 scores the directed pair (u, v).
+ * Computed from the base state through G = P_U Sigma P_V^T (no n x d buffers).
+ *   src, dst (device) int32[count] node ids; scores (device) float32[count] output.
+ * An id outside [0, n) gives score 0 and DAMF_ERR_INVALID through damf_sync_status.
+ * Waits for the most recent push (see damf_join). DAMF_ERR_INVALID for a bad argument
+ * (count < 0, context or symmetric not 0/1, a NULL array); such a rejection leaves the
+ * context usable.
+ */
+damf_status damf_score_pairs(damf_ctx* ctx, const int32_t* src, const int32_t* dst, int32_t count,
+                             int32_t context, int32_t symmetric, float* scores, void* stream);
+
+/*
+ * Top-k link candidates (the ranking behind precision@K of Sec. 5, "Graph Reconstruction"):
+ * for each query node u = rows[i], the k nodes v != u with the largest score(u, v) (same
+ * score, context and symmetric as damf_score_pairs), in decreasing score; equal scores in
+ * increasing node id.
+ *   rows (device) int32[count]; out_idx (device) int32[count x k] (row-major, -1 where fewer
+ *   than k candidates exist); out_score (device) float32[count x k] (-inf there).
+ *   1 <= k <= 64. Queries run in passes of 32; each pass reads V_b (and the context base for
+ *   symmetric scores) once. An invalid query id gives a row of -1 and DAMF_ERR_INVALID
+ *   through damf_sync_status. A bad argument (k, context, symmetric, NULL arrays) is
+ *   rejected with DAMF_ERR_INVALID and leaves the context usable.
+ */
+damf_status damf_topk(damf_ctx* ctx, const int32_t* rows, int32_t count, int32_t k, int32_t context,
+                      int32_t symmetric, int32_t* out_idx, float* out_score, void* stream);
 
 /*
  * Copies the base state to caller buffers (device), rows 0..n-1: Ub, Vb, Zb, r are

@@ -14,7 +14,10 @@ Contents, each following the cited passage of the paper:
             Eqs. "update", "f_edge", "g_edge", "x_edge", "y_edge").
   ppr.py    PPR (Sec. 4.4, Eq. "ppr"): dense closed form, the literal series,
             power iteration, the graph-change residual fix-up, and the
-            sequential FIFO push (plain C, oracle/c/oracle_graph.c).
+            sequential FIFO push (plain C, oracle/c/oracle_graph.c), with the
+            absolute or the degree-scaled threshold.
+  scoring.py  link-prediction scores and the per-query top-k ranking (Sec. 5,
+            "Link Prediction", "Graph Reconstruction").
 
 Pins (tests/test_oracle_*.py, `-m "not gpu"`): closed-form spectra of cliques,
 stars and cycles; Theorem 2 against the brute-force t-SVD on random tiny graphs;

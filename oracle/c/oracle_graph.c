@@ -143,15 +143,22 @@ static double row_absmax(const double* x, int32_t d) {
  * out-degrees deg(w).  Z and r are n x d row-major.  Returns the number of
  * pushes, or -1 when max_pushes was reached before convergence.
  */
+/* Threshold of node u: eps (absolute) or eps * max(outdeg(u), 1) (degree-scaled). */
+static double push_threshold(const og_graph* out_g, int32_t u, double eps, int32_t deg_scaled) {
+  if (!deg_scaled) return eps;
+  const int32_t k = out_g->len[u];
+  return eps * (double)(k > 1 ? k : 1);
+}
+
 int64_t og_push(const og_graph* in_g, const og_graph* out_g, int32_t d, double* Z, double* r,
-                double alpha, double eps, int64_t max_pushes) {
+                double alpha, double eps, int64_t max_pushes, int32_t deg_scaled) {
   const int32_t n = out_g->n;
   int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
   char* queued = (char*)calloc((size_t)n, 1);
   double* rho = (double*)malloc((size_t)d * sizeof(double));
   int64_t head = 0, count = 0; /* ring buffer of capacity n */
   for (int32_t u = 0; u < n; ++u) {
-    if (row_absmax(r + (size_t)u * d, d) > eps) {
+    if (row_absmax(r + (size_t)u * d, d) > push_threshold(out_g, u, eps, deg_scaled)) {
       queue[(head + count) % n] = u;
       queued[u] = 1;
       count++;
@@ -168,7 +175,7 @@ int64_t og_push(const og_graph* in_g, const og_graph* out_g, int32_t d, double* 
     count--;
     queued[u] = 0;
     double* ru = r + (size_t)u * d;
-    if (row_absmax(ru, d) <= eps) continue;
+    if (row_absmax(ru, d) <= push_threshold(out_g, u, eps, deg_scaled)) continue;
     double* zu = Z + (size_t)u * d;
     for (int32_t j = 0; j < d; ++j) {
       rho[j] = ru[j];
@@ -181,7 +188,7 @@ int64_t og_push(const og_graph* in_g, const og_graph* out_g, int32_t d, double* 
       double c = (1.0 - alpha) / (double)out_g->len[w];
       double* rw = r + (size_t)w * d;
       for (int32_t j = 0; j < d; ++j) rw[j] += c * rho[j];
-      if (!queued[w] && row_absmax(rw, d) > eps) {
+      if (!queued[w] && row_absmax(rw, d) > push_threshold(out_g, w, eps, deg_scaled)) {
         queue[(head + count) % n] = w;
         queued[w] = 1;
         count++;

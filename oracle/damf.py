@@ -51,10 +51,11 @@ def _sqrt_factor(G: np.ndarray, tol: float = 1e-12):
 class DamfOracle:
     def __init__(self, indptr, indices, d: int, alpha: float, eps: float, n_cap: int = None,
                  directed: bool = False, Omega: np.ndarray = None, power_iters: int = 4,
-                 exact_init: bool = False, propagate: bool = True):
+                 exact_init: bool = False, propagate: bool = True, degree_scaled: bool = False):
         n = int(len(indptr) - 1)
         n_cap = n if n_cap is None else n_cap
         self.d, self.alpha, self.eps, self.directed = d, alpha, eps, directed
+        self.degree_scaled = degree_scaled
         self.graph = DynGraph(indptr, indices, n_cap, directed=directed)
         A = sp.csr_matrix((np.ones(len(indices)), np.asarray(indices, dtype=np.int64),
                            np.asarray(indptr, dtype=np.int64)), shape=(n, n))
@@ -78,7 +79,7 @@ class DamfOracle:
         self.pushes = 0
         # line 5: propagation
         if propagate:
-            self.pushes += push(self.graph, self.Zb, self.r, alpha, eps)
+            self.pushes += push(self.graph, self.Zb, self.r, alpha, eps, degree_scaled=degree_scaled)
 
     @property
     def n(self) -> int:
@@ -162,6 +163,6 @@ class DamfOracle:
         return dXb_S
 
     def ppr_refresh(self, max_pushes: int = 1 << 40) -> int:
-        k = push(self.graph, self.Zb, self.r, self.alpha, self.eps, max_pushes)
+        k = push(self.graph, self.Zb, self.r, self.alpha, self.eps, max_pushes, self.degree_scaled)
         self.pushes += k
         return k

@@ -50,7 +50,7 @@ def _load():
         lib.og_num_entries.argtypes = [vp]
         lib.og_export_csr.argtypes = [vp, vp, vp]
         lib.og_push.restype = i64
-        lib.og_push.argtypes = [vp, vp, i32, vp, vp, dbl, dbl, i64]
+        lib.og_push.argtypes = [vp, vp, i32, vp, vp, dbl, dbl, i64, i32]
         _lib = lib
     return _lib
 

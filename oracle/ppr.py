@@ -87,14 +87,19 @@ def graph_change_fixup(r: np.ndarray, Z: np.ndarray, rows_old: dict, rows_new: d
 
 
 def push(graph: DynGraph, Z: np.ndarray, r: np.ndarray, alpha: float, eps: float,
-         max_pushes: int = 1 << 40) -> int:
-    """Sequential FIFO push in place (plain C); returns the number of pushes."""
+         max_pushes: int = 1 << 40, degree_scaled: bool = False) -> int:
+    """Sequential FIFO push in place (plain C); returns the number of pushes.
+
+    Node u is pushed while max_j |r[u][j]| exceeds its threshold: eps, or with degree_scaled
+    eps * max(deg(u), 1) with deg the out-degree (the degree factor c in the push cost of
+    Sec. 4.5, as in the push of InstantGNN that the paper builds on).
+    """
     assert Z.dtype == np.float64 and r.dtype == np.float64
     assert Z.flags.c_contiguous and r.flags.c_contiguous
     assert Z.shape[0] >= graph.n and r.shape[0] >= graph.n
     lib = _load()
     d = Z.shape[1]
-    k = lib.og_push(graph.inn.h, graph.out.h, d, _ptr(Z), _ptr(r), alpha, eps, max_pushes)
+    k = lib.og_push(graph.inn.h, graph.out.h, d, _ptr(Z), _ptr(r), alpha, eps, max_pushes, int(degree_scaled))
     if k < 0:
         raise RuntimeError("push did not converge within max_pushes")
     return int(k)

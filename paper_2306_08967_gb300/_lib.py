@@ -15,7 +15,8 @@ STATUS_NAMES = {0: "DAMF_OK", 1: "DAMF_ERR_INVALID", 2: "DAMF_ERR_CAPACITY", 3: 
 class Config(ctypes.Structure):
     _fields_ = [("n", c_i32), ("n_capacity", c_i32), ("m_capacity", c_i64), ("d", c_i32), ("directed", c_i32),
                 ("alpha", c_f64), ("eps", c_f64), ("refold_every", c_i32), ("rsvd_oversample", c_i32),
-                ("rsvd_power_iters", c_i32), ("max_push_rounds", c_i32), ("precision", c_i32)]
+                ("rsvd_power_iters", c_i32), ("max_push_rounds", c_i32), ("precision", c_i32),
+                ("threshold", c_i32)]
 
 
 class Stats(ctypes.Structure):
@@ -37,6 +38,8 @@ SIGNATURES = {
     "damf_join": (c_i32, [c_vp, c_vp]),
     "damf_record_event": (c_i32, [c_vp, c_vp]),
     "damf_get_embeddings": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "damf_score_pairs": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_i32, c_vp, c_vp]),
+    "damf_topk": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "damf_num_nodes": (c_i32, [c_vp]),
     "damf_core_svd_workspace_size": (c_sz, [c_i32, c_i32]),
     "damf_core_svd": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),

@@ -35,8 +35,10 @@ def _dev(x, dtype):
 
 
 def make_config(n, d, alpha, eps, n_capacity=None, m_capacity=None, nnz=0, directed=False, refold_every=0,
-                rsvd_oversample=10, rsvd_power_iters=4, max_push_rounds=100000, precision="mixed") -> Config:
-    """precision: "fp32" (SIMT everywhere) or "mixed" (tensor-core GEMMs for the fold, init, query)."""
+                rsvd_oversample=10, rsvd_power_iters=4, max_push_rounds=100000, precision="mixed",
+                threshold="absolute") -> Config:
+    """precision: "fp32" (SIMT everywhere) or "mixed" (tensor-core GEMMs for the fold, init, query).
+    threshold: "absolute" (push until max|r[u]| <= eps) or "degree" (until max|r[u]| <= eps max(deg(u), 1))."""
     n_capacity = n if n_capacity is None else n_capacity
     if m_capacity is None:
         # initial rows with 25% slack plus room for relocations and growth
@@ -44,7 +46,8 @@ def make_config(n, d, alpha, eps, n_capacity=None, m_capacity=None, nnz=0, direc
     return Config(n=n, n_capacity=n_capacity, m_capacity=m_capacity, d=d, directed=int(directed), alpha=alpha,
                   eps=eps, refold_every=refold_every, rsvd_oversample=rsvd_oversample,
                   rsvd_power_iters=rsvd_power_iters, max_push_rounds=max_push_rounds,
-                  precision={"fp32": 0, "mixed": 1}[precision])
+                  precision={"fp32": 0, "mixed": 1}[precision],
+                  threshold={"absolute": 0, "degree": 1}[threshold])
 
 
 def rsvd_width(cfg: Config) -> int:
@@ -83,6 +86,7 @@ class DamfGraph:
         self.lib = _lib.load()
         self.cfg = cfg
         self.d = cfg.d
+        self.directed = bool(cfg.directed)
         ip = _dev(indptr, torch.int32)
         ix = _dev(indices, torch.int32) if len(indices) else torch.zeros(1, dtype=torch.int32, device="cuda")
         om = _dev(omega, torch.float32)
@@ -157,6 +161,34 @@ class DamfGraph:
         self._check(self.lib.damf_get_embeddings(self.h, rp, count, ptrs[0], ptrs[1], ptrs[2], sp,
                                                  _stream_ptr(stream)))
         return out
+
+    def score_pairs(self, src, dst, context="Z", symmetric=None, stream=None):
+        """Link-prediction scores context(src[i]) . Y[dst[i]] (context "Z" enhanced or "X");
+        symmetric (default: the graph is undirected) takes the larger of both directions."""
+        src = _dev(src, torch.int32)
+        dst = _dev(dst, torch.int32)
+        count = int(src.numel())
+        if int(dst.numel()) != count:
+            raise ValueError("src and dst differ in length")
+        sym = (not self.directed) if symmetric is None else bool(symmetric)
+        out = torch.empty(count, dtype=torch.float32, device="cuda")
+        self._check(self.lib.damf_score_pairs(self.h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                              count, {"Z": 0, "X": 1}[context], int(sym),
+                                              ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def topk(self, rows, k, context="Z", symmetric=None, stream=None):
+        """The k best-scoring nodes v != u for each query u in rows: (ids int32, scores float32),
+        each count x k, decreasing score, equal scores by increasing id (-1 / -inf padding)."""
+        rows = _dev(rows, torch.int32)
+        count = int(rows.numel())
+        sym = (not self.directed) if symmetric is None else bool(symmetric)
+        idx = torch.empty((count, k), dtype=torch.int32, device="cuda")
+        sc = torch.empty((count, k), dtype=torch.float32, device="cuda")
+        self._check(self.lib.damf_topk(self.h, ctypes.c_void_p(rows.data_ptr()), count, int(k), {"Z": 0, "X": 1}[context],
+                                       int(sym), ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(sc.data_ptr()),
+                                       _stream_ptr(stream)))
+        return idx, sc
 
     def state(self, stream=None) -> dict:
         """Base state: Ub, Vb, Zb, r (n x d), PU, PV (d x d), sigma, s0 (d) as CUDA tensors."""

@@ -72,6 +72,7 @@ bool cfg_ok(const damf_config* cfg) {
   if (cfg->rsvd_oversample < 0 || cfg->rsvd_power_iters < 0 || cfg->max_push_rounds < 1) return false;
   if (cfg->refold_every < 0) return false;
   if (cfg->precision != 0 && cfg->precision != 1) return false;
+  if (cfg->threshold != 0 && cfg->threshold != 1) return false;
   return true;
 }
 
@@ -95,8 +96,15 @@ int gram_parts_of(const damf_config* cfg) {
 }
 
 // Sizes of every device allocation, in order (shared by damf_bytes_required and create).
+// scoring scratch: G, 1/s0, Lq, Rq, query ids, per-CTA top-k keys (256-byte aligned parts)
+size_t score_part(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+size_t score_bytes(size_t d) {
+  return score_part(d * d * 4) + score_part(d * 4) + 2 * score_part((size_t)kTopQ * d * 4) + score_part(kTopQ * 4) +
+         score_part((size_t)kTopMaxCtas * kTopQ * kMaxTopK * 8);
+}
+
 struct Plan {
-  size_t sz[64];
+  size_t sz[96];
   int count;
 };
 
@@ -137,6 +145,7 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // stamp pend pstamp
   s[k++] = 2 * (size_t)160 * 160 * 4;                        // gram (room for the init width)
   s[k++] = (size_t)gram_parts_of(cfg) * 160 * 160 * 4;       // gram_part
+  s[k++] = score_bytes(d);                                   // link-prediction scratch
   p.count = k;
   return p;
 }
@@ -147,6 +156,12 @@ damf_status fail(Ctx* c, damf_status st, const char* what, cudaError_t e) {
     if (st != DAMF_OK && c->sticky == DAMF_OK) c->sticky = st;
   }
   return st;
+}
+
+// A rejected argument of a query: the message is kept, the context stays usable.
+damf_status reject(Ctx* c, const char* what) {
+  snprintf(c->errbuf, sizeof(c->errbuf), "%s", what);
+  return DAMF_ERR_INVALID;
 }
 
 #define DAMF_CUDA(call, what)                                  \
@@ -331,6 +346,16 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   w.rho[0] = (float*)ptr[k++]; w.rho[1] = (float*)ptr[k++];
   w.stamp = (uint32_t*)ptr[k++]; w.pend = (int32_t*)ptr[k++]; w.pstamp = (uint32_t*)ptr[k++];
   w.gram = (float*)ptr[k++]; w.gram_part = (float*)ptr[k++]; w.gram_parts = gram_parts_of(cfg);
+  {
+    char* sp = (char*)ptr[k++];
+    const size_t d = (size_t)cfg->d;
+    w.sG = (float*)sp; sp += score_part(d * d * 4);
+    w.sIs0 = (float*)sp; sp += score_part(d * 4);
+    w.sLq = (float*)sp; sp += score_part((size_t)kTopQ * d * 4);
+    w.sRq = (float*)sp; sp += score_part((size_t)kTopQ * d * 4);
+    w.sQid = (int32_t*)sp; sp += score_part(kTopQ * 4);
+    w.sPart = (unsigned long long*)sp;
+  }
   cudaError_t e;
   unsigned int one = 1;
   if ((e = cudaMemcpyAsync(&c->hdr->epoch, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -473,6 +498,32 @@ damf_status damf_get_embeddings(damf_ctx* x, const int32_t* rows, int32_t count,
   if (count < 0 || (!rows && count > c->n)) return fail(c, DAMF_ERR_INVALID, "count", cudaSuccess);
   DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
   DAMF_CUDA(launch_query(c, rows, count, X, Y, Z, sigma, (cudaStream_t)stream), "query");
+  return DAMF_OK;
+}
+
+damf_status damf_score_pairs(damf_ctx* x, const int32_t* src, const int32_t* dst, int32_t count, int32_t context,
+                             int32_t symmetric, float* scores, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (count < 0 || (context != 0 && context != 1) || (symmetric != 0 && symmetric != 1) ||
+      (count > 0 && (!src || !dst || !scores)))
+    return reject(c, "score_pairs: bad argument");
+  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
+  DAMF_CUDA(launch_score_pairs(c, src, dst, count, context, symmetric, scores, (cudaStream_t)stream), "score_pairs");
+  return DAMF_OK;
+}
+
+damf_status damf_topk(damf_ctx* x, const int32_t* rows, int32_t count, int32_t k, int32_t context, int32_t symmetric,
+                      int32_t* out_idx, float* out_score, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (count < 0 || k < 1 || k > kMaxTopK || (context != 0 && context != 1) || (symmetric != 0 && symmetric != 1) ||
+      (count > 0 && (!rows || !out_idx || !out_score)))
+    return reject(c, "topk: bad argument (1 <= k <= 64, context and symmetric 0 or 1)");
+  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
+  DAMF_CUDA(launch_topk(c, rows, count, k, context, symmetric, out_idx, out_score, (cudaStream_t)stream), "topk");
   return DAMF_OK;
 }
 

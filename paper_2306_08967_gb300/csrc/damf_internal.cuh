@@ -23,6 +23,9 @@ constexpr int kMaxD = 128;
 constexpr int kMaxM = kMaxD + kMaxR;      // 224: largest core
 constexpr int kChainThreads = 512;        // one-CTA chain kernels: leave room beside a push
 constexpr long long kSpinLimit = 1ll << 26;  // iterations of a bounded wait (with nanosleep)
+constexpr int kTopQ = 32;                 // queries per top-k pass (score.cu)
+constexpr int kMaxTopK = 64;              // largest k of damf_topk
+constexpr int kTopMaxCtas = 256;          // top-k scan CTAs at most
 
 // Grid barrier state for persistent cooperative kernels.
 struct GridBar {
@@ -102,6 +105,13 @@ struct Workspace {
   uint32_t* stamp;   // [n_cap]
   int32_t* pend;     // [n_cap] rows queued for the next push
   uint32_t* pstamp;  // [n_cap]
+  // link-prediction scores (score.cu), one region
+  float* sG;         // [d x d] PU diag(sigma) PV^T
+  float* sIs0;       // [d] 1/s0
+  float* sLq;        // [kTopQ x d] query rows times G
+  float* sRq;        // [kTopQ x d] query content rows times G^T
+  int32_t* sQid;     // [kTopQ] query node ids (-1: invalid)
+  unsigned long long* sPart;  // [kTopMaxCtas x kTopQ x kMaxTopK] per-CTA sorted keys
   // fold
   float* gram;       // [2 x d x d] reduced Grams
   float* gram_part;  // [gram_parts x d x d]
@@ -137,7 +147,7 @@ struct Ctx {
   int ev_used;
   double stage_ms[DAMF_NUM_STAGES];
   long long stage_launches[DAMF_NUM_STAGES];
-  void* allocs[64];
+  void* allocs[96];
   int nallocs;
 };
 
@@ -198,6 +208,10 @@ cudaError_t launch_core(Ctx* c, cudaStream_t s);
 cudaError_t launch_transforms(Ctx* c, cudaStream_t s);
 cudaError_t launch_scatter(Ctx* c, cudaStream_t s);
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s);
+cudaError_t launch_score_pairs(Ctx* c, const int32_t* src, const int32_t* dst, int count, int context, int symmetric,
+                               float* scores, cudaStream_t s);
+cudaError_t launch_topk(Ctx* c, const int32_t* rows, int count, int k, int context, int symmetric, int32_t* out_idx,
+                        float* out_score, cudaStream_t s);
 cudaError_t launch_fold(Ctx* c, cudaStream_t s);
 cudaError_t launch_query(Ctx* c, const int32_t* rows, int count, float* X, float* Y, float* Z, float* sigma,
                          cudaStream_t s);

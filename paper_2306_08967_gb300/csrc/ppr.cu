@@ -4,7 +4,9 @@
 // Because Pi = alpha I + (1-alpha) Pi P, pushing node u moves alpha r[u] into Zb[u] and
 // adds (1-alpha) A[w][u] / deg(w) * r[u] to r[w] for every in-neighbour w of u. Any order of
 // pushes keeps the invariant. The push stops when no row has max_j |r[u][j]| > eps; then
-// |Zb - Pi X_b| <= eps elementwise since Pi is row-substochastic.
+// |Zb - Pi X_b| <= eps elementwise since Pi is row-substochastic. With the degree-scaled
+// threshold (damf_config.threshold = 1) the eps of row u reads eps * max(deg(u), 1), deg the
+// out-degree, and the bound becomes |Zb - Pi X_b|[i] <= (Pi t)[i] for those thresholds t.
 //
 // One persistent cooperative launch runs all rounds, with one bounded grid barrier per round.
 // Round k works on
@@ -79,23 +81,30 @@ __device__ __forceinline__ void enqueue(int w, unsigned tag, uint32_t* stamp, in
   }
 }
 
+// Threshold of a node with out-degree deg: eps, or eps * max(deg, 1) when SCALED.
+template <bool SCALED>
+__device__ __forceinline__ float threshold(float eps, int deg) {
+  return SCALED ? eps * (float)max(deg, 1) : eps;
+}
+
 // One chunk of a scatter by a row group: lane q < ne owns in-edge col[st + q] (node w) and
 // its coefficient (1-alpha)/deg(w); every lane adds coef * rv to its float4 of r[w] for each
 // of the ne in-edges, all atomics in flight before any result is looked at. A w that an add
-// left above eps is queued for the next round. Every lane of the warp calls this; a group
-// with nothing to do passes ne = 0.
-template <int D>
+// left above its threshold is queued for the next round. Every lane of the warp calls this;
+// a group with nothing to do passes ne = 0.
+template <int D, bool SCALED>
 __device__ __forceinline__ void scatter_chunk(const float4 rv, int st, int ne, const int32_t* __restrict__ col,
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
                                               unsigned tag, uint32_t* stamp, int* next_count, int32_t* next_list,
                                               int q, int sub, unsigned sub_mask) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int CH = PushShape<D>::CH;
-  int w_own = 0;
+  int w_own = 0, d_own = 1;
   float c_own = 0.f;
   if (q < ne) {
     w_own = __ldg(col + st + q);
-    c_own = beta / (float)__ldg(outdeg + w_own);
+    d_own = __ldg(outdeg + w_own);
+    c_own = beta / (float)d_own;
   }
   float4 nv[CH];
 #pragma unroll
@@ -111,14 +120,16 @@ __device__ __forceinline__ void scatter_chunk(const float4 rv, int st, int ne, c
   }
   unsigned crossed_bits = 0;
 #pragma unroll
-  for (int e = 0; e < CH; ++e)
-    if (__ballot_sync(0xffffffffu, max_abs4(nv[e]) > eps) & sub_mask) crossed_bits |= 1u << e;
+  for (int e = 0; e < CH; ++e) {
+    const float thr = SCALED ? __shfl_sync(0xffffffffu, threshold<true>(eps, d_own), sub * LPR + e) : eps;
+    if (__ballot_sync(0xffffffffu, max_abs4(nv[e]) > thr) & sub_mask) crossed_bits |= 1u << e;
+  }
   if (q < ne && ((crossed_bits >> q) & 1u)) enqueue(w_own, tag, stamp, next_count, next_list);
 }
 
 // 64 registers at most (min. 4 CTAs' worth per SM): two push CTAs (32k registers) then leave room
 // on every SM for the 768-thread core SVD CTA of the next update, which runs beside the push
-template <int D>
+template <int D, bool SCALED>
 __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
                                                  float* Zb, float* r, int n, float alpha, float eps, int max_rounds,
                                                  int check_all, int direct_max) {
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         wi = __ldcg(work_in + it);
         rv = f4_ldcg(rho_in + (size_t)wi.x * D + 4 * q);
       }
-      scatter_chunk<D>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
+      scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
                        sub_mask);
     }
     if (timer) time_mark(s_t, 0);
@@ -185,14 +196,16 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       const bool valid = ci < ncand;
       const int u = valid ? (cand ? __ldcg(cand + ci) : (int)ci) : 0;
       float4 v = zero4, z = zero4;
-      int st = 0, deg = 0;
+      int st = 0, deg = 0, dout = 1;
       if (valid) {   // everything that depends only on u is requested at once
         v = f4_ldcg(r + (size_t)u * D + 4 * q);
         z = f4_ldcg(Zb + (size_t)u * D + 4 * q);
         st = in.start[u];
         deg = in.len[u];
+        if (SCALED) dout = __ldg(outdeg + u);
       }
-      const bool push = group_max<LPR>(max_abs4(v)) > eps && valid;
+      const float thr_u = threshold<SCALED>(eps, dout);
+      const bool push = group_max<LPR>(max_abs4(v)) > thr_u && valid;
       float lm = 0.f;   // max |r[u]| right after the removal of v (over this lane's float4)
       if (push) {
         const float4 old =
@@ -245,12 +258,12 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       for (int c2 = 0; c2 < nmax; ++c2) {
         const int e0 = c2 * CH;
         const int ne = c2 < ndir ? min(CH, deg - e0) : 0;
-        scatter_chunk<D>(v, st + e0, ne, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
+        scatter_chunk<D, SCALED>(v, st + e0, ne, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
                          sub_mask);
       }
       // u itself: adds that reached r[u] between the read of v and its removal are still there
       lm = group_max<LPR>(lm);
-      if (push && q == 0 && lm > eps) enqueue(u, tag, ws.stamp, next_count, next_list);
+      if (push && q == 0 && lm > thr_u) enqueue(u, tag, ws.stamp, next_count, next_list);
     }
     if (timer) time_mark(s_t, 1);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
@@ -277,16 +290,17 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   }
 }
 
-template <int D>
+template <int D, bool SCALED>
 static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   if (c->push_blocks == 0) {
     // two CTAs per SM: leaves registers, threads and shared memory on every SM for the
     // one-CTA kernels of the next update's factor chain, which overlap the push
-    cudaFuncSetAttribute(k_push<D>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_push<D, SCALED>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D, SCALED>, 256, 0);
     int cap = kPushBlocksPerSM;
     if (const char* ev = getenv("DAMF_PUSH_CTAS_PER_SM")) {
       const int v = atoi(ev);
@@ -313,16 +327,21 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   int max_rounds = c->cfg.max_push_rounds;
   int direct_max = chunks * PushShape<D>::CH;
   void* args[] = {&h, &in, &outdeg, &ws, &Zb, &r, &n, &alpha, &eps, &max_rounds, &check_all, &direct_max};
-  return cudaLaunchCooperativeKernel((void*)k_push<D>, dim3(c->push_blocks), dim3(256), args, 0, s);
+  return cudaLaunchCooperativeKernel((void*)k_push<D, SCALED>, dim3(c->push_blocks), dim3(256), args, 0, s);
+}
+
+template <bool SCALED>
+static cudaError_t push_dispatch(Ctx* c, int check_all, cudaStream_t s) {
+  switch (c->d) {
+    case 16: return push_impl<16, SCALED>(c, check_all, s);
+    case 32: return push_impl<32, SCALED>(c, check_all, s);
+    case 64: return push_impl<64, SCALED>(c, check_all, s);
+    default: return push_impl<128, SCALED>(c, check_all, s);
+  }
 }
 
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s) {
-  switch (c->d) {
-    case 16: return push_impl<16>(c, check_all, s);
-    case 32: return push_impl<32>(c, check_all, s);
-    case 64: return push_impl<64>(c, check_all, s);
-    default: return push_impl<128>(c, check_all, s);
-  }
+  return c->cfg.threshold ? push_dispatch<true>(c, check_all, s) : push_dispatch<false>(c, check_all, s);
 }
 
 }  // namespace damf

@@ -41,6 +41,10 @@ def test_host_side_config_checks():
     assert bytes_required(bad) == 0
     bad = make_config(1000, 16, 0.0, 1e-4)           # alpha in (0, 1]
     assert bytes_required(bad) == 0
+    bad = make_config(1000, 16, 0.15, 1e-4)
+    bad.threshold = 2                                # 0 absolute, 1 degree-scaled
+    assert bytes_required(bad) == 0
+    assert bytes_required(make_config(1000, 16, 0.15, 1e-4, threshold="degree")) > 0
     # the C2 workload fits easily in a GB300's HBM
     c2 = make_config(200_000, 128, 0.15, 1e-5, n_capacity=250_000, nnz=2_000_000)
     assert bytes_required(c2) < 2 << 30
@@ -56,3 +60,5 @@ def test_init_rejects_bad_arguments_without_gpu_work():
     assert st == 1 and not h.value                   # DAMF_ERR_INVALID, nothing created
     assert lib.damf_apply_edges(None, None, None, None, 0, 0, None) == 1
     assert lib.damf_ppr_refresh(None, None) == 1
+    assert lib.damf_score_pairs(None, None, None, 0, 0, 0, None, None) == 1
+    assert lib.damf_topk(None, None, 0, 1, 0, 0, None, None, None) == 1

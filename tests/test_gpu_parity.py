@@ -1,6 +1,6 @@
 """CUDA path (through the C ABI) against the FP64 oracle and the paper's definitions.
 
-Tolerances (FP32 device arithmetic, derived in the design doc):
+Tolerances (from the FP32 device arithmetic: unit roundoff 6e-8 grown over the d-term sums and sweeps):
   * integer work (adjacency, touched sets S/T): bit-exact
   * one update vs the brute-force t-SVD of (previous product + dA) (Theorem 2):
     sigma rel 2e-4, X Y^T rel Frobenius 2e-4
@@ -126,6 +126,38 @@ def test_ppr_within_eps_of_exact(directed):
         exact = ppr_matrix_dense(A, alpha) @ Xb
         assert np.abs(r).max() <= eps
         assert np.abs(Zb - exact).max() <= eps * (1 + 1e-3) + 2e-6 * np.abs(Xb).max()
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_degree_scaled_threshold_bound(directed):
+    # threshold eps * max(deg(u), 1): every residual ends below its own threshold and
+    # |Zb - Pi Xb|[i] <= (Pi t)[i] for the thresholds t (FP32 slack as in the absolute test)
+    rng = np.random.default_rng(21)
+    n, d, alpha, eps = 500, 16, 0.15, 1e-4
+    g, _, _ = make_pair(n, 8.0, 2.5, d, alpha, eps, SEED + 17, directed=directed, oracle=False,
+                        threshold="degree")
+    above_eps = False
+    for step in range(5):
+        if step:
+            src, dst, op = _events(rng, n, 20)
+            g.apply_edges(src, dst, op)
+            g.ppr_refresh()
+        g.check()
+        st = g.state()
+        Xb = (st["Ub"] * st["s0"]).double().cpu().numpy()
+        Zb = st["Zb"].double().cpu().numpy()
+        r = st["r"].double().cpu().numpy()
+        rp, col = g.adjacency()
+        A = dense_adj(rp, col, g.n)
+        thr = eps * np.maximum(A.sum(axis=1), 1.0)
+        rmax = np.abs(r[: g.n]).max(axis=1)
+        assert np.all(rmax <= thr * (1 + 1e-6))
+        above_eps |= bool(np.any(rmax > eps))
+        Pi = ppr_matrix_dense(A, alpha)
+        err = np.abs(Zb - Pi @ Xb).max(axis=1)
+        assert np.all(err <= (Pi @ thr) * (1 + 1e-3) + 2e-6 * np.abs(Xb).max())
+    assert above_eps
     g.close()
 
 

@@ -60,6 +60,49 @@ def test_push_within_eps_of_exact(directed):
     np.testing.assert_allclose(Z + Pi @ r, exact, atol=1e-12)
 
 
+@pytest.mark.parametrize("directed", [False, True])
+def test_degree_scaled_push_bound(directed):
+    # threshold eps * max(deg(u), 1): every residual ends below its own threshold, the
+    # invariant Pi X = Z + Pi r still holds, so |Z - Pi X|[i] <= (Pi t)[i] with t the thresholds
+    rng = np.random.default_rng(18)
+    A = _graph_with_dangling(rng, 60, directed)
+    indptr, indices = csr_of_dense(A)
+    g = DynGraph(indptr, indices, 60, directed=directed)
+    X = rng.standard_normal((60, 4))
+    eps, alpha = 1e-4, 0.15
+    Z = np.zeros_like(X)
+    r = X.copy()
+    k = push(g, Z, r, alpha, eps, degree_scaled=True)
+    thr = eps * np.maximum(A.sum(axis=1), 1.0)
+    assert k > 0 and np.all(np.abs(r).max(axis=1) <= thr)
+    assert np.any(np.abs(r).max(axis=1) > eps)          # the scaled threshold was used somewhere
+    Pi = ppr_matrix_dense(A, alpha)
+    np.testing.assert_allclose(Z + Pi @ r, Pi @ X, atol=1e-12)
+    assert np.all(np.abs(Z - Pi @ X).max(axis=1) <= (Pi @ thr) * (1 + 1e-9))
+
+
+def test_degree_scaled_push_is_absolute_push_at_constant_out_degree():
+    # every node has out-degree 2 (in-degrees vary): the scaled push with eps / 2 takes the same
+    # decisions in the same order as the absolute push with eps, so the results are identical
+    rng = np.random.default_rng(19)
+    n = 40
+    A = np.zeros((n, n))
+    for u in range(n):
+        A[u, rng.choice([v for v in range(n) if v != u], size=2, replace=False)] = 1.0
+    assert len(set(A.sum(axis=0))) > 1
+    indptr, indices = csr_of_dense(A)
+    X = rng.standard_normal((n, 3))
+    out = []
+    for eps, scaled in ((1e-5, False), (0.5e-5, True)):
+        g = DynGraph(indptr, indices, n, directed=True)
+        Z, r = np.zeros_like(X), X.copy()
+        k = push(g, Z, r, 0.2, eps, degree_scaled=scaled)
+        out.append((k, Z, r))
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
 def test_alpha_one_gives_identity():
     # the paper's ablation (Sec. 5.6): alpha = 1 means no enhancement, Z = X exactly
     rng = np.random.default_rng(9)
