@@ -143,6 +143,44 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU leg
+def measure_scoring(g, c, torch):
+    """Link-prediction queries on the final state (Sec. 5): damf_score_pairs over 2^20 random
+    pairs and damf_topk for 256 queries with k = 64, both with the enhanced context Z and
+    symmetric scores on an undirected graph; inputs on the device, CUDA events."""
+    n, d = g.n, c.d
+    sym = not c.directed
+    rng = np.random.default_rng(c.seed + 5)
+    src = torch.from_numpy(rng.integers(0, n, 1 << 20).astype(np.int32)).cuda()
+    dst = torch.from_numpy(rng.integers(0, n, 1 << 20).astype(np.int32)).cuda()
+    rows = torch.from_numpy(rng.integers(0, n, 256).astype(np.int32)).cuda()
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_p = timed(lambda: g.score_pairs(src, dst, symmetric=sym))
+    ms_t = timed(lambda: g.topk(rows, 64, symmetric=sym))
+    g.check()
+    npairs = int(src.numel())
+    dirs = 2 if sym else 1
+    passes = (int(rows.numel()) + 31) // 32
+    return {
+        "score_pairs": {"pairs": npairs, "ms": ms_p, "pairs_per_s": npairs / (ms_p / 1e3),
+                        "fp32_tflops": npairs * dirs * 2 * (d * d + d) / (ms_p / 1e3) / 1e12},
+        "topk": {"queries": int(rows.numel()), "k": 64, "ms": ms_t, "queries_per_s": rows.numel() / (ms_t / 1e3),
+                 "scan_gb_per_s": passes * dirs * n * d * 4 / (ms_t / 1e3) / 1e9,
+                 "fp32_tflops": rows.numel() * n * dirs * 2 * d / (ms_t / 1e3) / 1e12},
+    }
+
+
 def run_ours(args, c, rank, world):
     import torch
     from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
@@ -265,6 +303,7 @@ def run_ours(args, c, rank, world):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_launch": push_bytes / max(push_launches, 1), "ms_per_launch": push_ms_per}
     launches = s1["launches"] - s0["launches"]
+    scoring = measure_scoring(g, c, torch) if args.scoring else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -283,6 +322,7 @@ def run_ours(args, c, rank, world):
         "roofline": roof,
         "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
         "dominant_stage": dominant,
+        "scoring": scoring,
         "counters": {"pushes": pushes, "push_edges": push_edges, "updates": s1["updates"] - s0["updates"],
                      "push_rounds": s1["push_rounds"] - s0["push_rounds"],
                      "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"],
@@ -290,7 +330,7 @@ def run_ours(args, c, rank, world):
                      "jacobi_full": s1["jacobi_full"] - s0["jacobi_full"],
                      "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"],
                      "push_phase_ms": {k: (s1["push_ns"][i] - s0["push_ns"][i]) / 1e6 for i, k in
-                                       enumerate(["deferred_items", "candidates", "barrier"])}},
+                                       enumerate(["seeding", "task_loop", "barriers"])}},
         "init_s": init_s,
         "clocks": clk.summary(),
         "err": err,
@@ -313,6 +353,8 @@ def main():
     ap.add_argument("--no-compare-precision", dest="compare_precision", action="store_false",
                     help="skip timing the other precision build of the path on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scoring", dest="scoring", action="store_false",
+                    help="skip the link-prediction query timing (score_pairs, topk) after the run")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)

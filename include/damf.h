@@ -43,7 +43,7 @@ typedef enum {
   DAMF_ERR_CUDA = 3,           /* a CUDA runtime call failed; damf_last_error() has the text */
   DAMF_ERR_NUMERIC = 4,        /* non-finite value in Sigma, a transform or a residual factor */
   DAMF_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
-  DAMF_ERR_NOT_CONVERGED = 6   /* the PPR push hit max_push_rounds before every residual was <= eps */
+  DAMF_ERR_NOT_CONVERGED = 6   /* the PPR push hit max_push_rounds phases before every residual was <= eps */
 } damf_status;
 
 typedef struct {
@@ -59,7 +59,8 @@ typedef struct {
   int32_t refold_every;     /* fold the transforms into the bases every this many updates; 0 = never */
   int32_t rsvd_oversample;  /* randomized t-SVD: l = round_up(d + rsvd_oversample, 32) test vectors */
   int32_t rsvd_power_iters; /* randomized t-SVD power iterations q */
-  int32_t max_push_rounds;  /* cap on frontier rounds per damf_ppr_refresh */
+  int32_t max_push_rounds;  /* cap on push phases per damf_ppr_refresh (a phase runs the work queue
+                               until it drains; another follows only when the queue overflowed) */
   int32_t precision;        /* 0: plain FP32 (SIMT for every kernel); 1: mixed, the n x d by d x d
                                GEMMs of the fold, the initialisation and the full query run on
                                the tensor cores (tcgen05, TF32 with a three-term split that keeps
@@ -122,12 +123,13 @@ damf_status damf_apply_edges_host(damf_ctx* ctx, const int32_t* src, const int32
                                   int32_t k, int32_t new_nodes, void* stream);
 
 /*
- * Dynamic embedding enhancement (Sec. 4.4; Algorithm 2, last step): frontier push
- * rounds on the current graph until max_j |r[u][j]| <= eps for every u, keeping the
- * invariant  Pi X_b = Z_b + Pi r  with Pi = alpha (I - (1-alpha) D^{-1} A)^{-1}, so
- * that |Z_b - Pi X_b| <= eps elementwise.  One persistent launch; frontier sizes stay
- * on the device.  DAMF_ERR_NOT_CONVERGED (via damf_sync_status) when
- * max_push_rounds is reached; DAMF_ERR_TIMEOUT when a grid barrier wait runs out.
+ * Dynamic embedding enhancement (Sec. 4.4; Algorithm 2, last step): pushes on the current
+ * graph until max_j |r[u][j]| <= eps for every u (eps * max(deg(u), 1) with the
+ * degree-scaled threshold), keeping the invariant  Pi X_b = Z_b + Pi r  with
+ * Pi = alpha (I - (1-alpha) D^{-1} A)^{-1}, so that |Z_b - Pi X_b| <= eps elementwise.
+ * One persistent launch over a device work queue seeded with the rows whose residual
+ * changed since the last push.  DAMF_ERR_NOT_CONVERGED (via damf_sync_status) when
+ * max_push_rounds phases did not finish; DAMF_ERR_TIMEOUT when a bounded wait runs out.
  */
 damf_status damf_ppr_refresh(damf_ctx* ctx, void* stream);
 
@@ -259,7 +261,7 @@ typedef struct {
   int64_t entries_changed;  /* net adjacency entries changed (set semantics) */
   int64_t pushes;           /* node pushes (rows moved from r to Z_b) */
   int64_t push_edges;       /* in-edges traversed by pushes */
-  int64_t push_rounds;      /* frontier rounds */
+  int64_t push_rounds;      /* push phases (1 per push unless the work queue overflowed) */
   int64_t fixup_edges;      /* adjacency entries gathered by the graph-change fix-up */
   int64_t touched_rows;     /* sum over updates of |S| + |T| */
   int64_t folds;            /* refolds of the transforms into the bases */
@@ -271,7 +273,7 @@ typedef struct {
   int64_t jacobi_sweeps;    /* Jacobi sweeps over all updates */
   int64_t jacobi_full;      /* updates whose core needed sweeps over every pair */
   int64_t jacobi_gersh;     /* updates that needed the exact Gershgorin gap check */
-  int64_t push_ns[4];       /* push time seen by one CTA (ns): deferred work items, candidate rows, grid barrier, unused */
+  int64_t push_ns[4];       /* push time seen by one CTA (ns): seeding, task loop, grid barriers, unused */
 } damf_stats;
 
 /* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */

@@ -85,7 +85,13 @@ int width_of(const damf_config* cfg) {
 }
 
 long long work_cap_of(const damf_config* cfg) {
-  return (long long)cfg->n_capacity + cfg->m_capacity / 4 + 64;   // items hold >= 4 in-edges
+  return 2 * ((long long)cfg->n_capacity + cfg->m_capacity / 4 + 64);   // hub items of one push
+}
+
+// push queue positions of one phase (a phase that needs more rescans every row)
+long long qcap_of(const damf_config* cfg) {
+  long long q = 4ll * cfg->n_capacity + (1ll << 20);
+  return q > 0x7fffff00ll ? 0x7fffff00ll : q;
 }
 
 int gram_parts_of(const damf_config* cfg) {
@@ -138,10 +144,9 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // YB YC
   s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;        // KU KV KUi KVi
   s[k++] = 4 * dd;                                           // tmp
-  s[k++] = n * 4; s[k++] = n * 4;                            // cand0 cand1
-  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // work0
-  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // work1
-  s[k++] = nd; s[k++] = nd;                                  // rho0 rho1
+  s[k++] = (size_t)qcap_of(cfg) * 4;                         // push queue
+  s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // hub items
+  s[k++] = 2 * nd;                                           // rho (2 n_cap slots)
   s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // stamp pend pstamp
   s[k++] = 2 * (size_t)160 * 160 * 4;                        // gram (room for the init width)
   s[k++] = (size_t)gram_parts_of(cfg) * 160 * 160 * 4;       // gram_part
@@ -341,9 +346,9 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   w.YB = (float*)ptr[k++]; w.YC = (float*)ptr[k++];
   w.KU = (float*)ptr[k++]; w.KV = (float*)ptr[k++]; w.KUi = (float*)ptr[k++]; w.KVi = (float*)ptr[k++];
   w.tmp = (float*)ptr[k++];
-  w.cand[0] = (int32_t*)ptr[k++]; w.cand[1] = (int32_t*)ptr[k++];
-  w.work[0] = (int4*)ptr[k++]; w.work[1] = (int4*)ptr[k++]; w.work_cap = work_cap_of(cfg);
-  w.rho[0] = (float*)ptr[k++]; w.rho[1] = (float*)ptr[k++];
+  w.queue = (int32_t*)ptr[k++]; w.qcap = qcap_of(cfg);
+  w.work = (int4*)ptr[k++]; w.work_cap = work_cap_of(cfg);
+  w.rho = (float*)ptr[k++]; w.rho_cap = 2ll * cfg->n_capacity;
   w.stamp = (uint32_t*)ptr[k++]; w.pend = (int32_t*)ptr[k++]; w.pstamp = (uint32_t*)ptr[k++];
   w.gram = (float*)ptr[k++]; w.gram_part = (float*)ptr[k++]; w.gram_parts = gram_parts_of(cfg);
   {
@@ -359,6 +364,7 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   cudaError_t e;
   unsigned int one = 1;
   if ((e = cudaMemcpyAsync(&c->hdr->epoch, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.queue, 0xff, (size_t)w.qcap * 4, s)) != cudaSuccess ||   // empty slots: -1
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_all(c);
     free(x);

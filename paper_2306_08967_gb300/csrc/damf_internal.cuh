@@ -50,12 +50,14 @@ struct DevHeader {
   int last_rank;
   int last_sweeps;       // Jacobi sweeps of the most recent update
   long long jacobi_sweeps, jacobi_full, jacobi_gersh;
-  unsigned long long push_ns[4];   // block 0 of the push: deferred items, candidates, barrier, - (ns)
-  // push control, indexed by round mod 3 (see ppr.cu): rows queued for a round, rho slots and
-  // deferred work items written for it
-  int cand_count[3];
-  int front_count[3];
-  int work_count[3];
+  unsigned long long push_ns[4];   // block 0 of the push: seeding, task loop, barriers, - (ns)
+  // push work queue (ppr.cu), zeroed before each launch: qstate = (tasks not finished << 32) |
+  // queue tail; q_head = next queue position to claim; bump counters of rho slots and items
+  unsigned long long qstate;
+  int q_head;
+  int overflow;
+  int rho_tail;
+  int item_tail;
   GridBar bar;
 };
 
@@ -98,11 +100,13 @@ struct Workspace {
   float* KVi;
   float* tmp;        // [4 x d x d] scratch for products
   // push
-  int32_t* cand[2];  // [n_cap] rows queued for the next round (by round parity)
-  int4* work[2];     // [work_cap] deferred items (rho slot, first in-edge, in-edge count, -)
+  int32_t* queue;    // [qcap] push tasks: row id >= 0, item i as -(i + 2), -1 empty
+  long long qcap;
+  int4* work;        // [work_cap] hub items (rho slot, first in-edge, in-edge count, -)
   long long work_cap;
-  float* rho[2];     // [n_cap x d] residuals of the deferred (high in-degree) pushes
-  uint32_t* stamp;   // [n_cap]
+  float* rho;        // [rho_cap x d] residuals of the hub pushes
+  long long rho_cap;
+  uint32_t* stamp;   // [n_cap] 1 while the row is in the push queue
   int32_t* pend;     // [n_cap] rows queued for the next push
   uint32_t* pstamp;  // [n_cap]
   // link-prediction scores (score.cu), one region

@@ -478,9 +478,10 @@ cudaError_t build_adjacency(Ctx* c, Adj* a, const int32_t* row_ptr, const int32_
   if (!transpose) {
     k_copy_rows<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, a->col);
   } else {
-    int32_t* fillpos = c->ws.cand[1];  // n_cap ints of scratch, unused until the first push
+    int32_t* fillpos = c->ws.queue;  // >= n ints of scratch, unused until the first push
     cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * (size_t)n, s);
     k_in_fill<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, fillpos, a->col);
+    cudaMemsetAsync(fillpos, 0xff, sizeof(int32_t) * (size_t)n, s);   // empty queue slots again
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);

@@ -1,29 +1,33 @@
-// Dynamic embedding enhancement (Sec. 4.4; Step 4 of Sec. 4.5): PPR push rounds.
+// Dynamic embedding enhancement (Sec. 4.4; Step 4 of Sec. 4.5): the PPR push.
 //
 // State (Zb, r) keeps  Pi X_b = Zb + Pi r  with P = D^{-1} A, Pi = alpha (I - (1-alpha) P)^{-1}.
-// Because Pi = alpha I + (1-alpha) Pi P, pushing node u moves alpha r[u] into Zb[u] and
-// adds (1-alpha) A[w][u] / deg(w) * r[u] to r[w] for every in-neighbour w of u. Any order of
-// pushes keeps the invariant. The push stops when no row has max_j |r[u][j]| > eps; then
-// |Zb - Pi X_b| <= eps elementwise since Pi is row-substochastic. With the degree-scaled
-// threshold (damf_config.threshold = 1) the eps of row u reads eps * max(deg(u), 1), deg the
-// out-degree, and the bound becomes |Zb - Pi X_b|[i] <= (Pi t)[i] for those thresholds t.
+// Because Pi = alpha I + (1-alpha) Pi P, pushing any vector x out of r[u] (r[u] -= x,
+// Zb[u] += alpha x, r[w] += (1-alpha) A[w][u] / deg(w) x for every in-neighbour w of u) keeps
+// the invariant, whatever the order and whatever x. The push stops when no row has
+// max_j |r[u][j]| > eps; then |Zb - Pi X_b| <= eps elementwise since Pi is row-substochastic.
+// With the degree-scaled threshold (damf_config.threshold = 1) the eps of row u reads
+// eps * max(deg(u), 1), deg the out-degree, and |Zb - Pi X_b|[i] <= (Pi t)[i] for those t.
 //
-// One persistent cooperative launch runs all rounds, with one bounded grid barrier per round.
-// Round k works on
-//   - the candidates queued for it (rows whose residual may exceed eps). A row group reads
-//     v = r[u]; if max|v| > eps it removes exactly v with a float4 atomic add of -v (adds of
-//     other pushes of the same round may land before or after it; both stay accounted for),
-//     adds alpha v to Zb[u], and scatters coef * v to the in-neighbours of u itself when u
-//     has few in-edges. For more, v goes to a rho slot and u's in-edges are cut into work
-//     items for round k+1, which spreads a hub's in-edges over every warp;
-//   - the work items that round k-1 deferred to it.
-// Every atomic add returns the old value, so the thread whose add (or removal) is the last
-// one on an element sees the value the round leaves there; a row left above eps is queued
-// once (per-round stamp) for round k+1. When round k queues no row and no item, no row
-// exceeds eps.
-// Lists and rho are double-buffered by round parity; their counters are indexed by round
-// mod 3, so block 0 resets the counters of round k+2 while those of rounds k and k+1 are
-// in use.
+// One persistent cooperative launch, no rounds: a FIFO work queue of tasks in HBM.
+//   * task "row u": clear u's in-queue flag, read v = r[u]; if max|v| > eps, remove exactly v
+//     (float4 atomic add of -v), add alpha v to Zb[u] (atomic), and scatter coef * v to the
+//     in-neighbours of u; a row with many in-edges (a hub) instead stores v in a rho slot and
+//     queues one "item" task per chunk of its in-edges, which spreads it over every warp.
+//   * task "item": scatter a hub's stored v to one chunk of its in-edges.
+// Every add returns the old value, so the thread whose add (or removal) is the last on an
+// element sees what it leaves there; a row left above eps is queued unless its flag says it
+// already is. The flag is cleared before the row is read, so an add that lands after that read
+// queues the row again. A row can thus be pushed by two warps at once; all changes to r and
+// Zb are atomic adds, so both pushes count.
+// Termination: qstate holds (unfinished tasks << 32) | tail in one 64-bit word. A task is
+// counted before it is published and uncounted in the same atomic that counts the tasks it
+// queued (or later), so the count reaches 0 only when no task is queued or running. A warp
+// claims kClaim positions at a time (q_head), keeps the tasks it queues in a shared-memory
+// buffer, and publishes them (one atomic, release stores) after each claim and before it
+// waits for an empty slot; it leaves when the count is 0.
+// The queue does not wrap within a phase. When it is full, rows stay flagged and unqueued and
+// the overflow flag is set; after the phase every row is cleared and checked again.
+// Every wait is bounded (kSpinLimit with __nanosleep; DAMF_ERR_TIMEOUT).
 #include <stdlib.h>
 
 #include "damf_internal.cuh"
@@ -34,9 +38,12 @@ namespace damf {
 // the one-CTA kernels of the next update's factor chain (overridable for tuning with the
 // environment variable DAMF_PUSH_CTAS_PER_SM).
 constexpr int kPushBlocksPerSM = 2;
-// A pushing row group scatters to at most this many chunks of in-edges itself; rows with
-// more in-edges are deferred as work items (overridable with DAMF_PUSH_DIRECT_CHUNKS).
-constexpr int kPushDirectChunks = 1;
+// A row with more than this many chunks of in-edges is a hub: its chunks become item tasks
+// (overridable with DAMF_PUSH_DIRECT_CHUNKS).
+constexpr int kPushDirectChunks = 8;
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kTask = 1ull << 32;   // one unfinished task in qstate
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -57,236 +64,367 @@ __device__ __forceinline__ float max_abs4(float4 v) {
   return fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
 }
 
-// in-edges per chunk: one per lane of a row group, at most 8
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// A warp runs one task at a time. A row of D floats is held by a row group of LPR lanes (a
+// float4 each); each of the RPW groups holds the same row and takes its own in-edges, CHL at
+// a time, so a chunk is EPC = RPW * CHL in-edges (one owner lane per in-edge).
 template <int D>
 struct PushShape {
-  static constexpr int LPR = D / 4;                 // lanes per row (float4 each)
-  static constexpr int RPW = 32 / LPR;              // row groups per warp
-  static constexpr int CH = LPR < 8 ? LPR : 8;      // in-edges per chunk
+  static constexpr int LPR = D / 4;
+  static constexpr int RPW = 32 / LPR;
+  static constexpr int CHL = RPW <= 4 ? 8 : 4;
+  static constexpr int EPC = RPW * CHL;   // 8, 16, 32, 32 for D = 128, 64, 32, 16
 };
 
 // maximum over the LPR lanes of a row group (every lane of the warp takes part)
 template <int LPR>
 __device__ __forceinline__ float group_max(float m) {
 #pragma unroll
-  for (int o = 1; o < LPR; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 1; o < LPR; o <<= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
   return m;
 }
 
-// queues w for the next round unless this round already has
-__device__ __forceinline__ void enqueue(int w, unsigned tag, uint32_t* stamp, int* count, int32_t* list) {
-  if (atomicExch(stamp + w, tag) != tag) {
-    const int p = atomicAdd(count, 1);
-    __stcg(list + p, w);
-  }
-}
-
-// Threshold of a node with out-degree deg: eps, or eps * max(deg, 1) when SCALED.
 template <bool SCALED>
 __device__ __forceinline__ float threshold(float eps, int deg) {
   return SCALED ? eps * (float)max(deg, 1) : eps;
 }
 
-// One chunk of a scatter by a row group: lane q < ne owns in-edge col[st + q] (node w) and
-// its coefficient (1-alpha)/deg(w); every lane adds coef * rv to its float4 of r[w] for each
-// of the ne in-edges, all atomics in flight before any result is looked at. A w that an add
-// left above its threshold is queued for the next round. Every lane of the warp calls this;
-// a group with nothing to do passes ne = 0.
+__device__ __forceinline__ unsigned exch_acq_rel(uint32_t* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.exch.acq_rel.gpu.global.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr int kQBuf = 256;    // per-warp buffer of tasks to publish (shared memory)
+constexpr int kClaim = 4;     // queue positions a warp claims at a time
+
+// A warp's tasks to publish and the count of its finished tasks not yet uncounted.
+struct WarpQ {
+  int32_t* buf;   // [kQBuf] in shared memory
+  int n;          // buffered entries (warp-uniform)
+  int done;       // finished tasks (warp-uniform)
+};
+
+// Publishes the buffered entries and uncounts the finished tasks in one atomic on qstate
+// (count += n - done, tail += n), then stores the entries with release semantics, so that a
+// consumer that sees an entry also sees the count that includes it and everything the warp
+// wrote before (rho, items). Entries past the queue's end are uncounted again and set the
+// overflow flag. Warp-level: every lane calls it.
+__device__ __forceinline__ void flush(WarpQ& wq, DevHeader* h, int32_t* queue, long long qcap, int lane) {
+  if (wq.n == 0 && wq.done == 0) return;
+  __syncwarp();
+  unsigned long long base = 0;
+  if (lane == 0)
+    base = atomicAdd(&h->qstate, (unsigned long long)(long long)(wq.n - wq.done) * kTask + (unsigned)wq.n);
+  base = __shfl_sync(kFull, base, 0) & 0xffffffffull;
+  int lost = 0;
+  for (int i = lane; i < wq.n; i += 32) {
+    const long long pos = (long long)base + i;
+    if (pos < qcap)
+      st_release(queue + pos, wq.buf[i]);
+    else
+      ++lost;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lost += __shfl_xor_sync(kFull, lost, o);
+  if (lost && lane == 0) {
+    atomicAdd(&h->qstate, (unsigned long long)(-(long long)lost * (long long)kTask));
+    atomicExch(&h->overflow, 1);
+  }
+  __syncwarp();
+  wq.n = 0;
+  wq.done = 0;
+}
+
+// Adds the entries of the lanes with `want` to the warp's buffer (flushing it first when full).
+__device__ __forceinline__ void stage(bool want, int entry, WarpQ& wq, DevHeader* h, int32_t* queue, long long qcap,
+                                      int lane) {
+  const unsigned m = __ballot_sync(kFull, want);
+  if (!m) return;
+  if (wq.n + __popc(m) > kQBuf) flush(wq, h, queue, qcap, lane);
+  if (want) wq.buf[wq.n + __popc(m & ((1u << lane) - 1u))] = entry;
+  wq.n += __popc(m);
+  __syncwarp();
+}
+
+// Queues row w for the lanes with `want` unless it is queued already (in-queue flag; the
+// exchange is a release, so the add that made w cross comes before it).
+__device__ __forceinline__ void enqueue_rows(bool want, int w, WarpQ& wq, DevHeader* h, uint32_t* inq,
+                                             int32_t* queue, long long qcap, int lane) {
+  const bool fresh = want && exch_acq_rel(inq + w, 1u) == 0u;
+  stage(fresh, w, wq, h, queue, qcap, lane);
+}
+
+// One chunk of a scatter (warp-level): in-edges col[st .. st+ne), ne <= EPC. Lane e < ne owns
+// in-edge e (node w, coef (1-alpha)/deg(w)); group g adds coef * v to its float4s of r[w] for
+// the in-edges g, g + RPW, ..., all CHL atomics in flight before any result is looked at.
+// Each w an add left above its threshold is queued.
 template <int D, bool SCALED>
-__device__ __forceinline__ void scatter_chunk(const float4 rv, int st, int ne, const int32_t* __restrict__ col,
+__device__ __forceinline__ void scatter_chunk(const float4 v, int st, int ne, const int32_t* __restrict__ col,
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
-                                              unsigned tag, uint32_t* stamp, int* next_count, int32_t* next_list,
-                                              int q, int sub, unsigned sub_mask) {
+                                              WarpQ& wq, DevHeader* h, uint32_t* inq, int32_t* queue, long long qcap,
+                                              int lane, int sub, int q) {
   constexpr int LPR = PushShape<D>::LPR;
-  constexpr int CH = PushShape<D>::CH;
+  constexpr int RPW = PushShape<D>::RPW;
+  constexpr int CHL = PushShape<D>::CHL;
   int w_own = 0, d_own = 1;
   float c_own = 0.f;
-  if (q < ne) {
-    w_own = __ldg(col + st + q);
+  if (lane < ne) {
+    w_own = __ldg(col + st + lane);
     d_own = __ldg(outdeg + w_own);
     c_own = beta / (float)d_own;
   }
-  float4 nv[CH];
+  float4 nv[CHL];
 #pragma unroll
-  for (int e = 0; e < CH; ++e) {
-    const int w = __shfl_sync(0xffffffffu, w_own, sub * LPR + e);
-    const float coef = __shfl_sync(0xffffffffu, c_own, sub * LPR + e);
-    nv[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < CHL; ++c) {
+    const int e = c * RPW + sub;
+    const int w = __shfl_sync(kFull, w_own, e);
+    const float coef = __shfl_sync(kFull, c_own, e);
+    nv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e < ne) {
-      const float4 add = make_float4(coef * rv.x, coef * rv.y, coef * rv.z, coef * rv.w);
+      const float4 add = make_float4(coef * v.x, coef * v.y, coef * v.z, coef * v.w);
       const float4 old = atomicAdd(reinterpret_cast<float4*>(r + (size_t)w * D) + q, add);
-      nv[e] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
+      nv[c] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
     }
   }
-  unsigned crossed_bits = 0;
+  // lane l owns in-edge l = c * RPW + g: its bit is group g's part of step c's ballot
+  const unsigned gmask = (LPR == 32) ? kFull : ((1u << LPR) - 1u);
+  bool crossed = false;
 #pragma unroll
-  for (int e = 0; e < CH; ++e) {
-    const float thr = SCALED ? __shfl_sync(0xffffffffu, threshold<true>(eps, d_own), sub * LPR + e) : eps;
-    if (__ballot_sync(0xffffffffu, max_abs4(nv[e]) > thr) & sub_mask) crossed_bits |= 1u << e;
+  for (int c = 0; c < CHL; ++c) {
+    const float thr = SCALED ? __shfl_sync(kFull, threshold<true>(eps, d_own), c * RPW + sub) : eps;
+    const unsigned b = __ballot_sync(kFull, max_abs4(nv[c]) > thr);
+    if (lane / RPW == c) crossed = ((b >> ((lane % RPW) * LPR)) & gmask) != 0u;
   }
-  if (q < ne && ((crossed_bits >> q) & 1u)) enqueue(w_own, tag, stamp, next_count, next_list);
+  enqueue_rows(lane < ne && crossed, w_own, wq, h, inq, queue, qcap, lane);
+}
+
+// Waits (lane 0) for queue position p: returns its entry, or -1 when no task is left (the
+// unfinished count is 0), the device status is set, or the wait runs out (DAMF_ERR_TIMEOUT).
+__device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long p, long long qcap) {
+  for (long long it = 0;; ++it) {
+    if (p < qcap) {
+      const int e = ld_acquire(queue + p);
+      if (e != -1) {
+        queue[p] = -1;                 // read once per phase; empty again for the next launch
+        return e;
+      }
+    }
+    if ((ld_volatile64(&h->qstate) >> 32) == 0ull) return -1;
+    if (*reinterpret_cast<volatile int*>(&h->status) != 0) return -1;
+    if (it > kSpinLimit) {
+      set_status(h, DAMF_ERR_TIMEOUT);
+      return -1;
+    }
+    if (it > 32) __nanosleep(it > 2048 ? 1024 : 128);
+  }
 }
 
 // 64 registers at most (min. 4 CTAs' worth per SM): two push CTAs (32k registers) then leave room
 // on every SM for the 768-thread core SVD CTA of the next update, which runs beside the push
 template <int D, bool SCALED>
 __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
-                                                 float* Zb, float* r, int n, float alpha, float eps, int max_rounds,
+                                                 float* Zb, float* r, int n, float alpha, float eps, int max_phases,
                                                  int check_all, int direct_max) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
-  constexpr int CH = PushShape<D>::CH;
+  constexpr int EPC = PushShape<D>::EPC;
   const unsigned nblocks = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR, q = lane % LPR;
-  const unsigned sub_mask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (sub * LPR));
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const unsigned epoch0 = h->epoch;
   const float beta = 1.0f - alpha;
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const long long qcap = ws.qcap;
+  int32_t* queue = ws.queue;
+  uint32_t* inq = ws.stamp;
   long long my_pushes = 0, my_edges = 0;
-  const int ncand0 = check_all ? n : h->pending;
-  // block 0's view of where the time goes (ns): deferred items, candidates, barrier;
-  // [4] is the last time mark. Kept in shared memory, where it costs no registers.
+  const int npend = h->pending;
+  // block 0's view of where the time goes (ns): seeding, task loop, barriers; [4] is the last
+  // mark. Kept in shared memory, where it costs no registers.
   __shared__ unsigned long long s_t[5];
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-  if (timer) s_t[0] = s_t[1] = s_t[2] = s_t[3] = 0ull;
-  int round = 0;
-  for (;;) {
-    if (round >= max_rounds) {
+  if (timer) {
+    s_t[0] = s_t[1] = s_t[2] = s_t[3] = 0ull;
+    s_t[4] = gtimer();
+  }
+  __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
+  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0};
+  int phase = 0;
+  for (;; ++phase) {
+    if (phase >= max_phases) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, DAMF_ERR_NOT_CONVERGED);
       break;
     }
-    if (timer) s_t[4] = gtimer();
-    const int P = round & 1;
-    const int K0 = round % 3, K1 = (round + 1) % 3, K2 = (round + 2) % 3;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {   // last read in round k-1, next written in round k+1
-      h->cand_count[K2] = 0;
-      h->front_count[K2] = 0;
-      h->work_count[K2] = 0;
-    }
-    const unsigned tag = epoch0 + (unsigned)round + 1u;
-    int* next_count = &h->cand_count[K1];
-    int32_t* next_list = ws.cand[P ^ 1];
-
-    // ---- work items deferred by the previous round ----
-    const int nwork = round == 0 ? 0 : __ldcg(&h->work_count[K0]);
-    const float* rho_in = ws.rho[P];
-    const int4* work_in = ws.work[P];
-    for (long long it = gwarp * RPW + sub; it - sub < nwork; it += nwarps * RPW) {
-      int4 wi = make_int4(0, 0, 0, 0);
-      float4 rv = zero4;
-      if (it < nwork) {
-        wi = __ldcg(work_in + it);
-        rv = f4_ldcg(rho_in + (size_t)wi.x * D + 4 * q);
-      }
-      scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
-                       sub_mask);
-    }
-    if (timer) time_mark(s_t, 0);
-
-    // ---- candidates ----
-    const int ncand = round == 0 ? ncand0 : __ldcg(&h->cand_count[K0]);
-    const int32_t* cand = round == 0 ? (check_all ? nullptr : ws.pend) : ws.cand[P];
-    float* rho_out = ws.rho[P ^ 1];
-    int4* work_out = ws.work[P ^ 1];
+    // ---- seeding: the rows whose residual changed (or every row), when above eps ----
+    const bool all = check_all || phase > 0;
+    const int ncand = all ? n : npend;
     for (long long base = gwarp * RPW; base < ncand; base += nwarps * RPW) {
       const long long ci = base + sub;
       const bool valid = ci < ncand;
-      const int u = valid ? (cand ? __ldcg(cand + ci) : (int)ci) : 0;
-      float4 v = zero4, z = zero4;
-      int st = 0, deg = 0, dout = 1;
-      if (valid) {   // everything that depends only on u is requested at once
+      const int u = valid ? (all ? (int)ci : __ldcg(ws.pend + ci)) : 0;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      int dout = 1;
+      if (valid) {
         v = f4_ldcg(r + (size_t)u * D + 4 * q);
-        z = f4_ldcg(Zb + (size_t)u * D + 4 * q);
-        st = in.start[u];
-        deg = in.len[u];
         if (SCALED) dout = __ldg(outdeg + u);
       }
-      const float thr_u = threshold<SCALED>(eps, dout);
-      const bool push = group_max<LPR>(max_abs4(v)) > thr_u && valid;
-      float lm = 0.f;   // max |r[u]| right after the removal of v (over this lane's float4)
-      if (push) {
-        const float4 old =
-            atomicAdd(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(-v.x, -v.y, -v.z, -v.w));
-        lm = max_abs4(make_float4(old.x - v.x, old.y - v.y, old.z - v.z, old.w - v.w));
-        z.x = fmaf(alpha, v.x, z.x);
-        z.y = fmaf(alpha, v.y, z.y);
-        z.z = fmaf(alpha, v.z, z.z);
-        z.w = fmaf(alpha, v.w, z.w);
-        __stcg(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q, z);
-        if (q == 0) {
-          my_pushes += 1;
-          my_edges += deg;
-        }
-      }
-      // many in-edges: a rho slot and work items for the next round (warp-aggregated slots)
-      const bool defer = push && deg > direct_max;
-      const unsigned bal = __ballot_sync(0xffffffffu, defer && q == 0);
-      if (bal) {
-        const int nch = defer ? (deg + CH - 1) / CH : 0;
-        int wsum = (q == 0) ? nch : 0, wpre = wsum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {   // inclusive prefix sum over the warp
-          const int t = __shfl_up_sync(0xffffffffu, wpre, o);
-          if (lane >= o) wpre += t;
-        }
-        const int wtot = __shfl_sync(0xffffffffu, wpre, 31);
-        int basepos = 0, wbase = 0;
-        if (lane == 0) {
-          basepos = atomicAdd(&h->front_count[K1], __popc(bal));
-          wbase = atomicAdd(&h->work_count[K1], wtot);
-        }
-        basepos = __shfl_sync(0xffffffffu, basepos, 0);
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        const int wmine = __shfl_sync(0xffffffffu, wpre - wsum, sub * LPR);   // exclusive prefix of my group
-        if (defer) {
-          const int pos = basepos + __popc(bal & ((1u << (sub * LPR)) - 1u));
-          __stcg(reinterpret_cast<float4*>(rho_out + (size_t)pos * D) + q, v);
-          for (int c2 = q; c2 < nch; c2 += LPR) {
-            const int e0 = c2 * CH;
-            __stcg(work_out + wbase + wmine + c2, make_int4(pos, st + e0, min(CH, deg - e0), 0));
-          }
-        }
-      }
-      // few in-edges: scatter now, one chunk of CH in-edges per step (warp-uniform trip count)
-      const int ndir = (push && !defer) ? (deg + CH - 1) / CH : 0;
-      int nmax = ndir;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-      for (int c2 = 0; c2 < nmax; ++c2) {
-        const int e0 = c2 * CH;
-        const int ne = c2 < ndir ? min(CH, deg - e0) : 0;
-        scatter_chunk<D, SCALED>(v, st + e0, ne, in.col, outdeg, r, beta, eps, tag, ws.stamp, next_count, next_list, q, sub,
-                         sub_mask);
-      }
-      // u itself: adds that reached r[u] between the read of v and its removal are still there
-      lm = group_max<LPR>(lm);
-      if (push && q == 0 && lm > thr_u) enqueue(u, tag, ws.stamp, next_count, next_list);
+      const bool above = group_max<LPR>(max_abs4(v)) > threshold<SCALED>(eps, dout);
+      enqueue_rows(valid && above && q == 0, u, wq, h, inq, queue, qcap, lane);
     }
-    if (timer) time_mark(s_t, 1);
+    flush(wq, h, queue, qcap, lane);
+    if (timer) time_mark(s_t, 0);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
     if (timer) time_mark(s_t, 2);
-    ++round;
-    if (__ldcg(&h->cand_count[K1]) == 0 && __ldcg(&h->work_count[K1]) == 0) break;
+
+    // ---- task loop: claim kClaim positions at a time ----
+    bool quit = false;
+    while (!quit) {
+      long long p0 = 0;
+      if (lane == 0) p0 = atomicAdd(&h->q_head, kClaim);
+      p0 = __shfl_sync(kFull, p0, 0);
+      for (int b = 0; b < kClaim; ++b) {
+      const long long p = p0 + b;
+      int e = -1;
+      if (lane == 0 && p < qcap) {
+        e = ld_acquire(queue + p);
+        if (e != -1) queue[p] = -1;      // read once per phase; empty again for the next launch
+      }
+      e = __shfl_sync(kFull, e, 0);
+      if (e == -1) {
+        flush(wq, h, queue, qcap, lane);   // publish and uncount before waiting
+        if (lane == 0) e = wait_slot(h, queue, p, qcap);
+        e = __shfl_sync(kFull, e, 0);
+        if (e == -1) {
+          quit = true;                     // positions after p are not filled either
+          break;
+        }
+      }
+      if (e >= 0) {
+        // row task
+        const int u = e;
+        if (lane == 0) exch_acq_rel(inq + u, 0u);   // acquire: r[u] is read after the flag is clear
+        __syncwarp();
+        // group 0 reads r[u] once and hands it to the other groups, so that every group
+        // scatters exactly the v that group 0 removes
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+        if (RPW > 1) {
+          v.x = __shfl_sync(kFull, v.x, q);
+          v.y = __shfl_sync(kFull, v.y, q);
+          v.z = __shfl_sync(kFull, v.z, q);
+          v.w = __shfl_sync(kFull, v.w, q);
+        }
+        const int st = __ldg(in.start + u), deg = __ldg(in.len + u);
+        const int dout = SCALED ? __ldg(outdeg + u) : 1;
+        const float thr_u = threshold<SCALED>(eps, dout);
+        if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
+          float lm = 0.f;                           // max |r[u]| right after the removal of v
+          if (sub == 0) {
+            const float4 old =
+                atomicAdd(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(-v.x, -v.y, -v.z, -v.w));
+            lm = max_abs4(make_float4(old.x - v.x, old.y - v.y, old.z - v.z, old.w - v.w));
+            atomicAdd(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q,
+                      make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w));
+          }
+          if (lane == 0) {
+            my_pushes += 1;
+            my_edges += deg;
+          }
+          bool direct = true;
+          if (deg > direct_max) {
+            // hub: a rho slot and one item task per chunk of in-edges
+            const int nch = (deg + EPC - 1) / EPC;
+            int slot = 0, ib = 0;
+            if (lane == 0) {
+              slot = atomicAdd(&h->rho_tail, 1);
+              ib = atomicAdd(&h->item_tail, nch);
+            }
+            slot = __shfl_sync(kFull, slot, 0);
+            ib = __shfl_sync(kFull, ib, 0);
+            if ((long long)slot < ws.rho_cap && (long long)ib + nch <= ws.work_cap) {
+              direct = false;
+              if (sub == 0) __stcg(reinterpret_cast<float4*>(ws.rho + (size_t)slot * D) + q, v);
+              for (int c0 = 0; c0 < nch; c0 += 32) {   // warp-uniform
+                const int c2 = c0 + lane;
+                if (c2 < nch)
+                  __stcg(ws.work + ib + c2, make_int4(slot, st + c2 * EPC, min(EPC, deg - c2 * EPC), 0));
+                stage(c2 < nch, -(ib + c2 + 2), wq, h, queue, qcap, lane);
+              }
+            }
+          }
+          if (direct)
+            for (int c0 = 0; c0 < deg; c0 += EPC)
+              scatter_chunk<D, SCALED>(v, st + c0, min(EPC, deg - c0), in.col, outdeg, r, beta, eps, wq, h, inq,
+                                       queue, qcap, lane, sub, q);
+          // u itself: adds that reached r[u] between the read of v and its removal are still there
+          lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
+          enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
+        }
+      } else {
+        // item task: one chunk of a hub's in-edges
+        const int4 wi = __ldcg(ws.work + (-e - 2));
+        const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
+        scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
+                                 q);
+      }
+      wq.done += 1;
+      }
+      flush(wq, h, queue, qcap, lane);
+    }
+    if (timer) time_mark(s_t, 1);
+    if (!grid_barrier(&h->bar, h, nblocks)) return;   // every warp has left the task loop
+    const bool again = *reinterpret_cast<volatile int*>(&h->overflow) != 0 &&
+                       *reinterpret_cast<volatile int*>(&h->status) == 0;
+    if (!again) {
+      if (timer) time_mark(s_t, 2);
+      ++phase;
+      break;
+    }
+    // overflow: unflag every row and start a phase that checks them all
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
+      inq[u] = 0u;
+    if (!grid_barrier(&h->bar, h, nblocks)) return;   // everyone has read the overflow flag
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      h->qstate = 0ull;
+      h->q_head = 0;
+      h->overflow = 0;
+      h->rho_tail = 0;
+      h->item_tail = 0;
+    }
+    if (!grid_barrier(&h->bar, h, nblocks)) return;
+    if (timer) time_mark(s_t, 2);
   }
   if (timer)
     for (int i = 0; i < 4; ++i) h->push_ns[i] += s_t[i];
   // counters and bookkeeping (block 0 after the last barrier; everyone has left the loop)
   for (int o = 16; o > 0; o >>= 1) {
-    my_pushes += __shfl_xor_sync(0xffffffffu, my_pushes, o);
-    my_edges += __shfl_xor_sync(0xffffffffu, my_edges, o);
+    my_pushes += __shfl_xor_sync(kFull, my_pushes, o);
+    my_edges += __shfl_xor_sync(kFull, my_edges, o);
   }
   if (lane == 0 && (my_pushes || my_edges)) {
     atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)my_pushes);
     atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)my_edges);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    h->push_rounds += round;
+    h->push_rounds += phase;
     h->pending = 0;
     h->check_all = 0;
-    h->epoch = epoch0 + (unsigned)round + 2u;
+    h->epoch = epoch0 + 2u;
   }
 }
 
@@ -312,9 +450,10 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   int chunks = kPushDirectChunks;
   if (const char* ev = getenv("DAMF_PUSH_DIRECT_CHUNKS")) {
     const int v = atoi(ev);
-    if (v >= 0 && v <= 64) chunks = v;
+    if (v >= 0 && v <= 1024) chunks = v;
   }
-  cudaError_t e = cudaMemsetAsync(&c->hdr->cand_count[0], 0, 9 * sizeof(int), s);
+  // qstate, q_head, overflow, rho_tail, item_tail
+  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 4 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   DevHeader* h = c->hdr;
   Adj in = c->cfg.directed ? c->in : c->out;
@@ -324,9 +463,9 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   float* r = c->r;
   int n = c->n;
   float alpha = (float)c->cfg.alpha, eps = (float)c->cfg.eps;
-  int max_rounds = c->cfg.max_push_rounds;
-  int direct_max = chunks * PushShape<D>::CH;
-  void* args[] = {&h, &in, &outdeg, &ws, &Zb, &r, &n, &alpha, &eps, &max_rounds, &check_all, &direct_max};
+  int max_phases = c->cfg.max_push_rounds;
+  int direct_max = chunks * PushShape<D>::EPC;
+  void* args[] = {&h, &in, &outdeg, &ws, &Zb, &r, &n, &alpha, &eps, &max_phases, &check_all, &direct_max};
   return cudaLaunchCooperativeKernel((void*)k_push<D, SCALED>, dim3(c->push_blocks), dim3(256), args, 0, s);
 }
 
