@@ -49,9 +49,10 @@ def make_inputs(c, n_batches):
 
 
 # ---------------------------------------------------------------- oracle (CPU) leg
-def oracle_run(c, steps, warmup, time_budget_s):
+def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
     """Times the FP64 oracle (as it stands) on the first warmup+steps batches, stopping
-    early once time_budget_s of timed work is spent.  Returns a dict."""
+    early once time_budget_s of timed work is spent.  Returns a dict; with save_path, also
+    writes the oracle's final X, Y, Z and sigma there (npz) for the error comparison."""
     from oracle.damf import DamfOracle
     from synth import gaussian_test_matrix
     ip, ix, st = make_inputs(c, warmup + steps)
@@ -73,6 +74,10 @@ def oracle_run(c, steps, warmup, time_budget_s):
         if time.perf_counter() - t_start > time_budget_s:
             break
     total = time.perf_counter() - t_start
+    if save_path:
+        n = orc.n
+        np.savez(save_path, X=orc.X()[:n], Y=orc.Y()[:n], Z=orc.Z()[:n], sigma=orc.sigma,
+                 batches=warmup + len(lat))
     return {"value": edges / total, "unit": UNIT, "cores": 1, "kind": "oracle", "batches": len(lat),
             "edges": edges, "seconds": total, "init_s": init_s,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
@@ -80,9 +85,9 @@ def oracle_run(c, steps, warmup, time_budget_s):
                       "1 thread" % (len(lat), c.name, warmup, edges)}
 
 
-def oracle_subprocess(c, steps, budget):
+def oracle_subprocess(c, steps, budget, save_path=None):
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", c.name, "--steps", str(steps),
-           "--budget", str(budget)]
+           "--budget", str(budget)] + (["--save-state", save_path] if save_path else [])
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
@@ -90,6 +95,55 @@ def oracle_subprocess(c, steps, budget):
         if line.startswith("{"):
             return json.loads(line)
     return {"error": (out.stderr or out.stdout)[-400:]}
+
+
+def err_vs_oracle(c, path, precisions):
+    """Replays the oracle's batches on the device (fresh context per precision) and compares
+    sigma, X Y^T and Z Y^T with the oracle's FP64 result: relative errors, the Frobenius
+    ones through d x d Grams (|A B^T|_F^2 = tr((A^T A)(B^T B)))."""
+    import torch
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    ref = np.load(path)
+    nb = int(ref["batches"])
+    dev = torch.device("cuda")
+    Xo, Yo, Zo = (torch.from_numpy(ref[k]).to(dev) for k in ("X", "Y", "Z"))
+    so = ref["sigma"]
+    ip, ix, st = make_inputs(c, nb)
+
+    def rel_fro(A, B, Ao, Bo):   # |A B^T - Ao Bo^T|_F / |Ao Bo^T|_F
+        gg = torch.trace((A.T @ A) @ (B.T @ B))
+        oo = torch.trace((Ao.T @ Ao) @ (Bo.T @ Bo))
+        go = torch.trace((A.T @ Ao) @ (Bo.T @ B))
+        return float(torch.sqrt(torch.clamp(gg - 2 * go + oo, min=0)) / torch.sqrt(oo))
+
+    out = {"batches": nb, "oracle": "FP64 incremental oracle (the paper's X-form) on the same batches"}
+    for prec in precisions:
+        cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=st.n_final + 16, nnz=len(ix), directed=c.directed,
+                          refold_every=256, precision=prec)
+        om = gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
+        g = DamfGraph(ip, ix, cfg, om)
+        for b in st.batches[:nb]:
+            g.apply_edges_host(b.src, b.dst, b.op, b.new_nodes)
+            g.ppr_refresh()
+        g.check()
+        e = g.embeddings()
+        X, Y, Z = (e[k].double() for k in ("X", "Y", "Z"))
+        sg = e["sigma"].double().cpu().numpy()
+        out[prec] = {"sigma_max_rel": float(np.max(np.abs(sg - so) / np.abs(so))),
+                     "xyt_rel_fro": rel_fro(X, Y, Xo, Yo), "zyt_rel_fro": rel_fro(Z, Y, Zo, Yo)}
+        if "zyt_eps_bound" not in out:
+            # each side's Z is within eps per element of Pi X (in the base space, mapped by P_X):
+            # |Z Y^T - Z* Y^T|_F <= |Z - Z*|_F |Y|_2, bounded per side by |r|_F <= eps sqrt(n d)
+            # times the largest scale of the base-to-embedding map; reported relative to |Zo Yo^T|_F
+            zy = float(torch.sqrt(torch.trace((Zo.T @ Zo) @ (Yo.T @ Yo))))
+            yn = float(torch.linalg.matrix_norm(Yo, ord=2))
+            out["zyt_fro"] = zy
+            out["zyt_eps_bound"] = 2 * c.eps * float(np.sqrt(X.shape[0] * c.d)) * yn * float(
+                np.sqrt(np.max(so) / np.min(so[so > 0]))) / zy
+        g.close()
+        del X, Y, Z, e
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -364,11 +418,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)
+    ap.add_argument("--save-state", default=None)
     args = ap.parse_args()
     from synth import CONFIGS
     c = CONFIGS[args.config]
     if args.oracle_worker:
-        print(json.dumps(oracle_run(c, args.steps, 2, args.budget)))
+        print(json.dumps(oracle_run(c, args.steps, 2, args.budget, args.save_state)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -411,7 +466,17 @@ def main():
                     "after the run; mixed runs the fold's n x d by d x d GEMMs on tcgen05 (TF32, 3-term split)"}
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            r = oracle_subprocess(c, 400, args.cpu_budget)
+            import tempfile
+            state = os.path.join(tempfile.mkdtemp(prefix="damf_oracle_"), "state.npz")
+            r = oracle_subprocess(c, 400, args.cpu_budget, state)
+            if os.path.exists(state):
+                try:
+                    precs = [args.precision] + (["fp32" if args.precision == "mixed" else "mixed"]
+                                                if args.compare_precision else [])
+                    out["err_vs_oracle"] = err_vs_oracle(c, state, precs)
+                except Exception as ex:   # reported, never fatal to the timing line
+                    out["err_vs_oracle"] = {"error": repr(ex)[:300]}
+                os.remove(state)
             if "value" in r:
                 out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                                        "sample": r["sample"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],

@@ -88,9 +88,14 @@ long long work_cap_of(const damf_config* cfg) {
   return 2 * ((long long)cfg->n_capacity + cfg->m_capacity / 4 + 64);   // hub items of one push
 }
 
-// push queue positions of one phase (a phase that needs more rescans every row)
+// push queue positions of one phase (a phase that needs more rescans every row); the
+// environment variable DAMF_PUSH_QUEUE_CAP overrides it (testing the overflow path)
 long long qcap_of(const damf_config* cfg) {
   long long q = 4ll * cfg->n_capacity + (1ll << 20);
+  if (const char* ev = getenv("DAMF_PUSH_QUEUE_CAP")) {
+    const long long v = atoll(ev);
+    if (v >= 64) q = v;
+  }
   return q > 0x7fffff00ll ? 0x7fffff00ll : q;
 }
 
@@ -147,6 +152,7 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = (size_t)qcap_of(cfg) * 4;                         // push queue
   s[k++] = (size_t)work_cap_of(cfg) * sizeof(int4);          // hub items
   s[k++] = 2 * nd;                                           // rho (2 n_cap slots)
+  s[k++] = (size_t)work_cap_of(cfg) * 4;                     // overflowed hub items
   s[k++] = n * 4; s[k++] = n * 4; s[k++] = n * 4;            // stamp pend pstamp
   s[k++] = 2 * (size_t)160 * 160 * 4;                        // gram (room for the init width)
   s[k++] = (size_t)gram_parts_of(cfg) * 160 * 160 * 4;       // gram_part
@@ -349,6 +355,7 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   w.queue = (int32_t*)ptr[k++]; w.qcap = qcap_of(cfg);
   w.work = (int4*)ptr[k++]; w.work_cap = work_cap_of(cfg);
   w.rho = (float*)ptr[k++]; w.rho_cap = 2ll * cfg->n_capacity;
+  w.ovf = (int32_t*)ptr[k++];
   w.stamp = (uint32_t*)ptr[k++]; w.pend = (int32_t*)ptr[k++]; w.pstamp = (uint32_t*)ptr[k++];
   w.gram = (float*)ptr[k++]; w.gram_part = (float*)ptr[k++]; w.gram_parts = gram_parts_of(cfg);
   {

@@ -58,6 +58,7 @@ struct DevHeader {
   int overflow;
   int rho_tail;
   int item_tail;
+  int ovf_count;    // hub items that found the queue full (processed at the end of the phase)
   GridBar bar;
 };
 
@@ -106,6 +107,7 @@ struct Workspace {
   long long work_cap;
   float* rho;        // [rho_cap x d] residuals of the hub pushes
   long long rho_cap;
+  int32_t* ovf;      // [work_cap] ids of hub items that found the queue full
   uint32_t* stamp;   // [n_cap] 1 while the row is in the push queue
   int32_t* pend;     // [n_cap] rows queued for the next push
   uint32_t* pstamp;  // [n_cap]

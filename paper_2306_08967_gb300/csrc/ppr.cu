@@ -116,6 +116,7 @@ struct WarpQ {
   int32_t* buf;   // [kQBuf] in shared memory
   int n;          // buffered entries (warp-uniform)
   int done;       // finished tasks (warp-uniform)
+  int32_t* ovf;   // list of hub items that found the queue full
 };
 
 // Publishes the buffered entries and uncounts the finished tasks in one atomic on qstate
@@ -123,7 +124,8 @@ struct WarpQ {
 // consumer that sees an entry also sees the count that includes it and everything the warp
 // wrote before (rho, items). Entries past the queue's end are uncounted again and set the
 // overflow flag. Warp-level: every lane calls it.
-__device__ __forceinline__ void flush(WarpQ& wq, DevHeader* h, int32_t* queue, long long qcap, int lane) {
+__device__ __forceinline__ void flush(WarpQ& wq, DevHeader* h, int32_t* queue, long long qcap, int lane,
+                                      int32_t* ovf) {
   if (wq.n == 0 && wq.done == 0) return;
   __syncwarp();
   unsigned long long base = 0;
@@ -133,10 +135,14 @@ __device__ __forceinline__ void flush(WarpQ& wq, DevHeader* h, int32_t* queue, l
   int lost = 0;
   for (int i = lane; i < wq.n; i += 32) {
     const long long pos = (long long)base + i;
-    if (pos < qcap)
+    if (pos < qcap) {
       st_release(queue + pos, wq.buf[i]);
-    else
+    } else {
       ++lost;
+      // a row stays flagged and is found again by the rescan; a hub item holds mass already
+      // taken out of r, so it is kept for the end of the phase
+      if (wq.buf[i] < -1) ovf[atomicAdd(&h->ovf_count, 1)] = -wq.buf[i] - 2;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lost += __shfl_xor_sync(kFull, lost, o);
@@ -154,7 +160,7 @@ __device__ __forceinline__ void stage(bool want, int entry, WarpQ& wq, DevHeader
                                       int lane) {
   const unsigned m = __ballot_sync(kFull, want);
   if (!m) return;
-  if (wq.n + __popc(m) > kQBuf) flush(wq, h, queue, qcap, lane);
+  if (wq.n + __popc(m) > kQBuf) flush(wq, h, queue, qcap, lane, wq.ovf);
   if (want) wq.buf[wq.n + __popc(m & ((1u << lane) - 1u))] = entry;
   wq.n += __popc(m);
   __syncwarp();
@@ -176,7 +182,7 @@ template <int D, bool SCALED>
 __device__ __forceinline__ void scatter_chunk(const float4 v, int st, int ne, const int32_t* __restrict__ col,
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
                                               WarpQ& wq, DevHeader* h, uint32_t* inq, int32_t* queue, long long qcap,
-                                              int lane, int sub, int q) {
+                                              int lane, int sub, int q, bool enq = true) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
   constexpr int CHL = PushShape<D>::CHL;
@@ -200,6 +206,7 @@ __device__ __forceinline__ void scatter_chunk(const float4 v, int st, int ne, co
       nv[c] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
     }
   }
+  if (!enq) return;   // warp-uniform: the adds only (the rescan that follows finds the rows)
   // lane l owns in-edge l = c * RPW + g: its bit is group g's part of step c's ballot
   const unsigned gmask = (LPR == 32) ? kFull : ((1u << LPR) - 1u);
   bool crossed = false;
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
     s_t[4] = gtimer();
   }
   __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
-  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0};
+  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0, ws.ovf};
   int phase = 0;
   for (;; ++phase) {
     if (phase >= max_phases) {
@@ -286,27 +293,27 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       const bool above = group_max<LPR>(max_abs4(v)) > threshold<SCALED>(eps, dout);
       enqueue_rows(valid && above && q == 0, u, wq, h, inq, queue, qcap, lane);
     }
-    flush(wq, h, queue, qcap, lane);
+    flush(wq, h, queue, qcap, lane, ws.ovf);
     if (timer) time_mark(s_t, 0);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
     if (timer) time_mark(s_t, 2);
 
-    // ---- task loop: claim kClaim positions at a time ----
+    // ---- task loop: claim kClaim positions at a time, lanes 0 .. kClaim-1 read their slots ----
     bool quit = false;
     while (!quit) {
       long long p0 = 0;
       if (lane == 0) p0 = atomicAdd(&h->q_head, kClaim);
       p0 = __shfl_sync(kFull, p0, 0);
+      int eb = -1;
+      if (lane < kClaim && p0 + lane < qcap) {
+        eb = ld_acquire(queue + p0 + lane);
+        if (eb != -1) queue[p0 + lane] = -1;   // read once per phase; empty again for the next launch
+      }
       for (int b = 0; b < kClaim; ++b) {
       const long long p = p0 + b;
-      int e = -1;
-      if (lane == 0 && p < qcap) {
-        e = ld_acquire(queue + p);
-        if (e != -1) queue[p] = -1;      // read once per phase; empty again for the next launch
-      }
-      e = __shfl_sync(kFull, e, 0);
+      int e = __shfl_sync(kFull, eb, b);
       if (e == -1) {
-        flush(wq, h, queue, qcap, lane);   // publish and uncount before waiting
+        flush(wq, h, queue, qcap, lane, ws.ovf);   // publish and uncount before waiting
         if (lane == 0) e = wait_slot(h, queue, p, qcap);
         e = __shfl_sync(kFull, e, 0);
         if (e == -1) {
@@ -315,9 +322,11 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         }
       }
       if (e >= 0) {
-        // row task
+        // row task. The flag is cleared first; the removal of v below is ordered after the
+        // clear (fence), so an add that lands after the removal finds the flag clear and queues
+        // u again, while an add between the read of v and the removal shows in `left`.
         const int u = e;
-        if (lane == 0) exch_acq_rel(inq + u, 0u);   // acquire: r[u] is read after the flag is clear
+        if (lane == 0) atomicExch(inq + u, 0u);
         __syncwarp();
         // group 0 reads r[u] once and hands it to the other groups, so that every group
         // scatters exactly the v that group 0 removes
@@ -334,6 +343,8 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         const float thr_u = threshold<SCALED>(eps, dout);
         if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
           float lm = 0.f;                           // max |r[u]| right after the removal of v
+          __syncwarp();
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");   // the flag's clear comes first
           if (sub == 0) {
             const float4 old =
                 atomicAdd(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(-v.x, -v.y, -v.z, -v.w));
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       }
       wq.done += 1;
       }
-      flush(wq, h, queue, qcap, lane);
+      flush(wq, h, queue, qcap, lane, ws.ovf);
     }
     if (timer) time_mark(s_t, 1);
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // every warp has left the task loop
@@ -395,7 +406,17 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       ++phase;
       break;
     }
-    // overflow: unflag every row and start a phase that checks them all
+    // overflow: scatter the hub items that found the queue full (their mass is out of r
+    // already), unflag every row and start a phase that checks them all
+    {
+      const int novf = *reinterpret_cast<volatile int*>(&h->ovf_count);
+      for (long long i = gwarp; i < novf; i += nwarps) {
+        const int4 wi = __ldcg(ws.work + __ldcg(ws.ovf + i));
+        const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
+        scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
+                                 false);
+      }
+    }
     for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
       inq[u] = 0u;
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // everyone has read the overflow flag
@@ -405,6 +426,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       h->overflow = 0;
       h->rho_tail = 0;
       h->item_tail = 0;
+      h->ovf_count = 0;
     }
     if (!grid_barrier(&h->bar, h, nblocks)) return;
     if (timer) time_mark(s_t, 2);
@@ -452,8 +474,8 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
     const int v = atoi(ev);
     if (v >= 0 && v <= 1024) chunks = v;
   }
-  // qstate, q_head, overflow, rho_tail, item_tail
-  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 4 * sizeof(int), s);
+  // qstate, q_head, overflow, rho_tail, item_tail, ovf_count
+  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 5 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   DevHeader* h = c->hdr;
   Adj in = c->cfg.directed ? c->in : c->out;

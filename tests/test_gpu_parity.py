@@ -130,6 +130,60 @@ def test_ppr_within_eps_of_exact(directed):
 
 
 @pytest.mark.parametrize("directed", [False, True])
+def test_ppr_bound_with_hub_rows(directed):
+    # d = 128 and a heavy-tailed graph: rows with more than 64 in-edges are pushed as hub
+    # items (rho slot + chunk tasks), rows with fewer directly; both must keep the eps bound
+    rng = np.random.default_rng(13)
+    n, d, alpha, eps = 2500, 128, 0.15, 1e-5
+    g, _, (ip, ix, _) = make_pair(n, 12.0, 2.05, d, alpha, eps, SEED + 27, directed=directed, oracle=False)
+    assert np.diff(ip).max() > 150                      # the graph has hubs
+    for step in range(4):
+        if step:
+            src, dst, op = _events(rng, n, 30)
+            g.apply_edges(src, dst, op)
+            g.ppr_refresh()
+        g.check()
+        st = g.state()
+        Xb = (st["Ub"] * st["s0"]).double().cpu().numpy()
+        Zb = st["Zb"].double().cpu().numpy()
+        r = st["r"].double().cpu().numpy()
+        rp, col = g.adjacency()
+        A = dense_adj(rp, col, g.n)
+        exact = ppr_matrix_dense(A, alpha) @ Xb
+        assert np.abs(r).max() <= eps
+        assert np.abs(Zb - exact).max() <= eps * (1 + 1e-3) + 2e-6 * np.abs(Xb).max()
+    g.close()
+
+
+def test_ppr_bound_when_the_queue_overflows(monkeypatch):
+    # a 2048-position work queue: the initial push (every row seeded) and the larger updates
+    # overflow it, so rows and hub items miss the queue; the rows are found again by the rescan
+    # that ends each phase and the hub items are scattered there, so the eps bound must hold
+    monkeypatch.setenv("DAMF_PUSH_QUEUE_CAP", "2048")
+    rng = np.random.default_rng(15)
+    n, d, alpha, eps = 1500, 128, 0.15, 1e-5
+    g, _, (ip, ix, _) = make_pair(n, 12.0, 2.05, d, alpha, eps, SEED + 29, oracle=False)
+    assert np.diff(ip).max() > 100
+    for step in range(3):
+        if step:
+            src, dst, op = _events(rng, n, 30)
+            g.apply_edges(src, dst, op)
+            g.ppr_refresh()
+        g.check()
+        st = g.state()
+        Xb = (st["Ub"] * st["s0"]).double().cpu().numpy()
+        Zb = st["Zb"].double().cpu().numpy()
+        r = st["r"].double().cpu().numpy()
+        rp, col = g.adjacency()
+        A = dense_adj(rp, col, g.n)
+        exact = ppr_matrix_dense(A, alpha) @ Xb
+        assert np.abs(r).max() <= eps
+        assert np.abs(Zb - exact).max() <= eps * (1 + 1e-3) + 2e-6 * np.abs(Xb).max()
+    assert g.stats()["push_rounds"] > 3           # the pushes took several phases
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
 def test_degree_scaled_threshold_bound(directed):
     # threshold eps * max(deg(u), 1): every residual ends below its own threshold and
     # |Zb - Pi Xb|[i] <= (Pi t)[i] for the thresholds t (FP32 slack as in the absolute test)
