@@ -117,6 +117,26 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
 damf_status damf_apply_edges(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,
                              int32_t k, int32_t new_nodes, void* stream);
 
+/* One batch of events for one graph (damf_apply_edges_multi). */
+typedef struct {
+  damf_ctx* ctx;          /* the graph's context */
+  const int32_t* src;     /* (device) int32[k] */
+  const int32_t* dst;     /* (device) int32[k] */
+  const int8_t* op;       /* (device) int8[k], +1 insert, -1 delete */
+  int32_t k;              /* events */
+  int32_t new_nodes;      /* node arrivals appended before the events */
+} damf_batch;
+
+/*
+ * Applies one batch to each of num_graphs independent graphs (the batching pattern: many
+ * graphs of uneven size per call), in order, on `stream`: each entry is exactly
+ * damf_apply_edges(batches[i].ctx, ...), so every graph's result is the same as when its
+ * batch is applied alone. Each graph's push still runs on its own context's stream
+ * (damf_ppr_refresh). Returns the first non-OK status (the remaining batches are not
+ * applied); DAMF_ERR_INVALID for num_graphs < 0 or a NULL batches array / context.
+ */
+damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
+
 /* Same as damf_apply_edges with src, dst, op in (host) memory: the library copies
  * them to the device on `stream` (k <= 4096). */
 damf_status damf_apply_edges_host(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,

@@ -19,6 +19,11 @@ class Config(ctypes.Structure):
                 ("threshold", c_i32)]
 
 
+class Batch(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("op", ctypes.c_void_p),
+                ("k", c_i32), ("new_nodes", c_i32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("updates", c_i64), ("edges_applied", c_i64), ("entries_changed", c_i64), ("pushes", c_i64),
                 ("push_edges", c_i64), ("push_rounds", c_i64), ("fixup_edges", c_i64), ("touched_rows", c_i64),
@@ -34,6 +39,7 @@ SIGNATURES = {
     "damf_init_factorize": (c_i32, [ctypes.POINTER(Config), c_vp, c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "damf_apply_edges": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
+    "damf_apply_edges_multi": (c_i32, [c_vp, c_i32, c_vp]),
     "damf_ppr_refresh": (c_i32, [c_vp, c_vp]),
     "damf_join": (c_i32, [c_vp, c_vp]),
     "damf_record_event": (c_i32, [c_vp, c_vp]),

@@ -79,6 +79,25 @@ def core_svd(sigma, L, R, stream=None):
     return E, H, th
 
 
+def apply_edges_multi(batches, stream=None):
+    """One batch per graph through damf_apply_edges_multi: batches is a list of
+    (DamfGraph, src, dst, op[, new_nodes]) with device-resident or array events."""
+    lib = _lib.load()
+    arr = (_lib.Batch * max(len(batches), 1))()
+    keep = []
+    for i, b in enumerate(batches):
+        g, src, dst, op = b[:4]
+        nn = int(b[4]) if len(b) > 4 else 0
+        s, t, o = _dev(src, torch.int32), _dev(dst, torch.int32), _dev(op, torch.int8)
+        keep += [s, t, o]
+        g._keep = (s, t, o)   # alive until the stream has consumed them
+        arr[i] = _lib.Batch(g.h.value if hasattr(g.h, "value") else g.h, s.data_ptr(), t.data_ptr(), o.data_ptr(),
+                            int(s.numel()), nn)
+    st = lib.damf_apply_edges_multi(arr, len(batches), _stream_ptr(stream))
+    if st != 0:
+        raise DamfError(st, "apply_edges_multi")
+
+
 class DamfGraph:
     """One graph's DAMF state on the current CUDA device (a damf_ctx)."""
 

@@ -449,6 +449,17 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
   return DAMF_OK;
 }
 
+damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream) {
+  if (num_graphs < 0 || (num_graphs > 0 && !batches)) return DAMF_ERR_INVALID;
+  for (int32_t i = 0; i < num_graphs; ++i) {
+    const damf_batch& b = batches[i];
+    if (!b.ctx) return DAMF_ERR_INVALID;
+    const damf_status st = damf_apply_edges(b.ctx, b.src, b.dst, b.op, b.k, b.new_nodes, stream);
+    if (st != DAMF_OK) return st;
+  }
+  return DAMF_OK;
+}
+
 damf_status damf_apply_edges_host(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
                                   int32_t new_nodes, void* stream) {
   if (!x) return DAMF_ERR_INVALID;

@@ -439,6 +439,25 @@ __global__ void k_in_fill(const int32_t* row_ptr, const int32_t* col_idx, int n,
   }
 }
 
+// Sorts every row of the in-adjacency by source id (insertion sort, one thread per row), so
+// the in-rows do not depend on the order in which k_in_fill's atomics ran: two contexts built
+// from the same graph hold the same adjacency, and sums over in-rows round the same way.
+__global__ void k_sort_rows(const int32_t* start, const int32_t* len, int n, int32_t* col) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int32_t* row = col + start[u];
+  const int k = len[u];
+  for (int i = 1; i < k; ++i) {
+    const int32_t x = row[i];
+    int j = i - 1;
+    while (j >= 0 && row[j] > x) {
+      row[j + 1] = row[j];
+      --j;
+    }
+    row[j + 1] = x;
+  }
+}
+
 __global__ void k_cap_from_len(const int32_t* len, int n, int32_t* cap) {
   int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n) return;
@@ -481,6 +500,7 @@ cudaError_t build_adjacency(Ctx* c, Adj* a, const int32_t* row_ptr, const int32_
     int32_t* fillpos = c->ws.queue;  // >= n ints of scratch, unused until the first push
     cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * (size_t)n, s);
     k_in_fill<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, fillpos, a->col);
+    k_sort_rows<<<nb, 256, 0, s>>>(a->start, a->len, n, a->col);
     cudaMemsetAsync(fillpos, 0xff, sizeof(int32_t) * (size_t)n, s);   // empty queue slots again
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

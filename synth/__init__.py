@@ -16,5 +16,6 @@ from .chung_lu import (  # noqa: F401
     edge_stream,
     gaussian_test_matrix,
     csr_from_edges,
+    node_arrival_stream,
 )
 from .configs import CONFIGS, small_config  # noqa: F401

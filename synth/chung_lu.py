@@ -190,3 +190,35 @@ def gaussian_test_matrix(n_rows: int, l: int, seed: int) -> np.ndarray:
     of the randomized t-SVD (Halko et al.), passed as an input to both sides."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((n_rows, l), dtype=np.float32)
+
+
+def node_arrival_stream(indptr: np.ndarray, indices: np.ndarray, n0: int, directed: bool = False):
+    """The paper's node-arrival protocol (Sec. 5.1, "Setting of Dynamicity"): the graph
+    induced on nodes 0 .. n0-1 is the initial graph; nodes n0, n0+1, ... then arrive one at a
+    time, each with its edges to the nodes already present (an undirected edge {u, v} arrives
+    with the later of u and v; a directed one with the later endpoint, in its direction).
+    Node ids are already a random permutation of the Chung-Lu weights, so arrival in id order
+    is arrival in random order.  Returns (indptr0, indices0, EdgeStream) with one Batch per
+    node, new_nodes = 1."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    indices = np.asarray(indices, dtype=np.int64)
+    n = len(indptr) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(indptr))
+    cols = indices
+    keep0 = (rows < n0) & (cols < n0)
+    ip0, ix0 = csr_from_edges(n0, rows[keep0], cols[keep0])
+    later = np.maximum(rows, cols)
+    if directed:
+        sel = later >= n0
+    else:
+        sel = (later >= n0) & (rows < cols)      # each undirected edge once
+    r, c, lt = rows[sel], cols[sel], later[sel]
+    order = np.lexsort((c, r, lt))
+    r, c, lt = r[order], c[order], lt[order]
+    bounds = np.searchsorted(lt, np.arange(n0, n + 1))
+    batches = []
+    for i, v in enumerate(range(n0, n)):
+        a, b = bounds[i], bounds[i + 1]
+        batches.append(Batch(src=r[a:b].astype(np.int32), dst=c[a:b].astype(np.int32),
+                             op=np.ones(b - a, dtype=np.int8), new_nodes=1))
+    return ip0, ix0, EdgeStream(n0=n0, batches=batches)

@@ -215,6 +215,42 @@ def test_degree_scaled_threshold_bound(directed):
     g.close()
 
 
+def test_apply_edges_multi_equals_each_graph_alone():
+    # graphs of uneven size and rank in one call: every graph's factor state must be the same,
+    # bit for bit, as when its batch is applied alone (the push order is free, so Z_b and r are
+    # compared through the eps bound elsewhere)
+    from paper_2306_08967_gb300 import apply_edges_multi
+    rng = np.random.default_rng(23)
+    specs = [(400, 16, False), (900, 32, True), (650, 64, False)]
+    mix = [make_pair(n, 8.0, 2.5, d, 0.15, 1e-5, SEED + 40 + i, directed=dr, oracle=False)[0]
+           for i, (n, d, dr) in enumerate(specs)]
+    alone = [make_pair(n, 8.0, 2.5, d, 0.15, 1e-5, SEED + 40 + i, directed=dr, oracle=False)[0]
+             for i, (n, d, dr) in enumerate(specs)]
+    for step in range(4):
+        batches = []
+        for (n, d, dr), gm, ga in zip(specs, mix, alone):
+            src, dst, op = _events(rng, n, int(rng.integers(1, 70)))
+            batches.append((gm, src, dst, op))
+            ga.apply_edges(src, dst, op)
+            ga.ppr_refresh()
+        apply_edges_multi(batches)
+        for gm in mix:
+            gm.ppr_refresh()
+    for i, (gm, ga) in enumerate(zip(mix, alone)):
+        gm.check()
+        ga.check()
+        a, b = gm.state(), ga.state()
+        for k in ("Ub", "Vb", "PU", "PV", "sigma"):
+            assert torch.equal(a[k], b[k]), (i, k)
+        ra, ca = gm.adjacency()
+        rb, cb = ga.adjacency()
+        assert np.array_equal(ra, rb)
+        for u in range(len(ra) - 1):
+            assert sorted(ca[ra[u]:ra[u + 1]].tolist()) == sorted(cb[rb[u]:rb[u + 1]].tolist())
+        gm.close()
+        ga.close()
+
+
 def test_alpha_one_gives_z_equal_x():
     # the paper's ablation: alpha = 1 means Z = X
     g, _, _ = make_pair(300, 8.0, 2.5, 16, 1.0, 1e-6, SEED + 9, oracle=False)
@@ -250,6 +286,39 @@ def test_c1_stream_against_oracle():
     # singular value), so compare the invariant product Z Y^T = PPR(X Y^T)
     Zg = g.embeddings()["Z"].double().cpu().numpy()
     assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_node_arrival_stream_against_oracle(directed):
+    # the paper's protocol (Sec. 5.1): an initial induced graph, then nodes arrive one at a time
+    # with their edges to the nodes already present; one call (and one push) per node event
+    from oracle.damf import DamfOracle
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix, node_arrival_stream
+    n, n0, d = 520, 220, 16
+    ip, ix, _ = chung_lu_graph(n, 8.0, 2.5, seed=SEED + 60, directed=directed)
+    ip0, ix0, stream = node_arrival_stream(ip, ix, n0, directed=directed)
+    cfg = make_config(n0, d, 0.15, 1e-4, n_capacity=n, nnz=len(ix0), directed=directed)
+    om = gaussian_test_matrix(n0, rsvd_width(cfg), seed=SEED + 61)
+    g = DamfGraph(ip0, ix0, cfg, om)
+    orc = DamfOracle(ip0, ix0, d, 0.15, 1e-4, n_cap=n, directed=directed, Omega=om)
+    for b in stream.batches:
+        g.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        g.ppr_refresh()
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        orc.ppr_refresh()
+    g.check()
+    assert g.n == n
+    Xg, Yg, sg = gpu_xy(g)
+    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
+    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    Zg = g.embeddings()["Z"].double().cpu().numpy()
+    assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
+    # the final graph is the full graph
+    rp, col = g.adjacency()
+    A = dense_adj(rp, col, n)
+    assert np.array_equal(A, dense_adj(ip, ix, n))
     g.close()
 
 
