@@ -137,6 +137,19 @@ typedef struct {
  */
 damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
 
+/*
+ * Node deletion (not treated by the paper, whose events add nodes): removes every edge of
+ * each node in nodes (host int32[count], ids < n), i.e. zeroes row u and column u of A, as
+ * ordinary updates: the node's current adjacency rows (out, and in for a directed graph) are
+ * expanded on the device into deletion events, applied like damf_apply_edges (so the result
+ * is the rank-d t-SVD of the previous product plus that change, Theorem 2), in chunks of at
+ * most 4096 events. The id stays valid as an isolated node; no id is renumbered. Reads each
+ * node's degree from the device (synchronises `stream` once per node and direction). The
+ * push (damf_ppr_refresh) follows as for any update. DAMF_ERR_INVALID (context usable) for
+ * a bad id or argument.
+ */
+damf_status damf_delete_nodes(damf_ctx* ctx, const int32_t* nodes, int32_t count, void* stream);
+
 /* Same as damf_apply_edges with src, dst, op in (host) memory: the library copies
  * them to the device on `stream` (k <= 4096). */
 damf_status damf_apply_edges_host(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,

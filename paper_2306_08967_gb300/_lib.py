@@ -40,6 +40,7 @@ SIGNATURES = {
     "damf_apply_edges": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_multi": (c_i32, [c_vp, c_i32, c_vp]),
+    "damf_delete_nodes": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
     "damf_ppr_refresh": (c_i32, [c_vp, c_vp]),
     "damf_join": (c_i32, [c_vp, c_vp]),
     "damf_record_event": (c_i32, [c_vp, c_vp]),

@@ -136,6 +136,12 @@ class DamfGraph:
                                               ctypes.c_void_p(o.data_ptr()), int(s.numel()), int(new_nodes),
                                               _stream_ptr(stream)))
 
+    def delete_nodes(self, nodes, stream=None):
+        """Removes every edge of the given nodes (host ids); the ids stay as isolated nodes."""
+        a = np.ascontiguousarray(nodes, dtype=np.int32)
+        self._check(self.lib.damf_delete_nodes(self.h, a.ctypes.data_as(ctypes.c_void_p), int(a.size),
+                                               _stream_ptr(stream)))
+
     def apply_edges_host(self, src: np.ndarray, dst: np.ndarray, op: np.ndarray, new_nodes: int = 0, stream=None):
         """Host events: the library copies them to the device on the stream."""
         s = np.ascontiguousarray(src, dtype=np.int32)

@@ -449,6 +449,50 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
   return DAMF_OK;
 }
 
+damf_status damf_delete_nodes(damf_ctx* x, const int32_t* nodes, int32_t count, void* stream) {
+  if (!x) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (count < 0 || (count > 0 && !nodes) || !c->dev_stage) return reject(c, "delete_nodes: bad argument");
+  for (int32_t i = 0; i < count; ++i)
+    if (nodes[i] < 0 || nodes[i] >= c->n) return reject(c, "delete_nodes: node id out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* es = c->dev_stage;
+  int32_t* ed = c->dev_stage + kHostStageMax;
+  int8_t* eo = (int8_t*)(c->dev_stage + 2 * kHostStageMax);
+  for (int32_t i = 0; i < count; ++i) {
+    const int u = nodes[i];
+    // the rows' current lengths (earlier deletions of this call may have shortened them)
+    int32_t dg[2] = {0, 0};
+    DAMF_CUDA(cudaMemcpyAsync(&dg[0], c->out.len + u, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "degree");
+    if (c->cfg.directed)
+      DAMF_CUDA(cudaMemcpyAsync(&dg[1], c->in.len + u, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "degree");
+    DAMF_CUDA(cudaStreamSynchronize(s), "degree sync");
+    if (dg[0] + dg[1] <= kHostStageMax) {   // both rows in one call
+      if (dg[0] > 0) DAMF_CUDA(launch_expand_row(c, u, dg[0], 0, es, ed, eo, s), "expand row");
+      if (dg[1] > 0) DAMF_CUDA(launch_expand_row(c, u, dg[1], 1, es + dg[0], ed + dg[0], eo + dg[0], s), "expand row");
+      c->launches += (dg[0] > 0) + (dg[1] > 0);
+      if (dg[0] + dg[1] > 0) {
+        const damf_status st = damf_apply_edges(x, es, ed, eo, dg[0] + dg[1], 0, stream);
+        if (st != DAMF_OK) return st;
+      }
+      continue;
+    }
+    for (int incoming = 0; incoming < (c->cfg.directed ? 2 : 1); ++incoming) {
+      int32_t deg = dg[incoming];
+      while (deg > 0) {
+        const int cnt = deg < kHostStageMax ? deg : kHostStageMax;
+        DAMF_CUDA(launch_expand_row(c, u, cnt, incoming, es, ed, eo, s), "expand row");
+        c->launches += 1;
+        const damf_status st = damf_apply_edges(x, es, ed, eo, cnt, 0, stream);
+        if (st != DAMF_OK) return st;
+        deg -= cnt;
+      }
+    }
+  }
+  return DAMF_OK;
+}
+
 damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream) {
   if (num_graphs < 0 || (num_graphs > 0 && !batches)) return DAMF_ERR_INVALID;
   for (int32_t i = 0; i < num_graphs; ++i) {

@@ -214,6 +214,8 @@ cudaError_t launch_core(Ctx* c, cudaStream_t s);
 cudaError_t launch_transforms(Ctx* c, cudaStream_t s);
 cudaError_t launch_scatter(Ctx* c, cudaStream_t s);
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s);
+cudaError_t launch_expand_row(Ctx* c, int u, int cnt, int incoming, int32_t* src, int32_t* dst, int8_t* op,
+                              cudaStream_t s);
 cudaError_t launch_score_pairs(Ctx* c, const int32_t* src, const int32_t* dst, int count, int context, int symmetric,
                                float* scores, cudaStream_t s);
 cudaError_t launch_topk(Ctx* c, const int32_t* rows, int count, int k, int context, int symmetric, int32_t* out_idx,

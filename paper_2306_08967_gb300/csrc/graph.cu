@@ -439,6 +439,25 @@ __global__ void k_in_fill(const int32_t* row_ptr, const int32_t* col_idx, int n,
   }
 }
 
+// Node deletion: the first cnt entries of row u as deletion events (u, w, -1), or (w, u, -1)
+// for a row of the in-adjacency.
+__global__ void k_expand_row(Adj a, int u, int cnt, int incoming, int32_t* src, int32_t* dst, int8_t* op) {
+  const int st = a.start[u];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int w = a.col[st + i];
+    src[i] = incoming ? w : u;
+    dst[i] = incoming ? u : w;
+    op[i] = -1;
+  }
+}
+
+cudaError_t launch_expand_row(Ctx* c, int u, int cnt, int incoming, int32_t* src, int32_t* dst, int8_t* op,
+                              cudaStream_t s) {
+  const Adj a = incoming ? c->in : c->out;
+  k_expand_row<<<(cnt + 255) / 256, 256, 0, s>>>(a, u, cnt, incoming, src, dst, op);
+  return cudaGetLastError();
+}
+
 // Sorts every row of the in-adjacency by source id (insertion sort, one thread per row), so
 // the in-rows do not depend on the order in which k_in_fill's atomics ran: two contexts built
 // from the same graph hold the same adjacency, and sums over in-rows round the same way.

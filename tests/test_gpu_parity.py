@@ -79,6 +79,49 @@ def test_each_update_equals_bruteforce_tsvd(directed):
 
 
 @pytest.mark.parametrize("directed", [False, True])
+def test_node_deletion(directed):
+    # deleting a node = zeroing its row and column of A; a node of degree <= 48 goes in one
+    # update, which must equal the brute-force t-SVD of (previous product + that change)
+    # (Theorem 2); a hub goes in several updates; the adjacency loses exactly its edges
+    n, d = 400, 16
+    g, _, (ip, ix, _) = make_pair(n, 8.0, 2.5, d, 0.15, 1e-4, SEED + 70, directed=directed, oracle=False)
+    rp, col = g.adjacency()
+    A = dense_adj(rp, col, n)
+    deg = A.sum(axis=1) + A.sum(axis=0)
+    small = int(np.argmax(np.where((deg >= 8) & (deg <= 40), deg, -1)))
+    checked = 0
+    for u in (small, int(np.argmax(deg))):
+        X1, Y1, _ = gpu_xy(g)
+        rp0, col0 = g.adjacency()
+        A0 = dense_adj(rp0, col0, n)
+        g.delete_nodes([u])
+        g.ppr_refresh()
+        g.check()
+        rp1, col1 = g.adjacency()
+        A1 = dense_adj(rp1, col1, n)
+        want = A0.copy()
+        want[u, :] = 0.0
+        want[:, u] = 0.0
+        assert np.array_equal(A1, want)
+        if u == small:
+            dA = A1 - A0
+            target = X1 @ Y1.T + dA
+            sv = np.linalg.svd(target, compute_uv=False)
+            if (sv[d - 1] - sv[d]) / sv[0] > 1e-3:
+                X2, Y2, s2 = brute_force_update(X1, Y1, dA, d)
+                Xg, Yg, sg = gpu_xy(g)
+                np.testing.assert_allclose(sg, s2, rtol=2e-4)
+                assert rel_fro(Xg @ Yg.T, X2 @ Y2.T) < 2e-4
+                checked += 1
+    assert checked == 1
+    from paper_2306_08967_gb300 import DamfError
+    with pytest.raises(DamfError):
+        g.delete_nodes([n + 5])
+    g.check()                      # a rejected id leaves the context usable
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
 def test_adjacency_and_touched_sets_bit_exact(directed):
     from oracle.graph import DynGraph
     rng = np.random.default_rng(9)
