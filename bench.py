@@ -455,6 +455,8 @@ def run_ours(args, c, rank, world):
                      "jacobi_sweeps": s1["jacobi_sweeps"] - s0["jacobi_sweeps"],
                      "jacobi_full": s1["jacobi_full"] - s0["jacobi_full"],
                      "jacobi_gersh": s1["jacobi_gersh"] - s0["jacobi_gersh"],
+                     "push_tasks": s1["push_tasks"] - s0["push_tasks"],
+                     "push_items": s1["push_items"] - s0["push_items"],
                      "push_phase_ms": {k: (s1["push_ns"][i] - s0["push_ns"][i]) / 1e6 for i, k in
                                        enumerate(["seeding", "task_loop", "barriers"])}},
         "init_s": init_s,

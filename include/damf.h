@@ -104,8 +104,8 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
  *     directions.  Set semantics: per ordered pair the last event decides whether
  *     the edge is present; inserting a present edge or deleting an absent one is a
  *     no-op.
- * The events are applied as ceil(k/48) consecutive updates of at most 48 events
- * each (rank r <= 96).  Each update: edits the adjacency; projects dA onto the
+ * The events are applied as ceil(k/64) consecutive updates of at most 64 events
+ * each (rank r <= 128).  Each update: edits the adjacency; projects dA onto the
  * bases (W_B = U^T B, W_C = V^T C); re-orthogonalises the residual blocks by
  * Cholesky of their Gram matrices (Prop. 1 for a block); takes the SVD of the
  * (d+r) x (d+r) core; folds the rotation into P_U, P_V and their inverses; rewrites
@@ -241,7 +241,7 @@ damf_status damf_export_adjacency(damf_ctx* ctx, int32_t outgoing, int64_t* row_
 
 /*
  * Touched sets of the most recent update (Lemma 1: the rows of U_b, V_b it rewrote):
- * S (host) int32[96] sorted source rows, T (host) int32[96] sorted target rows.
+ * S (host) int32[128] sorted source rows, T (host) int32[128] sorted target rows.
  * Blocks on the device.
  */
 damf_status damf_get_last_touched(damf_ctx* ctx, int32_t* S, int32_t* nS, int32_t* T, int32_t* nT);
@@ -252,7 +252,7 @@ damf_status damf_get_last_touched(damf_ctx* ctx, int32_t* S, int32_t* nS, int32_
  *     M = [[diag(sigma), 0], [0, 0]] + L R^T,
  * computed by the kernels of the update path (one-CTA one-sided Jacobi).  No context.
  *   sigma (device) float32[d]; L, R (device) float32[(d+r) x r] row-major (L = [W_B; R_B],
- *   R = [W_C; R_C] in the paper's notation); d in {16, 32, 64, 128}, 1 <= r <= 96.
+ *   R = [W_C; R_C] in the paper's notation); d in {16, 32, 64, 128}, 1 <= r <= 128.
  *   E, H (device) float32[(d+r) x d] row-major: column k is the k-th left / right
  *   singular vector (non-increasing singular values); theta (device) float32[d].
  *   workspace (device): at least damf_core_svd_workspace_size(d, r) bytes, 256-byte
@@ -272,9 +272,9 @@ damf_status damf_core_svd(const float* sigma, const float* L, const float* R, in
  * counterpart; this is a deployment variant of Step 2.
  *   Arguments and results are those of damf_core_svd.  The caller still provides and
  *   owns every input and output.  Nothing is allocated: the scratch (a status word and
- *   the assembled core) is one static device array of 200,960 bytes compiled into the
+ *   the assembled core) is one static device array of 262,400 bytes compiled into the
  *   library, which every GPU that loads the library holds until the process exits.
- *   Limit: d + r <= 224 (d in {16, 32, 64, 128}, 1 <= r <= 96); a larger r returns
+ *   Limit: d + r <= 256 (d in {16, 32, 64, 128}, 1 <= r <= 128); a larger r returns
  *   DAMF_ERR_CAPACITY, bad d or NULL pointers DAMF_ERR_INVALID.
  *   The first call on each device looks up the array's device address (with that device
  *   current); make that first call before any stream capture.
@@ -306,6 +306,8 @@ typedef struct {
   int64_t jacobi_sweeps;    /* Jacobi sweeps over all updates */
   int64_t jacobi_full;      /* updates whose core needed sweeps over every pair */
   int64_t jacobi_gersh;     /* updates that needed the exact Gershgorin gap check */
+  int64_t push_tasks;       /* push row tasks (a row taken from the queue, pushed or found below eps) */
+  int64_t push_items;       /* push hub-item tasks (one chunk of a hub's in-edges) */
   int64_t push_ns[4];       /* push time seen by one CTA (ns): seeding, task loop, grid barriers, unused */
 } damf_stats;
 

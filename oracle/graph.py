@@ -18,7 +18,7 @@ import numpy as np
 from .build import build
 
 # A call's edges are applied as consecutive updates of at most this many edges each.
-EDGES_PER_UPDATE = 48
+EDGES_PER_UPDATE = 64
 
 _lib = None
 

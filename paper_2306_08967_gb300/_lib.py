@@ -29,7 +29,8 @@ class Stats(ctypes.Structure):
                 ("push_edges", c_i64), ("push_rounds", c_i64), ("fixup_edges", c_i64), ("touched_rows", c_i64),
                 ("folds", c_i64), ("last_rank", c_i32), ("last_status", c_i32), ("launches", c_i64),
                 ("last_sweeps", c_i32), ("reserved", c_i32), ("jacobi_sweeps", c_i64), ("jacobi_full", c_i64),
-                ("jacobi_gersh", c_i64), ("push_ns", c_i64 * 4)]
+                ("jacobi_gersh", c_i64),
+                ("push_tasks", c_i64), ("push_items", c_i64), ("push_ns", c_i64 * 4)]
 
 
 # every symbol include/damf.h declares, with its ctypes signature

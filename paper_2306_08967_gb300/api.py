@@ -236,8 +236,8 @@ class DamfGraph:
         return rp, col[: rp[-1]]
 
     def last_touched(self):
-        S = np.zeros(96, dtype=np.int32)
-        T = np.zeros(96, dtype=np.int32)
+        S = np.zeros(128, dtype=np.int32)   # an update touches at most 128 rows
+        T = np.zeros(128, dtype=np.int32)
         ns = ctypes.c_int32()
         nt = ctypes.c_int32()
         self._check(self.lib.damf_get_last_touched(self.h, S.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ns),

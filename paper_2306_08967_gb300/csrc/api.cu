@@ -718,6 +718,8 @@ damf_status damf_get_stats(damf_ctx* x, damf_stats* o) {
   o->jacobi_sweeps = h.jacobi_sweeps;
   o->jacobi_full = h.jacobi_full;
   o->jacobi_gersh = h.jacobi_gersh;
+  o->push_tasks = h.push_tasks;
+  o->push_items = h.push_items;
   for (int i = 0; i < 4; ++i) o->push_ns[i] = (int64_t)h.push_ns[i];
   return DAMF_OK;
 }

@@ -16,11 +16,11 @@
 
 namespace damf {
 
-constexpr int kMaxR = 96;                 // maximum rank of one update
-constexpr int kEdgesPerUpdate = 48;       // events per update (undirected: 2 entries each)
+constexpr int kMaxR = 128;                // maximum rank of one update
+constexpr int kEdgesPerUpdate = 64;       // events per update (undirected: 2 entries each)
 constexpr int kMaxEntries = 2 * kEdgesPerUpdate;
 constexpr int kMaxD = 128;
-constexpr int kMaxM = kMaxD + kMaxR;      // 224: largest core
+constexpr int kMaxM = kMaxD + kMaxR;      // 256: largest core
 constexpr int kChainThreads = 512;        // one-CTA chain kernels: leave room beside a push
 constexpr long long kSpinLimit = 1ll << 26;  // iterations of a bounded wait (with nanosleep)
 constexpr int kTopQ = 32;                 // queries per top-k pass (score.cu)
@@ -50,6 +50,7 @@ struct DevHeader {
   int last_rank;
   int last_sweeps;       // Jacobi sweeps of the most recent update
   long long jacobi_sweeps, jacobi_full, jacobi_gersh;
+  long long push_tasks, push_items;
   unsigned long long push_ns[4];   // block 0 of the push: seeding, task loop, barriers, - (ns)
   // push work queue (ppr.cu), zeroed before each launch: qstate = (tasks not finished << 32) |
   // queue tail; q_head = next queue position to claim; bump counters of rho slots and items

@@ -32,10 +32,10 @@ namespace damf {
 constexpr int kClP = 8;                          // CTAs per cluster (the portable maximum)
 constexpr int kClBlocks = 2 * kClP;              // column blocks
 constexpr int kClL = kClBlocks - 1;              // steps per sweep
-constexpr int kClBsMax = kMaxM / kClBlocks;      // 14 columns per block at most
+constexpr int kClBsMax = kMaxM / kClBlocks;      // 16 columns per block at most
 // 16 warps at <= 64 registers: 4 warps of 2K registers per SM sub-partition, the half of its
 // 16K register file that two CTAs of the push (256 threads x 64 registers) leave free, so
-// the cluster runs beside a push (a 14th pair warp and up are idle in a round)
+// the cluster runs beside a push; one warp per pair of a round (16 pairs at most)
 constexpr int kClThreads = 512;
 constexpr int kClStride = 256;                   // floats per column: rows padded with zeros
 constexpr float kClTol = 1e-6f;                  // rotate while |a_p . a_q| > tol |a_p| |a_q|
@@ -112,15 +112,17 @@ __device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float
   const float aa = *np, bb = *nq;
   if (!(g * g > tol2 * aa * bb)) return false;
   // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g): the smaller root of
-  // t^2 + 2 zeta t - 1 = 0, so that the rotated columns are orthogonal. Hardware approximations
-  // (a few ulp) suffice: cs and sn are derived from the same t, so the rotation stays
-  // orthogonal to rounding and an inexact angle only leaves a smaller g for the next sweep.
+  // t^2 + 2 zeta t - 1 = 0, so that the rotated columns are orthogonal. The angle may come
+  // from hardware approximations (an inexact t only leaves a smaller g for the next sweep),
+  // but cs = 1/sqrt(1 + t^2) is rounded to nearest: the rotation scales both columns by
+  // cs^2 (1 + t^2), and the approximate reciprocal square root errs to one side, which over
+  // the ~700 rotations a column sees per update shrank every singular value by ~1e-5.
   const float zeta = __fdividef(bb - aa, 2.0f * g);
   const float az = fabsf(zeta);
   const float s1 = fmaf(az, az, 1.0f);
   const float ta = az < 1e15f ? __fdividef(1.0f, fmaf(s1, rsqrtf(s1), az)) : __fdividef(0.5f, az);
   const float t = copysignf(ta, zeta);
-  const float cs = rsqrtf(fmaf(t, t, 1.0f));
+  const float cs = __frsqrt_rn(fmaf(t, t, 1.0f));
   const float sn = cs * t;
   const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ms2 = make_float2(-sn, -sn);
   {

@@ -22,7 +22,7 @@ namespace {
 
 constexpr size_t kHeaderBytes = 256;
 static_assert(sizeof(DevHeader) <= kHeaderBytes, "status area too small");
-// status word area + the largest core (d + r <= 224) in FP32: 200,960 bytes
+// status word area + the largest core (d + r <= 256) in FP32: 262,400 bytes
 constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxM * kMaxM * sizeof(float);
 
 // Held by every GPU that loads the library, until the process exits.
@@ -38,7 +38,7 @@ extern "C" damf_status damf_core_svd_noalloc(const float* sigma, const float* L,
                                              int32_t r, float* E, float* H, float* theta, void* stream) {
   if (!(d == 16 || d == 32 || d == 64 || d == 128) || !sigma || !L || !R || !E || !H || !theta)
     return DAMF_ERR_INVALID;
-  if (r < 1 || r > kMaxR) return DAMF_ERR_CAPACITY;   // the scratch holds cores up to (128 + 96)^2
+  if (r < 1 || r > kMaxR) return DAMF_ERR_CAPACITY;   // the scratch holds cores up to (128 + 128)^2
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DAMF_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return DAMF_ERR_INVALID;

@@ -12,8 +12,8 @@
 //   * task "row u": clear u's in-queue flag, read v = r[u]; if max|v| > eps, remove exactly v
 //     (float4 atomic add of -v), add alpha v to Zb[u] (atomic), and scatter coef * v to the
 //     in-neighbours of u; a row with many in-edges (a hub) instead stores v in a rho slot and
-//     queues one "item" task per chunk of its in-edges, which spreads it over every warp.
-//   * task "item": scatter a hub's stored v to one chunk of its in-edges.
+//     queues one "item" task per kItemEdges of its in-edges, which spreads it over every warp.
+//   * task "item": scatter a hub's stored v to up to kItemEdges of its in-edges.
 // Every add returns the old value, so the thread whose add (or removal) is the last on an
 // element sees what it leaves there; a row left above eps is queued unless its flag says it
 // already is. The flag is cleared before the row is read, so an add that lands after that read
@@ -41,6 +41,8 @@ constexpr int kPushBlocksPerSM = 2;
 // A row with more than this many chunks of in-edges is a hub: its chunks become item tasks
 // (overridable with DAMF_PUSH_DIRECT_CHUNKS).
 constexpr int kPushDirectChunks = 8;
+// in-edges per hub item: small items spread a hub over many warps (measured: 8 beats 32)
+constexpr int kItemEdges = 8;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kTask = 1ull << 32;   // one unfinished task in qstate
@@ -174,49 +176,60 @@ __device__ __forceinline__ void enqueue_rows(bool want, int w, WarpQ& wq, DevHea
   stage(fresh, w, wq, h, queue, qcap, lane);
 }
 
-// One chunk of a scatter (warp-level): in-edges col[st .. st+ne), ne <= EPC. Lane e < ne owns
-// in-edge e (node w, coef (1-alpha)/deg(w)); group g adds coef * v to its float4s of r[w] for
-// the in-edges g, g + RPW, ..., all CHL atomics in flight before any result is looked at.
-// Each w an add left above its threshold is queued.
+// Scatter (warp-level): adds coef(w) * v to r[w] for the in-edges col[st .. st+ne) of a row,
+// coef(w) = (1-alpha)/deg(w). The in-edges and their out-degrees are loaded 32 at a time, one
+// per lane; then chunks of EPC in-edges follow, group g taking in-edges g, g + RPW, ... of
+// the chunk with all CHL atomics in flight before any result is looked at. Each w an add left
+// above its threshold is queued (unless enq is false: the adds only). Every lane calls it.
 template <int D, bool SCALED>
-__device__ __forceinline__ void scatter_chunk(const float4 v, int st, int ne, const int32_t* __restrict__ col,
+__device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, const int32_t* __restrict__ col,
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
                                               WarpQ& wq, DevHeader* h, uint32_t* inq, int32_t* queue, long long qcap,
                                               int lane, int sub, int q, bool enq = true) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
   constexpr int CHL = PushShape<D>::CHL;
-  int w_own = 0, d_own = 1;
-  float c_own = 0.f;
-  if (lane < ne) {
-    w_own = __ldg(col + st + lane);
-    d_own = __ldg(outdeg + w_own);
-    c_own = beta / (float)d_own;
-  }
-  float4 nv[CHL];
+  constexpr int EPC = PushShape<D>::EPC;
+  const unsigned gmask = (LPR == 32) ? kFull : ((1u << LPR) - 1u);
+  for (int b0 = 0; b0 < ne; b0 += 32) {   // warp-uniform
+    const int nb = min(32, ne - b0);
+    int w_own = 0, d_own = 1;
+    float c_own = 0.f;
+    if (lane < nb) {
+      w_own = __ldg(col + st + b0 + lane);
+      d_own = __ldg(outdeg + w_own);
+      c_own = beta / (float)d_own;
+    }
+    for (int c0 = 0; c0 < nb; c0 += EPC) {   // warp-uniform; the chunk's in-edges are lanes c0 ..
+      const int ncur = min(EPC, nb - c0);
+      float4 nv[CHL];
 #pragma unroll
-  for (int c = 0; c < CHL; ++c) {
-    const int e = c * RPW + sub;
-    const int w = __shfl_sync(kFull, w_own, e);
-    const float coef = __shfl_sync(kFull, c_own, e);
-    nv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < ne) {
-      const float4 add = make_float4(coef * v.x, coef * v.y, coef * v.z, coef * v.w);
-      const float4 old = atomicAdd(reinterpret_cast<float4*>(r + (size_t)w * D) + q, add);
-      nv[c] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
+      for (int c = 0; c < CHL; ++c) {
+        const int e = c * RPW + sub;
+        const int src = min(c0 + e, 31);
+        const int w = __shfl_sync(kFull, w_own, src);
+        const float coef = __shfl_sync(kFull, c_own, src);
+        nv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < ncur) {
+          const float4 add = make_float4(coef * v.x, coef * v.y, coef * v.z, coef * v.w);
+          const float4 old = atomicAdd(reinterpret_cast<float4*>(r + (size_t)w * D) + q, add);
+          nv[c] = make_float4(old.x + add.x, old.y + add.y, old.z + add.z, old.w + add.w);
+        }
+      }
+      if (!enq) continue;   // warp-uniform: the adds only (a rescan follows)
+      // lane l = c0 + c * RPW + g owns the chunk's in-edge c * RPW + g: its bit is group g's
+      // part of step c's ballot
+      const int le = lane - c0;
+      bool crossed = false;
+#pragma unroll
+      for (int c = 0; c < CHL; ++c) {
+        const float thr = SCALED ? __shfl_sync(kFull, threshold<true>(eps, d_own), min(c0 + c * RPW + sub, 31)) : eps;
+        const unsigned b = __ballot_sync(kFull, max_abs4(nv[c]) > thr);
+        if (le >= 0 && le / RPW == c) crossed = ((b >> ((le % RPW) * LPR)) & gmask) != 0u;
+      }
+      enqueue_rows(le >= 0 && le < ncur && crossed, w_own, wq, h, inq, queue, qcap, lane);
     }
   }
-  if (!enq) return;   // warp-uniform: the adds only (the rescan that follows finds the rows)
-  // lane l owns in-edge l = c * RPW + g: its bit is group g's part of step c's ballot
-  const unsigned gmask = (LPR == 32) ? kFull : ((1u << LPR) - 1u);
-  bool crossed = false;
-#pragma unroll
-  for (int c = 0; c < CHL; ++c) {
-    const float thr = SCALED ? __shfl_sync(kFull, threshold<true>(eps, d_own), c * RPW + sub) : eps;
-    const unsigned b = __ballot_sync(kFull, max_abs4(nv[c]) > thr);
-    if (lane / RPW == c) crossed = ((b >> ((lane % RPW) * LPR)) & gmask) != 0u;
-  }
-  enqueue_rows(lane < ne && crossed, w_own, wq, h, inq, queue, qcap, lane);
 }
 
 // Waits (lane 0) for queue position p: returns its entry, or -1 when no task is left (the
@@ -248,7 +261,6 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
                                                  int check_all, int direct_max) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
-  constexpr int EPC = PushShape<D>::EPC;
   const unsigned nblocks = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR, q = lane % LPR;
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   int32_t* queue = ws.queue;
   uint32_t* inq = ws.stamp;
   long long my_pushes = 0, my_edges = 0;
+  int my_rows = 0, my_items = 0;   // tasks taken by this warp (lane 0)
   const int npend = h->pending;
   // block 0's view of where the time goes (ns): seeding, task loop, barriers; [4] is the last
   // mark. Kept in shared memory, where it costs no registers.
@@ -322,6 +335,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         }
       }
       if (e >= 0) {
+        if (lane == 0) ++my_rows;
         // row task. The flag is cleared first; the removal of v below is ordered after the
         // clear (fence), so an add that lands after the removal finds the flag clear and queues
         // u again, while an add between the read of v and the removal shows in `left`.
@@ -358,8 +372,8 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
           }
           bool direct = true;
           if (deg > direct_max) {
-            // hub: a rho slot and one item task per chunk of in-edges
-            const int nch = (deg + EPC - 1) / EPC;
+            // hub: a rho slot and one item task per kItemEdges in-edges
+            const int nch = (deg + kItemEdges - 1) / kItemEdges;
             int slot = 0, ib = 0;
             if (lane == 0) {
               slot = atomicAdd(&h->rho_tail, 1);
@@ -373,24 +387,24 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
               for (int c0 = 0; c0 < nch; c0 += 32) {   // warp-uniform
                 const int c2 = c0 + lane;
                 if (c2 < nch)
-                  __stcg(ws.work + ib + c2, make_int4(slot, st + c2 * EPC, min(EPC, deg - c2 * EPC), 0));
+                  __stcg(ws.work + ib + c2,
+                         make_int4(slot, st + c2 * kItemEdges, min(kItemEdges, deg - c2 * kItemEdges), 0));
                 stage(c2 < nch, -(ib + c2 + 2), wq, h, queue, qcap, lane);
               }
             }
           }
           if (direct)
-            for (int c0 = 0; c0 < deg; c0 += EPC)
-              scatter_chunk<D, SCALED>(v, st + c0, min(EPC, deg - c0), in.col, outdeg, r, beta, eps, wq, h, inq,
-                                       queue, qcap, lane, sub, q);
+            scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q);
           // u itself: adds that reached r[u] between the read of v and its removal are still there
           lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
           enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
         }
       } else {
         // item task: one chunk of a hub's in-edges
+        if (lane == 0) ++my_items;
         const int4 wi = __ldcg(ws.work + (-e - 2));
         const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
-        scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
+        scatter_edges<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
                                  q);
       }
       wq.done += 1;
@@ -413,7 +427,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       for (long long i = gwarp; i < novf; i += nwarps) {
         const int4 wi = __ldcg(ws.work + __ldcg(ws.ovf + i));
         const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
-        scatter_chunk<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
+        scatter_edges<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
                                  false);
       }
     }
@@ -441,6 +455,10 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   if (lane == 0 && (my_pushes || my_edges)) {
     atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)my_pushes);
     atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)my_edges);
+  }
+  if (lane == 0 && (my_rows || my_items)) {
+    atomicAdd((unsigned long long*)&h->push_tasks, (unsigned long long)my_rows);
+    atomicAdd((unsigned long long*)&h->push_items, (unsigned long long)my_items);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     h->push_rounds += phase;

@@ -83,94 +83,77 @@ __global__ void __launch_bounds__(256) k_wct(DevHeader* h, Workspace ws) {
   }
 }
 
-// ---- a3: residual Grams and semi-definite Cholesky (one CTA) ----
+// ---- a3: residual Grams and semi-definite Cholesky (one CTA per Gram) ----
 template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace ws) {
+  // CTA 0: G_B = I - U[S] U[S]^T -> R_B; CTA 1: G_C = N N^T - (N V[T])(N V[T])^T -> R_C
   extern __shared__ float smem[];
-  float* GB = smem;                      // kMaxR x kMaxR
-  float* GC = GB + kMaxR * kMaxR;
-  float* US = GC + kMaxR * kMaxR;        // nS x D
-  float* WC = US + kMaxR * D;            // nS x D
-  float* Ns = WC + kMaxR * D;            // nS x nT
-  __shared__ float pivB, pivC;
-  __shared__ int keptB, keptC;
-  __shared__ float scaleB, scaleC;
+  const bool isC = blockIdx.x == 1;
+  float* G = smem;                       // kMaxR x kMaxR
+  float* X = G + kMaxR * kMaxR;          // nS x D: U[S] or W_C^T
+  float* Ns = X + kMaxR * D;             // nS x nT (CTA 1)
+  __shared__ float piv, scale;
+  __shared__ int kept;
   if (h->status != 0) return;
   const int nS = h->nS, nT = h->nT;
   if (nS == 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < nS * D / 4; i += nt) {
-    reinterpret_cast<float4*>(US)[i] = reinterpret_cast<const float4*>(ws.UST)[i];
-    reinterpret_cast<float4*>(WC)[i] = reinterpret_cast<const float4*>(ws.WCt)[i];
-  }
-  for (int i = tid; i < nS * nT; i += nt) Ns[i] = ws.N[i];
+  const float4* src = reinterpret_cast<const float4*>(isC ? ws.WCt : ws.UST);
+  for (int i = tid; i < nS * D / 4; i += nt) reinterpret_cast<float4*>(X)[i] = src[i];
+  if (isC)
+    for (int i = tid; i < nS * nT; i += nt) Ns[i] = ws.N[i];
   __syncthreads();
   for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
     if (b < a) continue;
-    float gb = (a == b) ? 1.0f : 0.0f, gc = 0.f;
-    for (int t = 0; t < nT; ++t) gc = fmaf(Ns[a * nT + t], Ns[b * nT + t], gc);
-    float sb = 0.f, sc = 0.f;
+    float g = (!isC && a == b) ? 1.0f : 0.0f;
+    if (isC)
+      for (int t = 0; t < nT; ++t) g = fmaf(Ns[a * nT + t], Ns[b * nT + t], g);
+    float sx = 0.f;
 #pragma unroll 4
-    for (int k = 0; k < D; ++k) {
-      sb = fmaf(US[a * D + k], US[b * D + k], sb);
-      sc = fmaf(WC[a * D + k], WC[b * D + k], sc);
-    }
-    gb -= sb;
-    gc -= sc;
-    GB[a * kMaxR + b] = GB[b * kMaxR + a] = gb;
-    GC[a * kMaxR + b] = GC[b * kMaxR + a] = gc;
+    for (int k = 0; k < D; ++k) sx = fmaf(X[a * D + k], X[b * D + k], sx);
+    g -= sx;
+    G[a * kMaxR + b] = G[b * kMaxR + a] = g;
   }
   __syncthreads();
   if (tid == 0) {
-    float mb = 1.0f, mc = 1.0f;
-    for (int a = 0; a < nS; ++a) {
-      mb = fmaxf(mb, GB[a * kMaxR + a]);
-      mc = fmaxf(mc, GC[a * kMaxR + a]);
-    }
-    scaleB = mb * kPivotTol;
-    scaleC = mc * kPivotTol;
-    keptB = keptC = 0;
+    float mx = 1.0f;
+    for (int a = 0; a < nS; ++a) mx = fmaxf(mx, G[a * kMaxR + a]);
+    scale = mx * kPivotTol;
+    kept = 0;
   }
   __syncthreads();
   // right-looking Cholesky G = R^T R (R upper); rows with a pivot <= tol are zero
   for (int j = 0; j < nS; ++j) {
     if (tid == 0) {
-      const float pb = GB[j * kMaxR + j], pc = GC[j * kMaxR + j];
-      pivB = pb > scaleB ? sqrtf(pb) : 0.0f;
-      pivC = pc > scaleC ? sqrtf(pc) : 0.0f;
-      keptB += pivB > 0.f;
-      keptC += pivC > 0.f;
+      const float p = G[j * kMaxR + j];
+      piv = p > scale ? sqrtf(p) : 0.0f;
+      kept += piv > 0.f;
     }
     __syncthreads();
-    const float ib = pivB > 0.f ? 1.0f / pivB : 0.0f, ic = pivC > 0.f ? 1.0f / pivC : 0.0f;
-    // row j of R
-    for (int l = j + tid; l < nS; l += nt) {
-      GB[j * kMaxR + l] = (l == j) ? pivB : GB[j * kMaxR + l] * ib;
-      GC[j * kMaxR + l] = (l == j) ? pivC : GC[j * kMaxR + l] * ic;
-    }
+    const float ip = piv > 0.f ? 1.0f / piv : 0.0f;
+    for (int l = j + tid; l < nS; l += nt) G[j * kMaxR + l] = (l == j) ? piv : G[j * kMaxR + l] * ip;
     __syncthreads();
     const int rem = nS - j - 1;
     for (int i = tid; i < rem * rem; i += nt) {
       const int a = j + 1 + i / rem, b = j + 1 + i % rem;
       if (b < a) continue;
-      const float vb = GB[a * kMaxR + b] - GB[j * kMaxR + a] * GB[j * kMaxR + b];
-      const float vc = GC[a * kMaxR + b] - GC[j * kMaxR + a] * GC[j * kMaxR + b];
-      GB[a * kMaxR + b] = vb;
-      GC[a * kMaxR + b] = vc;
-      GB[b * kMaxR + a] = vb;
-      GC[b * kMaxR + a] = vc;
+      const float v = G[a * kMaxR + b] - G[j * kMaxR + a] * G[j * kMaxR + b];
+      G[a * kMaxR + b] = v;
+      G[b * kMaxR + a] = v;
     }
     __syncthreads();
   }
+  float* R = isC ? ws.RC : ws.RB;
   for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
-    ws.RB[a * kMaxR + b] = b >= a ? GB[a * kMaxR + b] : 0.0f;
-    ws.RC[a * kMaxR + b] = b >= a ? GC[a * kMaxR + b] : 0.0f;
+    R[a * kMaxR + b] = b >= a ? G[a * kMaxR + b] : 0.0f;
   }
   if (tid == 0) {
-    h->rankB = keptB;
-    h->rankC = keptC;
+    if (isC)
+      h->rankC = kept;
+    else
+      h->rankB = kept;
   }
 }
 
@@ -547,9 +530,9 @@ static cudaError_t chol_impl(Ctx* c, cudaStream_t s) {
   k_wct<D><<<kMaxR / 16, 256, smw, s>>>(c->hdr, c->ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t sm = (size_t)(3 * kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
+  const size_t sm = (size_t)(2 * kMaxR * kMaxR + kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_chol<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_chol<D><<<1, kChainThreads, sm, s>>>(c->hdr, c->ws);
+  k_chol<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
   return cudaGetLastError();
 }
 

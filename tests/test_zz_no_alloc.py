@@ -58,7 +58,7 @@ def test_noalloc_matches_workspace_entry_point_twice():
 def test_noalloc_rejects_cores_beyond_its_scratch():
     from paper_2306_08967_gb300 import _lib
     lib = _lib.load()
-    # r = 97 exceeds the static scratch (d + r <= 224): refused before any device work
+    # r = 129 exceeds the static scratch (d + r <= 256): refused before any device work
     dummy = ctypes.c_void_p(16)
-    assert lib.damf_core_svd_noalloc(dummy, dummy, dummy, 128, 97, dummy, dummy, dummy, None) == 2
+    assert lib.damf_core_svd_noalloc(dummy, dummy, dummy, 128, 129, dummy, dummy, dummy, None) == 2
     assert lib.damf_core_svd_noalloc(dummy, dummy, dummy, 24, 8, dummy, dummy, dummy, None) == 1
