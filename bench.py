@@ -198,7 +198,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one k_push launch of this workload, from the ncu capture
 # summarised in profiles/k_push_C2.md; None once k_push changes until it is captured again
-PUSH_DRAM_BYTES = 459.29e6
+PUSH_DRAM_BYTES = 478.21e6
 
 # ---------------------------------------------------------------- GPU leg
 def measure_scoring(g, c, torch):
