@@ -458,7 +458,7 @@ def run_ours(args, c, rank, world):
                      "push_tasks": s1["push_tasks"] - s0["push_tasks"],
                      "push_items": s1["push_items"] - s0["push_items"],
                      "push_phase_ms": {k: (s1["push_ns"][i] - s0["push_ns"][i]) / 1e6 for i, k in
-                                       enumerate(["seeding", "task_loop", "barriers"])}},
+                                       enumerate(["seeding", "task_loop", "barriers", "idle_per_warp"])}},
         "init_s": init_s,
         "clocks": clk.summary(),
         "err": err,

@@ -308,7 +308,8 @@ typedef struct {
   int64_t jacobi_gersh;     /* updates that needed the exact Gershgorin gap check */
   int64_t push_tasks;       /* push row tasks (a row taken from the queue, pushed or found below eps) */
   int64_t push_items;       /* push hub-item tasks (one chunk of a hub's in-edges) */
-  int64_t push_ns[4];       /* push time seen by one CTA (ns): seeding, task loop, grid barriers, unused */
+  int64_t push_ns[4];       /* push time seen by one CTA (ns): seeding, task loop, grid barriers; [3] the time a warp
+                               waited for work, averaged over the push's warps */
 } damf_stats;
 
 /* Stages timed by damf_set_timing (indices into damf_get_timing's arrays). */

@@ -51,7 +51,7 @@ struct DevHeader {
   int last_sweeps;       // Jacobi sweeps of the most recent update
   long long jacobi_sweeps, jacobi_full, jacobi_gersh;
   long long push_tasks, push_items;
-  unsigned long long push_ns[4];   // block 0 of the push: seeding, task loop, barriers, - (ns)
+  unsigned long long push_ns[4];   // block 0 of the push: seeding, task loop, barriers; [3] mean idle (ns)
   // push work queue (ppr.cu), zeroed before each launch: qstate = (tasks not finished << 32) |
   // queue tail; q_head = next queue position to claim; bump counters of rho slots and items
   unsigned long long qstate;

@@ -185,7 +185,8 @@ template <int D, bool SCALED>
 __device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, const int32_t* __restrict__ col,
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
                                               WarpQ& wq, DevHeader* h, uint32_t* inq, int32_t* queue, long long qcap,
-                                              int lane, int sub, int q, bool enq = true) {
+                                              int lane, int sub, int q, bool enq = true, bool pre0 = false,
+                                              int w_pre = 0, int d_pre = 1) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
   constexpr int CHL = PushShape<D>::CHL;
@@ -195,7 +196,11 @@ __device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, co
     const int nb = min(32, ne - b0);
     int w_own = 0, d_own = 1;
     float c_own = 0.f;
-    if (lane < nb) {
+    if (b0 == 0 && pre0) {   // the caller loaded the first 32 in-edges and their degrees
+      w_own = w_pre;
+      d_own = d_pre;
+      if (lane < nb) c_own = beta / (float)d_own;
+    } else if (lane < nb) {
       w_own = __ldg(col + st + b0 + lane);
       d_own = __ldg(outdeg + w_own);
       c_own = beta / (float)d_own;
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   uint32_t* inq = ws.stamp;
   long long my_pushes = 0, my_edges = 0;
   int my_rows = 0, my_items = 0;   // tasks taken by this warp (lane 0)
+  unsigned long long my_wait = 0;  // ns this warp waited for a queue slot (lane 0)
   const int npend = h->pending;
   // block 0's view of where the time goes (ns): seeding, task loop, barriers; [4] is the last
   // mark. Kept in shared memory, where it costs no registers.
@@ -322,12 +328,33 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         eb = ld_acquire(queue + p0 + lane);
         if (eb != -1) queue[p0 + lane] = -1;   // read once per phase; empty again for the next launch
       }
+      // and the entries' read-only data in the same pass: a row's in-edge range (and out-degree),
+      // an item's (rho slot, first in-edge, count)
+      int m0 = 0, m1 = 0, m2 = 1;
+      if (lane < kClaim && eb != -1) {
+        if (eb >= 0) {
+          m0 = __ldg(in.start + eb);
+          m1 = __ldg(in.len + eb);
+          if (SCALED) m2 = __ldg(outdeg + eb);
+        } else {
+          const int4 wi = __ldcg(ws.work + (-eb - 2));
+          m0 = wi.y;
+          m1 = wi.z;
+          m2 = wi.x;
+        }
+      }
       for (int b = 0; b < kClaim; ++b) {
       const long long p = p0 + b;
       int e = __shfl_sync(kFull, eb, b);
+      const bool pre = e != -1;    // the batch pass read this entry's data
+      int st = __shfl_sync(kFull, m0, b), deg = __shfl_sync(kFull, m1, b), aux = __shfl_sync(kFull, m2, b);
       if (e == -1) {
         flush(wq, h, queue, qcap, lane, ws.ovf);   // publish and uncount before waiting
-        if (lane == 0) e = wait_slot(h, queue, p, qcap);
+        if (lane == 0) {
+          const unsigned long long t0 = gtimer();
+          e = wait_slot(h, queue, p, qcap);
+          my_wait += gtimer() - t0;
+        }
         e = __shfl_sync(kFull, e, 0);
         if (e == -1) {
           quit = true;                     // positions after p are not filled either
@@ -344,16 +371,26 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
         __syncwarp();
         // group 0 reads r[u] once and hands it to the other groups, so that every group
         // scatters exactly the v that group 0 removes
+        if (!pre) {
+          st = __ldg(in.start + u);
+          deg = __ldg(in.len + u);
+          aux = SCALED ? __ldg(outdeg + u) : 1;
+        }
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+        // the first 32 in-edges and their out-degrees are requested beside the row, so that they
+        // arrive while the removal below is still in flight
+        const bool pre0 = deg <= direct_max;
+        int w0 = 0, d0 = 1;
+        if (pre0 && lane < min(deg, 32)) w0 = __ldg(in.col + st + lane);
         if (RPW > 1) {
           v.x = __shfl_sync(kFull, v.x, q);
           v.y = __shfl_sync(kFull, v.y, q);
           v.z = __shfl_sync(kFull, v.z, q);
           v.w = __shfl_sync(kFull, v.w, q);
         }
-        const int st = __ldg(in.start + u), deg = __ldg(in.len + u);
-        const int dout = SCALED ? __ldg(outdeg + u) : 1;
+        if (pre0 && lane < min(deg, 32)) d0 = __ldg(outdeg + w0);
+        const int dout = aux;
         const float thr_u = threshold<SCALED>(eps, dout);
         if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
           float lm = 0.f;                           // max |r[u]| right after the removal of v
@@ -394,7 +431,8 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
             }
           }
           if (direct)
-            scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q);
+            scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
+                                     true, pre0, w0, d0);
           // u itself: adds that reached r[u] between the read of v and its removal are still there
           lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
           enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
@@ -402,10 +440,18 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
       } else {
         // item task: one chunk of a hub's in-edges
         if (lane == 0) ++my_items;
-        const int4 wi = __ldcg(ws.work + (-e - 2));
-        const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
-        scatter_edges<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
-                                 q);
+        if (!pre) {
+          const int4 wi = __ldcg(ws.work + (-e - 2));
+          st = wi.y;
+          deg = wi.z;
+          aux = wi.x;
+        }
+        const float4 rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
+        int w0 = 0, d0 = 1;
+        if (lane < deg) w0 = __ldg(in.col + st + lane);
+        if (lane < deg) d0 = __ldg(outdeg + w0);
+        scatter_edges<D, SCALED>(rv, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
+                                 q, true, true, w0, d0);
       }
       wq.done += 1;
       }
@@ -446,7 +492,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
     if (timer) time_mark(s_t, 2);
   }
   if (timer)
-    for (int i = 0; i < 4; ++i) h->push_ns[i] += s_t[i];
+    for (int i = 0; i < 3; ++i) h->push_ns[i] += s_t[i];
   // counters and bookkeeping (block 0 after the last barrier; everyone has left the loop)
   for (int o = 16; o > 0; o >>= 1) {
     my_pushes += __shfl_xor_sync(kFull, my_pushes, o);
@@ -456,6 +502,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
     atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)my_pushes);
     atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)my_edges);
   }
+  if (lane == 0 && my_wait) atomicAdd(&h->push_ns[3], my_wait / (unsigned long long)nwarps);
   if (lane == 0 && (my_rows || my_items)) {
     atomicAdd((unsigned long long*)&h->push_tasks, (unsigned long long)my_rows);
     atomicAdd((unsigned long long*)&h->push_items, (unsigned long long)my_items);
