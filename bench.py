@@ -196,7 +196,7 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one k_push launch of this workload, from the ncu capture
+# DRAM bytes (read + write) of one k_push launch of the C2 workload, from the ncu capture
 # summarised in profiles/k_push_C2.md; None once k_push changes until it is captured again
 PUSH_DRAM_BYTES = 478.21e6
 
@@ -423,7 +423,7 @@ def run_ours(args, c, rank, world):
     push_ms_per = stage_ms["push"] / max(push_launches, 1)
     achieved = (push_bytes / max(push_launches, 1)) / (push_ms_per * 1e-3) / 1e9 if push_launches else 0.0
     roof = {"bound": "hbm", "kernel": "k_push", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": PUSH_DRAM_BYTES,
+            "frac": round(achieved / hbm_peak, 4), "traffic": PUSH_DRAM_BYTES if c.name == "C2" else None,
             "traffic_note": "dram read + write of one captured launch of the current k_push (ncu, "
                             "profiles/k_push_C2.md); most of the algorithmic bytes are L2 atomics",
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

@@ -5,6 +5,10 @@ C1  small FP64-checkable case: undirected Chung-Lu, gamma 2.5, n = 2,000, ~10k e
 C2  single-GPU workload: undirected Chung-Lu, gamma 2.2, n = 200,000, mean degree 10,
     d = 128, alpha = 0.15, eps = 1e-5; 10,000 batches of U[1, 64] edges with 5% node
     arrivals and 10% deletions.
+C3  large graph: undirected Chung-Lu, gamma 2.1, n = 2,000,000, m = 40M edges (mean degree
+    40), d = 128; 50,000 batches of U[1, 256] edges (up to four updates per call), node
+    arrivals and deletions as in C2 (the workload states neither; C2's rates are used), alpha
+    and eps as in C2, the fold every 256 updates.
 """
 
 import dataclasses
@@ -43,6 +47,8 @@ CONFIGS = {
                    k_lo=10, k_hi=10, p_node=0.0, p_del=0.0, nodes_per_batch=1, seed=SEED_BASE + 0),
     "C2": Workload("C2", n=200_000, avg_deg=10.0, gamma=2.2, d=128, alpha=0.15, eps=1e-5, n_batches=10_000,
                    k_lo=1, k_hi=64, p_node=0.05, p_del=0.10, nodes_per_batch=0, seed=SEED_BASE + 1),
+    "C3": Workload("C3", n=2_000_000, avg_deg=40.0, gamma=2.1, d=128, alpha=0.15, eps=1e-5, n_batches=50_000,
+                   k_lo=1, k_hi=256, p_node=0.05, p_del=0.10, nodes_per_batch=0, seed=SEED_BASE + 2),
 }
 
 

@@ -367,6 +367,71 @@ def test_node_arrival_stream_against_oracle(directed):
     g.close()
 
 
+def test_c3_shaped_stream_against_oracle():
+    # the C3 shape at a checkable size: gamma 2.1, mean degree 40, calls of up to 256 events
+    # (up to four updates each), node arrivals and deletions, the fold every 256 updates
+    from oracle.damf import DamfOracle
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    n, d = 3000, 32
+    ip, ix, w = chung_lu_graph(n, 40.0, 2.1, seed=SEED + 80)
+    st = edge_stream(ip, ix, w, 24, 1, 256, 0.05, 0.10, SEED + 81)
+    cfg = make_config(n, d, 0.15, 1e-4, n_capacity=st.n_final, nnz=len(ix), refold_every=256)
+    om = gaussian_test_matrix(n, rsvd_width(cfg), seed=SEED + 82)
+    g = DamfGraph(ip, ix, cfg, om)
+    orc = DamfOracle(ip, ix, d, 0.15, 1e-4, n_cap=st.n_final, Omega=om)
+    for b in st.batches:
+        g.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        g.ppr_refresh()
+        orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+        orc.ppr_refresh()
+    g.check()
+    assert g.stats()["updates"] > len(st.batches)     # calls above 64 events took several updates
+    Xg, Yg, sg = gpu_xy(g)
+    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
+    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    Zg = g.embeddings()["Z"].double().cpu().numpy()
+    assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
+    g.close()
+
+
+def test_c4_shaped_graphs_in_one_call_against_oracles():
+    # the C4 shape at a checkable size: graphs of log-uniform n, mean degree U[4, 32] and
+    # d in {32, 64, 128}, one batch of U[1, 128] events per graph per damf_apply_edges_multi
+    # call; each graph against its own FP64 oracle
+    from oracle.damf import DamfOracle
+    from paper_2306_08967_gb300 import DamfGraph, apply_edges_multi, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    rng = np.random.default_rng(SEED + 90)
+    graphs = []
+    for i in range(6):
+        n = int(np.exp(rng.uniform(np.log(300), np.log(2500))))
+        d = int(rng.choice([32, 64, 128]))
+        if d >= n // 4:
+            d = 32
+        ip, ix, w = chung_lu_graph(n, float(rng.uniform(4, 32)), 2.3, seed=SEED + 91 + i)
+        st = edge_stream(ip, ix, w, 8, 1, 128, 0.05, 0.10, SEED + 101 + i)
+        cfg = make_config(n, d, 0.15, 1e-4, n_capacity=st.n_final, nnz=len(ix))
+        om = gaussian_test_matrix(n, rsvd_width(cfg), seed=SEED + 111 + i)
+        graphs.append((DamfGraph(ip, ix, cfg, om), DamfOracle(ip, ix, d, 0.15, 1e-4, n_cap=st.n_final, Omega=om), st))
+    for t in range(8):
+        apply_edges_multi([(g, st.batches[t].src, st.batches[t].dst, st.batches[t].op, st.batches[t].new_nodes)
+                           for g, _, st in graphs])
+        for g, orc, st in graphs:
+            b = st.batches[t]
+            g.ppr_refresh()
+            orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
+            orc.ppr_refresh()
+    for g, orc, _ in graphs:
+        g.check()
+        Xg, Yg, sg = gpu_xy(g)
+        np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
+        assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+        Zg = g.embeddings()["Z"].double().cpu().numpy()
+        assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
+        g.close()
+
+
 def test_edge_cases():
     from paper_2306_08967_gb300 import DamfError
     g, _, _ = make_pair(200, 6.0, 2.5, 16, 0.2, 1e-4, SEED + 11, n_extra=4, oracle=False)
