@@ -119,9 +119,11 @@ struct WarpQ {
   int n;          // buffered entries (warp-uniform)
   int done;       // finished tasks (warp-uniform)
   int32_t* ovf;   // list of hub items that found the queue full
+  uint32_t* inq;  // in-queue flags of the rows
 };
 
-// Publishes the buffered entries and uncounts the finished tasks in one atomic on qstate
+// Claims the buffered rows (in-queue flags), then publishes the kept entries and uncounts the
+// finished tasks in one atomic on qstate
 // (count += n - done, tail += n), then stores the entries with release semantics, so that a
 // consumer that sees an entry also sees the count that includes it and everything the warp
 // wrote before (rho, items). Entries past the queue's end are uncounted again and set the
@@ -130,6 +132,32 @@ __device__ __forceinline__ void flush(WarpQ& wq, DevHeader* h, int32_t* queue, l
                                       int32_t* ovf) {
   if (wq.n == 0 && wq.done == 0) return;
   __syncwarp();
+  // claim the buffered rows: a row whose in-queue flag was set already is queued (or being
+  // queued) by someone else and is dropped; all exchanges are in flight at once
+  constexpr int kRounds = kQBuf / 32;
+  unsigned keep = 0;   // bit j: entry lane + 32 j stays
+#pragma unroll
+  for (int j = 0; j < kRounds; ++j) {
+    const int i = lane + 32 * j;
+    if (i < wq.n) {
+      const int e = wq.buf[i];
+      keep |= (unsigned)(e < -1 || exch_acq_rel(wq.inq + e, 1u) == 0u) << j;
+    }
+  }
+  int kept = 0;
+#pragma unroll
+  for (int j = 0; j < kRounds; ++j) {
+    if (32 * j >= wq.n) break;   // warp-uniform
+    const int i = lane + 32 * j;
+    const int e = i < wq.n ? wq.buf[i] : 0;
+    const bool k = i < wq.n && ((keep >> j) & 1u);
+    const unsigned m = __ballot_sync(kFull, k);
+    __syncwarp();                // this round's entries are read before any is overwritten
+    if (k) wq.buf[kept + __popc(m & ((1u << lane) - 1u))] = e;
+    kept += __popc(m);
+  }
+  __syncwarp();
+  wq.n = kept;
   unsigned long long base = 0;
   if (lane == 0)
     base = atomicAdd(&h->qstate, (unsigned long long)(long long)(wq.n - wq.done) * kTask + (unsigned)wq.n);
@@ -168,12 +196,12 @@ __device__ __forceinline__ void stage(bool want, int entry, WarpQ& wq, DevHeader
   __syncwarp();
 }
 
-// Queues row w for the lanes with `want` unless it is queued already (in-queue flag; the
-// exchange is a release, so the add that made w cross comes before it).
+// Queues row w for the lanes with `want`: buffered now, claimed at the flush unless it is
+// queued already (in-queue flag; the exchange is a release, so the add that made w cross
+// comes before it).
 __device__ __forceinline__ void enqueue_rows(bool want, int w, WarpQ& wq, DevHeader* h, uint32_t* inq,
                                              int32_t* queue, long long qcap, int lane) {
-  const bool fresh = want && exch_acq_rel(inq + w, 1u) == 0u;
-  stage(fresh, w, wq, h, queue, qcap, lane);
+  stage(want, w, wq, h, queue, qcap, lane);
 }
 
 // Scatter (warp-level): adds coef(w) * v to r[w] for the in-edges col[st .. st+ne) of a row,
@@ -289,7 +317,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
     s_t[4] = gtimer();
   }
   __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
-  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0, ws.ovf};
+  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0, ws.ovf, ws.stamp};
   int phase = 0;
   for (;; ++phase) {
     if (phase >= max_phases) {
