@@ -12,6 +12,7 @@ workload (bounded sample per step) and prints the same metric with "impl": "refe
 """
 
 import argparse
+import dataclasses
 import json
 import os
 import sys
@@ -200,6 +201,23 @@ class ClockSampler:
 # summarised in profiles/k_push_C2.md; None once k_push changes until it is captured again
 PUSH_DRAM_BYTES = 478.21e6
 
+# ---------------------------------------------------------------- ranks
+def reduce_over_ranks(elapsed_ms, edges, world):
+    """Replicas (one graph per rank, no collective on the data path): the job's time is the
+    slowest rank's, its work the sum of the ranks' edges. Returns (max elapsed, total edges).
+    Works on NCCL (CUDA tensors) and gloo (CPU tensors) process groups."""
+    if world <= 1:
+        return float(elapsed_ms), int(edges)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=dev)
+    e = torch.tensor([float(edges)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(e.item()))
+
+
 # ---------------------------------------------------------------- GPU leg
 def measure_scoring(g, c, torch):
     """Link-prediction queries on the final state (Sec. 5): damf_score_pairs over 2^20 random
@@ -313,6 +331,8 @@ def run_ours(args, c, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     K, W, E = args.steps, args.warmup, args.e2e_steps
+    if rank > 0:   # replicas: every rank its own graph and stream of the same shape
+        c = dataclasses.replace(c, seed=c.seed + 1000 * rank)
     ip, ix, st = make_inputs(c, W + K + E)
     cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=st.n_final + 16, nnz=len(ix), directed=c.directed,
                       refold_every=args.refold_every, precision=args.precision)
@@ -374,11 +394,8 @@ def run_ours(args, c, rank, world):
     g.set_timing(False)
     s1 = g.stats()
     edges = int(ks[W:W + K].sum())
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = edges * world / (elapsed_ms / 1e3)
+    elapsed_ms, total_edges = reduce_over_ranks(elapsed_ms, edges, world)
+    value = total_edges / (elapsed_ms / 1e3)
 
     # e2e: host buffers through damf_apply_edges_host, a D2H read of sigma every step
     sig = torch.empty(c.d, dtype=torch.float32).pin_memory()
