@@ -175,6 +175,13 @@ damf_status damf_ppr_refresh(damf_ctx* ctx, void* stream);
  * damf_join makes `stream` wait for the most recent push (e.g. before the caller reads
  * results produced by it through other means); damf_record_event records a caller's
  * cudaEvent_t (passed as void*) on the push stream after the most recent push.
+ *
+ * CUDA graph capture: damf_apply_edges (device events), damf_ppr_refresh and damf_join can
+ * be captured on `stream`. Call damf_join on `stream` before the capture begins and end the
+ * captured work with damf_join (which brings the push stream back into the capture). A
+ * replay repeats the captured calls with their k, new_nodes and event pointers (the caller
+ * rewrites the event buffers between replays); the host-side fold schedule and node count
+ * do not advance on replay, so capture with refold_every = 0 and new_nodes = 0.
  */
 damf_status damf_join(damf_ctx* ctx, void* stream);
 damf_status damf_record_event(damf_ctx* ctx, void* event);

@@ -175,6 +175,19 @@ damf_status reject(Ctx* c, const char* what) {
   return DAMF_ERR_INVALID;
 }
 
+// Makes `s` wait for the most recent push. Under stream capture: a push captured in the same
+// capture is waited for through its own event; a push from before the capture is the caller's
+// to join before capturing (so nothing is added). Outside a capture: the last push recorded
+// outside any capture (work after a graph replay is ordered by the graph's final join).
+cudaError_t wait_push(Ctx* c, cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  unsigned long long id = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cap, &id);
+  if (e != cudaSuccess) return e;
+  if (cap == cudaStreamCaptureStatusNone) return cudaStreamWaitEvent(s, c->ev_push, 0);
+  return c->push_capture_id == id ? cudaStreamWaitEvent(s, c->ev_push_cap, 0) : cudaSuccess;
+}
+
 #define DAMF_CUDA(call, what)                                  \
   do {                                                         \
     cudaError_t e_ = (call);                                   \
@@ -185,6 +198,8 @@ void free_all(Ctx* c) {
   if (c->push_stream) cudaStreamDestroy(c->push_stream);
   if (c->ev_caller) cudaEventDestroy(c->ev_caller);
   if (c->ev_push) cudaEventDestroy(c->ev_push);
+  if (c->ev_push_cap) cudaEventDestroy(c->ev_push_cap);
+  c->ev_push_cap = nullptr;
   c->push_stream = nullptr;
   c->ev_caller = c->ev_push = nullptr;
   if (c->ev) {
@@ -387,6 +402,7 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->push_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_caller, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push_cap, cudaEventDisableTiming);
   if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
   if (e == cudaSuccess) e = launch_push(c, 1, s);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_push, s);
@@ -434,7 +450,7 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
     DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 7, launch_transforms(c, s), "transforms");
     // writes to the adjacency, Zb and r follow the push
-    DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_push, 0), "join push");
+    DAMF_CUDA(wait_push(c, s), "join push");
     DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_edit(c, s), "edit");
     DAMF_STAGE(DAMF_STAGE_FIXUP, 1, launch_fixup(c, s), "fixup");
     DAMF_STAGE(DAMF_STAGE_SCATTER, 1, launch_scatter(c, s), "scatter");
@@ -538,7 +554,12 @@ damf_status damf_ppr_refresh(damf_ctx* x, void* stream) {
   cudaStream_t s = c->push_stream;
   DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_caller, 0), "push wait");
   DAMF_STAGE(DAMF_STAGE_PUSH, 1, launch_push(c, c->check_all_next, s), "push");
-  DAMF_CUDA(cudaEventRecord(c->ev_push, s), "record");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  unsigned long long id = 0;
+  DAMF_CUDA(cudaStreamGetCaptureInfo((cudaStream_t)stream, &cap, &id), "capture status");
+  const bool captured = cap != cudaStreamCaptureStatusNone;
+  c->push_capture_id = captured ? id : 0;
+  DAMF_CUDA(cudaEventRecord(captured ? c->ev_push_cap : c->ev_push, s), "record");
   c->launches += 1;
   c->check_all_next = 0;
   return DAMF_OK;
@@ -547,7 +568,7 @@ damf_status damf_ppr_refresh(damf_ctx* x, void* stream) {
 damf_status damf_join(damf_ctx* x, void* stream) {
   if (!x) return DAMF_ERR_INVALID;
   Ctx* c = &x->c;
-  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join");
+  DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join");
   return DAMF_OK;
 }
 
@@ -564,7 +585,7 @@ damf_status damf_get_embeddings(damf_ctx* x, const int32_t* rows, int32_t count,
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
   if (count < 0 || (!rows && count > c->n)) return fail(c, DAMF_ERR_INVALID, "count", cudaSuccess);
-  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
+  DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join push");
   DAMF_CUDA(launch_query(c, rows, count, X, Y, Z, sigma, (cudaStream_t)stream), "query");
   return DAMF_OK;
 }
@@ -577,7 +598,7 @@ damf_status damf_score_pairs(damf_ctx* x, const int32_t* src, const int32_t* dst
   if (count < 0 || (context != 0 && context != 1) || (symmetric != 0 && symmetric != 1) ||
       (count > 0 && (!src || !dst || !scores)))
     return reject(c, "score_pairs: bad argument");
-  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
+  DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join push");
   DAMF_CUDA(launch_score_pairs(c, src, dst, count, context, symmetric, scores, (cudaStream_t)stream), "score_pairs");
   return DAMF_OK;
 }
@@ -590,7 +611,7 @@ damf_status damf_topk(damf_ctx* x, const int32_t* rows, int32_t count, int32_t k
   if (count < 0 || k < 1 || k > kMaxTopK || (context != 0 && context != 1) || (symmetric != 0 && symmetric != 1) ||
       (count > 0 && (!rows || !out_idx || !out_score)))
     return reject(c, "topk: bad argument (1 <= k <= 64, context and symmetric 0 or 1)");
-  DAMF_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_push, 0), "join push");
+  DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join push");
   DAMF_CUDA(launch_topk(c, rows, count, k, context, symmetric, out_idx, out_score, (cudaStream_t)stream), "topk");
   return DAMF_OK;
 }
@@ -631,7 +652,7 @@ damf_status damf_get_state(damf_ctx* x, float* Ub, float* Vb, float* Zb, float* 
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nd = (size_t)c->n * c->d * sizeof(float), dd = (size_t)c->d * c->d * sizeof(float);
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-  DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_push, 0), "join push");
+  DAMF_CUDA(wait_push(c, s), "join push");
   if (Ub) DAMF_CUDA(cudaMemcpyAsync(Ub, c->Ub, nd, k, s), "state");
   if (Vb) DAMF_CUDA(cudaMemcpyAsync(Vb, c->Vb, nd, k, s), "state");
   if (Zb) DAMF_CUDA(cudaMemcpyAsync(Zb, c->Zb, nd, k, s), "state");

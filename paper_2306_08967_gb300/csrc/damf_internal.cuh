@@ -146,6 +146,8 @@ struct Ctx {
   cudaStream_t push_stream;
   cudaEvent_t ev_caller;  // caller-stream work a push must follow
   cudaEvent_t ev_push;    // the most recent push
+  cudaEvent_t ev_push_cap;  // the most recent push recorded inside a stream capture
+  unsigned long long push_capture_id;  // capture that recorded ev_push_cap (0: none)
   long long launches;    // kernels this context has launched (host count)
   // per-stage timing (api.cu)
   int timing;

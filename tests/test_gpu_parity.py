@@ -294,6 +294,63 @@ def test_apply_edges_multi_equals_each_graph_alone():
         ga.close()
 
 
+def test_captured_step_replays_like_direct_calls():
+    # one step (apply a 40-event batch, push, join) captured in a CUDA graph and replayed with
+    # new events written into its input buffers must leave the same factor state, bit for bit,
+    # as the same batches applied by direct calls to a twin context
+    from paper_2306_08967_gb300 import DamfGraph
+    rng = np.random.default_rng(31)
+    n, k = 500, 40
+    g, _, _ = make_pair(n, 8.0, 2.5, 32, 0.15, 1e-5, SEED + 120, oracle=False)
+    twin, _, _ = make_pair(n, 8.0, 2.5, 32, 0.15, 1e-5, SEED + 120, oracle=False)
+    batches = [_events(rng, n, k) for _ in range(6)]
+    src = torch.empty(k, dtype=torch.int32, device="cuda")
+    dst = torch.empty(k, dtype=torch.int32, device="cuda")
+    op = torch.empty(k, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.Stream()
+    lib, h = g.lib, g.h
+    sp = __import__("ctypes").c_void_p
+    sptr = sp(stream.cuda_stream)
+
+    def step_calls():
+        assert lib.damf_apply_edges(h, sp(src.data_ptr()), sp(dst.data_ptr()), sp(op.data_ptr()), k, 0, sptr) == 0
+        assert lib.damf_ppr_refresh(h, sptr) == 0
+        assert lib.damf_join(h, sptr) == 0
+
+    def load(b):
+        src.copy_(torch.from_numpy(b[0]))
+        dst.copy_(torch.from_numpy(b[1]))
+        op.copy_(torch.from_numpy(b[2]))
+
+    # the first batch by direct calls on both, then capture
+    load(batches[0])
+    with torch.cuda.stream(stream):
+        assert lib.damf_join(h, sptr) == 0
+        step_calls()
+    stream.synchronize()
+    twin.apply_edges(*batches[0])
+    twin.ppr_refresh()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        step_calls()
+    for b in batches[1:]:
+        load(b)
+        graph.replay()
+        torch.cuda.synchronize()
+        twin.apply_edges(*b)
+        twin.ppr_refresh()
+    g.check()
+    twin.check()
+    a, b = g.state(), twin.state()
+    for key in ("Ub", "Vb", "PU", "PV", "sigma"):
+        assert torch.equal(a[key], b[key]), key
+    ra, ca = g.adjacency()
+    rb, cb = twin.adjacency()
+    assert np.array_equal(ra, rb)
+    g.close()
+    twin.close()
+
+
 def test_alpha_one_gives_z_equal_x():
     # the paper's ablation: alpha = 1 means Z = X
     g, _, _ = make_pair(300, 8.0, 2.5, 16, 1.0, 1e-6, SEED + 9, oracle=False)
