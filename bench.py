@@ -485,6 +485,313 @@ def run_ours(args, c, rank, world):
     return out
 
 
+def run_fleet(args, fw, rank, world):
+    """Many graphs per step (one batch each) through a fleet (damf_fleet_step: every graph's
+    update on its own stream, then one grouped push of all graphs), each step one CUDA graph
+    replay after the push shares are autotuned; beside it the same step issued graph by graph
+    on one stream, by direct damf_step_multi calls (one cooperative push per graph) and by
+    direct (uncaptured) fleet steps."""
+    import ctypes
+    import torch
+    from paper_2306_08967_gb300 import DamfFleet, DamfGraph, _lib, make_config, rsvd_width
+    from paper_2306_08967_gb300.api import _batch_array
+    from paper_2306_08967_gb300.autotune import DEFAULT_DIRECT_CHUNKS, DEFAULT_EXPONENTS, tune_shares
+    from synth import fleet_inputs, gaussian_test_matrix
+
+    members = fw.members()
+    if args.graphs:
+        members = members[: args.graphs]
+    if rank > 0:   # replicas: every rank its own fleet of the same shape
+        members = [dataclasses.replace(c, seed=c.seed + 1000 * rank) for c in members]
+    K, W, E, S, T = args.steps, args.warmup, args.e2e_steps, args.compare_steps, args.tune_steps
+    n_cand = len(DEFAULT_EXPONENTS) + len(DEFAULT_DIRECT_CHUNKS)
+    # warm-up, tuning (T per candidate), the three comparison forms, one untimed replay, timed, e2e,
+    # phase-timed direct steps
+    n_steps = W + T * n_cand + 3 * S + 1 + K + E + S
+    t0 = time.perf_counter()
+    data = fleet_inputs(members, n_steps, 1 if world > 1 else 0)
+    gen_s = time.perf_counter() - t0
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    graphs = []
+    for c, ip, ix, st in data:
+        cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=c.n, nnz=len(ix), refold_every=0,
+                          precision=args.precision)
+        graphs.append(DamfGraph(ip, ix, cfg, gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)))
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    G, KMAX = len(graphs), fw.k_hi
+    # every step's events on the device, padded to KMAX per graph: [step][graph][KMAX]
+    src = np.zeros((n_steps, G, KMAX), np.int32)
+    dst = np.zeros((n_steps, G, KMAX), np.int32)
+    opv = np.zeros((n_steps, G, KMAX), np.int8)
+    cnt = np.zeros((n_steps, G), np.int32)
+    for gi, (c, ip, ix, st) in enumerate(data):
+        for t, b in enumerate(st.batches):
+            src[t, gi, :b.k], dst[t, gi, :b.k], opv[t, gi, :b.k] = b.src, b.dst, b.op
+            cnt[t, gi] = b.k
+    d_src, d_dst = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+    d_op, d_cnt = torch.from_numpy(opv).to(dev), torch.from_numpy(cnt).to(dev)
+    # the fixed buffers a captured step reads
+    b_src, b_dst = torch.zeros((G, KMAX), dtype=torch.int32, device=dev), torch.zeros((G, KMAX), dtype=torch.int32,
+                                                                                      device=dev)
+    b_op, b_cnt = torch.zeros((G, KMAX), dtype=torch.int8, device=dev), torch.zeros(G, dtype=torch.int32, device=dev)
+    sig = torch.zeros((G, 128), dtype=torch.float32, device=dev)
+    batches = [(g, b_src[i], b_dst[i], b_op[i], 0, b_cnt[i:i + 1]) for i, g in enumerate(graphs)]
+    arr = _batch_array(batches)
+    lib = _lib.load()
+    fs = torch.cuda.Stream(device=dev)
+    fptr = ctypes.c_void_p(fs.cuda_stream)
+    pos = [0]
+
+    def load(t):   # step t's events into the fixed buffers (device to device)
+        b_src.copy_(d_src[t], non_blocking=True)
+        b_dst.copy_(d_dst[t], non_blocking=True)
+        b_op.copy_(d_op[t], non_blocking=True)
+        b_cnt.copy_(d_cnt[t], non_blocking=True)
+
+    def next_step():
+        t = pos[0]
+        pos[0] += 1
+        return t
+
+    fleet = DamfFleet(graphs)
+
+    def capture():
+        with torch.cuda.stream(fs):
+            for g in graphs:
+                g.join(fs)
+        fs.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        l0 = sum(g.stats()["launches"] for g in graphs) + fleet.launches
+        with torch.cuda.graph(cg, stream=fs, capture_error_mode="relaxed"):
+            fleet.step_array(arr, fs)
+        cg.kernels = sum(g.stats()["launches"] for g in graphs) + fleet.launches - l0
+        return cg
+
+    def run_captured(cg, steps, record=None):
+        with torch.cuda.stream(fs):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(fs)
+            for j in range(steps):
+                t = next_step()
+                if record is not None:
+                    record[0][j].record(fs)
+                load(t)
+                cg.replay()
+                if record is not None:
+                    record[1][j].record(fs)
+            ev1.record(fs)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / max(steps, 1)
+
+    # warm-up: direct fleet steps under the default shares
+    with torch.cuda.stream(fs):
+        for _ in range(W):
+            load(next_step())
+            fleet.step_array(arr, fs)
+    fs.synchronize()
+    for g in graphs:
+        g.check()
+
+    # the same step issued graph by graph on one stream (each graph's push joined before the
+    # next graph's update), then by direct damf_step_multi calls, both with the default shape
+    def run_sequential(steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(fs):
+            ev0.record(fs)
+            for _ in range(steps):
+                t = next_step()
+                load(t)
+                for i, g in enumerate(graphs):
+                    k = int(cnt[t, i])
+                    g.apply_edges(b_src[i, :k], b_dst[i, :k], b_op[i, :k], stream=fs)
+                    g.ppr_refresh(stream=fs)
+                    g.join(fs)
+            ev1.record(fs)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / max(steps, 1)
+
+    def run_direct(steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(fs):
+            ev0.record(fs)
+            for _ in range(steps):
+                load(next_step())
+                if lib.damf_step_multi(arr, G, fptr) != 0:
+                    raise RuntimeError("step_multi")
+            ev1.record(fs)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / max(steps, 1)
+
+    def run_fleet_direct(steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(fs):
+            ev0.record(fs)
+            for _ in range(steps):
+                load(next_step())
+                fleet.step_array(arr, fs)
+            ev1.record(fs)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / max(steps, 1)
+
+    seq_ms = run_sequential(S)
+    direct_ms = run_direct(S)
+    fleet_direct_ms = run_fleet_direct(S)
+
+    # autotune the push shares on real steps (each candidate recaptured, one untimed replay)
+    def measure():
+        cg = capture()
+        run_captured(cg, 1)
+        return run_captured(cg, T - 1)
+
+    t0 = time.perf_counter()
+    tune = tune_shares(fleet, graphs, measure) if T >= 2 else None
+    tune_s = time.perf_counter() - t0
+    cg = capture()
+    run_captured(cg, 1)
+    for g in graphs:
+        g.check()
+
+    # timed: K captured steps
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    t_first = pos[0]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        run_captured(cg, K, (ev_a, ev_b))
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    for g in graphs:
+        g.check()
+    launches = cg.kernels * K
+    lat_ms = np.array([ev_a[j].elapsed_time(ev_b[j]) for j in range(K)])
+    elapsed_ms = float(ev_a[0].elapsed_time(ev_b[K - 1]))
+    edges = int(cnt[t_first:t_first + K].sum())
+    elapsed_all, total_edges = reduce_over_ranks(elapsed_ms, edges, world)
+    value = total_edges / (elapsed_all / 1e3)
+
+    # e2e: each step's events from pinned host memory, the captured step, every graph's
+    # sigma read back to the host
+    h_src = torch.empty((G, KMAX), dtype=torch.int32).pin_memory()
+    h_dst = torch.empty((G, KMAX), dtype=torch.int32).pin_memory()
+    h_op = torch.empty((G, KMAX), dtype=torch.int8).pin_memory()
+    h_cnt = torch.empty(G, dtype=torch.int32).pin_memory()
+    h_sig = torch.empty((G, 128), dtype=torch.float32).pin_memory()
+    with torch.cuda.stream(fs):
+        for g in graphs:
+            g.join(fs)
+    fs.synchronize()
+    rg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(rg, stream=fs, capture_error_mode="relaxed"):
+        for i, g in enumerate(graphs):
+            if lib.damf_get_embeddings(g.h, None, 0, None, None, None, ctypes.c_void_p(sig[i].data_ptr()), fptr):
+                raise RuntimeError("readout capture")
+    e2e_edges = 0
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    for _ in range(E):
+        t = next_step()
+        h_src.numpy()[:] = src[t]
+        h_dst.numpy()[:] = dst[t]
+        h_op.numpy()[:] = opv[t]
+        h_cnt.numpy()[:] = cnt[t]
+        with torch.cuda.stream(fs):
+            b_src.copy_(h_src, non_blocking=True)
+            b_dst.copy_(h_dst, non_blocking=True)
+            b_op.copy_(h_op, non_blocking=True)
+            b_cnt.copy_(h_cnt, non_blocking=True)
+            cg.replay()
+            rg.replay()
+            h_sig.copy_(sig, non_blocking=True)
+        fs.synchronize()
+        e2e_edges += int(cnt[t].sum())
+    e2e_s = max(time.perf_counter() - t_e, 1e-9)
+    for g in graphs:
+        g.check()
+
+    # phase split and push roofline from S more steps issued directly with the fleet's phase
+    # timing (events at the fork, after every update, after the grouped push); the push's
+    # algorithmic bytes come from the graphs' push counters over the same steps
+    fleet.set_timing(True)
+    s2 = [g.stats() for g in graphs]
+    run_fleet_direct(S)
+    tm = fleet.timing()
+    fleet.set_timing(False)
+    s3 = [g.stats() for g in graphs]
+    for g in graphs:
+        g.check()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    push_bytes, pushes, push_edges = 0.0, 0, 0
+    for g, a, b in zip(graphs, s2, s3):
+        B = 4 * g.d
+        dp, de = b["pushes"] - a["pushes"], b["push_edges"] - a["push_edges"]
+        pushes, push_edges = pushes + dp, push_edges + de
+        push_bytes += dp * 3 * B + de * (8 + 2 * B)
+    shares, n_launch = fleet.shares()
+    push_ms_per = tm["push_ms"] / max(tm["steps"], 1)
+    achieved = (push_bytes / max(tm["steps"], 1)) / max(push_ms_per * 1e-3, 1e-12) / 1e9
+    d_mix = {dd: sum(1 for g in graphs if g.d == dd) for dd in (32, 64, 128)}
+    n_all = np.array([g.n for g in graphs])
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Chung-Lu graphs and edge streams)",
+        "config": {"workload": "%s: %d undirected Chung-Lu graphs, gamma %.1f, n log-uniform in [%d, %d] (total %d), "
+                               "mean degree U[%g, %g], d %s; one batch of U[%d, %d] edge events per graph per step, "
+                               "%.0f%% deletions; alpha %g eps %g"
+                               % (fw.name, G, fw.gamma, fw.n_lo, fw.n_hi, int(n_all.sum()), fw.deg_lo, fw.deg_hi,
+                                  d_mix, fw.k_lo, fw.k_hi, 100 * fw.p_del, fw.alpha, fw.eps),
+                   "precision": args.precision, "edges_timed": edges, "launch": "one CUDA graph replay per step (damf_fleet_step "
+                   "captured: every graph's update on its own stream, then one grouped cooperative push of all "
+                   "graphs)",
+                   "l2": "state of all graphs > 129 MB L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "definition": "per step (all graphs' batches): event before the step's event copy to event "
+                                     "after its replay (every graph's update and push done)"},
+        "compare_ms_per_step": {"graph_by_graph_one_stream": seq_ms,
+                                "step_multi_direct (one cooperative push per graph)": direct_ms,
+                                "fleet_direct_default_shares": fleet_direct_ms,
+                                "fleet_captured_tuned": elapsed_ms / K, "steps_each": S},
+        "autotune": dict(tune or {}, seconds=tune_s, steps_per_candidate=T),
+        "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": G * KMAX * 9 + 4 * G, "d2h_bytes_per_step": G * 128 * 4, "steps": E},
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "kernels per captured step (counted while capturing) x timed steps",
+        "roofline": {"bound": "hbm", "kernel": "k_push_group", "achieved": round(achieved, 1), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                     "note": "achieved = algorithmic push bytes of all graphs per step / the grouped push's "
+                             "device time per step (events around the push phase of %d direct fleet steps)"
+                             % tm["steps"],
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                     "grouped_launches_per_step": n_launch, "pushes": pushes, "push_edges": push_edges,
+                     "bytes_per_step": push_bytes / max(tm["steps"], 1), "ms_per_step": push_ms_per},
+        "phase_ms_per_step": {"updates": tm["update_ms"] / max(tm["steps"], 1), "push": push_ms_per,
+                              "note": "direct fleet steps: fork to the last graph's update done; then the "
+                                      "grouped push"},
+        "shares": {"owners": int(sum(1 for b in shares if b > 0)), "sharing_a_cta": int(sum(1 for b in shares
+                                                                                          if b == 0)),
+                   "max_ctas": int(max(shares))},
+        "init_s": init_s, "generate_s": gen_s,
+        "clocks": clk.summary(),
+    }
+    fleet.close()
+    for g in graphs:
+        g.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,11 +811,21 @@ def main():
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
+    ap.add_argument("--graphs", type=int, default=0, help="C4: the first this many graphs of the fleet (0: all)")
+    ap.add_argument("--compare-steps", type=int, default=5, help="C4: steps of each comparison launch form")
+    ap.add_argument("--tune-steps", type=int, default=3, help="C4: steps per autotuner candidate (< 2: no tuning)")
     ap.add_argument("--mode", default="batches", choices=["batches", "node-stream"],
                     help="node-stream: ms per node event under the paper's node-arrival protocol")
     args = ap.parse_args()
-    from synth import CONFIGS
-    c = CONFIGS[args.config]
+    from synth import CONFIGS, FLEETS
+    if "." in args.config:     # one member graph of a fleet, e.g. C4.17 (the oracle's sample)
+        base, idx = args.config.split(".", 1)
+        c = FLEETS[base].members()[int(idx)]
+    elif args.config in FLEETS:
+        main_fleet(args, FLEETS[args.config])
+        return
+    else:
+        c = CONFIGS[args.config]
     if args.oracle_worker:
         print(json.dumps(oracle_run(c, args.steps, 2, args.budget, args.save_state)))
         return
@@ -572,6 +889,52 @@ def main():
                 out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                                        "sample": r["sample"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                                        "init_s": r["init_s"]}
+            else:
+                out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": "failed: " + r.get("error", "")}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+def main_fleet(args, fw):
+    # more hardware work queues for the graphs' streams (read when the CUDA context starts)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    members = fw.members()[: args.graphs] if args.graphs else fw.members()
+    # the oracle's sample: the fleet member closest to the median size
+    order = np.argsort([c.n for c in members])
+    sample = members[int(order[len(order) // 2])]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = min(120.0, 0.5 * args.steps + 10.0)
+        r = oracle_run(sample, args.steps, args.warmup, budget)
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 0,
+                "steps": r["batches"], "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / max(r["batches"], 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Chung-Lu graphs and edge streams)",
+                "config": {"workload": "%s: the oracle on one member graph (%s, n = %d, d = %d)"
+                                       % (fw.name, sample.name, sample.n, sample.d), "precision": "fp64"},
+                "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_fleet(args, fw, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            r = oracle_subprocess(sample, 400, args.cpu_budget)
+            if "value" in r:
+                out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                       "sample": r["sample"] + "; graph %s (n = %d, d = %d, the median size of the "
+                                       "fleet); edge-updates/s of one graph at a time" % (sample.name, sample.n,
+                                                                                          sample.d)}
             else:
                 out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                        "sample": "failed: " + r.get("error", "")}

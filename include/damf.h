@@ -117,14 +117,28 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
 damf_status damf_apply_edges(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,
                              int32_t k, int32_t new_nodes, void* stream);
 
+/*
+ * damf_apply_edges with the event count on the device: the live events are the first
+ * *k_dev of src/dst/op (k_dev: device int32, read when the work runs, clamped to
+ * [0, k_max]); the arrays hold k_max entries.  The call enqueues ceil(k_max / 64) updates;
+ * an update whose events all lie beyond the live count finds no net change and leaves the
+ * state as it is.  So one captured call (CUDA graph) replays batches of any size up to
+ * k_max, written into the same buffers between replays; the result of each replay equals
+ * damf_apply_edges on the live events.  DAMF_ERR_INVALID for a NULL k_dev.
+ */
+damf_status damf_apply_edges_counted(damf_ctx* ctx, const int32_t* src, const int32_t* dst, const int8_t* op,
+                                     int32_t k_max, const int32_t* k_dev, int32_t new_nodes, void* stream);
+
 /* One batch of events for one graph (damf_apply_edges_multi). */
 typedef struct {
   damf_ctx* ctx;          /* the graph's context */
   const int32_t* src;     /* (device) int32[k] */
   const int32_t* dst;     /* (device) int32[k] */
   const int8_t* op;       /* (device) int8[k], +1 insert, -1 delete */
-  int32_t k;              /* events */
+  int32_t k;              /* events (with k_dev: the capacity of the arrays, k_max) */
   int32_t new_nodes;      /* node arrivals appended before the events */
+  const int32_t* k_dev;   /* NULL, or (device) int32: the live event count, as for
+                             damf_apply_edges_counted */
 } damf_batch;
 
 /*
@@ -136,6 +150,100 @@ typedef struct {
  * applied); DAMF_ERR_INVALID for num_graphs < 0 or a NULL batches array / context.
  */
 damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
+
+/*
+ * One step of many independent graphs (the batching pattern: graphs of uneven size and
+ * rank, one batch each): for every entry, the batch's update (as damf_apply_edges, or
+ * damf_apply_edges_counted when k_dev is set) and then its push (damf_ppr_refresh), run on
+ * streams the graph's context owns, forked from `stream` after the work enqueued on it
+ * before the call; `stream` then waits for every graph's update and push.  The graphs'
+ * kernels overlap on the device, and each graph's result equals its result when its batch
+ * is applied and pushed alone.  Capturable in one CUDA graph (join each context, damf_join,
+ * before the capture starts); a replay then runs the whole step as one launch.  A context
+ * may appear once per call (DAMF_ERR_INVALID otherwise, nothing enqueued).  Returns the
+ * first non-OK status; the graphs before it have been enqueued.
+ */
+damf_status damf_step_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
+
+/*
+ * Fleets: many independent graphs stepped together with their pushes in one launch.
+ *
+ * damf_step_multi runs one cooperative push per graph, and cooperative launches do not run
+ * side by side, so a fleet of small graphs spends its time in one push after another.  A
+ * fleet instead pushes all its graphs in one grouped cooperative launch (one per threshold
+ * mode): graph i owns a share of the CTAs and runs its own push (Sec. 4.4) over them, with
+ * its own work queue and its own barrier among its CTAs, so each graph's result is the same
+ * as when it is pushed alone.  Graphs too small for a CTA of their own share one, which
+ * pushes them one after another.
+ */
+typedef struct damf_fleet damf_fleet;
+
+/* Creates a fleet over count distinct contexts (the fleet order; the contexts stay owned by
+ * the caller and must outlive the fleet).  Shares start proportional to d (n + m) (m the
+ * initial adjacency entries).  Synchronous (uploads its tables).  DAMF_ERR_INVALID for
+ * count < 1, a NULL, repeated or poisoned context. */
+damf_status damf_fleet_create(damf_ctx* const* ctxs, int32_t count, damf_fleet** out);
+
+/*
+ * One step: batches[i] (fleet order; its ctx NULL or the fleet's i-th context) is applied to
+ * graph i as by damf_apply_edges (damf_apply_edges_counted when k_dev is set), each graph's
+ * update on its context's own stream, forked from `stream`; then the grouped push of every
+ * graph; `stream` waits for all of it.  Capturable in one CUDA graph (join every context,
+ * damf_join, before the capture starts; new_nodes = 0 and refold_every = 0 keep the host
+ * bookkeeping of a captured step the same at every replay).  Afterwards each context reads
+ * and joins like after damf_ppr_refresh.
+ */
+damf_status damf_fleet_step(damf_fleet* fleet, const damf_batch* batches, void* stream);
+
+/* Sets the CTAs of each graph's push: blocks (host int32[count], each >= 1, the graphs of one
+ * threshold mode summing to at most the resident push CTAs), or with blocks = NULL shares in
+ * proportion to (d (n + m))^exponent, exponent in [0, 4]: a graph whose share is below one CTA
+ * shares a CTA with other such graphs (first fit, largest first).  Also takes each
+ * context's push_direct_chunks (damf_set_tuning) as it is now.  Synchronous; not while a
+ * capture is in progress.  DAMF_ERR_INVALID (shares unchanged) for bad values. */
+damf_status damf_fleet_set_shares(damf_fleet* fleet, const int32_t* blocks, double exponent);
+
+/* Phase timing of the following (uncaptured) fleet steps: when enabled, each step records
+ * events at its fork, after every graph's update and after the pushes. */
+damf_status damf_fleet_set_timing(damf_fleet* fleet, int32_t enable);
+
+/* Waits for the timed steps and returns their summed update-phase and push-phase device time
+ * (ms) and their number, then starts counting afresh; any pointer may be NULL. */
+damf_status damf_fleet_get_timing(damf_fleet* fleet, double* update_ms, double* push_ms, int32_t* steps);
+
+/* The CTAs each graph's push owns alone (host int32[count], fleet order; 0 for a small graph
+ * that shares one CTA with other small graphs, which it pushes after or before them) and the
+ * number of grouped launches per step; either pointer may be NULL. */
+damf_status damf_fleet_get_shares(const damf_fleet* fleet, int32_t* blocks, int32_t* launches);
+
+/* Kernels the fleet itself has launched (two per grouped push: queue reset and push); the
+ * updates' kernels count in each context's damf_stats.launches. */
+int64_t damf_fleet_launches(const damf_fleet* fleet);
+
+/* Text of the fleet's most recent error. */
+const char* damf_fleet_last_error(const damf_fleet* fleet);
+
+/* Waits for the fleet's pushes and frees the fleet (not the contexts). */
+void damf_fleet_destroy(damf_fleet* fleet);
+
+/* Launch shape of a context's PPR push (damf_set_tuning, damf_get_tuning). */
+typedef struct {
+  int32_t push_blocks;        /* CTAs of the persistent push, 256 threads each; 0 = the most that
+                                 stay resident beside the factor chain (two per SM); larger
+                                 values are clamped to it.  Graphs that share the GPU
+                                 (damf_step_multi) take fewer, so that their pushes overlap. */
+  int32_t push_direct_chunks; /* a row with more in-edges than this many chunks (a chunk is 8,
+                                 16, 32, 32 in-edges for d = 128, 64, 32, 16) is pushed as hub
+                                 items of 8 in-edges spread over warps; -1 = 8 chunks */
+} damf_tuning;
+
+/* Sets the push launch shape for the following pushes (the results stay within the push
+ * bound; the order of the floating-point adds changes).  DAMF_ERR_INVALID for
+ * push_blocks < 0 or push_direct_chunks outside [-1, 1024] (context unchanged). */
+damf_status damf_set_tuning(damf_ctx* ctx, const damf_tuning* tuning);
+
+/* The launch shape the next push uses (defaults and clamping resolved). */
+damf_status damf_get_tuning(const damf_ctx* ctx, damf_tuning* tuning);
 
 /*
  * Node deletion (not treated by the paper, whose events add nodes): removes every edge of

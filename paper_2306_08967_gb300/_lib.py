@@ -21,7 +21,11 @@ class Config(ctypes.Structure):
 
 class Batch(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("op", ctypes.c_void_p),
-                ("k", c_i32), ("new_nodes", c_i32)]
+                ("k", c_i32), ("new_nodes", c_i32), ("k_dev", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("push_blocks", c_i32), ("push_direct_chunks", c_i32)]
 
 
 class Stats(ctypes.Structure):
@@ -40,7 +44,20 @@ SIGNATURES = {
     "damf_init_factorize": (c_i32, [ctypes.POINTER(Config), c_vp, c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "damf_apply_edges": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
+    "damf_apply_edges_counted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
     "damf_apply_edges_multi": (c_i32, [c_vp, c_i32, c_vp]),
+    "damf_step_multi": (c_i32, [c_vp, c_i32, c_vp]),
+    "damf_set_tuning": (c_i32, [c_vp, ctypes.POINTER(Tuning)]),
+    "damf_fleet_create": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    "damf_fleet_step": (c_i32, [c_vp, c_vp, c_vp]),
+    "damf_fleet_set_shares": (c_i32, [c_vp, c_vp, c_f64]),
+    "damf_fleet_get_shares": (c_i32, [c_vp, c_vp, c_vp]),
+    "damf_fleet_launches": (c_i64, [c_vp]),
+    "damf_fleet_set_timing": (c_i32, [c_vp, c_i32]),
+    "damf_fleet_get_timing": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "damf_fleet_last_error": (ctypes.c_char_p, [c_vp]),
+    "damf_fleet_destroy": (None, [c_vp]),
+    "damf_get_tuning": (c_i32, [c_vp, ctypes.POINTER(Tuning)]),
     "damf_delete_nodes": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
     "damf_ppr_refresh": (c_i32, [c_vp, c_vp]),
     "damf_join": (c_i32, [c_vp, c_vp]),

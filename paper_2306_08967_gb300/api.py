@@ -79,23 +79,107 @@ def core_svd(sigma, L, R, stream=None):
     return E, H, th
 
 
-def apply_edges_multi(batches, stream=None):
-    """One batch per graph through damf_apply_edges_multi: batches is a list of
-    (DamfGraph, src, dst, op[, new_nodes]) with device-resident or array events."""
-    lib = _lib.load()
+def _batch_array(batches):
+    """damf_batch[] for a list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]]); with a k_dev
+    (device int32 tensor of one element) the arrays hold k_max events of which *k_dev are live."""
     arr = (_lib.Batch * max(len(batches), 1))()
-    keep = []
     for i, b in enumerate(batches):
         g, src, dst, op = b[:4]
         nn = int(b[4]) if len(b) > 4 else 0
+        kd = b[5] if len(b) > 5 else None
         s, t, o = _dev(src, torch.int32), _dev(dst, torch.int32), _dev(op, torch.int8)
-        keep += [s, t, o]
-        g._keep = (s, t, o)   # alive until the stream has consumed them
+        if kd is not None and (not isinstance(kd, torch.Tensor) or not kd.is_cuda or kd.dtype != torch.int32):
+            raise ValueError("k_dev must be a CUDA int32 tensor")
+        g._keep = (s, t, o, kd)   # alive until the stream has consumed them
         arr[i] = _lib.Batch(g.h.value if hasattr(g.h, "value") else g.h, s.data_ptr(), t.data_ptr(), o.data_ptr(),
-                            int(s.numel()), nn)
-    st = lib.damf_apply_edges_multi(arr, len(batches), _stream_ptr(stream))
+                            int(s.numel()), nn, None if kd is None else kd.data_ptr())
+    return arr
+
+
+def apply_edges_multi(batches, stream=None):
+    """One batch per graph through damf_apply_edges_multi, in order on one stream: batches is a
+    list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]])."""
+    st = _lib.load().damf_apply_edges_multi(_batch_array(batches), len(batches), _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "apply_edges_multi")
+
+
+def step_multi(batches, stream=None):
+    """One step of many graphs through damf_step_multi: each graph's update and push on its own
+    streams, joined back to `stream`. batches as for apply_edges_multi."""
+    st = _lib.load().damf_step_multi(_batch_array(batches), len(batches), _stream_ptr(stream))
+    if st != 0:
+        raise DamfError(st, "step_multi")
+
+
+class DamfFleet:
+    """Many graphs stepped together, their pushes in one grouped launch (damf_fleet_*).
+    The DamfGraphs stay owned by the caller and must outlive the fleet."""
+
+    def __init__(self, graphs):
+        self.lib = _lib.load()
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.h.value for g in self.graphs])
+        h = ctypes.c_void_p()
+        st = self.lib.damf_fleet_create(arr, len(self.graphs), ctypes.byref(h))
+        if st != 0:
+            raise DamfError(st, "fleet_create")
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise DamfError(st, self.lib.damf_fleet_last_error(self.h).decode())
+
+    def step(self, batches, stream=None):
+        """batches: one (src, dst, op[, new_nodes[, k_dev]]) per graph, fleet order."""
+        arr = _batch_array([(g, *b) for g, b in zip(self.graphs, batches)])
+        self._keep = arr
+        self._check(self.lib.damf_fleet_step(self.h, arr, _stream_ptr(stream)))
+
+    def step_array(self, arr, stream=None):
+        """A prepared damf_batch array (api._batch_array), e.g. for a captured step."""
+        self._check(self.lib.damf_fleet_step(self.h, arr, _stream_ptr(stream)))
+
+    def set_shares(self, blocks=None, exponent: float = 1.0):
+        """Push CTAs per graph (list of ints), or shares proportional to (d (n + m))^exponent."""
+        if blocks is None:
+            self._check(self.lib.damf_fleet_set_shares(self.h, None, float(exponent)))
+        else:
+            a = np.ascontiguousarray(blocks, dtype=np.int32)
+            if a.size != len(self.graphs):
+                raise ValueError("one share per graph")
+            self._check(self.lib.damf_fleet_set_shares(self.h, a.ctypes.data_as(ctypes.c_void_p), 0.0))
+
+    def shares(self):
+        """(CTAs per graph as a list, grouped launches per step)."""
+        a = np.zeros(len(self.graphs), dtype=np.int32)
+        nl = ctypes.c_int32()
+        self._check(self.lib.damf_fleet_get_shares(self.h, a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nl)))
+        return a.tolist(), int(nl.value)
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.damf_fleet_launches(self.h))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.lib.damf_fleet_set_timing(self.h, int(enable)))
+
+    def timing(self) -> dict:
+        """{"update_ms", "push_ms", "steps"} of the steps timed since the last call."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        self._check(self.lib.damf_fleet_get_timing(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return {"update_ms": a.value, "push_ms": b.value, "steps": n.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.damf_fleet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class DamfGraph:
@@ -135,6 +219,29 @@ class DamfGraph:
         self._check(self.lib.damf_apply_edges(self.h, ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                               ctypes.c_void_p(o.data_ptr()), int(s.numel()), int(new_nodes),
                                               _stream_ptr(stream)))
+
+    def apply_edges_counted(self, src, dst, op, k_dev, new_nodes: int = 0, stream=None):
+        """Device events of which the first k_dev[0] (a CUDA int32 tensor, read when the work
+        runs) are live; src/dst/op hold k_max events."""
+        s, t, o = _dev(src, torch.int32), _dev(dst, torch.int32), _dev(op, torch.int8)
+        if not isinstance(k_dev, torch.Tensor) or not k_dev.is_cuda or k_dev.dtype != torch.int32:
+            raise ValueError("k_dev must be a CUDA int32 tensor")
+        self._keep = (s, t, o, k_dev)
+        self._check(self.lib.damf_apply_edges_counted(self.h, ctypes.c_void_p(s.data_ptr()),
+                                                      ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                                      int(s.numel()), ctypes.c_void_p(k_dev.data_ptr()),
+                                                      int(new_nodes), _stream_ptr(stream)))
+
+    def set_tuning(self, push_blocks: int = 0, push_direct_chunks: int = -1):
+        """Launch shape of the following pushes (0 / -1: the defaults)."""
+        t = _lib.Tuning(push_blocks=int(push_blocks), push_direct_chunks=int(push_direct_chunks))
+        self._check(self.lib.damf_set_tuning(self.h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        """The push launch shape the next push uses."""
+        t = _lib.Tuning()
+        self._check(self.lib.damf_get_tuning(self.h, ctypes.byref(t)))
+        return {"push_blocks": int(t.push_blocks), "push_direct_chunks": int(t.push_direct_chunks)}
 
     def delete_nodes(self, nodes, stream=None):
         """Removes every edge of the given nodes (host ids); the ids stay as isolated nodes."""

@@ -4,6 +4,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
+#include <utility>
+#include <vector>
+
 #include "damf_internal.cuh"
 
 namespace damf {
@@ -188,6 +193,18 @@ cudaError_t wait_push(Ctx* c, cudaStream_t s) {
   return c->push_capture_id == id ? cudaStreamWaitEvent(s, c->ev_push_cap, 0) : cudaSuccess;
 }
 
+// Records that the most recent push of `c` ends at the current tail of `s` (the stream the
+// push ran on): its own event inside a stream capture (keyed by the capture), ev_push outside.
+cudaError_t note_push(Ctx* c, cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  unsigned long long id = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cap, &id);
+  if (e != cudaSuccess) return e;
+  const bool captured = cap != cudaStreamCaptureStatusNone;
+  c->push_capture_id = captured ? id : 0;
+  return cudaEventRecord(captured ? c->ev_push_cap : c->ev_push, s);
+}
+
 #define DAMF_CUDA(call, what)                                  \
   do {                                                         \
     cudaError_t e_ = (call);                                   \
@@ -199,7 +216,11 @@ void free_all(Ctx* c) {
   if (c->ev_caller) cudaEventDestroy(c->ev_caller);
   if (c->ev_push) cudaEventDestroy(c->ev_push);
   if (c->ev_push_cap) cudaEventDestroy(c->ev_push_cap);
-  c->ev_push_cap = nullptr;
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  c->own_stream = nullptr;
+  c->ev_fork = c->ev_done = c->ev_push_cap = nullptr;
   c->push_stream = nullptr;
   c->ev_caller = c->ev_push = nullptr;
   if (c->ev) {
@@ -305,6 +326,179 @@ done:
 
 }  // namespace damf
 
+// ---- fleets: many graphs stepped together, their pushes in one grouped launch ----
+struct FleetLaunch {
+  int scaled;        // threshold mode of its graphs
+  int first_graph;   // its graphs: descriptor positions first_graph .. first_graph + count
+  int count;
+  int nslots;
+  int blocks;
+  int table_off;     // its sfirst / gfirst table in d_table
+};
+
+struct damf_fleet {
+  std::vector<damf_ctx*> ctxs;   // fleet order (damf_fleet_step's batches follow it)
+  std::vector<int> blocks;       // CTAs each graph owns alone (0: it shares one CTA with others)
+  std::vector<FleetLaunch> launches;
+  PushArgs* d_descs = nullptr;   // per launch position
+  int* d_table = nullptr;
+  size_t table_cap = 0;
+  cudaStream_t push_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+  long long launches_total = 0;
+  // phase timing (damf_fleet_set_timing): per step, events at the fork, before and after the pushes
+  int timing = 0;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
+  char errbuf[256] = {0};
+};
+
+namespace {
+
+damf_status fleet_fail(damf_fleet* f, damf_status st, const char* what, cudaError_t e = cudaSuccess) {
+  snprintf(f->errbuf, sizeof(f->errbuf), "%s%s%s", what, e == cudaSuccess ? "" : ": ",
+           e == cudaSuccess ? "" : cudaGetErrorString(e));
+  return st;
+}
+
+struct Slot {
+  int blocks;
+  std::vector<int> graphs;   // fleet indices
+};
+
+// Slots of one threshold mode's graphs (idx) over at most maxb CTAs. With `given`, one slot per
+// graph with those CTAs. Otherwise graph j's fair share is x_j = maxb w_j / sum(w), w_j =
+// (d (n + m))^exponent: a graph with x_j >= cap owns floor(x_j) CTAs (at least one), the rest are
+// packed first-fit-decreasing into one-CTA bins of total share <= cap, and CTAs left over go
+// to the owners by largest remainders; cap starts at 1 and grows until the slots fit.
+bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, const int32_t* given, double exponent,
+                std::vector<Slot>* out) {
+  out->clear();
+  if (given) {
+    long long tot = 0;
+    for (int i : idx) {
+      out->push_back(Slot{given[i], {i}});
+      tot += given[i];
+    }
+    return tot <= maxb;
+  }
+  const int cnt = (int)idx.size();
+  std::vector<double> x(cnt);
+  double wsum = 0.0;
+  for (int j = 0; j < cnt; ++j) {
+    const Ctx& c = f->ctxs[idx[j]]->c;
+    x[j] = std::pow((double)c.d * (double)(c.n + c.m_init + 1), exponent);
+    wsum += x[j];
+  }
+  for (int j = 0; j < cnt; ++j) x[j] = maxb * x[j] / wsum;
+  std::vector<int> by_x(cnt);
+  for (int j = 0; j < cnt; ++j) by_x[j] = j;
+  std::sort(by_x.begin(), by_x.end(), [&](int a, int b) { return x[a] > x[b] || (x[a] == x[b] && a < b); });
+  for (double cap = 1.0;; cap *= 1.25) {
+    std::vector<Slot> owners, bins;
+    std::vector<double> bin_load, rem;
+    for (int j : by_x) {
+      if (x[j] >= cap) {
+        owners.push_back(Slot{std::max(1, (int)std::floor(x[j])), {idx[j]}});
+        rem.push_back(x[j] - std::floor(x[j]));
+        continue;
+      }
+      size_t b = 0;
+      while (b < bins.size() && bin_load[b] + x[j] > cap) ++b;
+      if (b == bins.size()) {
+        bins.push_back(Slot{1, {}});
+        bin_load.push_back(0.0);
+      }
+      bins[b].graphs.push_back(idx[j]);
+      bin_load[b] += x[j];
+    }
+    long long used = (long long)bins.size();
+    for (const Slot& o : owners) used += o.blocks;
+    if (used > maxb) continue;   // cap >= maxb leaves one bin, so this ends
+    std::vector<int> order(owners.size());
+    for (size_t k = 0; k < owners.size(); ++k) order[k] = (int)k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return rem[a] > rem[b] || (rem[a] == rem[b] && a < b); });
+    for (long long left = maxb - used, k = 0; left > 0 && !owners.empty(); --left, ++k)
+      owners[order[k % (long long)owners.size()]].blocks += 1;
+    *out = owners;
+    out->insert(out->end(), bins.begin(), bins.end());
+    return true;
+  }
+}
+
+// Builds every launch's slots and uploads the descriptor and slot tables.
+damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent) {
+  const int G = (int)f->ctxs.size();
+  std::vector<int> blocks(G, 0);
+  std::vector<FleetLaunch> launches;
+  std::vector<PushArgs> descs;
+  std::vector<int> table;
+  for (int scaled = 0; scaled < 2; ++scaled) {
+    std::vector<int> idx;
+    for (int i = 0; i < G; ++i)
+      if ((f->ctxs[i]->c.cfg.threshold != 0) == (scaled != 0)) idx.push_back(i);
+    if (idx.empty()) continue;
+    const int maxb = push_group_max_blocks(scaled);
+    if (maxb < 1) return fleet_fail(f, DAMF_ERR_CUDA, "fleet: no resident push CTA");
+    std::vector<Slot> slots;
+    if (!plan_slots(f, idx, maxb, given, exponent, &slots))
+      return fleet_fail(f, DAMF_ERR_INVALID, "fleet: shares exceed the resident push CTAs");
+    FleetLaunch L{scaled, (int)descs.size(), 0, (int)slots.size(), 0, (int)table.size()};
+    std::vector<int> sfirst(1, 0), gfirst(1, 0);
+    for (const Slot& sl : slots) {
+      for (int gi : sl.graphs) {
+        descs.push_back(push_args(&f->ctxs[gi]->c, f->ctxs[gi]->c.push_direct_chunks));
+        blocks[gi] = sl.graphs.size() == 1 ? sl.blocks : 0;
+      }
+      L.count += (int)sl.graphs.size();
+      L.blocks += sl.blocks;
+      sfirst.push_back(L.blocks);
+      gfirst.push_back(L.count);
+    }
+    table.insert(table.end(), sfirst.begin(), sfirst.end());
+    table.insert(table.end(), gfirst.begin(), gfirst.end());
+    launches.push_back(L);
+  }
+  cudaError_t e = cudaSuccess;
+  if (!f->d_descs) e = cudaMalloc(&f->d_descs, sizeof(PushArgs) * (size_t)G);
+  if (e == cudaSuccess && table.size() > f->table_cap) {
+    if (f->d_table) cudaFree(f->d_table);
+    f->d_table = nullptr;
+    f->table_cap = table.size() + 64;
+    e = cudaMalloc(&f->d_table, sizeof(int) * f->table_cap);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(f->d_descs, descs.data(), sizeof(PushArgs) * descs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f->d_table, table.data(), sizeof(int) * table.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet tables", e);
+  f->blocks = blocks;
+  f->launches = launches;
+  return DAMF_OK;
+}
+
+cudaError_t fleet_mark(damf_fleet* f, cudaStream_t s) {
+  if (!f->timing) return cudaSuccess;
+  if (f->tev_used == f->tev.size()) {
+    if (f->tev.size() >= 3 * 4096) return cudaSuccess;   // full: the later steps go unmeasured
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    f->tev.push_back(ev);
+  }
+  return cudaEventRecord(f->tev[f->tev_used++], s);
+}
+
+void fleet_free(damf_fleet* f) {
+  if (f->d_descs) cudaFree(f->d_descs);
+  if (f->d_table) cudaFree(f->d_table);
+  if (f->push_stream) cudaStreamDestroy(f->push_stream);
+  if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+  if (f->ev_done) cudaEventDestroy(f->ev_done);
+  for (cudaEvent_t ev : f->tev) cudaEventDestroy(ev);
+  delete f;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t damf_bytes_required(const damf_config* cfg) {
@@ -331,6 +525,7 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   c->d = cfg->d;
   c->n = cfg->n;
   c->l = width_of(cfg);
+  c->m_init = m;
   Plan p = plan_of(cfg);
   void* ptr[64];
   for (int i = 0; i < p.count; ++i) {
@@ -385,7 +580,9 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   }
   cudaError_t e;
   unsigned int one = 1;
+  const int n0 = cfg->n;
   if ((e = cudaMemcpyAsync(&c->hdr->epoch, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&c->hdr->n_nodes, &n0, sizeof(n0), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.queue, 0xff, (size_t)w.qcap * 4, s)) != cudaSuccess ||   // empty slots: -1
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_all(c);
@@ -403,6 +600,10 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_caller, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_push_cap, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
+  c->push_direct_chunks = -1;
   if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
   if (e == cudaSuccess) e = launch_push(c, 1, s);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_push, s);
@@ -427,24 +628,26 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   return DAMF_OK;
 }
 
-damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
-                             int32_t new_nodes, void* stream) {
+// Events src/dst/op[0 .. k), or the first *kdev of them (clamped to [0, k]) when kdev is
+// given: ceil(k / 64) updates are enqueued either way, and an update whose events are all
+// beyond the live count finds no net change and leaves every state untouched.
+static damf_status apply_impl(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                              const int32_t* kdev, int32_t new_nodes, cudaStream_t s) {
   if (!x) return DAMF_ERR_INVALID;
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
   if (k < 0 || new_nodes < 0 || (k > 0 && (!src || !dst || !op))) return fail(c, DAMF_ERR_INVALID, "arguments", cudaSuccess);
   if ((long long)c->n + new_nodes > c->cfg.n_capacity) return fail(c, DAMF_ERR_CAPACITY, "node capacity", cudaSuccess);
-  cudaStream_t s = (cudaStream_t)stream;
   const int n_after = c->n + new_nodes;
-  DAMF_CUDA(launch_validate(c, src, dst, op, k, n_after, s), "validate");
-  c->launches += k > 0 ? 1 : 0;
+  DAMF_CUDA(launch_validate(c, src, dst, op, k, kdev, n_after, s), "validate");
+  c->launches += 1;
   c->n = n_after;
   for (int lo = 0; lo < k; lo += kEdgesPerUpdate) {
     const int kk = (k - lo) < kEdgesPerUpdate ? (k - lo) : kEdgesPerUpdate;
     // read-only part: net change, projection, residual factors, core SVD, transforms.
     // It runs on the caller's stream while the previous push may still run on the
     // push stream (both only read the adjacency).
-    DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_prepare(c, src + lo, dst + lo, op + lo, kk, n_after, s), "prepare");
+    DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_prepare(c, src, dst, op, kk, kdev, lo, s), "prepare");
     DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
     DAMF_STAGE(DAMF_STAGE_CHOL, 2, launch_chol(c, s), "chol");
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
@@ -463,6 +666,17 @@ damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst
     }
   }
   return DAMF_OK;
+}
+
+damf_status damf_apply_edges(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                             int32_t new_nodes, void* stream) {
+  return apply_impl(x, src, dst, op, k, nullptr, new_nodes, (cudaStream_t)stream);
+}
+
+damf_status damf_apply_edges_counted(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op,
+                                     int32_t k_max, const int32_t* k_dev, int32_t new_nodes, void* stream) {
+  if (x && !k_dev) return fail(&x->c, DAMF_ERR_INVALID, "arguments", cudaSuccess);
+  return apply_impl(x, src, dst, op, k_max, k_dev, new_nodes, (cudaStream_t)stream);
 }
 
 damf_status damf_delete_nodes(damf_ctx* x, const int32_t* nodes, int32_t count, void* stream) {
@@ -514,9 +728,53 @@ damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs
   for (int32_t i = 0; i < num_graphs; ++i) {
     const damf_batch& b = batches[i];
     if (!b.ctx) return DAMF_ERR_INVALID;
-    const damf_status st = damf_apply_edges(b.ctx, b.src, b.dst, b.op, b.k, b.new_nodes, stream);
+    const damf_status st = apply_impl(b.ctx, b.src, b.dst, b.op, b.k, b.k_dev, b.new_nodes, (cudaStream_t)stream);
     if (st != DAMF_OK) return st;
   }
+  return DAMF_OK;
+}
+
+damf_status damf_step_multi(const damf_batch* batches, int32_t num_graphs, void* stream) {
+  if (num_graphs < 0 || (num_graphs > 0 && !batches)) return DAMF_ERR_INVALID;
+  for (int32_t i = 0; i < num_graphs; ++i) {
+    if (!batches[i].ctx) return DAMF_ERR_INVALID;
+    if (batches[i].ctx->c.sticky) return (damf_status)batches[i].ctx->c.sticky;
+    for (int32_t j = 0; j < i; ++j)
+      if (batches[j].ctx == batches[i].ctx) return reject(&batches[i].ctx->c, "step_multi: a graph appears twice");
+  }
+  cudaStream_t caller = (cudaStream_t)stream;
+  for (int32_t i = 0; i < num_graphs; ++i) {
+    const damf_batch& b = batches[i];
+    Ctx* c = &b.ctx->c;
+    // fork: the graph's update and push on its own streams, after the caller's earlier work
+    DAMF_CUDA(cudaEventRecord(c->ev_fork, caller), "fork");
+    DAMF_CUDA(cudaStreamWaitEvent(c->own_stream, c->ev_fork, 0), "fork");
+    damf_status st = apply_impl(b.ctx, b.src, b.dst, b.op, b.k, b.k_dev, b.new_nodes, c->own_stream);
+    if (st == DAMF_OK) st = damf_ppr_refresh(b.ctx, c->own_stream);
+    if (st != DAMF_OK) return st;
+    // join: the caller's stream waits for the push
+    DAMF_CUDA(wait_push(c, c->own_stream), "join push");
+    DAMF_CUDA(cudaEventRecord(c->ev_done, c->own_stream), "join");
+    DAMF_CUDA(cudaStreamWaitEvent(caller, c->ev_done, 0), "join");
+  }
+  return DAMF_OK;
+}
+
+damf_status damf_set_tuning(damf_ctx* x, const damf_tuning* t) {
+  if (!x || !t) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (t->push_blocks < 0 || t->push_direct_chunks < -1 || t->push_direct_chunks > 1024)
+    return reject(c, "set_tuning: value out of range");
+  c->push_blocks = t->push_blocks;
+  c->push_direct_chunks = t->push_direct_chunks;
+  return DAMF_OK;
+}
+
+damf_status damf_get_tuning(const damf_ctx* x, damf_tuning* t) {
+  if (!x || !t) return DAMF_ERR_INVALID;
+  const Ctx* c = &x->c;
+  t->push_blocks = (c->push_blocks > 0 && c->push_blocks < c->push_max) ? c->push_blocks : c->push_max;
+  t->push_direct_chunks = c->push_direct_chunks >= 0 ? c->push_direct_chunks : push_default_direct_chunks();
   return DAMF_OK;
 }
 
@@ -554,12 +812,7 @@ damf_status damf_ppr_refresh(damf_ctx* x, void* stream) {
   cudaStream_t s = c->push_stream;
   DAMF_CUDA(cudaStreamWaitEvent(s, c->ev_caller, 0), "push wait");
   DAMF_STAGE(DAMF_STAGE_PUSH, 1, launch_push(c, c->check_all_next, s), "push");
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  unsigned long long id = 0;
-  DAMF_CUDA(cudaStreamGetCaptureInfo((cudaStream_t)stream, &cap, &id), "capture status");
-  const bool captured = cap != cudaStreamCaptureStatusNone;
-  c->push_capture_id = captured ? id : 0;
-  DAMF_CUDA(cudaEventRecord(captured ? c->ev_push_cap : c->ev_push, s), "record");
+  DAMF_CUDA(note_push(c, s), "record");
   c->launches += 1;
   c->check_all_next = 0;
   return DAMF_OK;
@@ -766,6 +1019,145 @@ void damf_destroy(damf_ctx* x) {
   cudaDeviceSynchronize();
   free_all(&x->c);
   free(x);
+}
+
+damf_status damf_fleet_create(damf_ctx* const* ctxs, int32_t count, damf_fleet** out) {
+  if (!out) return DAMF_ERR_INVALID;
+  *out = nullptr;
+  if (count < 1 || !ctxs) return DAMF_ERR_INVALID;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!ctxs[i] || ctxs[i]->c.sticky) return DAMF_ERR_INVALID;
+    for (int32_t j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return DAMF_ERR_INVALID;
+  }
+  damf_fleet* f = new (std::nothrow) damf_fleet();
+  if (!f) return DAMF_ERR_CUDA;
+  f->ctxs.assign(ctxs, ctxs + count);
+  cudaError_t e = cudaStreamCreateWithFlags(&f->push_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fleet_free(f);
+    return DAMF_ERR_CUDA;
+  }
+  const damf_status st = fleet_plan(f, nullptr, 1.0);
+  if (st != DAMF_OK) {
+    fleet_free(f);
+    return st;
+  }
+  *out = f;
+  return DAMF_OK;
+}
+
+damf_status damf_fleet_set_shares(damf_fleet* f, const int32_t* blocks, double exponent) {
+  if (!f) return DAMF_ERR_INVALID;
+  if (blocks) {
+    for (size_t i = 0; i < f->ctxs.size(); ++i)
+      if (blocks[i] < 1) return fleet_fail(f, DAMF_ERR_INVALID, "fleet: a share below one CTA");
+  } else if (!(exponent >= 0.0 && exponent <= 4.0)) {
+    return fleet_fail(f, DAMF_ERR_INVALID, "fleet: exponent outside [0, 4]");
+  }
+  // a failed plan leaves the previous one in place
+  std::vector<int> ob = f->blocks;
+  const damf_status st = fleet_plan(f, blocks, exponent);
+  if (st != DAMF_OK && !ob.empty()) {
+    std::vector<int32_t> keep(ob.begin(), ob.end());
+    fleet_plan(f, keep.data(), 1.0);
+  }
+  return st;
+}
+
+damf_status damf_fleet_get_shares(const damf_fleet* f, int32_t* blocks, int32_t* launches) {
+  if (!f) return DAMF_ERR_INVALID;
+  if (blocks)
+    for (size_t i = 0; i < f->blocks.size(); ++i) blocks[i] = f->blocks[i];
+  if (launches) *launches = (int32_t)f->launches.size();
+  return DAMF_OK;
+}
+
+damf_status damf_fleet_step(damf_fleet* f, const damf_batch* batches, void* stream) {
+  if (!f || !batches) return DAMF_ERR_INVALID;
+  const int G = (int)f->ctxs.size();
+  for (int i = 0; i < G; ++i) {
+    if (batches[i].ctx && batches[i].ctx != f->ctxs[i]) return fleet_fail(f, DAMF_ERR_INVALID, "fleet: batch order");
+    if (f->ctxs[i]->c.sticky) return (damf_status)f->ctxs[i]->c.sticky;
+  }
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaError_t e = fleet_mark(f, caller);
+  if (e == cudaSuccess) e = cudaEventRecord(f->ev_fork, caller);
+  if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet fork", e);
+  // every graph's update on its own stream; the fleet's push stream then waits for all of them
+  for (int i = 0; i < G; ++i) {
+    damf_ctx* x = f->ctxs[i];
+    Ctx* c = &x->c;
+    const damf_batch& b = batches[i];
+    DAMF_CUDA(cudaStreamWaitEvent(c->own_stream, f->ev_fork, 0), "fleet fork");
+    const damf_status st = apply_impl(x, b.src, b.dst, b.op, b.k, b.k_dev, b.new_nodes, c->own_stream);
+    if (st != DAMF_OK) return st;
+    DAMF_CUDA(cudaEventRecord(c->ev_done, c->own_stream), "fleet join");
+    DAMF_CUDA(cudaStreamWaitEvent(f->push_stream, c->ev_done, 0), "fleet join");
+  }
+  // the pushes: one grouped cooperative launch per threshold mode
+  e = fleet_mark(f, f->push_stream);
+  if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet timing", e);
+  for (size_t l = 0; l < f->launches.size(); ++l) {
+    const FleetLaunch& L = f->launches[l];
+    e = launch_push_group(f->d_descs + L.first_graph, L.count, f->d_table + L.table_off, L.nslots, L.blocks,
+                          L.scaled, f->push_stream);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < G; ++i) fail(&f->ctxs[i]->c, DAMF_ERR_CUDA, "fleet push", e);
+      return fleet_fail(f, DAMF_ERR_CUDA, "fleet push", e);
+    }
+    f->launches_total += 2;
+  }
+  for (int i = 0; i < G; ++i) {
+    Ctx* c = &f->ctxs[i]->c;
+    DAMF_CUDA(note_push(c, f->push_stream), "fleet record");
+    c->check_all_next = 0;
+  }
+  e = fleet_mark(f, f->push_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(f->ev_done, f->push_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, f->ev_done, 0);
+  if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet join", e);
+  return DAMF_OK;
+}
+
+damf_status damf_fleet_set_timing(damf_fleet* f, int32_t enable) {
+  if (!f) return DAMF_ERR_INVALID;
+  f->timing = enable ? 1 : 0;
+  f->tev_used = 0;
+  return DAMF_OK;
+}
+
+damf_status damf_fleet_get_timing(damf_fleet* f, double* update_ms, double* push_ms, int32_t* steps) {
+  if (!f) return DAMF_ERR_INVALID;
+  double a = 0.0, b = 0.0;
+  int n = 0;
+  for (size_t i = 0; i + 3 <= f->tev_used; i += 3) {
+    cudaError_t e = cudaEventSynchronize(f->tev[i + 2]);
+    float t01 = 0.f, t12 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t01, f->tev[i], f->tev[i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t12, f->tev[i + 1], f->tev[i + 2]);
+    if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet timing", e);
+    a += t01;
+    b += t12;
+    ++n;
+  }
+  f->tev_used = 0;
+  if (update_ms) *update_ms = a;
+  if (push_ms) *push_ms = b;
+  if (steps) *steps = n;
+  return DAMF_OK;
+}
+
+int64_t damf_fleet_launches(const damf_fleet* f) { return f ? f->launches_total : 0; }
+
+const char* damf_fleet_last_error(const damf_fleet* f) { return f ? f->errbuf : "no fleet"; }
+
+void damf_fleet_destroy(damf_fleet* f) {
+  if (!f) return;
+  cudaStreamSynchronize(f->push_stream);
+  fleet_free(f);
 }
 
 }  // extern "C"

@@ -41,7 +41,8 @@ struct DevHeader {
   int nrowS;             // distinct source rows edited (== nS)
   int rankB, rankC;      // pivots kept by the residual Cholesky factors
   int pending;           // rows queued for the next push (signal or graph changed)
-  int check_all;         // next push starts from every node
+  int check_all;         // next push starts from every node (set by the fold)
+  int n_nodes;           // node count after the most recent update (the push's row range)
   unsigned int epoch;    // stamp generation for push dedupe
   long long tail_out, tail_in;   // adjacency bump allocators
   // counters (damf_stats)
@@ -135,7 +136,14 @@ struct Ctx {
   float *PU, *PV, *PUi, *PVi, *sigma, *s0;
   Adj out, in;
   Workspace ws;
-  int push_blocks;       // persistent push grid size
+  long long m_init;      // adjacency entries of the initial graph (a size hint for shares)
+  int push_blocks;       // requested persistent push grid size (0: push_max)
+  int push_max;          // co-resident push CTAs on the device, at most two per SM (0: not yet known)
+  int push_direct_chunks;  // in-edge chunks a row task scatters itself (-1: default)
+  // damf_step_multi runs this graph's update on its own stream, forked from the caller's
+  cudaStream_t own_stream;
+  cudaEvent_t ev_fork;    // caller-stream point the graph's work follows
+  cudaEvent_t ev_done;    // the graph's update and push, joined on own_stream
   int updates_since_fold;
   int32_t* host_stage;   // pinned staging for damf_apply_edges_host
   int32_t* dev_stage;    // device copy of staged events
@@ -206,16 +214,40 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigne
 
 // ---- launchers implemented in the .cu files ----
 cudaError_t launch_edit(Ctx* c, cudaStream_t s);
-cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
-                            cudaStream_t s);
-cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
-                           cudaStream_t s);
+// k events, or (kdev != NULL) the first *kdev of them clamped to [0, k]; the update starting
+// at event lo takes events lo .. lo + k - 1 of the arrays, of which *kdev - lo are live
+cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
+                            const int32_t* kdev, int n_after, cudaStream_t s);
+cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
+                           const int32_t* kdev, int lo, cudaStream_t s);
 cudaError_t launch_fixup(Ctx* c, cudaStream_t s);
 cudaError_t launch_gather(Ctx* c, cudaStream_t s);
 cudaError_t launch_chol(Ctx* c, cudaStream_t s);
 cudaError_t launch_core(Ctx* c, cudaStream_t s);
 cudaError_t launch_transforms(Ctx* c, cudaStream_t s);
 cudaError_t launch_scatter(Ctx* c, cudaStream_t s);
+int push_default_direct_chunks();
+// One graph's push operands (the grouped push reads them from device memory).
+struct PushArgs {
+  DevHeader* h;
+  Adj in;                  // in-adjacency (the out-adjacency of an undirected graph)
+  const int32_t* outdeg;
+  Workspace ws;
+  float* Zb;
+  float* r;
+  float alpha, eps;
+  int max_phases;
+  int direct_max;          // in-edges a row task scatters itself
+  int d;
+  int pad;
+};
+PushArgs push_args(const Ctx* c, int direct_chunks);
+int push_group_max_blocks(int scaled);
+// Grouped push of descs[0 .. ngraphs): table holds sfirst[nslots + 1] (CTA prefix sums, ending at
+// `blocks`) then gfirst[nslots + 1] (graph prefix sums, ending at ngraphs); a slot of several
+// graphs has one CTA.
+cudaError_t launch_push_group(const PushArgs* descs, int ngraphs, const int* table, int nslots, int blocks,
+                              int scaled, cudaStream_t s);
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s);
 cudaError_t launch_expand_row(Ctx* c, int u, int cnt, int incoming, int32_t* src, int32_t* dst, int8_t* op,
                               cudaStream_t s);

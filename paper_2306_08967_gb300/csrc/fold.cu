@@ -143,7 +143,10 @@ __global__ void k_fold_finish(const float* TU, float* TX, float* s0, float* sigm
     sigma[k] = theta[k];
     s0[k] = sqrtf(fmaxf(theta[k], 0.f));
   }
-  if (threadIdx.x == 0) h->folds += 1;
+  if (threadIdx.x == 0) {
+    h->folds += 1;
+    h->check_all = 1;   // the next push seeds every row (the base changed under all of them)
+  }
 }
 
 cudaError_t jacobi_svd_dense(const float* Min, int m, int d, float* E, float* H, float* theta, float* work_M,

@@ -17,9 +17,18 @@
 
 namespace damf {
 
-__global__ void k_validate(DevHeader* h, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
-                           int n_after) {
+// Events in use: k, or *kdev clamped to [0, k] when the count lives on the device.
+__device__ __forceinline__ int live_events(int k, const int32_t* kdev, int lo) {
+  if (!kdev) return k;
+  const int kd = *kdev - lo;
+  return kd < 0 ? 0 : (kd < k ? kd : k);
+}
+
+__global__ void k_validate(DevHeader* h, const int32_t* src, const int32_t* dst, const int8_t* op, int kmax,
+                           const int32_t* kdev, int n_after) {
+  const int k = live_events(kmax, kdev, 0);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) h->n_nodes = n_after;
   if (i >= k) return;
   int u = src[i], v = dst[i], o = op[i];
   bool bad = u < 0 || v < 0 || u >= n_after || v >= n_after || u == v || (o != 1 && o != -1);
@@ -27,10 +36,10 @@ __global__ void k_validate(DevHeader* h, const int32_t* src, const int32_t* dst,
   if (i == 0) atomicAdd((unsigned long long*)&h->edges_applied, (unsigned long long)k);
 }
 
-cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int n_after,
-                            cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
-  k_validate<<<(k + 255) / 256, 256, 0, s>>>(c->hdr, src, dst, op, k, n_after);
+cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
+                            const int32_t* kdev, int n_after, cudaStream_t s) {
+  // launched for every call: it also records the node count the push works over
+  k_validate<<<k > 0 ? (k + 255) / 256 : 1, 256, 0, s>>>(c->hdr, src, dst, op, k, kdev, n_after);
   return cudaGetLastError();
 }
 
@@ -98,7 +107,9 @@ __device__ void apply_row_edits(Adj a, const int* rows, int nrows, const int* fi
 
 template <int DIRECTED>
 __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, Workspace ws, const int32_t* src,
-                                                 const int32_t* dst, const int8_t* op, int k) {
+                                                 const int32_t* dst, const int8_t* op, int kmax,
+                                                 const int32_t* kdev, int lo) {
+  const int k = live_events(kmax, kdev, lo);
   __shared__ unsigned long long key[kMaxEntries];
   __shared__ int evt[kMaxEntries];
   __shared__ int eop[kMaxEntries];
@@ -327,12 +338,12 @@ cudaError_t launch_edit(Ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k, int,
-                           cudaStream_t s) {
+cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const int8_t* op, int k,
+                           const int32_t* kdev, int lo, cudaStream_t s) {
   if (c->cfg.directed)
-    k_prepare<1><<<1, 512, 0, s>>>(c->hdr, c->out, c->in, c->ws, src, dst, op, k);
+    k_prepare<1><<<1, 512, 0, s>>>(c->hdr, c->out, c->in, c->ws, src + lo, dst + lo, op + lo, k, kdev, lo);
   else
-    k_prepare<0><<<1, 512, 0, s>>>(c->hdr, c->out, c->out, c->ws, src, dst, op, k);
+    k_prepare<0><<<1, 512, 0, s>>>(c->hdr, c->out, c->out, c->ws, src + lo, dst + lo, op + lo, k, kdev, lo);
   return cudaGetLastError();
 }
 

@@ -28,18 +28,18 @@
 // The queue does not wrap within a phase. When it is full, rows stay flagged and unqueued and
 // the overflow flag is set; after the phase every row is cleared and checked again.
 // Every wait is bounded (kSpinLimit with __nanosleep; DAMF_ERR_TIMEOUT).
-#include <stdlib.h>
+#include <string.h>
 
 #include "damf_internal.cuh"
 
 namespace damf {
 
-// CTAs of the push per SM: leaves registers, threads and shared memory on every SM for
-// the one-CTA kernels of the next update's factor chain (overridable for tuning with the
-// environment variable DAMF_PUSH_CTAS_PER_SM).
+// CTAs of the push per SM at most: leaves registers, threads and shared memory on every SM
+// for the one-CTA kernels of the next update's factor chain. A context's grid is this many
+// per SM unless damf_set_tuning asks for fewer (graphs that share the GPU).
 constexpr int kPushBlocksPerSM = 2;
 // A row with more than this many chunks of in-edges is a hub: its chunks become item tasks
-// (overridable with DAMF_PUSH_DIRECT_CHUNKS).
+// (per context: damf_set_tuning).
 constexpr int kPushDirectChunks = 8;
 // in-edges per hub item: small items spread a hub over many warps (measured: 8 beats 32)
 constexpr int kItemEdges = 8;
@@ -286,19 +286,26 @@ __device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long
   }
 }
 
-// 64 registers at most (min. 4 CTAs' worth per SM): two push CTAs (32k registers) then leave room
-// on every SM for the 768-thread core SVD CTA of the next update, which runs beside the push
+// The push of one graph by `nblocks` CTAs of 256 threads (this one is CTA `blk` of them): the
+// whole launch for one graph (k_push), or one graph's share of a launch over many (k_push_group).
+// s_t (5 words) and s_buf (8 warps x kQBuf) are the CTA's shared timers and warp queue buffers.
 template <int D, bool SCALED>
-__global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int32_t* __restrict__ outdeg, Workspace ws,
-                                                 float* Zb, float* r, int n, float alpha, float eps, int max_phases,
-                                                 int check_all, int direct_max) {
+__device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_all, unsigned blk, unsigned nblocks,
+                                          unsigned long long* s_t, int32_t (*s_buf)[kQBuf]) {
+  DevHeader* const h = a.h;
+  const Adj in = a.in;
+  const int32_t* __restrict__ outdeg = a.outdeg;
+  const Workspace& ws = a.ws;
+  float* const Zb = a.Zb;
+  float* const r = a.r;
+  const float alpha = a.alpha, eps = a.eps;
+  const int max_phases = a.max_phases, direct_max = a.direct_max;
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
-  const unsigned nblocks = gridDim.x;
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR, q = lane % LPR;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long gwarp = ((long long)blk * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)nblocks * blockDim.x) >> 5;
   const unsigned epoch0 = h->epoch;
   const float beta = 1.0f - alpha;
   const long long qcap = ws.qcap;
@@ -310,18 +317,16 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   const int npend = h->pending;
   // block 0's view of where the time goes (ns): seeding, task loop, barriers; [4] is the last
   // mark. Kept in shared memory, where it costs no registers.
-  __shared__ unsigned long long s_t[5];
-  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool timer = blk == 0 && threadIdx.x == 0;
   if (timer) {
     s_t[0] = s_t[1] = s_t[2] = s_t[3] = 0ull;
     s_t[4] = gtimer();
   }
-  __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
   WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0, ws.ovf, ws.stamp};
   int phase = 0;
   for (;; ++phase) {
     if (phase >= max_phases) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, DAMF_ERR_NOT_CONVERGED);
+      if (blk == 0 && threadIdx.x == 0) set_status(h, DAMF_ERR_NOT_CONVERGED);
       break;
     }
     // ---- seeding: the rows whose residual changed (or every row), when above eps ----
@@ -505,10 +510,10 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
                                  false);
       }
     }
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
+    for (long long u = (long long)blk * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
       inq[u] = 0u;
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // everyone has read the overflow flag
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blk == 0 && threadIdx.x == 0) {
       h->qstate = 0ull;
       h->q_head = 0;
       h->overflow = 0;
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
     atomicAdd((unsigned long long*)&h->push_tasks, (unsigned long long)my_rows);
     atomicAdd((unsigned long long*)&h->push_items, (unsigned long long)my_items);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blk == 0 && threadIdx.x == 0) {
     h->push_rounds += phase;
     h->pending = 0;
     h->check_all = 0;
@@ -543,45 +548,152 @@ __global__ void __launch_bounds__(256, 4) k_push(DevHeader* h, Adj in, const int
   }
 }
 
+// 64 registers at most (min. 4 CTAs' worth per SM): two push CTAs (32k registers) then leave room
+// on every SM for the 768-thread core SVD CTA of the next update, which runs beside the push
+template <int D, bool SCALED>
+__global__ void __launch_bounds__(256, 4) k_push(PushArgs a, int n, int check_all) {
+  __shared__ unsigned long long s_t[5];
+  __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
+  push_body<D, SCALED>(a, n, check_all, blockIdx.x, gridDim.x, s_t, s_buf);
+}
+
+// Zeroes the work-queue words of every graph of a grouped push (one thread per graph).
+__global__ void k_push_reset(const PushArgs* __restrict__ descs, int count) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  DevHeader* h = descs[g].h;
+  h->qstate = 0ull;
+  h->q_head = 0;
+  h->overflow = 0;
+  h->rho_tail = 0;
+  h->item_tail = 0;
+  h->ovf_count = 0;
+}
+
+// The pushes of many graphs in one cooperative launch, in slots: slot s owns CTAs
+// sfirst[s] .. sfirst[s+1]-1 and graphs gfirst[s] .. gfirst[s+1]-1 of descs. A slot of one graph
+// runs that graph's push over its CTAs (its own queue, header and grid barrier among them); a
+// slot of several graphs has one CTA, which pushes them one after another. The rank d of each
+// graph selects the row shape; node count and full seeding come from the graph's device header,
+// so one captured launch serves every step.
+template <bool SCALED>
+__global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restrict__ descs,
+                                                       const int* __restrict__ sfirst,
+                                                       const int* __restrict__ gfirst, int nslots) {
+  __shared__ PushArgs sa;
+  __shared__ int s_s, s_n, s_all;
+  __shared__ unsigned long long s_t[5];
+  __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nslots - 1;   // the last slot with sfirst[s] <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sfirst[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_s = lo;
+  }
+  __syncthreads();
+  const int slot = s_s;
+  const unsigned blk = blockIdx.x - (unsigned)sfirst[slot];
+  const unsigned nb = (unsigned)(sfirst[slot + 1] - sfirst[slot]);
+  const int g1 = gfirst[slot + 1];
+  for (int g = gfirst[slot]; g < g1; ++g) {
+    __syncthreads();   // the previous graph's push no longer reads sa
+    {
+      const int* src = reinterpret_cast<const int*>(descs + g);
+      int* dst = reinterpret_cast<int*>(&sa);
+      for (int i = threadIdx.x; i < (int)(sizeof(PushArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_n = *reinterpret_cast<volatile int*>(&sa.h->n_nodes);
+      s_all = *reinterpret_cast<volatile int*>(&sa.h->check_all);
+    }
+    __syncthreads();
+    switch (sa.d) {
+      case 16: push_body<16, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
+      case 32: push_body<32, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
+      case 64: push_body<64, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
+      default: push_body<128, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
+    }
+  }
+}
+
+PushArgs push_args(const Ctx* c, int direct_chunks) {
+  PushArgs a;
+  memset(&a, 0, sizeof(a));
+  a.h = c->hdr;
+  a.in = c->cfg.directed ? c->in : c->out;
+  a.outdeg = c->out.len;
+  a.ws = c->ws;
+  a.Zb = c->Zb;
+  a.r = c->r;
+  a.alpha = (float)c->cfg.alpha;
+  a.eps = (float)c->cfg.eps;
+  a.max_phases = c->cfg.max_push_rounds;
+  a.d = c->d;
+  const int epc = c->d == 128 ? PushShape<128>::EPC : c->d == 64 ? PushShape<64>::EPC
+                : c->d == 32 ? PushShape<32>::EPC : PushShape<16>::EPC;
+  a.direct_max = (direct_chunks >= 0 ? direct_chunks : kPushDirectChunks) * epc;
+  return a;
+}
+
+// co-resident CTAs of the grouped push on the current device: a fleet's push runs after every
+// update of its step, so it may take the whole occupancy (not only two CTAs per SM)
+template <bool SCALED>
+static int group_max_blocks() {
+  static int cached = 0;
+  if (cached == 0) {
+    cudaFuncSetAttribute(k_push_group<SCALED>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_group<SCALED>, 256, 0);
+    cached = sms * (per_sm < 1 ? 1 : per_sm);
+  }
+  return cached;
+}
+
+int push_group_max_blocks(int scaled) { return scaled ? group_max_blocks<true>() : group_max_blocks<false>(); }
+
+cudaError_t launch_push_group(const PushArgs* descs, int ngraphs, const int* table, int nslots, int blocks,
+                              int scaled, cudaStream_t s) {
+  if (ngraphs <= 0 || nslots <= 0) return cudaSuccess;
+  k_push_reset<<<(ngraphs + 255) / 256, 256, 0, s>>>(descs, ngraphs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int* sfirst = table;
+  const int* gfirst = table + nslots + 1;
+  void* args[] = {(void*)&descs, (void*)&sfirst, (void*)&gfirst, &nslots};
+  return scaled ? cudaLaunchCooperativeKernel((void*)k_push_group<true>, dim3(blocks), dim3(256), args, 0, s)
+                : cudaLaunchCooperativeKernel((void*)k_push_group<false>, dim3(blocks), dim3(256), args, 0, s);
+}
+
 template <int D, bool SCALED>
 static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
-  if (c->push_blocks == 0) {
-    // two CTAs per SM: leaves registers, threads and shared memory on every SM for the
-    // one-CTA kernels of the next update's factor chain, which overlap the push
+  if (c->push_max == 0) {
     cudaFuncSetAttribute(k_push<D, SCALED>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D, SCALED>, 256, 0);
-    int cap = kPushBlocksPerSM;
-    if (const char* ev = getenv("DAMF_PUSH_CTAS_PER_SM")) {
-      const int v = atoi(ev);
-      if (v >= 1 && v <= 8) cap = v;
-    }
-    if (per_sm > cap) per_sm = cap;
-    c->push_blocks = sms * (per_sm < 1 ? 1 : per_sm);
+    if (per_sm > kPushBlocksPerSM) per_sm = kPushBlocksPerSM;
+    c->push_max = sms * (per_sm < 1 ? 1 : per_sm);
   }
-  int chunks = kPushDirectChunks;
-  if (const char* ev = getenv("DAMF_PUSH_DIRECT_CHUNKS")) {
-    const int v = atoi(ev);
-    if (v >= 0 && v <= 1024) chunks = v;
-  }
+  // a cooperative grid must fit on the device at once
+  const int blocks = (c->push_blocks > 0 && c->push_blocks < c->push_max) ? c->push_blocks : c->push_max;
+  const int chunks = c->push_direct_chunks;
   // qstate, q_head, overflow, rho_tail, item_tail, ovf_count
   cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 5 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  DevHeader* h = c->hdr;
-  Adj in = c->cfg.directed ? c->in : c->out;
-  const int32_t* outdeg = c->out.len;
-  Workspace ws = c->ws;
-  float* Zb = c->Zb;
-  float* r = c->r;
+  PushArgs a = push_args(c, chunks);
   int n = c->n;
-  float alpha = (float)c->cfg.alpha, eps = (float)c->cfg.eps;
-  int max_phases = c->cfg.max_push_rounds;
-  int direct_max = chunks * PushShape<D>::EPC;
-  void* args[] = {&h, &in, &outdeg, &ws, &Zb, &r, &n, &alpha, &eps, &max_phases, &check_all, &direct_max};
-  return cudaLaunchCooperativeKernel((void*)k_push<D, SCALED>, dim3(c->push_blocks), dim3(256), args, 0, s);
+  check_all = check_all ? 1 : 0;
+  void* args[] = {&a, &n, &check_all};
+  return cudaLaunchCooperativeKernel((void*)k_push<D, SCALED>, dim3(blocks), dim3(256), args, 0, s);
 }
 
 template <bool SCALED>
@@ -593,6 +705,8 @@ static cudaError_t push_dispatch(Ctx* c, int check_all, cudaStream_t s) {
     default: return push_impl<128, SCALED>(c, check_all, s);
   }
 }
+
+int push_default_direct_chunks() { return kPushDirectChunks; }
 
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s) {
   return c->cfg.threshold ? push_dispatch<true>(c, check_all, s) : push_dispatch<false>(c, check_all, s);

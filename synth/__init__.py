@@ -18,4 +18,4 @@ from .chung_lu import (  # noqa: F401
     csr_from_edges,
     node_arrival_stream,
 )
-from .configs import CONFIGS, small_config  # noqa: F401
+from .configs import CONFIGS, FLEETS, FleetWorkload, fleet_inputs, member_inputs, small_config  # noqa: F401

@@ -41,12 +41,23 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray):
     rows sorted by column."""
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
-    order = np.lexsort((dst, src))
+    order = np.argsort(src * max(n, 1) + dst, kind="stable")   # by (src, dst), as a lexicographic sort
     src, dst = src[order], dst[order]
     counts = np.bincount(src, minlength=n)
     indptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=indptr[1:])
     return indptr.astype(np.int32), dst.astype(np.int32)
+
+
+def _sorted_unique(key: np.ndarray) -> np.ndarray:
+    """The distinct values of key in increasing order (np.unique's result, by one sort)."""
+    key = np.sort(key)
+    if key.shape[0] == 0:
+        return key
+    keep = np.empty(key.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    return key[keep]
 
 
 def chung_lu_graph(n: int, avg_deg: float, gamma: float, seed: int, directed: bool = False):
@@ -67,12 +78,12 @@ def chung_lu_graph(n: int, avg_deg: float, gamma: float, seed: int, directed: bo
     u, v = u[keep], v[keep]
     if not directed:
         a, b = np.minimum(u, v), np.maximum(u, v)
-        key = np.unique(a.astype(np.int64) * n + b)
+        key = _sorted_unique(a.astype(np.int64) * n + b)
         a, b = key // n, key % n
         src = np.concatenate([a, b])
         dst = np.concatenate([b, a])
     else:
-        key = np.unique(u.astype(np.int64) * n + v)
+        key = _sorted_unique(u.astype(np.int64) * n + v)
         src, dst = key // n, key % n
     indptr, indices = csr_from_edges(n, src, dst)
     return indptr, indices, w_by_id

@@ -9,9 +9,17 @@ C3  large graph: undirected Chung-Lu, gamma 2.1, n = 2,000,000, m = 40M edges (m
     40), d = 128; 50,000 batches of U[1, 256] edges (up to four updates per call), node
     arrivals and deletions as in C2 (the workload states neither; C2's rates are used), alpha
     and eps as in C2, the fold every 256 updates.
+C4  many graphs: 256 undirected Chung-Lu graphs, n log-uniform in [1,000, 500,000], mean
+    degree uniform in [4, 32], d drawn from {32, 64, 128}; one batch of U[1, 128] edge events
+    per graph per step. The workload names no node arrivals, deletion rate, gamma, alpha or
+    eps: 10% deletions, no arrivals (so the step replays as one captured launch), and C2's
+    gamma, alpha and eps are used.
 """
 
 import dataclasses
+import math
+
+import numpy as np
 
 SEED_BASE = 0xDA3F0000
 
@@ -54,3 +62,68 @@ CONFIGS = {
 
 def small_config(name: str = "C1", **over) -> Workload:
     return dataclasses.replace(CONFIGS[name], **over)
+
+
+@dataclasses.dataclass(frozen=True)
+class FleetWorkload:
+    """Many independent graphs stepped together (one batch per graph per step)."""
+    name: str
+    graphs: int
+    n_lo: int
+    n_hi: int
+    deg_lo: float
+    deg_hi: float
+    ds: tuple
+    gamma: float
+    alpha: float
+    eps: float
+    k_lo: int
+    k_hi: int
+    p_del: float
+    seed: int
+
+    def members(self) -> list:
+        """The graphs as Workloads: n log-uniform in [n_lo, n_hi], mean degree uniform in
+        [deg_lo, deg_hi], d uniform over ds; each graph's own seed."""
+        rng = np.random.Generator(np.random.PCG64(self.seed))
+        out = []
+        for i in range(self.graphs):
+            n = int(round(math.exp(rng.uniform(math.log(self.n_lo), math.log(self.n_hi)))))
+            deg = float(rng.uniform(self.deg_lo, self.deg_hi))
+            d = int(self.ds[int(rng.integers(0, len(self.ds)))])
+            out.append(Workload("%s.%d" % (self.name, i), n=n, avg_deg=deg, gamma=self.gamma, d=d, alpha=self.alpha,
+                                eps=self.eps, n_batches=0, k_lo=self.k_lo, k_hi=self.k_hi, p_node=0.0,
+                                p_del=self.p_del, nodes_per_batch=0, seed=self.seed + 7919 * (i + 1)))
+        return out
+
+
+FLEETS = {
+    "C4": FleetWorkload("C4", graphs=256, n_lo=1000, n_hi=500_000, deg_lo=4.0, deg_hi=32.0, ds=(32, 64, 128),
+                        gamma=2.2, alpha=0.15, eps=1e-5, k_lo=1, k_hi=128, p_del=0.10, seed=SEED_BASE + 3),
+}
+
+
+def member_inputs(c: Workload, n_batches: int):
+    """One graph's inputs: (indptr, indices, EdgeStream of n_batches batches)."""
+    from .chung_lu import chung_lu_graph, edge_stream
+    ip, ix, w = chung_lu_graph(c.n, c.avg_deg, c.gamma, seed=c.seed, directed=c.directed)
+    st = edge_stream(ip, ix, w, n_batches, c.k_lo, c.k_hi, c.p_node, c.p_del, c.seed + 1,
+                     max_new_degree=c.max_new_degree, directed=c.directed, nodes_per_batch=c.nodes_per_batch)
+    return ip, ix, st
+
+
+def fleet_inputs(members, n_batches: int, workers: int = 0):
+    """member_inputs for every graph, in a pool of `workers` spawned processes (0: the host's
+    cores, at most 16; 1: in this process). Spawned, so that it is safe in a process that
+    already uses a GPU. Returns [(workload, indptr, indices, stream)] in member order."""
+    import os
+    members = list(members)
+    if workers <= 0:
+        workers = min(16, os.cpu_count() or 1, len(members))
+    if workers <= 1:
+        return [(c, *member_inputs(c, n_batches)) for c in members]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(member_inputs, members, [n_batches] * len(members), chunksize=1))
+    return [(c, *r) for c, r in zip(members, res)]
