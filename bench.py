@@ -504,7 +504,8 @@ def run_fleet(args, fw, rank, world):
     if rank > 0:   # replicas: every rank its own fleet of the same shape
         members = [dataclasses.replace(c, seed=c.seed + 1000 * rank) for c in members]
     K, W, E, S, T = args.steps, args.warmup, args.e2e_steps, args.compare_steps, args.tune_steps
-    n_cand = len(DEFAULT_EXPONENTS) + len(DEFAULT_DIRECT_CHUNKS)
+    rebalance_rounds = 3
+    n_cand = len(DEFAULT_EXPONENTS) + len(DEFAULT_DIRECT_CHUNKS) + 1 + rebalance_rounds
     # warm-up, tuning (T per candidate), the three comparison forms, one untimed replay, timed, e2e,
     # phase-timed direct steps
     n_steps = W + T * n_cand + 3 * S + 1 + K + E + S
@@ -647,8 +648,19 @@ def run_fleet(args, fw, rank, world):
         run_captured(cg, 1)
         return run_captured(cg, T - 1)
 
+    last = {"ns": None, "pos": 0}
+
+    def push_times():   # each graph's push time per step (ns, its own global timer) since the last call
+        cur = np.array([float(sum(g.stats()["push_ns"][:3])) for g in graphs])
+        prev, p0 = last["ns"], last["pos"]
+        last["ns"], last["pos"] = cur, pos[0]
+        if prev is None:
+            return [1.0] * G
+        return list((cur - prev) / max(pos[0] - p0, 1))
+
     t0 = time.perf_counter()
-    tune = tune_shares(fleet, graphs, measure) if T >= 2 else None
+    tune = tune_shares(fleet, graphs, measure, push_times=push_times,
+                       rebalance_rounds=rebalance_rounds) if T >= 2 else None
     tune_s = time.perf_counter() - t0
     cg = capture()
     run_captured(cg, 1)
@@ -814,10 +826,21 @@ def main():
     ap.add_argument("--graphs", type=int, default=0, help="C4: the first this many graphs of the fleet (0: all)")
     ap.add_argument("--compare-steps", type=int, default=5, help="C4: steps of each comparison launch form")
     ap.add_argument("--tune-steps", type=int, default=3, help="C4: steps per autotuner candidate (< 2: no tuning)")
+    ap.add_argument("--rates", default="25,100,400", help="C5: request rates (req/s) of the phases")
+    ap.add_argument("--phase-seconds", type=float, default=10.0, help="C5: seconds per rate phase")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="C5: HBM budget (0: the big graph and 3/4 of "
+                    "the small sessions)")
+    ap.add_argument("--pool", type=int, default=48, help="C5: distinct small graphs generated")
+    ap.add_argument("--drain-seconds", type=float, default=60.0, help="C5: wall time allowed after the last phase")
+    ap.add_argument("--share-exponent", type=float, default=0.5, help="C5: push CTAs ~ (d (n + m))^exponent")
     ap.add_argument("--mode", default="batches", choices=["batches", "node-stream"],
                     help="node-stream: ms per node event under the paper's node-arrival protocol")
     args = ap.parse_args()
-    from synth import CONFIGS, FLEETS
+    from synth import CONFIGS, FLEETS, SERVING
+    if args.config in SERVING:
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+        print(json.dumps(run_serving(args, SERVING[args.config])))
+        return
     if "." in args.config:     # one member graph of a fleet, e.g. C4.17 (the oracle's sample)
         base, idx = args.config.split(".", 1)
         c = FLEETS[base].members()[int(idx)]
@@ -896,6 +919,176 @@ def main():
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def serving_inputs(sw, n_pool, big_batches, small_batches):
+    """The big graph and a pool of small graphs, each with its request stream (log-uniform sizes),
+    generated in spawned processes before the first GPU call."""
+    from synth import fleet_inputs
+    small = fleet_inputs([sw.small(i) for i in range(n_pool)], small_batches, log_sizes=True)
+    big = fleet_inputs([sw.big()], big_batches, workers=1, log_sizes=True)[0]
+    return big, small
+
+
+def run_serving(args, sw):
+    """Continuous batching of update requests over a changing set of resident graphs: a Poisson
+    request stream in phases of rising rate, sessions admitted by device memory, one fleet step
+    per server turn with at most one request per graph. Latency per request: arrival (host
+    clock) to the host seeing its step complete."""
+    import torch
+    from paper_2306_08967_gb300 import bytes_required, make_config, rsvd_width
+    from paper_2306_08967_gb300.serving import Server
+    from synth import gaussian_test_matrix
+
+    rates = [float(x) for x in args.rates.split(",")]
+    dur = float(args.phase_seconds)
+    R = sw.requests_per_session
+    total_req = int(sum(rates) * dur * 1.3) + 64
+    n_pool = sw.open_small + int(total_req / R) + 8
+    n_pool = min(n_pool, args.pool)
+    t0 = time.perf_counter()
+    big, pool = serving_inputs(sw, n_pool, max(64, total_req // (sw.open_small + 1) * 3), R)
+    gen_s = time.perf_counter() - t0
+    print("[serving] inputs generated in %.1f s" % gen_s, file=sys.stderr, flush=True)
+    torch.cuda.set_device(0)
+
+    def spec(c, ip, ix):
+        cfg = make_config(c.n, c.d, c.alpha, c.eps, nnz=len(ix), directed=True)
+        return ip, ix, cfg, gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
+
+    need_big = bytes_required(spec(big[0], big[1], big[2])[2])
+    need_small = [bytes_required(make_config(c.n, c.d, c.alpha, c.eps, nnz=len(ix), directed=True))
+                  for c, ip, ix, _ in pool]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(args.budget_gb * 1e9) if args.budget_gb else int(need_big + 0.75 * sum(need_small[:sw.open_small]))
+    budget = min(budget, int(free * 0.9))
+    srv = Server(budget, max_events=sw.k_hi, run_ahead=2, share_exponent=args.share_exponent)
+    # sessions: the big graph for the whole run, small ones each for R requests, then replaced
+    srv.open(0, *spec(big[0], big[1], big[2]))
+    nxt_pool = 0
+    open_small = {}          # sid -> (pool index, requests submitted)
+    sid_next = 1
+
+    def open_one():
+        nonlocal nxt_pool, sid_next
+        c, ip, ix, _ = pool[nxt_pool % len(pool)]
+        srv.open(sid_next, *spec(c, ip, ix))
+        open_small[sid_next] = [nxt_pool % len(pool), 0]
+        nxt_pool += 1
+        sid_next += 1
+
+    for _ in range(sw.open_small):
+        open_one()
+    t_init = time.perf_counter()
+    srv.poll()                              # the first admissions (graph initialisations)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t_init
+    print("[serving] %d graphs initialised in %.1f s" % (len(srv.graphs), init_s), file=sys.stderr, flush=True)
+    big_pos = 0
+    rng = np.random.default_rng(sw.seed + 99)
+    arrivals = []
+    t_off = 0.0
+    for ph, lam in enumerate(rates):
+        a = sw.arrivals(lam, dur, sw.seed + 1000 + ph) + t_off
+        arrivals += [(t, ph) for t in a]
+        t_off += dur
+    def progress(tag):
+        print("[serving] %s t=%.1fs submitted=%d done=%d steps=%d inflight=%d resident=%d waiting=%d "
+              "backlog=%d used=%.1fGB" % (tag, srv.now(), i, len(srv.completed), srv.steps_issued, len(srv.inflight),
+                                         len(srv.sched.resident()), len(srv.sched.waiting), srv.sched.backlog(),
+                                         srv.sched.used / 1e9), file=sys.stderr, flush=True)
+
+    srv.t0 = time.perf_counter()           # the arrival clock starts now
+    reqs = []
+    i = 0
+    used_max = 0
+    t_report = 0.0
+    wall_limit = len(rates) * dur + args.drain_seconds
+    with ClockSampler(0) as clk:
+        while i < len(arrivals) and srv.now() < wall_limit:
+            now = srv.now()
+            if now - t_report > 5.0:
+                progress("run")
+                t_report = now
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                t_arr, ph = arrivals[i]
+                choice = int(rng.integers(0, len(open_small) + 1))
+                if choice == 0:
+                    src, dst, op = (big[3].batches[big_pos % len(big[3].batches)].src,
+                                    big[3].batches[big_pos % len(big[3].batches)].dst,
+                                    big[3].batches[big_pos % len(big[3].batches)].op)
+                    big_pos += 1
+                    sid = 0
+                else:
+                    sid = sorted(open_small)[choice - 1]
+                    pi, cnt = open_small[sid]
+                    b = pool[pi][3].batches[cnt]
+                    src, dst, op = b.src, b.dst, b.op
+                    open_small[sid][1] += 1
+                r = srv.submit(i, sid, src, dst, op, t_arrive=t_arr)
+                reqs.append((r, ph))
+                if sid != 0 and open_small[sid][1] == R:   # its last request: close, open the next
+                    srv.close(sid)
+                    del open_small[sid]
+                    open_one()
+                i += 1
+            srv.poll()
+            used_max = max(used_max, srv.sched.used)
+            if i < len(arrivals) and not srv.inflight:
+                time.sleep(max(0.0, min(arrivals[i][0] - srv.now(), 0.002)))
+        progress("arrivals over")
+        for sid in list(open_small) + [0]:   # every session ends with the trace
+            srv.close(sid)
+        drained = srv.drain(max(10.0, wall_limit - srv.now()))
+        progress("drained" if drained else "drain cut short")
+    t_end = srv.now()
+    reqs = [(r, p) for r, p in reqs if r.t_done is not None]
+    for g in list(srv.graphs.values()):
+        g.check()
+    phases = []
+    for ph, lam in enumerate(rates):
+        rs = [r for r, p in reqs if p == ph]
+        lat = np.array([r.t_done - r.t_arrive for r in rs]) * 1e3
+        edges = sum(r.k for r in rs)
+        last = max(r.t_done for r in rs) if rs else ph * dur
+        phases.append({"rate_req_s": lam, "requests": len(rs), "edges": int(edges),
+                       "edge_updates_s": edges / max(last - ph * dur, 1e-9),
+                       "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                      "mean": float(lat.mean())} if len(rs) else None})
+    sess = srv.sched.sessions.values()
+    waits = np.array([(s.t_admit - s.t_open) for s in sess if s.t_admit is not None and s.sid != 0])
+    steps = srv.steps_issued
+    served = sum(r.k for r, _ in reqs)
+    out = {
+        "metric": METRIC, "value": served / max(t_end, 1e-9), "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": 0, "ms_per_step": 1e3 * t_end / max(steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded directed Chung-Lu graphs, Poisson request arrivals)",
+        "config": {"workload": "%s at a tenth of the stated node counts: a directed graph of n = %d (m = %d) for "
+                               "the whole run and %d open sessions of directed graphs of n log-U[%d, %d] "
+                               "(each closes after %d requests and a new one opens); d = %d, alpha %g, eps %g; "
+                               "requests of log-U[%d, %d] edge events, Poisson arrivals in phases of %s req/s, "
+                               "%g s each" % (sw.name, sw.big_n, len(big[2]), sw.open_small, sw.small_lo,
+                                              sw.small_hi, R, sw.d, sw.alpha, sw.eps, sw.k_lo, sw.k_hi,
+                                              args.rates, dur),
+                   "budget_gb": budget / 1e9, "used_max_gb": used_max / 1e9,
+                   "big_graph_gb": need_big / 1e9, "launch": "one fleet step per server turn (every resident "
+                   "graph, at most one request each; graphs' updates overlapped, one grouped push)",
+                   "parallelism": "single GPU"},
+        "value_definition": "all served edge events / (last completion - first arrival), over every phase",
+        "phases": phases,
+        "e2e": {"value": served / max(t_end, 1e-9), "unit": UNIT,
+                "h2d_bytes_per_step": 9 * served / max(steps, 1), "d2h_bytes_per_step": 0,
+                "note": "every request goes host -> device (pinned staging, one copy per step); completion is "
+                        "observed on the host through an event"},
+        "sessions": {"opened": len(srv.sched.sessions), "admission_wait_s": {
+            "p50": float(np.percentile(waits, 50)) if len(waits) else None,
+            "p99": float(np.percentile(waits, 99)) if len(waits) else None}},
+        "gpu_launches": None,
+        "init_s": init_s, "generate_s": gen_s, "clocks": clk.summary(),
+    }
+    srv.shutdown()
+    return out
 
 
 def main_fleet(args, fw):

@@ -203,6 +203,12 @@ damf_status damf_fleet_step(damf_fleet* fleet, const damf_batch* batches, void* 
  * capture is in progress.  DAMF_ERR_INVALID (shares unchanged) for bad values. */
 damf_status damf_fleet_set_shares(damf_fleet* fleet, const int32_t* blocks, double exponent);
 
+/* Sets the shares from per-graph work estimates (host double[count], each > 0, e.g. a
+ * graph's measured push time times its CTAs): CTAs in proportion to the weights, graphs below
+ * one CTA's worth packed as with damf_fleet_set_shares.  Synchronous; not while capturing.
+ * DAMF_ERR_INVALID (shares unchanged) for a weight that is not > 0. */
+damf_status damf_fleet_set_weights(damf_fleet* fleet, const double* weights);
+
 /* Phase timing of the following (uncaptured) fleet steps: when enabled, each step records
  * events at its fork, after every graph's update and after the pushes. */
 damf_status damf_fleet_set_timing(damf_fleet* fleet, int32_t enable);

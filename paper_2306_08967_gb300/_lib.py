@@ -51,6 +51,7 @@ SIGNATURES = {
     "damf_fleet_create": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
     "damf_fleet_step": (c_i32, [c_vp, c_vp, c_vp]),
     "damf_fleet_set_shares": (c_i32, [c_vp, c_vp, c_f64]),
+    "damf_fleet_set_weights": (c_i32, [c_vp, c_vp]),
     "damf_fleet_get_shares": (c_i32, [c_vp, c_vp, c_vp]),
     "damf_fleet_launches": (c_i64, [c_vp]),
     "damf_fleet_set_timing": (c_i32, [c_vp, c_i32]),

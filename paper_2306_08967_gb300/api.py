@@ -150,6 +150,13 @@ class DamfFleet:
                 raise ValueError("one share per graph")
             self._check(self.lib.damf_fleet_set_shares(self.h, a.ctypes.data_as(ctypes.c_void_p), 0.0))
 
+    def set_weights(self, weights):
+        """Shares in proportion to per-graph work estimates (e.g. measured push time x CTAs)."""
+        a = np.ascontiguousarray(weights, dtype=np.float64)
+        if a.size != len(self.graphs):
+            raise ValueError("one weight per graph")
+        self._check(self.lib.damf_fleet_set_weights(self.h, a.ctypes.data_as(ctypes.c_void_p)))
+
     def shares(self):
         """(CTAs per graph as a list, grouped launches per step)."""
         a = np.zeros(len(self.graphs), dtype=np.int32)

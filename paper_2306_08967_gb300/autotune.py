@@ -8,7 +8,9 @@ graph owns a share of the resident CTAs. How the CTAs are best split depends on 
   the tuner times whole fleet steps (the caller's `measure` callback runs real steps and
   returns milliseconds per step) for each exponent p and keeps the fastest;
 * under that rule it then tries the hub threshold (push_direct_chunks: how many in-edge
-  chunks a row task scatters itself before its row is split into items).
+  chunks a row task scatters itself before its row is split into items);
+* then it measures each graph's push time in the grouped launch and re-plans the shares in
+  proportion to the measured work (time x CTAs), for a few rounds, keeping the fastest.
 
 For graphs pushed one launch each (damf_step_multi), tune_grids picks the push grid per graph
 by a rows-per-CTA rule instead. Tuning changes only launch shapes: every result stays within
@@ -91,16 +93,29 @@ def tune_grids(graphs, measure_step_ms: Callable[[], float], rows_per_cta: Seque
             "ms_per_step": t_chunks[chunks]}
 
 
+def measured_weights(push_ns: Sequence[float], blocks: Sequence[int]) -> List[float]:
+    """Work of each graph's push from one grouped launch: its push time times the CTAs it ran
+    on (one for a graph sharing a CTA); a floor keeps every weight positive."""
+    w = [float(t) * max(int(b), 1) for t, b in zip(push_ns, blocks)]
+    floor = max(max(w) * 1e-6, 1e-9) if w else 1.0
+    return [max(x, floor) for x in w]
+
+
 def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
                 exponents: Sequence[float] = DEFAULT_EXPONENTS,
-                direct_chunks: Sequence[int] = DEFAULT_DIRECT_CHUNKS, repeats: int = 1) -> Dict:
+                direct_chunks: Sequence[int] = DEFAULT_DIRECT_CHUNKS, repeats: int = 1,
+                push_times: Callable[[], Sequence[float]] = None, rebalance_rounds: int = 3) -> Dict:
     """Tunes a fleet's grouped push by timing fleet steps.
 
-    fleet: .set_shares(blocks=None, exponent=p) and .shares() (DamfFleet). graphs: the fleet's
-    graphs with .set_tuning(push_blocks, push_direct_chunks) (DamfGraph). measure_step_ms():
-    runs a few real fleet steps under the current shape and returns ms per step (it must
-    rebuild any captured launch first). Leaves the best shape set and returns {"exponent",
-    "push_direct_chunks", "table_exponents", "table_chunks", "ms_per_step", "shares"}."""
+    fleet: .set_shares(blocks=None, exponent=p), .set_weights(w) and .shares() (DamfFleet).
+    graphs: the fleet's graphs with .set_tuning(push_blocks, push_direct_chunks) (DamfGraph).
+    measure_step_ms(): runs a few real fleet steps under the current shape and returns ms per
+    step (it must rebuild any captured launch first). push_times(): each graph's push time
+    per step (any unit) over the steps since its previous call; with it, after the exponent
+    and hub-threshold searches, `rebalance_rounds` rounds set the shares from the measured
+    work (push time x CTAs) of the previous round. Leaves the fastest shape seen set and
+    returns {"exponent", "push_direct_chunks", "table_exponents", "table_chunks",
+    "rebalance_ms", "chosen", "ms_per_step", "shares"}."""
     graphs = list(graphs)
     for g in graphs:
         g.set_tuning(0, -1)
@@ -121,7 +136,24 @@ def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
     for g in graphs:
         g.set_tuning(0, c)
     fleet.set_shares(exponent=p)
+    best_ms, best_w, chosen = t_chunks[c], None, "exponent"
+    reb = []
+    if push_times is not None and rebalance_rounds > 0:
+        push_times()                                   # start counting under the exponent rule
+        ms = measure_step_ms()
+        for _ in range(rebalance_rounds):
+            w = measured_weights(push_times(), fleet.shares()[0])
+            fleet.set_weights(w)
+            ms = min(measure_step_ms() for _ in range(max(1, repeats)))
+            reb.append(ms)
+            if ms < best_ms:
+                best_ms, best_w, chosen = ms, w, "measured"
+        if best_w is None:
+            fleet.set_shares(exponent=p)
+        else:
+            fleet.set_weights(best_w)
     blocks, launches = fleet.shares()
     return {"exponent": p, "push_direct_chunks": c, "table_exponents": {str(k): v for k, v in t_exp.items()},
-            "table_chunks": {str(k): v for k, v in t_chunks.items()}, "ms_per_step": t_chunks[c],
+            "table_chunks": {str(k): v for k, v in t_chunks.items()}, "rebalance_ms": reb, "chosen": chosen,
+            "ms_per_step": best_ms,
             "shares": {"min": min(blocks), "max": max(blocks), "launches": launches}}

@@ -372,7 +372,7 @@ struct Slot {
 // packed first-fit-decreasing into one-CTA bins of total share <= cap, and CTAs left over go
 // to the owners by largest remainders; cap starts at 1 and grows until the slots fit.
 bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, const int32_t* given, double exponent,
-                std::vector<Slot>* out) {
+                const double* weights, std::vector<Slot>* out) {
   out->clear();
   if (given) {
     long long tot = 0;
@@ -387,7 +387,7 @@ bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, cons
   double wsum = 0.0;
   for (int j = 0; j < cnt; ++j) {
     const Ctx& c = f->ctxs[idx[j]]->c;
-    x[j] = std::pow((double)c.d * (double)(c.n + c.m_init + 1), exponent);
+    x[j] = weights ? weights[idx[j]] : std::pow((double)c.d * (double)(c.n + c.m_init + 1), exponent);
     wsum += x[j];
   }
   for (int j = 0; j < cnt; ++j) x[j] = maxb * x[j] / wsum;
@@ -426,8 +426,9 @@ bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, cons
   }
 }
 
-// Builds every launch's slots and uploads the descriptor and slot tables.
-damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent) {
+// Builds every launch's slots and uploads the descriptor and slot tables; the fleet's plan
+// changes only when every launch could be planned.
+damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent, const double* weights = nullptr) {
   const int G = (int)f->ctxs.size();
   std::vector<int> blocks(G, 0);
   std::vector<FleetLaunch> launches;
@@ -441,7 +442,7 @@ damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent) {
     const int maxb = push_group_max_blocks(scaled);
     if (maxb < 1) return fleet_fail(f, DAMF_ERR_CUDA, "fleet: no resident push CTA");
     std::vector<Slot> slots;
-    if (!plan_slots(f, idx, maxb, given, exponent, &slots))
+    if (!plan_slots(f, idx, maxb, given, exponent, weights, &slots))
       return fleet_fail(f, DAMF_ERR_INVALID, "fleet: shares exceed the resident push CTAs");
     FleetLaunch L{scaled, (int)descs.size(), 0, (int)slots.size(), 0, (int)table.size()};
     std::vector<int> sfirst(1, 0), gfirst(1, 0);
@@ -1057,14 +1058,14 @@ damf_status damf_fleet_set_shares(damf_fleet* f, const int32_t* blocks, double e
   } else if (!(exponent >= 0.0 && exponent <= 4.0)) {
     return fleet_fail(f, DAMF_ERR_INVALID, "fleet: exponent outside [0, 4]");
   }
-  // a failed plan leaves the previous one in place
-  std::vector<int> ob = f->blocks;
-  const damf_status st = fleet_plan(f, blocks, exponent);
-  if (st != DAMF_OK && !ob.empty()) {
-    std::vector<int32_t> keep(ob.begin(), ob.end());
-    fleet_plan(f, keep.data(), 1.0);
-  }
-  return st;
+  return fleet_plan(f, blocks, exponent);   // a rejected plan leaves the previous one in place
+}
+
+damf_status damf_fleet_set_weights(damf_fleet* f, const double* weights) {
+  if (!f || !weights) return DAMF_ERR_INVALID;
+  for (size_t i = 0; i < f->ctxs.size(); ++i)
+    if (!(weights[i] > 0.0 && weights[i] < 1e300)) return fleet_fail(f, DAMF_ERR_INVALID, "fleet: a weight not > 0");
+  return fleet_plan(f, nullptr, 1.0, weights);
 }
 
 damf_status damf_fleet_get_shares(const damf_fleet* f, int32_t* blocks, int32_t* launches) {

@@ -18,4 +18,5 @@ from .chung_lu import (  # noqa: F401
     csr_from_edges,
     node_arrival_stream,
 )
-from .configs import CONFIGS, FLEETS, FleetWorkload, fleet_inputs, member_inputs, small_config  # noqa: F401
+from .configs import (CONFIGS, FLEETS, SERVING, FleetWorkload, ServingWorkload, fleet_inputs,  # noqa: F401
+                      member_inputs, small_config)

@@ -122,8 +122,11 @@ class EdgeStream:
 
 def edge_stream(indptr: np.ndarray, indices: np.ndarray, weights: np.ndarray, n_batches: int,
                 k_lo: int, k_hi: int, p_node: float, p_del: float, seed: int,
-                max_new_degree: int = 32, directed: bool = False, nodes_per_batch: int = 0) -> EdgeStream:
-    """Seeded stream of edge batches over a graph given in CSR (see module docstring)."""
+                max_new_degree: int = 32, directed: bool = False, nodes_per_batch: int = 0,
+                log_sizes: bool = False) -> EdgeStream:
+    """Seeded stream of edge batches over a graph given in CSR (see module docstring).
+    log_sizes: k drawn log-uniformly from [k_lo, k_hi] (round(exp(U[ln k_lo, ln(k_hi + 1)])),
+    clipped) instead of uniformly."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n0 = int(indptr.shape[0] - 1)
     # initial edges (canonical for undirected) in a random order, consumed by deletions
@@ -142,7 +145,10 @@ def edge_stream(indptr: np.ndarray, indices: np.ndarray, weights: np.ndarray, n_
     n_cur = n0
     batches = []
     for _ in range(n_batches):
-        k_other = int(rng.integers(k_lo, k_hi + 1))
+        if log_sizes:
+            k_other = int(min(k_hi, max(k_lo, np.floor(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi + 1)))))))
+        else:
+            k_other = int(rng.integers(k_lo, k_hi + 1))
         src, dst, op = [], [], []
         new_nodes = 0
 

@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_2306_08967_gb300.autotune import blocks_for, choose, plan, tune_grids, tune_shares
+from paper_2306_08967_gb300.autotune import blocks_for, choose, measured_weights, plan, tune_grids, tune_shares
 from synth import FLEETS
 
 
@@ -89,10 +89,14 @@ class FakeFleet:
 
     def set_shares(self, blocks=None, exponent=1.0):
         self.p = exponent
+        self.w = None
         self.snap = [g.chunks for g in self.graphs]     # the fleet snapshots the hub threshold
 
+    def set_weights(self, w):
+        self.w = list(w)
+
     def shares(self):
-        w = [g.n ** self.p for g in self.graphs]
+        w = self.w if self.w is not None else [g.n ** self.p for g in self.graphs]
         return [max(1, int(self.maxb * x / sum(w))) for x in w], 1
 
 
@@ -108,3 +112,28 @@ def test_tune_shares_picks_exponent_then_hub_threshold():
     assert fleet.p == 0.75 and fleet.snap == [4, 4, 4]
     assert res["ms_per_step"] == 0.0 and res["shares"]["launches"] == 1
     assert set(res["table_exponents"]) == {"0.5", "0.75", "1.0", "1.25"}
+
+
+def test_measured_weights():
+    assert measured_weights([10.0, 4.0, 0.0], [3, 0, 1]) == [30.0, 4.0, 30.0 * 1e-6]
+
+
+def test_tune_shares_rebalances_on_measured_work():
+    # true work per graph is not its size: graph 0 is slow for its size. Time per step is the
+    # slowest graph's work / CTAs; measured rebalancing must find shares near the work ratio
+    graphs = [FakeGraph(n, 304) for n in (1000, 20_000, 400_000)]
+    work = [900.0, 100.0, 3000.0]
+    fleet = FakeFleet(graphs)
+
+    def times():
+        return [wk / b for wk, b in zip(work, fleet.shares()[0])]
+
+    def step_ms():
+        return max(times())
+
+    res = tune_shares(fleet, graphs, step_ms, exponents=(0.5, 1.0), direct_chunks=(-1,), push_times=times,
+                      rebalance_rounds=2)
+    assert res["chosen"] == "measured"
+    b = fleet.shares()[0]
+    assert abs(b[0] / b[2] - 900.0 / 3000.0) < 0.05
+    assert res["ms_per_step"] < min(res["table_exponents"].values())

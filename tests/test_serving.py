@@ -1,0 +1,96 @@
+"""Host logic of the serving scheduler (admission by memory, one request per graph per step,
+release after the last step), with no device: the Server's library side is covered by the GPU
+tests."""
+
+import numpy as np
+import pytest
+
+from paper_2306_08967_gb300.serving import Request, Scheduler
+
+
+def _req(rid, sid, k=3, t=0.0):
+    z = np.zeros(k, np.int32)
+    return Request(rid, sid, z, z + 1, np.ones(k, np.int8), t)
+
+
+def test_admission_is_first_come_within_the_budget():
+    s = Scheduler(budget_bytes=100)
+    s.open(1, 40)
+    s.open(2, 50)
+    s.open(3, 30)          # fits beside 1 alone, but waits behind 2
+    s.open(4, 5)
+    assert s.admissions() == [1, 2]
+    assert s.used == 90
+    assert s.admissions() == []            # 3 needs 30, 10 left; 4 waits behind it
+    with pytest.raises(ValueError):
+        s.open(5, 101)                     # never fits
+    with pytest.raises(ValueError):
+        s.open(1, 10)                      # exists
+
+
+def test_each_step_takes_the_oldest_request_of_each_resident_graph():
+    s = Scheduler(budget_bytes=100, max_events=8)
+    s.open(1, 10)
+    s.open(2, 10)
+    s.open(3, 90)                          # waits until 1 or 2 is freed
+    for sid in s.admissions():
+        s.admitted(sid)
+    for rid, sid in enumerate([1, 1, 2, 3, 1]):
+        s.submit(_req(rid, sid))
+    with pytest.raises(ValueError):
+        s.submit(_req(9, 1, k=9))          # more than max_events
+    st, pick = s.next_step()
+    assert st == 0 and {k: v.rid for k, v in pick.items()} == {1: 0, 2: 2}
+    st, pick = s.next_step()
+    assert st == 1 and {k: v.rid for k, v in pick.items()} == {1: 1}
+    st, pick = s.next_step()
+    assert st == 2 and {k: v.rid for k, v in pick.items()} == {1: 4}
+    assert s.next_step() is None           # graph 3 is not resident: its request waits
+    assert not s.idle()
+
+
+def test_release_waits_for_the_last_step_and_frees_memory():
+    s = Scheduler(budget_bytes=100)
+    s.open(1, 60)
+    s.open(2, 60)
+    for sid in s.admissions():
+        s.admitted(sid)
+    assert s.resident() == [1]
+    s.submit(_req(0, 1))
+    s.submit(_req(1, 1))
+    s.close(1)
+    with pytest.raises(ValueError):
+        s.submit(_req(2, 1))               # closing
+    a = s.next_step(t=1.0)
+    b = s.next_step(t=1.5)
+    s.step_done(a[0], a[1], t=2.0)
+    assert s.releases() == []                           # its second request still runs
+    assert a[1][1].t_done == 2.0 and a[1][1].t_issue == 1.0
+    s.step_done(b[0], b[1], t=3.0)
+    assert s.releases() == [1] and s.releases() == []
+    assert s.resident() == [] and s.admissions() == []   # memory not yet freed
+    s.freed(1)
+    assert s.admissions() == [2] and s.used == 60
+    with pytest.raises(ValueError):
+        s.freed(1)
+
+
+def test_a_session_closed_while_empty_is_released_without_a_step():
+    s = Scheduler(budget_bytes=10)
+    s.open(1, 5)
+    s.open(2, 5)
+    s.open(3, 5)
+    for sid in s.admissions():
+        s.admitted(sid)
+    s.submit(_req(0, 2))
+    s.submit(_req(1, 3))                 # 3 waits for memory
+    s.close(1)
+    assert s.releases() == [1]           # it never took part in a step
+    s.freed(1)
+    assert s.admissions() == [3]
+    s.admitted(3)
+    assert s.backlog() == 2
+    st = s.next_step()
+    assert sorted(st[1]) == [2, 3]
+    s.step_done(st[0], st[1], 1.0)
+    assert s.idle() and s.backlog() == 0
