@@ -393,7 +393,7 @@ damf_status damf_core_svd(const float* sigma, const float* L, const float* R, in
  * counterpart; this is a deployment variant of Step 2.
  *   Arguments and results are those of damf_core_svd.  The caller still provides and
  *   owns every input and output.  Nothing is allocated: the scratch (a status word and
- *   the assembled core) is one static device array of 262,400 bytes compiled into the
+ *   the assembled core) is one static device array of 262,656 bytes compiled into the
  *   library, which every GPU that loads the library holds until the process exits.
  *   Limit: d + r <= 256 (d in {16, 32, 64, 128}, 1 <= r <= 128); a larger r returns
  *   DAMF_ERR_CAPACITY, bad d or NULL pointers DAMF_ERR_INVALID.

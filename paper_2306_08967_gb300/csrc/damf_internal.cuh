@@ -61,6 +61,10 @@ struct DevHeader {
   int rho_tail;
   int item_tail;
   int ovf_count;    // hub items that found the queue full (processed at the end of the phase)
+  // grouped push: warps of other graphs may join this graph's task loop while help_open is set
+  // (between the seeding barrier and the end of the loop); helpers counts those inside
+  int help_open;
+  int helpers;
   GridBar bar;
 };
 

@@ -20,9 +20,9 @@ using namespace damf;
 
 namespace {
 
-constexpr size_t kHeaderBytes = 256;
+constexpr size_t kHeaderBytes = 512;
 static_assert(sizeof(DevHeader) <= kHeaderBytes, "status area too small");
-// status word area + the largest core (d + r <= 256) in FP32: 262,400 bytes
+// status word area + the largest core (d + r <= 256) in FP32: 262,656 bytes
 constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxM * kMaxM * sizeof(float);
 
 // Held by every GPU that loads the library, until the process exits.

@@ -286,6 +286,172 @@ __device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long
   }
 }
 
+// The task loop of one graph's push for one warp: claims queue positions kClaim at a time and
+// runs the row and item tasks it finds, until no task is left (the unfinished count is zero),
+// the device status is set, or a wait runs out. The warp's counters accumulate in my_*.
+// Owners call it between the grid barriers of a phase; in a grouped push, warps whose own
+// graphs are done call it on another graph's queue while that graph's loop is open.
+template <int D, bool SCALED>
+__device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long long& my_pushes, long long& my_edges,
+                                          int& my_rows, int& my_items, unsigned long long& my_wait) {
+  DevHeader* const h = a.h;
+  const Adj in = a.in;
+  const int32_t* __restrict__ outdeg = a.outdeg;
+  const Workspace& ws = a.ws;
+  float* const Zb = a.Zb;
+  float* const r = a.r;
+  const float alpha = a.alpha, eps = a.eps;
+  const int direct_max = a.direct_max;
+  constexpr int LPR = PushShape<D>::LPR;
+  constexpr int RPW = PushShape<D>::RPW;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPR, q = lane % LPR;
+  const float beta = 1.0f - alpha;
+  const long long qcap = ws.qcap;
+  int32_t* queue = ws.queue;
+  uint32_t* inq = ws.stamp;
+  // ---- task loop: claim kClaim positions at a time, lanes 0 .. kClaim-1 read their slots ----
+  bool quit = false;
+  while (!quit) {
+    long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&h->q_head, kClaim);
+    p0 = __shfl_sync(kFull, p0, 0);
+    int eb = -1;
+    if (lane < kClaim && p0 + lane < qcap) {
+      eb = ld_acquire(queue + p0 + lane);
+      if (eb != -1) queue[p0 + lane] = -1;   // read once per phase; empty again for the next launch
+    }
+    // and the entries' read-only data in the same pass: a row's in-edge range (and out-degree),
+    // an item's (rho slot, first in-edge, count)
+    int m0 = 0, m1 = 0, m2 = 1;
+    if (lane < kClaim && eb != -1) {
+      if (eb >= 0) {
+        m0 = __ldg(in.start + eb);
+        m1 = __ldg(in.len + eb);
+        if (SCALED) m2 = __ldg(outdeg + eb);
+      } else {
+        const int4 wi = __ldcg(ws.work + (-eb - 2));
+        m0 = wi.y;
+        m1 = wi.z;
+        m2 = wi.x;
+      }
+    }
+    for (int b = 0; b < kClaim; ++b) {
+    const long long p = p0 + b;
+    int e = __shfl_sync(kFull, eb, b);
+    const bool pre = e != -1;    // the batch pass read this entry's data
+    int st = __shfl_sync(kFull, m0, b), deg = __shfl_sync(kFull, m1, b), aux = __shfl_sync(kFull, m2, b);
+    if (e == -1) {
+      flush(wq, h, queue, qcap, lane, ws.ovf);   // publish and uncount before waiting
+      if (lane == 0) {
+        const unsigned long long t0 = gtimer();
+        e = wait_slot(h, queue, p, qcap);
+        my_wait += gtimer() - t0;
+      }
+      e = __shfl_sync(kFull, e, 0);
+      if (e == -1) {
+        quit = true;                     // positions after p are not filled either
+        break;
+      }
+    }
+    if (e >= 0) {
+      if (lane == 0) ++my_rows;
+      // row task. The flag is cleared first; the removal of v below is ordered after the
+      // clear (fence), so an add that lands after the removal finds the flag clear and queues
+      // u again, while an add between the read of v and the removal shows in `left`.
+      const int u = e;
+      if (lane == 0) atomicExch(inq + u, 0u);
+      __syncwarp();
+      // group 0 reads r[u] once and hands it to the other groups, so that every group
+      // scatters exactly the v that group 0 removes
+      if (!pre) {
+        st = __ldg(in.start + u);
+        deg = __ldg(in.len + u);
+        aux = SCALED ? __ldg(outdeg + u) : 1;
+      }
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+      // the first 32 in-edges and their out-degrees are requested beside the row, so that they
+      // arrive while the removal below is still in flight
+      const bool pre0 = deg <= direct_max;
+      int w0 = 0, d0 = 1;
+      if (pre0 && lane < min(deg, 32)) w0 = __ldg(in.col + st + lane);
+      if (RPW > 1) {
+        v.x = __shfl_sync(kFull, v.x, q);
+        v.y = __shfl_sync(kFull, v.y, q);
+        v.z = __shfl_sync(kFull, v.z, q);
+        v.w = __shfl_sync(kFull, v.w, q);
+      }
+      if (pre0 && lane < min(deg, 32)) d0 = __ldg(outdeg + w0);
+      const int dout = aux;
+      const float thr_u = threshold<SCALED>(eps, dout);
+      if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
+        float lm = 0.f;                           // max |r[u]| right after the removal of v
+        __syncwarp();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");   // the flag's clear comes first
+        if (sub == 0) {
+          const float4 old =
+              atomicAdd(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(-v.x, -v.y, -v.z, -v.w));
+          lm = max_abs4(make_float4(old.x - v.x, old.y - v.y, old.z - v.z, old.w - v.w));
+          atomicAdd(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q,
+                    make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w));
+        }
+        if (lane == 0) {
+          my_pushes += 1;
+          my_edges += deg;
+        }
+        bool direct = true;
+        if (deg > direct_max) {
+          // hub: a rho slot and one item task per kItemEdges in-edges
+          const int nch = (deg + kItemEdges - 1) / kItemEdges;
+          int slot = 0, ib = 0;
+          if (lane == 0) {
+            slot = atomicAdd(&h->rho_tail, 1);
+            ib = atomicAdd(&h->item_tail, nch);
+          }
+          slot = __shfl_sync(kFull, slot, 0);
+          ib = __shfl_sync(kFull, ib, 0);
+          if ((long long)slot < ws.rho_cap && (long long)ib + nch <= ws.work_cap) {
+            direct = false;
+            if (sub == 0) __stcg(reinterpret_cast<float4*>(ws.rho + (size_t)slot * D) + q, v);
+            for (int c0 = 0; c0 < nch; c0 += 32) {   // warp-uniform
+              const int c2 = c0 + lane;
+              if (c2 < nch)
+                __stcg(ws.work + ib + c2,
+                       make_int4(slot, st + c2 * kItemEdges, min(kItemEdges, deg - c2 * kItemEdges), 0));
+              stage(c2 < nch, -(ib + c2 + 2), wq, h, queue, qcap, lane);
+            }
+          }
+        }
+        if (direct)
+          scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
+                                   true, pre0, w0, d0);
+        // u itself: adds that reached r[u] between the read of v and its removal are still there
+        lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
+        enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
+      }
+    } else {
+      // item task: one chunk of a hub's in-edges
+      if (lane == 0) ++my_items;
+      if (!pre) {
+        const int4 wi = __ldcg(ws.work + (-e - 2));
+        st = wi.y;
+        deg = wi.z;
+        aux = wi.x;
+      }
+      const float4 rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
+      int w0 = 0, d0 = 1;
+      if (lane < deg) w0 = __ldg(in.col + st + lane);
+      if (lane < deg) d0 = __ldg(outdeg + w0);
+      scatter_edges<D, SCALED>(rv, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
+                               q, true, true, w0, d0);
+    }
+    wq.done += 1;
+    }
+    flush(wq, h, queue, qcap, lane, ws.ovf);
+  }
+}
+
 // The push of one graph by `nblocks` CTAs of 256 threads (this one is CTA `blk` of them): the
 // whole launch for one graph (k_push), or one graph's share of a launch over many (k_push_group).
 // s_t (5 words) and s_buf (8 warps x kQBuf) are the CTA's shared timers and warp queue buffers.
@@ -296,10 +462,9 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
   const Adj in = a.in;
   const int32_t* __restrict__ outdeg = a.outdeg;
   const Workspace& ws = a.ws;
-  float* const Zb = a.Zb;
   float* const r = a.r;
   const float alpha = a.alpha, eps = a.eps;
-  const int max_phases = a.max_phases, direct_max = a.direct_max;
+  const int max_phases = a.max_phases;
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
   const int lane = threadIdx.x & 31;
@@ -349,149 +514,13 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
     if (timer) time_mark(s_t, 0);
     if (!grid_barrier(&h->bar, h, nblocks)) return;
     if (timer) time_mark(s_t, 2);
+    if (blk == 0 && threadIdx.x == 0) atomicExch(&h->help_open, 1);   // the queue is seeded
 
-    // ---- task loop: claim kClaim positions at a time, lanes 0 .. kClaim-1 read their slots ----
-    bool quit = false;
-    while (!quit) {
-      long long p0 = 0;
-      if (lane == 0) p0 = atomicAdd(&h->q_head, kClaim);
-      p0 = __shfl_sync(kFull, p0, 0);
-      int eb = -1;
-      if (lane < kClaim && p0 + lane < qcap) {
-        eb = ld_acquire(queue + p0 + lane);
-        if (eb != -1) queue[p0 + lane] = -1;   // read once per phase; empty again for the next launch
-      }
-      // and the entries' read-only data in the same pass: a row's in-edge range (and out-degree),
-      // an item's (rho slot, first in-edge, count)
-      int m0 = 0, m1 = 0, m2 = 1;
-      if (lane < kClaim && eb != -1) {
-        if (eb >= 0) {
-          m0 = __ldg(in.start + eb);
-          m1 = __ldg(in.len + eb);
-          if (SCALED) m2 = __ldg(outdeg + eb);
-        } else {
-          const int4 wi = __ldcg(ws.work + (-eb - 2));
-          m0 = wi.y;
-          m1 = wi.z;
-          m2 = wi.x;
-        }
-      }
-      for (int b = 0; b < kClaim; ++b) {
-      const long long p = p0 + b;
-      int e = __shfl_sync(kFull, eb, b);
-      const bool pre = e != -1;    // the batch pass read this entry's data
-      int st = __shfl_sync(kFull, m0, b), deg = __shfl_sync(kFull, m1, b), aux = __shfl_sync(kFull, m2, b);
-      if (e == -1) {
-        flush(wq, h, queue, qcap, lane, ws.ovf);   // publish and uncount before waiting
-        if (lane == 0) {
-          const unsigned long long t0 = gtimer();
-          e = wait_slot(h, queue, p, qcap);
-          my_wait += gtimer() - t0;
-        }
-        e = __shfl_sync(kFull, e, 0);
-        if (e == -1) {
-          quit = true;                     // positions after p are not filled either
-          break;
-        }
-      }
-      if (e >= 0) {
-        if (lane == 0) ++my_rows;
-        // row task. The flag is cleared first; the removal of v below is ordered after the
-        // clear (fence), so an add that lands after the removal finds the flag clear and queues
-        // u again, while an add between the read of v and the removal shows in `left`.
-        const int u = e;
-        if (lane == 0) atomicExch(inq + u, 0u);
-        __syncwarp();
-        // group 0 reads r[u] once and hands it to the other groups, so that every group
-        // scatters exactly the v that group 0 removes
-        if (!pre) {
-          st = __ldg(in.start + u);
-          deg = __ldg(in.len + u);
-          aux = SCALED ? __ldg(outdeg + u) : 1;
-        }
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
-        // the first 32 in-edges and their out-degrees are requested beside the row, so that they
-        // arrive while the removal below is still in flight
-        const bool pre0 = deg <= direct_max;
-        int w0 = 0, d0 = 1;
-        if (pre0 && lane < min(deg, 32)) w0 = __ldg(in.col + st + lane);
-        if (RPW > 1) {
-          v.x = __shfl_sync(kFull, v.x, q);
-          v.y = __shfl_sync(kFull, v.y, q);
-          v.z = __shfl_sync(kFull, v.z, q);
-          v.w = __shfl_sync(kFull, v.w, q);
-        }
-        if (pre0 && lane < min(deg, 32)) d0 = __ldg(outdeg + w0);
-        const int dout = aux;
-        const float thr_u = threshold<SCALED>(eps, dout);
-        if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
-          float lm = 0.f;                           // max |r[u]| right after the removal of v
-          __syncwarp();
-          asm volatile("fence.acq_rel.gpu;" ::: "memory");   // the flag's clear comes first
-          if (sub == 0) {
-            const float4 old =
-                atomicAdd(reinterpret_cast<float4*>(r + (size_t)u * D) + q, make_float4(-v.x, -v.y, -v.z, -v.w));
-            lm = max_abs4(make_float4(old.x - v.x, old.y - v.y, old.z - v.z, old.w - v.w));
-            atomicAdd(reinterpret_cast<float4*>(Zb + (size_t)u * D) + q,
-                      make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w));
-          }
-          if (lane == 0) {
-            my_pushes += 1;
-            my_edges += deg;
-          }
-          bool direct = true;
-          if (deg > direct_max) {
-            // hub: a rho slot and one item task per kItemEdges in-edges
-            const int nch = (deg + kItemEdges - 1) / kItemEdges;
-            int slot = 0, ib = 0;
-            if (lane == 0) {
-              slot = atomicAdd(&h->rho_tail, 1);
-              ib = atomicAdd(&h->item_tail, nch);
-            }
-            slot = __shfl_sync(kFull, slot, 0);
-            ib = __shfl_sync(kFull, ib, 0);
-            if ((long long)slot < ws.rho_cap && (long long)ib + nch <= ws.work_cap) {
-              direct = false;
-              if (sub == 0) __stcg(reinterpret_cast<float4*>(ws.rho + (size_t)slot * D) + q, v);
-              for (int c0 = 0; c0 < nch; c0 += 32) {   // warp-uniform
-                const int c2 = c0 + lane;
-                if (c2 < nch)
-                  __stcg(ws.work + ib + c2,
-                         make_int4(slot, st + c2 * kItemEdges, min(kItemEdges, deg - c2 * kItemEdges), 0));
-                stage(c2 < nch, -(ib + c2 + 2), wq, h, queue, qcap, lane);
-              }
-            }
-          }
-          if (direct)
-            scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
-                                     true, pre0, w0, d0);
-          // u itself: adds that reached r[u] between the read of v and its removal are still there
-          lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
-          enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
-        }
-      } else {
-        // item task: one chunk of a hub's in-edges
-        if (lane == 0) ++my_items;
-        if (!pre) {
-          const int4 wi = __ldcg(ws.work + (-e - 2));
-          st = wi.y;
-          deg = wi.z;
-          aux = wi.x;
-        }
-        const float4 rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
-        int w0 = 0, d0 = 1;
-        if (lane < deg) w0 = __ldg(in.col + st + lane);
-        if (lane < deg) d0 = __ldg(outdeg + w0);
-        scatter_edges<D, SCALED>(rv, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
-                                 q, true, true, w0, d0);
-      }
-      wq.done += 1;
-      }
-      flush(wq, h, queue, qcap, lane, ws.ovf);
-    }
+    // ---- task loop ----
+    task_loop<D, SCALED>(a, wq, my_pushes, my_edges, my_rows, my_items, my_wait);
     if (timer) time_mark(s_t, 1);
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // every warp has left the task loop
+    if (blk == 0 && threadIdx.x == 0) atomicExch(&h->help_open, 0);   // no task is left to help with
     const bool again = *reinterpret_cast<volatile int*>(&h->overflow) != 0 &&
                        *reinterpret_cast<volatile int*>(&h->status) == 0;
     if (!again) {
@@ -512,6 +541,18 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
     }
     for (long long u = (long long)blk * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
       inq[u] = 0u;
+    // helpers that joined before the gate closed leave before the queue words are reset
+    if (blk == 0 && threadIdx.x == 0) {
+      __threadfence();   // the gate's close (above) is ordered before this read of helpers
+      long long it = 0;
+      while (*reinterpret_cast<volatile int*>(&h->helpers) != 0) {
+        if (++it > kSpinLimit) {
+          set_status(h, DAMF_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // everyone has read the overflow flag
     if (blk == 0 && threadIdx.x == 0) {
       h->qstate = 0ull;
@@ -568,6 +609,75 @@ __global__ void k_push_reset(const PushArgs* __restrict__ descs, int count) {
   h->rho_tail = 0;
   h->item_tail = 0;
   h->ovf_count = 0;
+  h->help_open = 0;
+  h->helpers = 0;
+}
+
+constexpr int kHelpMinTasks = 64;   // a graph with fewer unfinished tasks is left to its own warps
+constexpr int kHelpRounds = 256;    // graphs one warp may help in turn
+
+// A warp whose own graphs are pushed joins the task loop of the open graph with the most
+// unfinished tasks, until none is left with at least kHelpMinTasks. It registers (helpers) and
+// then checks the gate, so that a graph that closes its gate and then finds helpers == 0 has no
+// warp of another graph left in its loop; its tasks' counters go to that graph's header.
+template <bool SCALED>
+__device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, int ngraphs, int32_t* buf) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < kHelpRounds; ++round) {
+    unsigned best = 0;
+    int bg = -1;
+    for (int g = lane; g < ngraphs; g += 32) {
+      DevHeader* hg = descs[g].h;
+      if (*reinterpret_cast<volatile int*>(&hg->help_open) != 0) {
+        const unsigned u = (unsigned)(ld_volatile64(&hg->qstate) >> 32);
+        if (u > best) {
+          best = u;
+          bg = g;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned ob = __shfl_xor_sync(kFull, best, o);
+      const int og = __shfl_xor_sync(kFull, bg, o);
+      if (ob > best || (ob == best && og > bg)) {
+        best = ob;
+        bg = og;
+      }
+    }
+    if (bg < 0 || best < (unsigned)kHelpMinTasks) return;
+    const PushArgs& a = descs[bg];
+    int ok = 0;
+    if (lane == 0) {
+      atomicAdd(&a.h->helpers, 1);
+      __threadfence();
+      ok = *reinterpret_cast<volatile int*>(&a.h->help_open);
+      if (!ok) atomicSub(&a.h->helpers, 1);
+    }
+    if (!__shfl_sync(kFull, ok, 0)) continue;
+    WarpQ wq{buf, 0, 0, a.ws.ovf, a.ws.stamp};
+    long long pushes = 0, edges = 0;
+    int rows = 0, items = 0;
+    unsigned long long wait = 0;
+    switch (a.d) {
+      case 16: task_loop<16, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
+      case 32: task_loop<32, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
+      case 64: task_loop<64, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
+      default: task_loop<128, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
+    }
+    if (lane == 0) {
+      if (pushes || edges) {
+        atomicAdd((unsigned long long*)&a.h->pushes, (unsigned long long)pushes);
+        atomicAdd((unsigned long long*)&a.h->push_edges, (unsigned long long)edges);
+      }
+      if (rows || items) {
+        atomicAdd((unsigned long long*)&a.h->push_tasks, (unsigned long long)rows);
+        atomicAdd((unsigned long long*)&a.h->push_items, (unsigned long long)items);
+      }
+      __threadfence();
+      atomicSub(&a.h->helpers, 1);
+    }
+    __syncwarp();
+  }
 }
 
 // The pushes of many graphs in one cooperative launch, in slots: slot s owns CTAs
@@ -618,6 +728,8 @@ __global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restric
       default: push_body<128, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
     }
   }
+  // this CTA's graphs are pushed: its warps help the graphs still running
+  help_others<SCALED>(descs, gfirst[nslots], s_buf[threadIdx.x >> 5]);
 }
 
 PushArgs push_args(const Ctx* c, int direct_chunks) {
@@ -686,8 +798,8 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   // a cooperative grid must fit on the device at once
   const int blocks = (c->push_blocks > 0 && c->push_blocks < c->push_max) ? c->push_blocks : c->push_max;
   const int chunks = c->push_direct_chunks;
-  // qstate, q_head, overflow, rho_tail, item_tail, ovf_count
-  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 5 * sizeof(int), s);
+  // qstate, q_head, overflow, rho_tail, item_tail, ovf_count, help_open, helpers
+  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 7 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   PushArgs a = push_args(c, chunks);
   int n = c->n;
