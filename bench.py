@@ -1045,16 +1045,21 @@ def run_serving(args, sw):
     reqs = [(r, p) for r, p in reqs if r.t_done is not None]
     for g in list(srv.graphs.values()):
         g.check()
+    def pct(rs):
+        lat = np.array([r.t_done - r.t_arrive for r in rs]) * 1e3
+        return {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "mean": float(lat.mean()), "n": len(rs)} if len(rs) else None
+
     phases = []
     for ph, lam in enumerate(rates):
         rs = [r for r, p in reqs if p == ph]
-        lat = np.array([r.t_done - r.t_arrive for r in rs]) * 1e3
         edges = sum(r.k for r in rs)
         last = max(r.t_done for r in rs) if rs else ph * dur
         phases.append({"rate_req_s": lam, "requests": len(rs), "edges": int(edges),
                        "edge_updates_s": edges / max(last - ph * dur, 1e-9),
-                       "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                      "mean": float(lat.mean())} if len(rs) else None})
+                       "latency_ms": pct(rs),
+                       "latency_ms_resident_at_arrival": pct([r for r in rs if r.resident_at_arrival]),
+                       "latency_ms_waiting_for_admission": pct([r for r in rs if not r.resident_at_arrival])})
     sess = srv.sched.sessions.values()
     waits = np.array([(s.t_admit - s.t_open) for s in sess if s.t_admit is not None and s.sid != 0])
     steps = srv.steps_issued
@@ -1084,7 +1089,8 @@ def run_serving(args, sw):
         "sessions": {"opened": len(srv.sched.sessions), "admission_wait_s": {
             "p50": float(np.percentile(waits, 50)) if len(waits) else None,
             "p99": float(np.percentile(waits, 99)) if len(waits) else None}},
-        "gpu_launches": None,
+        "gpu_launches": int(srv.kernel_count()),
+        "gpu_launches_note": "kernels of every graph (initialisations included) and fleet of the run",
         "init_s": init_s, "generate_s": gen_s, "clocks": clk.summary(),
     }
     srv.shutdown()

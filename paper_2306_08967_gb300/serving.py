@@ -41,6 +41,7 @@ class Request:
     t_issue: Optional[float] = None
     t_done: Optional[float] = None
     step: Optional[int] = None
+    resident_at_arrival: Optional[bool] = None
 
     @property
     def k(self) -> int:
@@ -90,6 +91,7 @@ class Scheduler:
             raise ValueError("session %d is closing" % req.sid)
         if req.k > self.max_events:
             raise ValueError("request of %d events; at most %d" % (req.k, self.max_events))
+        req.resident_at_arrival = s.state == "resident"
         s.queue.append(req)
 
     def admissions(self, t: float = 0.0) -> List[int]:
@@ -187,6 +189,7 @@ class Server:
         self.completed: List[Request] = []
         self.t0 = time.perf_counter()
         self.steps_issued = 0
+        self.kernels = 0           # kernels of graphs and fleets already closed
         self.ring = []             # staging buffers (pinned host, device), reused round robin
         self.ring_rows = 0
         self.ring_pos = 0
@@ -217,6 +220,7 @@ class Server:
             return
         if self.fleet is not None:
             self.retired.append((self.fleet, self.sched.next_step_id - 1))
+            self.kernels += self.fleet.launches
         self.fleet = DamfFleet([self.graphs[s] for s in sids]) if sids else None
         if self.fleet is not None and self.share_exponent != 1.0:
             self.fleet.set_shares(exponent=self.share_exponent)
@@ -295,6 +299,7 @@ class Server:
                 g.check()
                 if self.on_release is not None:
                     self.on_release(sid, g)
+                self.kernels += g.stats()["launches"]
                 g.close()
                 self.sched.freed(sid)
             else:
@@ -333,6 +338,12 @@ class Server:
 
     def graph(self, sid: int):
         return self.graphs.get(sid)
+
+    def kernel_count(self) -> int:
+        """Kernels launched by every graph (initialisation included) and fleet so far."""
+        live = sum(g.stats()["launches"] for g in self.graphs.values())
+        live += sum(g.stats()["launches"] for _, g, _ in self.to_destroy)
+        return self.kernels + live + (self.fleet.launches if self.fleet is not None else 0)
 
     def shutdown(self, max_seconds: float = 600.0):
         self.drain(max_seconds)

@@ -12,7 +12,7 @@ C3  large graph: undirected Chung-Lu, gamma 2.1, n = 2,000,000, m = 40M edges (m
 C5  serving (the workload's graph of n = 50M, m = 1B and 32 graphs of 1M-5M nodes need about
     300 GB at d = 128, more than one GPU holds; run here at a tenth of the node counts): one
     directed Chung-Lu graph, gamma 2.2, n = 5M, m = 100M, and sessions of directed graphs with
-    n log-uniform in [100k, 500k] (32 open at a time; each closes after 100 requests and a new
+    n log-uniform in [100k, 500k] (32 open at a time; each closes after 50 requests and a new
     one opens), d = 128, alpha and eps as in C2; Poisson arrivals of requests
     of log-uniform size in [1, 1024] edge events (10% deletions), each to a uniformly chosen
     open session; admission by the bytes each graph needs against an HBM budget.
@@ -179,6 +179,6 @@ class ServingWorkload:
 
 SERVING = {
     "C5": ServingWorkload("C5", big_n=5_000_000, big_deg=20.0, small_lo=100_000, small_hi=500_000, small_deg=12.0,
-                          open_small=32, requests_per_session=100, d=128, gamma=2.2, alpha=0.15, eps=1e-5, k_lo=1,
+                          open_small=32, requests_per_session=50, d=128, gamma=2.2, alpha=0.15, eps=1e-5, k_lo=1,
                           k_hi=1024, p_del=0.10, seed=SEED_BASE + 4),
 }
