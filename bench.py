@@ -199,7 +199,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one k_push launch of the C2 workload, from the ncu capture
 # summarised in profiles/k_push_C2.md; None once k_push changes until it is captured again
-PUSH_DRAM_BYTES = 478.21e6
+PUSH_DRAM_BYTES = 482.82e6
 
 # ---------------------------------------------------------------- ranks
 def reduce_over_ranks(elapsed_ms, edges, world):
