@@ -199,13 +199,17 @@ damf_status damf_fleet_step(damf_fleet* fleet, const damf_batch* batches, void* 
  * threshold mode summing to at most the resident push CTAs), or with blocks = NULL shares in
  * proportion to (d (n + m))^exponent, exponent in [0, 4]: a graph whose share is below one CTA
  * shares a CTA with other such graphs (first fit, largest first).  Also takes each
- * context's push_direct_chunks (damf_set_tuning) as it is now.  Synchronous; not while a
- * capture is in progress.  DAMF_ERR_INVALID (shares unchanged) for bad values. */
+ * context's push_direct_chunks (damf_set_tuning) as it is now.  Synchronous: waits for all
+ * device work (pushes already enqueued or replayed read the old tables); not while a capture
+ * is in progress.  A CUDA graph that captured a step of this fleet must be captured again:
+ * its grouped push no longer matches the tables, and a replay only sets DAMF_ERR_INVALID on
+ * the fleet's contexts.  DAMF_ERR_INVALID (shares unchanged) for bad values. */
 damf_status damf_fleet_set_shares(damf_fleet* fleet, const int32_t* blocks, double exponent);
 
 /* Sets the shares from per-graph work estimates (host double[count], each > 0, e.g. a
  * graph's measured push time times its CTAs): CTAs in proportion to the weights, graphs below
- * one CTA's worth packed as with damf_fleet_set_shares.  Synchronous; not while capturing.
+ * one CTA's worth packed as with damf_fleet_set_shares (and, like it, synchronous, not while
+ * capturing, and requiring captured steps to be captured again).
  * DAMF_ERR_INVALID (shares unchanged) for a weight that is not > 0. */
 damf_status damf_fleet_set_weights(damf_fleet* fleet, const double* weights);
 
@@ -229,7 +233,9 @@ int64_t damf_fleet_launches(const damf_fleet* fleet);
 /* Text of the fleet's most recent error. */
 const char* damf_fleet_last_error(const damf_fleet* fleet);
 
-/* Waits for the fleet's pushes and frees the fleet (not the contexts). */
+/* Waits for the fleet's pushes and frees the fleet (not the contexts).  A CUDA graph that
+ * captured damf_fleet_step of this fleet must not be replayed afterwards (it reads the
+ * fleet's tables). */
 void damf_fleet_destroy(damf_fleet* fleet);
 
 /* Launch shape of a context's PPR push (damf_set_tuning, damf_get_tuning). */

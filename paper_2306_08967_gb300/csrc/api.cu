@@ -346,6 +346,7 @@ struct damf_fleet {
   cudaStream_t push_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
   long long launches_total = 0;
+  int plan_id = 0;               // changes with every plan; captured launches carry theirs
   // phase timing (damf_fleet_set_timing): per step, events at the fork, before and after the pushes
   int timing = 0;
   std::vector<cudaEvent_t> tev;
@@ -446,6 +447,7 @@ damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent, con
       return fleet_fail(f, DAMF_ERR_INVALID, "fleet: shares exceed the resident push CTAs");
     FleetLaunch L{scaled, (int)descs.size(), 0, (int)slots.size(), 0, (int)table.size()};
     std::vector<int> sfirst(1, 0), gfirst(1, 0);
+    const int plan_id = f->plan_id + 1;
     for (const Slot& sl : slots) {
       for (int gi : sl.graphs) {
         descs.push_back(push_args(&f->ctxs[gi]->c, f->ctxs[gi]->c.push_direct_chunks));
@@ -456,12 +458,17 @@ damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent, con
       sfirst.push_back(L.blocks);
       gfirst.push_back(L.count);
     }
+    table.push_back((int)slots.size());
+    table.push_back(L.blocks);
+    table.push_back(plan_id);
     table.insert(table.end(), sfirst.begin(), sfirst.end());
     table.insert(table.end(), gfirst.begin(), gfirst.end());
     launches.push_back(L);
   }
-  cudaError_t e = cudaSuccess;
-  if (!f->d_descs) e = cudaMalloc(&f->d_descs, sizeof(PushArgs) * (size_t)G);
+  // pushes of earlier steps (direct or replayed from a CUDA graph) may still read the
+  // tables: let them finish before the tables change
+  cudaError_t e = f->launches.empty() ? cudaSuccess : cudaDeviceSynchronize();
+  if (e == cudaSuccess && !f->d_descs) e = cudaMalloc(&f->d_descs, sizeof(PushArgs) * (size_t)G);
   if (e == cudaSuccess && table.size() > f->table_cap) {
     if (f->d_table) cudaFree(f->d_table);
     f->d_table = nullptr;
@@ -473,6 +480,7 @@ damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent, con
   if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet tables", e);
   f->blocks = blocks;
   f->launches = launches;
+  f->plan_id += 1;
   return DAMF_OK;
 }
 
@@ -1104,7 +1112,7 @@ damf_status damf_fleet_step(damf_fleet* f, const damf_batch* batches, void* stre
   for (size_t l = 0; l < f->launches.size(); ++l) {
     const FleetLaunch& L = f->launches[l];
     e = launch_push_group(f->d_descs + L.first_graph, L.count, f->d_table + L.table_off, L.nslots, L.blocks,
-                          L.scaled, f->push_stream);
+                          f->plan_id, L.scaled, f->push_stream);
     if (e != cudaSuccess) {
       for (int i = 0; i < G; ++i) fail(&f->ctxs[i]->c, DAMF_ERR_CUDA, "fleet push", e);
       return fleet_fail(f, DAMF_ERR_CUDA, "fleet push", e);

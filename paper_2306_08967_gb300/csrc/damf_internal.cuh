@@ -247,11 +247,12 @@ struct PushArgs {
 };
 PushArgs push_args(const Ctx* c, int direct_chunks);
 int push_group_max_blocks(int scaled);
-// Grouped push of descs[0 .. ngraphs): table holds sfirst[nslots + 1] (CTA prefix sums, ending at
-// `blocks`) then gfirst[nslots + 1] (graph prefix sums, ending at ngraphs); a slot of several
-// graphs has one CTA.
+// Grouped push of descs[0 .. ngraphs): table holds (nslots, blocks, plan), then sfirst[nslots + 1]
+// (CTA prefix sums, ending at `blocks`), then gfirst[nslots + 1] (graph prefix sums, ending at
+// ngraphs); a slot of several graphs has one CTA. A launch whose (nslots, blocks, plan) differ
+// from the table's does nothing but set DAMF_ERR_INVALID on its graphs.
 cudaError_t launch_push_group(const PushArgs* descs, int ngraphs, const int* table, int nslots, int blocks,
-                              int scaled, cudaStream_t s);
+                              int plan, int scaled, cudaStream_t s);
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s);
 cudaError_t launch_expand_row(Ctx* c, int u, int cnt, int incoming, int32_t* src, int32_t* dst, int8_t* op,
                               cudaStream_t s);

@@ -687,13 +687,21 @@ __device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, 
 // graph selects the row shape; node count and full seeding come from the graph's device header,
 // so one captured launch serves every step.
 template <bool SCALED>
-__global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restrict__ descs,
-                                                       const int* __restrict__ sfirst,
-                                                       const int* __restrict__ gfirst, int nslots) {
+__global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restrict__ descs, const int* __restrict__ table,
+                                                       int nslots, int plan, int ngraphs) {
   __shared__ PushArgs sa;
   __shared__ int s_s, s_n, s_all;
   __shared__ unsigned long long s_t[5];
   __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
+  // a launch captured under an earlier plan of the fleet must not run on this plan's tables:
+  // every CTA returns before any barrier and the graphs' status reports it
+  if (table[0] != nslots || table[1] != (int)gridDim.x || table[2] != plan) {
+    if (blockIdx.x == 0)
+      for (int g = threadIdx.x; g < ngraphs; g += blockDim.x) set_status(descs[g].h, DAMF_ERR_INVALID);
+    return;
+  }
+  const int* __restrict__ sfirst = table + 3;
+  const int* __restrict__ gfirst = sfirst + nslots + 1;
   if (threadIdx.x == 0) {
     int lo = 0, hi = nslots - 1;   // the last slot with sfirst[s] <= blockIdx.x
     while (lo < hi) {
@@ -771,14 +779,12 @@ static int group_max_blocks() {
 int push_group_max_blocks(int scaled) { return scaled ? group_max_blocks<true>() : group_max_blocks<false>(); }
 
 cudaError_t launch_push_group(const PushArgs* descs, int ngraphs, const int* table, int nslots, int blocks,
-                              int scaled, cudaStream_t s) {
+                              int plan, int scaled, cudaStream_t s) {
   if (ngraphs <= 0 || nslots <= 0) return cudaSuccess;
   k_push_reset<<<(ngraphs + 255) / 256, 256, 0, s>>>(descs, ngraphs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int* sfirst = table;
-  const int* gfirst = table + nslots + 1;
-  void* args[] = {(void*)&descs, (void*)&sfirst, (void*)&gfirst, &nslots};
+  void* args[] = {(void*)&descs, (void*)&table, &nslots, &plan, &ngraphs};
   return scaled ? cudaLaunchCooperativeKernel((void*)k_push_group<true>, dim3(blocks), dim3(256), args, 0, s)
                 : cudaLaunchCooperativeKernel((void*)k_push_group<false>, dim3(blocks), dim3(256), args, 0, s);
 }

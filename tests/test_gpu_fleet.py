@@ -352,3 +352,36 @@ def test_captured_fleet_step_replays_like_direct_calls():
     fleet.close()
     for g in gs + twins:
         g.close()
+
+
+def test_captured_step_after_new_shares_reports_instead_of_running():
+    # a captured grouped push carries its plan; after the shares change it must not run on the
+    # new tables: every CTA returns at once and the contexts report DAMF_ERR_INVALID
+    from paper_2306_08967_gb300 import DamfFleet
+    from paper_2306_08967_gb300.api import _batch_array
+    gs, twins = _fleet(SPECS[:3], SEED + 170)
+    fleet = DamfFleet(gs)
+    kmax = 64
+    bufs = [(torch.zeros(kmax, dtype=torch.int32, device="cuda"), torch.zeros(kmax, dtype=torch.int32, device="cuda"),
+             torch.zeros(kmax, dtype=torch.int8, device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"))
+            for _ in gs]
+    arr = _batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for g in gs:
+            g.join(stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        fleet.step_array(arr, stream)
+    graph.replay()                          # the plan it was captured with: fine
+    torch.cuda.synchronize()
+    assert all(g.sync_status() == 0 for g in gs)
+    fleet.set_shares(exponent=0.0)          # a new plan
+    graph.replay()
+    torch.cuda.synchronize()
+    assert all(g.sync_status() == 1 for g in gs)   # DAMF_ERR_INVALID
+    del graph
+    fleet.close()
+    for g in gs + twins:
+        g.close()
