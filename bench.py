@@ -341,6 +341,8 @@ def run_ours(args, c, rank, world):
     g = DamfGraph(ip, ix, cfg, om)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
+    if args.push_blocks or args.push_chunks >= 0:
+        g.set_tuning(args.push_blocks, args.push_chunks)
     # device-resident inputs for every step
     batches = st.batches
     ks = np.array([b.k for b in batches], np.int64)
@@ -452,6 +454,7 @@ def run_ours(args, c, rank, world):
         "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded Chung-Lu graph and edge stream)",
         "config": {"workload": workload_desc(c), "precision": args.precision, "edges_timed": edges,
+                   "push_shape": g.tuning(),
                    "l2": "state %.2f GB (Ub, Vb, Zb, r) > 129 MB L2; no flush" % (4 * st.n_final * d * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU", "refold_every": args.refold_every},
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -823,6 +826,9 @@ def main():
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
+    ap.add_argument("--push-blocks", type=int, default=0, help="push CTAs (0: two per SM)")
+    ap.add_argument("--push-chunks", type=int, default=-1,
+                    help="in-edge chunks a row task scatters itself before its row becomes hub items (-1: 8)")
     ap.add_argument("--graphs", type=int, default=0, help="C4: the first this many graphs of the fleet (0: all)")
     ap.add_argument("--compare-steps", type=int, default=5, help="C4: steps of each comparison launch form")
     ap.add_argument("--tune-steps", type=int, default=3, help="C4: steps per autotuner candidate (< 2: no tuning)")

@@ -291,7 +291,8 @@ damf_status damf_ppr_refresh(damf_ctx* ctx, void* stream);
  * after all work enqueued on `stream` before the call; the next damf_apply_edges on
  * `stream` overlaps its read-only part (net change, projection, residual factors, core
  * SVD, transform update) with that push and waits for it before editing the adjacency
- * and the PPR state.  damf_get_embeddings and damf_get_state wait for it as well.
+ * and the PPR state.  damf_get_embeddings waits for it when Z is requested (X, Y and sigma
+ * are final when the update's work on `stream` is), damf_get_state always.
  * damf_join makes `stream` wait for the most recent push (e.g. before the caller reads
  * results produced by it through other means); damf_record_event records a caller's
  * cudaEvent_t (passed as void*) on the push stream after the most recent push.
@@ -313,6 +314,9 @@ damf_status damf_record_event(damf_ctx* ctx, void* event);
  *   rows (device) int32[count] node ids, or NULL for rows 0..count-1.
  *   X, Y, Z (device) float32[count x d] outputs, sigma (device) float32[d]; any
  *   output may be NULL.
+ * Only Z depends on the push: with Z = NULL the call follows the work enqueued on `stream`
+ * and does not wait for the most recent damf_ppr_refresh, so reading Σ (or X, Y) after each
+ * update leaves that push running beside the next update's factor chain.
  */
 damf_status damf_get_embeddings(damf_ctx* ctx, const int32_t* rows, int32_t count, float* X, float* Y,
                                 float* Z, float* sigma, void* stream);

@@ -847,7 +847,8 @@ damf_status damf_get_embeddings(damf_ctx* x, const int32_t* rows, int32_t count,
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
   if (count < 0 || (!rows && count > c->n)) return fail(c, DAMF_ERR_INVALID, "count", cudaSuccess);
-  DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join push");
+  // only Z reads the push's output; X, Y and sigma follow the update's work on `stream`
+  if (Z) DAMF_CUDA(wait_push(c, (cudaStream_t)stream), "join push");
   DAMF_CUDA(launch_query(c, rows, count, X, Y, Z, sigma, (cudaStream_t)stream), "query");
   return DAMF_OK;
 }

@@ -607,3 +607,25 @@ def test_mixed_precision_matches_plain_fp32():
     np.testing.assert_allclose(sm, sp, rtol=2e-5)
     assert rel_fro(Xm @ Ym.T, Xp @ Yp.T) < 2e-5
     assert rel_fro(Zm @ Ym.T, Zp @ Yp.T) < 1e-3
+
+
+def test_factor_reads_do_not_depend_on_the_push():
+    # X, Y and sigma are final when the update's work on the caller's stream is; reading them
+    # right after damf_ppr_refresh (the push possibly still running) gives what a read after
+    # the push gives, and Z (which waits for the push) is the push's result
+    rng = np.random.default_rng(61)
+    g, _, _ = make_pair(3000, 10.0, 2.2, 64, 0.15, 1e-5, SEED + 140, oracle=False)
+    for _ in range(4):
+        g.apply_edges(*_events(rng, g.n, 60))
+        g.ppr_refresh()
+        early = g.embeddings(want=("X", "Y", "sigma"))
+        g.join()
+        torch.cuda.synchronize()
+        late = g.embeddings(want=("X", "Y", "Z", "sigma"))
+        for k in ("X", "Y", "sigma"):
+            assert torch.equal(early[k], late[k]), k
+        st = g.state()
+        Z = ((st["Zb"].double() / st["s0"].double()) @ st["PU"].double()) * st["sigma"].double().sqrt()
+        assert torch.allclose(late["Z"].double(), Z, rtol=1e-4, atol=1e-6)
+    g.check()
+    g.close()
