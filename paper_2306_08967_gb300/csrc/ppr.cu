@@ -385,7 +385,23 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
       if (pre0 && lane < min(deg, 32)) d0 = __ldg(outdeg + w0);
       const int dout = aux;
       const float thr_u = threshold<SCALED>(eps, dout);
-      if (group_max<LPR>(max_abs4(v)) > thr_u) {   // the same in every group: warp-uniform
+      bool go = group_max<LPR>(max_abs4(v)) > thr_u;   // the same in every group: warp-uniform
+      if (!go) {
+        // about to let u go: the read above may have passed the flag's clear, so an add whose
+        // adder still found the flag set (its claim is a release) could be missing from v.
+        // After a fence that orders the clear first, a second read must see every such add.
+        __syncwarp();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
+        if (RPW > 1) {
+          v.x = __shfl_sync(kFull, v.x, q);
+          v.y = __shfl_sync(kFull, v.y, q);
+          v.z = __shfl_sync(kFull, v.z, q);
+          v.w = __shfl_sync(kFull, v.w, q);
+        }
+        go = group_max<LPR>(max_abs4(v)) > thr_u;
+      }
+      if (go) {
         float lm = 0.f;                           // max |r[u]| right after the removal of v
         __syncwarp();
         asm volatile("fence.acq_rel.gpu;" ::: "memory");   // the flag's clear comes first
