@@ -9,6 +9,16 @@ PPR residual fix-up) followed by damf_ppr_refresh (push until every residual <= 
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the same
 workload (bounded sample per step) and prints the same metric with "impl": "reference".
+
+Other workloads (not the default line):
+  --config C3                     the 2M-node graph, batches of 1-256 events, the fold every 256
+  --config C4 [--graphs G]        many graphs per step: a fleet (every graph's update on its own
+                                  stream, one grouped push), each step one CUDA graph replay
+                                  after the push shares are autotuned; beside it the same step
+                                  graph by graph, by damf_step_multi and by direct fleet calls
+  --config C5 [--rates a,b,c]     serving: sessions admitted by device memory, Poisson requests
+                                  in phases of rising rate, continuous batching of fleet steps
+  --mode node-stream              the paper's node-arrival protocol, ms per node event
 """
 
 import argparse
