@@ -997,6 +997,7 @@ def run_serving(args, sw):
         open_one()
     t_init = time.perf_counter()
     srv.poll()                              # the first admissions (graph initialisations)
+    srv.wait_admissions()
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t_init
     print("[serving] %d graphs initialised in %.1f s" % (len(srv.graphs), init_s), file=sys.stderr, flush=True)

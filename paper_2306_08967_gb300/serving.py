@@ -15,14 +15,16 @@ Sessions (one graph each) open, receive edge-update requests and close. The sche
 * release: a closed session's memory returns to the budget once every step it took part in
   has completed.
 
-The Server couples the scheduler to the library: each admitted graph is a DamfGraph; each step
-is one damf_fleet_step over the resident graphs (graphs without a request take an empty batch),
-its events copied from pinned host memory in one transfer.
+The Server couples the scheduler to the library: each admitted graph is a DamfGraph, built on
+a worker thread and its own stream so that the loop keeps serving the resident graphs while it
+initialises; each step is one damf_fleet_step over the resident graphs (graphs without a
+request take an empty batch), its events copied from pinned host memory in one transfer.
 """
 
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import time
 from typing import Deque, Dict, List, Optional
@@ -190,6 +192,9 @@ class Server:
         self.t0 = time.perf_counter()
         self.steps_issued = 0
         self.kernels = 0           # kernels of graphs and fleets already closed
+        self.init_pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        self.init_stream = None
+        self.initializing = {}     # sid -> future of its DamfGraph
         self.ring = []             # staging buffers (pinned host, device), reused round robin
         self.ring_rows = 0
         self.ring_pos = 0
@@ -226,12 +231,30 @@ class Server:
             self.fleet.set_shares(exponent=self.share_exponent)
         self.fleet_sids = sids
 
-    def _admit(self):
+    def _build(self, spec):
+        # worker thread: the graph's initialisation on its own stream (the library synchronises
+        # that stream before returning), beside the steps the loop keeps issuing
         from .api import DamfGraph
+        torch = self.torch
+        with torch.cuda.stream(self.init_stream):
+            g = DamfGraph(*spec, stream=self.init_stream)
+            self.init_stream.synchronize()
+        return g
+
+    def _admit(self, block: bool = False):
+        if self.init_stream is None:
+            self.init_stream = self.torch.cuda.Stream()
         for sid in self.sched.admissions(self.now()):
-            ip, ix, cfg, om = self.specs.pop(sid)
-            self.graphs[sid] = DamfGraph(ip, ix, cfg, om)
-            self.sched.admitted(sid)
+            self.initializing[sid] = self.init_pool.submit(self._build, self.specs.pop(sid))
+        for sid, fut in list(self.initializing.items()):
+            if block or fut.done():
+                self.graphs[sid] = fut.result()
+                del self.initializing[sid]
+                self.sched.admitted(sid)
+
+    def wait_admissions(self):
+        """Blocks until every graph being initialised is resident."""
+        self._admit(block=True)
 
     def _issue(self) -> bool:
         torch = self.torch
@@ -333,6 +356,9 @@ class Server:
                 if self.to_destroy and not self.inflight:
                     self._retire(block=False)
                 continue
+            if self.initializing:
+                self._admit(block=True)
+                continue
             return True
         return False
 
@@ -347,6 +373,8 @@ class Server:
 
     def shutdown(self, max_seconds: float = 600.0):
         self.drain(max_seconds)
+        self._admit(block=True)
+        self.init_pool.shutdown(wait=True)
         self.torch.cuda.synchronize()
         if self.fleet is not None:
             self.fleet.close()
