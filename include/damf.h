@@ -199,9 +199,9 @@ damf_status damf_fleet_step(damf_fleet* fleet, const damf_batch* batches, void* 
  * threshold mode summing to at most the resident push CTAs), or with blocks = NULL shares in
  * proportion to (d (n + m))^exponent, exponent in [0, 4]: a graph whose share is below one CTA
  * shares a CTA with other such graphs (first fit, largest first).  Also takes each
- * context's push_direct_chunks (damf_set_tuning) as it is now.  Synchronous: waits for all
- * device work (pushes already enqueued or replayed read the old tables); not while a capture
- * is in progress.  A CUDA graph that captured a step of this fleet must be captured again:
+ * context's push_direct_chunks (damf_set_tuning) as it is now.  Synchronous: once the fleet
+ * has taken a step it waits for all device work (pushes already enqueued or replayed read the
+ * old tables); not while a capture is in progress.  A CUDA graph that captured a step of this fleet must be captured again:
  * its grouped push no longer matches the tables, and a replay only sets DAMF_ERR_INVALID on
  * the fleet's contexts.  DAMF_ERR_INVALID (shares unchanged) for bad values. */
 damf_status damf_fleet_set_shares(damf_fleet* fleet, const int32_t* blocks, double exponent);

@@ -347,6 +347,7 @@ struct damf_fleet {
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
   long long launches_total = 0;
   int plan_id = 0;               // changes with every plan; captured launches carry theirs
+  int stepped = 0;               // damf_fleet_step was called (directly or while capturing)
   // phase timing (damf_fleet_set_timing): per step, events at the fork, before and after the pushes
   int timing = 0;
   std::vector<cudaEvent_t> tev;
@@ -466,8 +467,8 @@ damf_status fleet_plan(damf_fleet* f, const int32_t* given, double exponent, con
     launches.push_back(L);
   }
   // pushes of earlier steps (direct or replayed from a CUDA graph) may still read the
-  // tables: let them finish before the tables change
-  cudaError_t e = f->launches.empty() ? cudaSuccess : cudaDeviceSynchronize();
+  // tables: let them finish before the tables change (a fleet never stepped has none)
+  cudaError_t e = f->stepped ? cudaDeviceSynchronize() : cudaSuccess;
   if (e == cudaSuccess && !f->d_descs) e = cudaMalloc(&f->d_descs, sizeof(PushArgs) * (size_t)G);
   if (e == cudaSuccess && table.size() > f->table_cap) {
     if (f->d_table) cudaFree(f->d_table);
@@ -1093,6 +1094,7 @@ damf_status damf_fleet_step(damf_fleet* f, const damf_batch* batches, void* stre
     if (f->ctxs[i]->c.sticky) return (damf_status)f->ctxs[i]->c.sticky;
   }
   cudaStream_t caller = (cudaStream_t)stream;
+  f->stepped = 1;
   cudaError_t e = fleet_mark(f, caller);
   if (e == cudaSuccess) e = cudaEventRecord(f->ev_fork, caller);
   if (e != cudaSuccess) return fleet_fail(f, DAMF_ERR_CUDA, "fleet fork", e);
