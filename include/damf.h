@@ -230,6 +230,17 @@ damf_status damf_fleet_get_shares(const damf_fleet* fleet, int32_t* blocks, int3
  * updates' kernels count in each context's damf_stats.launches. */
 int64_t damf_fleet_launches(const damf_fleet* fleet);
 
+/* The CTA plan of one grouped push, on the host (what damf_fleet_set_shares and
+ * damf_fleet_set_weights compute; exposed for capacity planning and tests).  weights (host
+ * double[count], each > 0): the graphs' work; max_blocks: the resident push CTAs.  Graph i's
+ * fair share is x_i = max_blocks w_i / sum(w); a graph with x_i >= 1 owns floor(x_i) CTAs,
+ * the others are packed largest-first into one-CTA slots of total share <= 1, CTAs left over
+ * go to the owners by largest remainder (if the slots do not fit, the packing limit grows by
+ * 1.25x until they do).  Writes slot_of[i] (host int32[count]) and ctas[s] (host int32[count];
+ * a slot holding several graphs has one CTA).  Returns the number of slots; -1 for bad
+ * arguments. */
+int32_t damf_plan_slots(const double* weights, int32_t count, int32_t max_blocks, int32_t* slot_of, int32_t* ctas);
+
 /* Text of the fleet's most recent error. */
 const char* damf_fleet_last_error(const damf_fleet* fleet);
 

@@ -112,6 +112,19 @@ def step_multi(batches, stream=None):
         raise DamfError(st, "step_multi")
 
 
+def plan_slots(weights, max_blocks: int):
+    """The grouped push's CTA plan for work weights (damf_plan_slots, host only): returns
+    (slot of each graph, CTAs of each slot)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    slot_of = np.zeros(w.size, dtype=np.int32)
+    ctas = np.zeros(max(w.size, 1), dtype=np.int32)
+    n = int(_lib.load().damf_plan_slots(w.ctypes.data_as(ctypes.c_void_p), int(w.size), int(max_blocks),
+                                        slot_of.ctypes.data_as(ctypes.c_void_p), ctas.ctypes.data_as(ctypes.c_void_p)))
+    if n < 0:
+        raise DamfError(1, "plan_slots")
+    return slot_of, ctas[:n]
+
+
 class DamfFleet:
     """Many graphs stepped together, their pushes in one grouped launch (damf_fleet_*).
     The DamfGraphs stay owned by the caller and must outlive the fleet."""

@@ -373,26 +373,17 @@ struct Slot {
 // (d (n + m))^exponent: a graph with x_j >= cap owns floor(x_j) CTAs (at least one), the rest are
 // packed first-fit-decreasing into one-CTA bins of total share <= cap, and CTAs left over go
 // to the owners by largest remainders; cap starts at 1 and grows until the slots fit.
-bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, const int32_t* given, double exponent,
-                const double* weights, std::vector<Slot>* out) {
-  out->clear();
-  if (given) {
-    long long tot = 0;
-    for (int i : idx) {
-      out->push_back(Slot{given[i], {i}});
-      tot += given[i];
-    }
-    return tot <= maxb;
-  }
-  const int cnt = (int)idx.size();
+// Slots of `w.size()` graphs with work weights w over at most maxb CTAs (Slot.graphs holds
+// positions in w): graph j's fair share is x_j = maxb w_j / sum(w); a graph with x_j >= cap
+// owns floor(x_j) CTAs (at least one), the rest are packed first-fit-decreasing into one-CTA
+// bins of total share <= cap, and CTAs left over go to the owners by largest remainders; cap
+// starts at 1 and grows until the slots fit.
+void pack_slots(const std::vector<double>& w, int maxb, std::vector<Slot>* out) {
+  const int cnt = (int)w.size();
   std::vector<double> x(cnt);
   double wsum = 0.0;
-  for (int j = 0; j < cnt; ++j) {
-    const Ctx& c = f->ctxs[idx[j]]->c;
-    x[j] = weights ? weights[idx[j]] : std::pow((double)c.d * (double)(c.n + c.m_init + 1), exponent);
-    wsum += x[j];
-  }
-  for (int j = 0; j < cnt; ++j) x[j] = maxb * x[j] / wsum;
+  for (int j = 0; j < cnt; ++j) wsum += w[j];
+  for (int j = 0; j < cnt; ++j) x[j] = maxb * w[j] / wsum;
   std::vector<int> by_x(cnt);
   for (int j = 0; j < cnt; ++j) by_x[j] = j;
   std::sort(by_x.begin(), by_x.end(), [&](int a, int b) { return x[a] > x[b] || (x[a] == x[b] && a < b); });
@@ -401,7 +392,7 @@ bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, cons
     std::vector<double> bin_load, rem;
     for (int j : by_x) {
       if (x[j] >= cap) {
-        owners.push_back(Slot{std::max(1, (int)std::floor(x[j])), {idx[j]}});
+        owners.push_back(Slot{std::max(1, (int)std::floor(x[j])), {j}});
         rem.push_back(x[j] - std::floor(x[j]));
         continue;
       }
@@ -411,7 +402,7 @@ bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, cons
         bins.push_back(Slot{1, {}});
         bin_load.push_back(0.0);
       }
-      bins[b].graphs.push_back(idx[j]);
+      bins[b].graphs.push_back(j);
       bin_load[b] += x[j];
     }
     long long used = (long long)bins.size();
@@ -424,8 +415,33 @@ bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, cons
       owners[order[k % (long long)owners.size()]].blocks += 1;
     *out = owners;
     out->insert(out->end(), bins.begin(), bins.end());
-    return true;
+    return;
   }
+}
+
+// Slots of one threshold mode's graphs (idx, fleet positions) over at most maxb CTAs: with
+// `given`, one slot per graph with those CTAs; otherwise pack_slots on the weights (given, or
+// (d (n + m))^exponent).
+bool plan_slots(const damf_fleet* f, const std::vector<int>& idx, int maxb, const int32_t* given, double exponent,
+                const double* weights, std::vector<Slot>* out) {
+  out->clear();
+  if (given) {
+    long long tot = 0;
+    for (int i : idx) {
+      out->push_back(Slot{given[i], {i}});
+      tot += given[i];
+    }
+    return tot <= maxb;
+  }
+  std::vector<double> w(idx.size());
+  for (size_t j = 0; j < idx.size(); ++j) {
+    const Ctx& c = f->ctxs[idx[j]]->c;
+    w[j] = weights ? weights[idx[j]] : std::pow((double)c.d * (double)(c.n + c.m_init + 1), exponent);
+  }
+  pack_slots(w, maxb, out);
+  for (Slot& sl : *out)
+    for (int& g : sl.graphs) g = idx[g];
+  return true;
 }
 
 // Builds every launch's slots and uploads the descriptor and slot tables; the fleet's plan
@@ -1030,6 +1046,20 @@ void damf_destroy(damf_ctx* x) {
   cudaDeviceSynchronize();
   free_all(&x->c);
   free(x);
+}
+
+int32_t damf_plan_slots(const double* weights, int32_t count, int32_t max_blocks, int32_t* slot_of, int32_t* ctas) {
+  if (!weights || !slot_of || !ctas || count < 1 || max_blocks < 1) return -1;
+  std::vector<double> w(weights, weights + count);
+  for (double x : w)
+    if (!(x > 0.0 && x < 1e300)) return -1;
+  std::vector<Slot> slots;
+  pack_slots(w, max_blocks, &slots);
+  for (size_t s = 0; s < slots.size(); ++s) {
+    ctas[s] = slots[s].blocks;
+    for (int g : slots[s].graphs) slot_of[g] = (int32_t)s;
+  }
+  return (int32_t)slots.size();
 }
 
 damf_status damf_fleet_create(damf_ctx* const* ctxs, int32_t count, damf_fleet** out) {
