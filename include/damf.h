@@ -230,6 +230,18 @@ damf_status damf_fleet_get_shares(const damf_fleet* fleet, int32_t* blocks, int3
  * updates' kernels count in each context's damf_stats.launches. */
 int64_t damf_fleet_launches(const damf_fleet* fleet);
 
+/*
+ * Failure detection without a GPU fault: runs one of the push's bounded waits against a
+ * condition that never comes true, with an iteration limit of `limit` (1 .. the library's own
+ * limit; each iteration sleeps up to about a microsecond), and writes the device status the
+ * wait left in *status_out: DAMF_ERR_TIMEOUT (5) when it gave up as it must.  which = 0: the
+ * grid barrier, counting one CTA more than are launched; which = 1: the wait for a queue
+ * position that nobody fills while a task is still counted.  Uses its own small device
+ * allocation (no context) and synchronises `stream`; the device stays usable.
+ * DAMF_ERR_INVALID for bad arguments, DAMF_ERR_CUDA when a CUDA call fails.
+ */
+damf_status damf_selftest_wait(int32_t which, int64_t limit, int32_t* status_out, void* stream);
+
 /* The CTA plan of one grouped push, on the host (what damf_fleet_set_shares and
  * damf_fleet_set_weights compute; exposed for capacity planning and tests).  weights (host
  * double[count], each > 0): the graphs' work; max_blocks: the resident push CTAs.  Graph i's

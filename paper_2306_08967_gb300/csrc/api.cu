@@ -1048,6 +1048,28 @@ void damf_destroy(damf_ctx* x) {
   free(x);
 }
 
+damf_status damf_selftest_wait(int32_t which, int64_t limit, int32_t* status_out, void* stream) {
+  if (!status_out || (which != 0 && which != 1) || limit < 1 || limit > (int64_t)kSpinLimit) return DAMF_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevHeader* h = nullptr;
+  int32_t* q = nullptr;
+  cudaError_t e = cudaMalloc(&h, sizeof(DevHeader));
+  if (e == cudaSuccess) e = cudaMalloc(&q, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h, 0, sizeof(DevHeader), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q, 0xff, sizeof(int32_t), s);   // the position stays empty (-1)
+  const unsigned long long one_task = 1ull << 32;                          // one unfinished task, tail 0
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h->qstate, &one_task, sizeof(one_task), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_wait_selftest(h, q, which, (long long)limit, s);
+  int32_t st = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &h->status, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (h) cudaFree(h);
+  if (q) cudaFree(q);
+  if (e != cudaSuccess) return DAMF_ERR_CUDA;
+  *status_out = st;
+  return DAMF_OK;
+}
+
 int32_t damf_plan_slots(const double* weights, int32_t count, int32_t max_blocks, int32_t* slot_of, int32_t* ctas) {
   if (!weights || !slot_of || !ctas || count < 1 || max_blocks < 1) return -1;
   std::vector<double> w(weights, weights + count);

@@ -185,7 +185,8 @@ __device__ __forceinline__ void set_status(DevHeader* h, int code) {
 
 // Bounded sense-free grid barrier: every block must call it the same number of times.
 // Returns false (and records DAMF_ERR_TIMEOUT) when a wait runs out.
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigned int nblocks,
+                                             long long limit = kSpinLimit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -201,7 +202,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigne
     } else {
       long long it = 0;
       while (*vgen == gen) {
-        if (++it > kSpinLimit) {
+        if (++it > limit) {
           ok = 0;
           set_status(h, DAMF_ERR_TIMEOUT);
           break;
@@ -231,6 +232,7 @@ cudaError_t launch_core(Ctx* c, cudaStream_t s);
 cudaError_t launch_transforms(Ctx* c, cudaStream_t s);
 cudaError_t launch_scatter(Ctx* c, cudaStream_t s);
 int push_default_direct_chunks();
+cudaError_t launch_wait_selftest(DevHeader* h, int32_t* queue, int which, long long limit, cudaStream_t s);
 // One graph's push operands (the grouped push reads them from device memory).
 struct PushArgs {
   DevHeader* h;

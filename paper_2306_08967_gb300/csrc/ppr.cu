@@ -267,7 +267,8 @@ __device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, co
 
 // Waits (lane 0) for queue position p: returns its entry, or -1 when no task is left (the
 // unfinished count is 0), the device status is set, or the wait runs out (DAMF_ERR_TIMEOUT).
-__device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long p, long long qcap) {
+__device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long p, long long qcap,
+                                         long long limit = kSpinLimit) {
   for (long long it = 0;; ++it) {
     if (p < qcap) {
       const int e = ld_acquire(queue + p);
@@ -278,7 +279,7 @@ __device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long
     }
     if ((ld_volatile64(&h->qstate) >> 32) == 0ull) return -1;
     if (*reinterpret_cast<volatile int*>(&h->status) != 0) return -1;
-    if (it > kSpinLimit) {
+    if (it > limit) {
       set_status(h, DAMF_ERR_TIMEOUT);
       return -1;
     }
@@ -841,6 +842,24 @@ static cudaError_t push_dispatch(Ctx* c, int check_all, cudaStream_t s) {
 }
 
 int push_default_direct_chunks() { return kPushDirectChunks; }
+
+// Failure detection without a fault: the push's own bounded waits, run against conditions that
+// never come true, must give up after `limit` iterations, record DAMF_ERR_TIMEOUT and return.
+// which = 0: a grid barrier that counts one CTA more than the launch has (this one CTA
+// waits for a second that never arrives); which = 1: a wait for a queue position that nobody
+// fills while one task is still counted as unfinished.
+__global__ void k_wait_selftest(DevHeader* h, int32_t* queue, int which, long long limit) {
+  if (which == 0) {
+    grid_barrier(&h->bar, h, gridDim.x + 1, limit);
+  } else if (threadIdx.x == 0) {
+    wait_slot(h, queue, 0, 1, limit);
+  }
+}
+
+cudaError_t launch_wait_selftest(DevHeader* h, int32_t* queue, int which, long long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(h, queue, which, limit);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_push(Ctx* c, int check_all, cudaStream_t s) {
   return c->cfg.threshold ? push_dispatch<true>(c, check_all, s) : push_dispatch<false>(c, check_all, s);

@@ -62,3 +62,14 @@ def test_init_rejects_bad_arguments_without_gpu_work():
     assert lib.damf_ppr_refresh(None, None) == 1
     assert lib.damf_score_pairs(None, None, None, 0, 0, 0, None, None) == 1
     assert lib.damf_topk(None, None, 0, 1, 0, 0, None, None, None) == 1
+
+
+def test_wait_selftest_rejects_bad_arguments_without_gpu_work():
+    from paper_2306_08967_gb300 import _lib
+    lib = _lib.load()
+    st = ctypes.c_int32(-1)
+    assert lib.damf_selftest_wait(2, 1000, ctypes.byref(st), None) == 1     # which: 0 or 1
+    assert lib.damf_selftest_wait(0, 0, ctypes.byref(st), None) == 1        # limit >= 1
+    assert lib.damf_selftest_wait(0, 1 << 40, ctypes.byref(st), None) == 1  # above the library's limit
+    assert lib.damf_selftest_wait(0, 1000, None, None) == 1
+    assert st.value == -1

@@ -1,0 +1,33 @@
+"""Failure detection without a GPU fault: the push's bounded waits, run against conditions
+that never come true (a grid barrier short of one CTA; a queue position nobody fills while a
+task is still counted), give up after their iteration limit, leave DAMF_ERR_TIMEOUT in the
+device status for the host to read, and the device stays usable afterwards."""
+
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import make_pair
+
+pytestmark = pytest.mark.gpu
+
+DAMF_ERR_TIMEOUT = 5
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_waits_give_up_and_report(which):
+    from paper_2306_08967_gb300 import _lib
+    lib = _lib.load()
+    st = ctypes.c_int32(-1)
+    t0 = time.perf_counter()
+    assert lib.damf_selftest_wait(which, 200_000, ctypes.byref(st), None) == 0
+    assert st.value == DAMF_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    # the device and the library stay usable: a graph initialises, updates and pushes
+    g, _, _ = make_pair(400, 6.0, 2.5, 16, 0.15, 1e-4, 0xDA3F0000 + 600 + which, oracle=False)
+    g.apply_edges(np.array([1, 2], np.int32), np.array([5, 9], np.int32), np.array([1, 1], np.int8))
+    g.ppr_refresh()
+    g.check()
+    g.close()
