@@ -385,6 +385,44 @@ damf_status damf_get_state(damf_ctx* ctx, float* Ub, float* Vb, float* Zb, float
                            float* sigma, float* s0, void* stream);
 
 /*
+ * Checkpoint and resume.  A context's full state, in buffers the caller owns: U_b, V_b, Z_b,
+ * r (device) float32[n x d]; P_U, P_V and their inverses (device) float32[d x d] (the
+ * library updates the inverses incrementally, so they are saved rather than recomputed);
+ * Sigma and s0 (device) float32[d]; and the host count of updates since the last fold.
+ */
+typedef struct {
+  float* Ub;
+  float* Vb;
+  float* Zb;
+  float* r;
+  float* PU;
+  float* PV;
+  float* PUi;
+  float* PVi;
+  float* sigma;
+  float* s0;
+  int32_t updates_since_fold;
+} damf_state;
+
+/* Copies the state into st's buffers on `stream` after the most recent push (n = the
+ * context's current node count, damf_num_nodes) and sets st->updates_since_fold.  With the
+ * adjacency from damf_export_adjacency (outgoing) it is everything damf_restore needs. */
+damf_status damf_save_state(damf_ctx* ctx, damf_state* st, void* stream);
+
+/*
+ * Creates a context from a saved state instead of a factorisation: cfg as for the original
+ * (cfg->n = the saved node count; capacities may differ), the adjacency in CSR (device,
+ * int32 row_ptr[n+1] and col_idx[m], rows in the exported order), the saved buffers (device;
+ * read, not kept).  The result continues the original: the same further calls give
+ * bit-identical factors and adjacency (the push, whose add order depends on timing, keeps its
+ * eps bound); the next push starts from every row.  A directed graph's in-adjacency is rebuilt
+ * from the out-adjacency.  Synchronises `stream`.  DAMF_ERR_INVALID for a bad cfg or a NULL
+ * buffer.
+ */
+damf_status damf_restore(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
+                         const damf_state* saved, void* stream, damf_ctx** out);
+
+/*
  * Copies the current adjacency into (host) CSR buffers: row_ptr int64[n+1] and
  * col int32[col_capacity] (row order as stored, not sorted).  outgoing = 1 gives the
  * out-adjacency A[u][.], 0 the in-adjacency (same as outgoing for undirected graphs).

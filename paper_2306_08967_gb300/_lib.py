@@ -24,6 +24,11 @@ class Batch(ctypes.Structure):
                 ("k", c_i32), ("new_nodes", c_i32), ("k_dev", ctypes.c_void_p)]
 
 
+class State(ctypes.Structure):
+    _fields_ = [("Ub", c_vp), ("Vb", c_vp), ("Zb", c_vp), ("r", c_vp), ("PU", c_vp), ("PV", c_vp), ("PUi", c_vp),
+                ("PVi", c_vp), ("sigma", c_vp), ("s0", c_vp), ("updates_since_fold", c_i32)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("push_blocks", c_i32), ("push_direct_chunks", c_i32)]
 
@@ -43,6 +48,9 @@ SIGNATURES = {
     "damf_rsvd_width": (c_i32, [ctypes.POINTER(Config)]),
     "damf_init_factorize": (c_i32, [ctypes.POINTER(Config), c_vp, c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "damf_apply_edges": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
+    "damf_save_state": (c_i32, [c_vp, ctypes.POINTER(State), c_vp]),
+    "damf_restore": (c_i32, [ctypes.POINTER(Config), c_vp, c_vp, c_i64, ctypes.POINTER(State), c_vp,
+                             ctypes.POINTER(c_vp)]),
     "damf_apply_edges_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp]),
     "damf_apply_edges_counted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
     "damf_apply_edges_multi": (c_i32, [c_vp, c_i32, c_vp]),

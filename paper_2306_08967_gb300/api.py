@@ -228,6 +228,46 @@ class DamfGraph:
         if st != 0:
             raise DamfError(st, self.lib.damf_last_error(self.h).decode())
 
+    def save(self, stream=None) -> dict:
+        """A checkpoint: the full state (CUDA tensors), the out-adjacency (host CSR) and the
+        config; DamfGraph.restore(checkpoint) continues from it."""
+        n, d = self.n, self.d
+        t = {k: torch.empty((n, d), dtype=torch.float32, device="cuda") for k in ("Ub", "Vb", "Zb", "r")}
+        t.update({k: torch.empty((d, d), dtype=torch.float32, device="cuda") for k in ("PU", "PV", "PUi", "PVi")})
+        t.update({k: torch.empty(d, dtype=torch.float32, device="cuda") for k in ("sigma", "s0")})
+        st = _lib.State(**{k: v.data_ptr() for k, v in t.items()})
+        self._check(self.lib.damf_save_state(self.h, ctypes.byref(st), _stream_ptr(stream)))
+        rp, col = self.adjacency(outgoing=True)
+        cfg = Config()
+        ctypes.memmove(ctypes.byref(cfg), ctypes.byref(self.cfg), ctypes.sizeof(Config))
+        cfg.n = n
+        return {"state": t, "updates_since_fold": int(st.updates_since_fold), "indptr": rp.astype(np.int32),
+                "indices": col.copy(), "cfg": cfg}
+
+    @classmethod
+    def restore(cls, ckpt: dict, stream=None) -> "DamfGraph":
+        """A new context continuing a checkpoint from DamfGraph.save (damf_restore)."""
+        self = cls.__new__(cls)
+        self.lib = _lib.load()
+        cfg = ckpt["cfg"]
+        self.cfg = cfg
+        self.d = cfg.d
+        self.directed = bool(cfg.directed)
+        ip = _dev(ckpt["indptr"], torch.int32)
+        ix = _dev(ckpt["indices"], torch.int32) if len(ckpt["indices"]) else torch.zeros(1, dtype=torch.int32,
+                                                                                         device="cuda")
+        t = ckpt["state"]
+        st = _lib.State(**{k: v.data_ptr() for k, v in t.items()},
+                        updates_since_fold=int(ckpt["updates_since_fold"]))
+        h = ctypes.c_void_p()
+        code = self.lib.damf_restore(ctypes.byref(cfg), ctypes.c_void_p(ip.data_ptr()), ctypes.c_void_p(ix.data_ptr()),
+                                     int(len(ckpt["indices"])), ctypes.byref(st), _stream_ptr(stream),
+                                     ctypes.byref(h))
+        if code != 0:
+            raise DamfError(code, "restore")
+        self.h = h
+        return self
+
     @property
     def n(self) -> int:
         return int(self.lib.damf_num_nodes(self.h))

@@ -537,12 +537,11 @@ size_t damf_bytes_required(const damf_config* cfg) {
 
 int32_t damf_rsvd_width(const damf_config* cfg) { return cfg_ok(cfg) ? width_of(cfg) : 0; }
 
-damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
-                                const float* omega, void* stream, damf_ctx** out) {
-  if (!out) return DAMF_ERR_INVALID;
-  *out = nullptr;
-  if (!cfg_ok(cfg) || !row_ptr || !omega || m < 0 || (m > 0 && !col_idx)) return DAMF_ERR_INVALID;
-  if (width_of(cfg) < cfg->d + 1 && cfg->rsvd_oversample > 0) return DAMF_ERR_INVALID;
+// A context for cfg and the adjacency (row_ptr, col_idx): with omega, its initial state by the
+// randomized t-SVD and a push from every row (damf_init_factorize); with saved, the state
+// copied from a damf_save_state (damf_restore).
+static damf_status ctx_open(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
+                            const float* omega, const damf_state* saved, void* stream, damf_ctx** out) {
   cudaStream_t s = (cudaStream_t)stream;
   damf_ctx* x = (damf_ctx*)calloc(1, sizeof(damf_ctx));
   if (!x) return DAMF_ERR_CUDA;
@@ -630,8 +629,21 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
   c->push_direct_chunks = -1;
-  if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
-  if (e == cudaSuccess) e = launch_push(c, 1, s);
+  if (!saved) {
+    if (e == cudaSuccess) e = init_factorize(c, row_ptr, col_idx, m, omega, s);
+    if (e == cudaSuccess) e = launch_push(c, 1, s);
+  } else {
+    const size_t nd = (size_t)cfg->n * cfg->d * sizeof(float), dd = (size_t)cfg->d * cfg->d * sizeof(float);
+    const size_t dv = (size_t)cfg->d * sizeof(float);
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    float* dst[10] = {c->Ub, c->Vb, c->Zb, c->r, c->PU, c->PV, c->PUi, c->PVi, c->sigma, c->s0};
+    const float* src[10] = {saved->Ub, saved->Vb, saved->Zb, saved->r, saved->PU, saved->PV, saved->PUi, saved->PVi,
+                            saved->sigma, saved->s0};
+    const size_t sz[10] = {nd, nd, nd, nd, dd, dd, dd, dd, dv, dv};
+    for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaMemcpyAsync(dst[i], src[i], sz[i], kd, s);
+    c->updates_since_fold = saved->updates_since_fold;
+    c->check_all_next = 1;   // the next push looks at every row (whatever was pending at the save)
+  }
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_push, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -651,6 +663,46 @@ damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, 
       c->allocs[c->nallocs++] = c->dev_stage;
   }
   *out = x;
+  return DAMF_OK;
+}
+
+damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                const float* omega, void* stream, damf_ctx** out) {
+  if (!out) return DAMF_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg_ok(cfg) || !row_ptr || !omega || m < 0 || (m > 0 && !col_idx)) return DAMF_ERR_INVALID;
+  if (width_of(cfg) < cfg->d + 1 && cfg->rsvd_oversample > 0) return DAMF_ERR_INVALID;
+  return ctx_open(cfg, row_ptr, col_idx, m, omega, nullptr, stream, out);
+}
+
+damf_status damf_restore(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
+                         const damf_state* saved, void* stream, damf_ctx** out) {
+  if (!out) return DAMF_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg_ok(cfg) || !row_ptr || !saved || m < 0 || (m > 0 && !col_idx)) return DAMF_ERR_INVALID;
+  if (!saved->Ub || !saved->Vb || !saved->Zb || !saved->r || !saved->PU || !saved->PV || !saved->PUi ||
+      !saved->PVi || !saved->sigma || !saved->s0 || saved->updates_since_fold < 0)
+    return DAMF_ERR_INVALID;
+  return ctx_open(cfg, row_ptr, col_idx, m, nullptr, saved, stream, out);
+}
+
+damf_status damf_save_state(damf_ctx* x, damf_state* st, void* stream) {
+  if (!x || !st) return DAMF_ERR_INVALID;
+  Ctx* c = &x->c;
+  if (c->sticky) return (damf_status)c->sticky;
+  if (!st->Ub || !st->Vb || !st->Zb || !st->r || !st->PU || !st->PV || !st->PUi || !st->PVi || !st->sigma ||
+      !st->s0)
+    return reject(c, "save_state: a NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nd = (size_t)c->n * c->d * sizeof(float), dd = (size_t)c->d * c->d * sizeof(float);
+  const size_t dv = (size_t)c->d * sizeof(float);
+  const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+  DAMF_CUDA(wait_push(c, s), "join push");
+  float* dst[10] = {st->Ub, st->Vb, st->Zb, st->r, st->PU, st->PV, st->PUi, st->PVi, st->sigma, st->s0};
+  const float* src[10] = {c->Ub, c->Vb, c->Zb, c->r, c->PU, c->PV, c->PUi, c->PVi, c->sigma, c->s0};
+  const size_t sz[10] = {nd, nd, nd, nd, dd, dd, dd, dd, dv, dv};
+  for (int i = 0; i < 10; ++i) DAMF_CUDA(cudaMemcpyAsync(dst[i], src[i], sz[i], kd, s), "save");
+  st->updates_since_fold = c->updates_since_fold;
   return DAMF_OK;
 }
 
