@@ -13,7 +13,12 @@ Sessions (one graph each) open, receive edge-update requests and close. The sche
   up to `run_ahead` steps are in flight at once, and sessions are admitted and released
   between steps as memory frees up;
 * release: a closed session's memory returns to the budget once every step it took part in
-  has completed.
+  has completed;
+* eviction: when the first waiting session does not fit, resident sessions that are idle (no
+  request waiting or running) are evicted, least recently active first, if that makes room:
+  their graph is checkpointed to host memory and freed, and a request for an evicted session
+  puts it back in the admission queue, where it is restored from the checkpoint (the restored
+  graph continues exactly where it stopped).
 
 The Server couples the scheduler to the library: each admitted graph is a DamfGraph, built on
 a worker thread and its own stream so that the loop keeps serving the resident graphs while it
@@ -54,12 +59,15 @@ class Request:
 class Session:
     sid: int
     nbytes: int
-    state: str = "waiting"          # waiting -> admitting -> resident -> released -> freed
+    state: str = "waiting"          # waiting -> admitting -> resident -> released -> freed;
+                                    # resident -> evicting -> evicted -> waiting (readmission)
     queue: Deque[Request] = dataclasses.field(default_factory=collections.deque)
     closing: bool = False
     last_step: int = -1             # the latest step that holds one of its requests
     t_open: float = 0.0
     t_admit: Optional[float] = None
+    t_active: float = 0.0           # the latest arrival of one of its requests
+    evictions: int = 0
 
 
 class Scheduler:
@@ -95,6 +103,51 @@ class Scheduler:
             raise ValueError("request of %d events; at most %d" % (req.k, self.max_events))
         req.resident_at_arrival = s.state == "resident"
         s.queue.append(req)
+        s.t_active = max(s.t_active, req.t_arrive)
+        if s.state == "evicted":        # readmission: back in the admission queue
+            s.state = "waiting"
+            self.waiting.append(s.sid)
+
+    def plan_evictions(self) -> List[int]:
+        """Idle resident sessions (no request waiting or in a running step, not closing) to evict,
+        least recently active first, so that the first waiting session fits; none when it fits
+        already or when evicting every idle session would not make room."""
+        if not self.waiting:
+            return []
+        on_the_way = sum(s.nbytes for s in self.sessions.values() if s.state == "evicting")
+        need = self.sessions[self.waiting[0]].nbytes - (self.budget - self.used) - on_the_way
+        if need <= 0:
+            return []
+        idle = sorted((s for s in self.sessions.values()
+                       if s.state == "resident" and not s.closing and not s.queue and s.last_step <= self.done_upto),
+                      key=lambda s: (s.t_active, s.sid))
+        out, freed = [], 0
+        for s in idle:
+            if freed >= need:
+                break
+            out.append(s.sid)
+            freed += s.nbytes
+        return out if freed >= need else []
+
+    def evicting(self, sid: int):
+        """The session leaves the device (it takes no further step)."""
+        s = self.sessions[sid]
+        if s.state != "resident":
+            raise ValueError("session %d is not resident" % sid)
+        s.state = "evicting"
+
+    def evicted(self, sid: int):
+        """Its graph is checkpointed and freed: the memory returns to the budget; with requests
+        waiting it is queued for readmission at once."""
+        s = self.sessions[sid]
+        if s.state != "evicting":
+            raise ValueError("session %d is not being evicted" % sid)
+        s.state = "evicted"
+        s.evictions += 1
+        self.used -= s.nbytes
+        if s.queue:
+            s.state = "waiting"
+            self.waiting.append(sid)
 
     def admissions(self, t: float = 0.0) -> List[int]:
         """Sessions to bring onto the device now (first come, while they fit)."""
@@ -143,12 +196,14 @@ class Scheduler:
     def releases(self) -> List[int]:
         """Sessions to release now: closing, served, and with none of their requests still
         running. A released session takes no further step; its memory returns to the budget at
-        freed()."""
+        freed(). An evicted session that closes is released at once (nothing is on the device)."""
         out = []
         for s in self.sessions.values():
             if s.state == "resident" and s.closing and not s.queue and s.last_step <= self.done_upto:
                 s.state = "released"
                 out.append(s.sid)
+            elif s.state == "evicted" and s.closing and not s.queue:
+                s.state = "freed"
         return out
 
     def freed(self, sid: int):
@@ -172,10 +227,14 @@ class Server:
     """Scheduler + library: graphs as DamfGraphs, steps as fleet steps on one stream."""
 
     def __init__(self, budget_bytes: int, max_events: int = 1024, run_ahead: int = 2, stream=None,
-                 on_release=None, share_exponent: float = 1.0):
+                 on_release=None, share_exponent: float = 1.0, evict: bool = True):
         import torch
         self.torch = torch
-        self.on_release = on_release   # called (sid, graph) after a released graph's last step
+        self.on_release = on_release   # called (sid, graph) after a released graph's last step, or
+        #                                (sid, checkpoint) for a session that closes while evicted
+        self.evict = bool(evict)
+        self.evicting = []         # (sid, graph, last step it took part in)
+        self.checkpoints = {}      # sid -> checkpoint of an evicted session (host memory)
         self.share_exponent = float(share_exponent)   # push CTAs ~ (d (n + m))^exponent per graph
         self.sched = Scheduler(budget_bytes, max_events)
         self.max_events = int(max_events)
@@ -231,21 +290,38 @@ class Server:
             self.fleet.set_shares(exponent=self.share_exponent)
         self.fleet_sids = sids
 
-    def _build(self, spec):
-        # worker thread: the graph's initialisation on its own stream (the library synchronises
-        # that stream before returning), beside the steps the loop keeps issuing
+    def _build(self, spec, ckpt):
+        # worker thread: the graph's initialisation (or its restore from an eviction's checkpoint)
+        # on its own stream (the library synchronises that stream before returning), beside the
+        # steps the loop keeps issuing
         from .api import DamfGraph
         torch = self.torch
         with torch.cuda.stream(self.init_stream):
-            g = DamfGraph(*spec, stream=self.init_stream)
+            if ckpt is not None:
+                dev = dict(ckpt, state={k: v.to("cuda", non_blocking=True) for k, v in ckpt["state"].items()})
+                g = DamfGraph.restore(dev, stream=self.init_stream)
+            else:
+                g = DamfGraph(*spec, stream=self.init_stream)
             self.init_stream.synchronize()
         return g
+
+    def _checkpoint(self, g):
+        """The graph's checkpoint with its tensors in pinned host memory."""
+        ck = g.save()
+        ck["state"] = {k: v.cpu().pin_memory() for k, v in ck["state"].items()}
+        return ck
 
     def _admit(self, block: bool = False):
         if self.init_stream is None:
             self.init_stream = self.torch.cuda.Stream()
+        if self.evict:
+            for sid in self.sched.plan_evictions():
+                self.sched.evicting(sid)
+                # it takes part (empty batch) in every step issued so far
+                self.evicting.append((sid, self.graphs.pop(sid), self.sched.next_step_id - 1))
         for sid in self.sched.admissions(self.now()):
-            self.initializing[sid] = self.init_pool.submit(self._build, self.specs.pop(sid))
+            self.initializing[sid] = self.init_pool.submit(self._build, self.specs.pop(sid, None),
+                                                           self.checkpoints.pop(sid, None))
         for sid, fut in list(self.initializing.items()):
             if block or fut.done():
                 self.graphs[sid] = fut.result()
@@ -308,7 +384,23 @@ class Server:
         for sid in self.sched.releases():
             # it took part (empty batch) in every step issued so far
             self.to_destroy.append((sid, self.graphs.pop(sid), self.sched.next_step_id - 1))
+        for sid, s in self.sched.sessions.items():   # sessions that closed while evicted
+            if s.state == "freed" and sid in self.checkpoints:
+                ck = self.checkpoints.pop(sid)
+                if self.on_release is not None:
+                    self.on_release(sid, ck)
         done = self.sched.done_upto
+        keep = []
+        for sid, g, last in self.evicting:
+            if last <= done:
+                g.check()
+                self.checkpoints[sid] = self._checkpoint(g)
+                self.kernels += g.stats()["launches"]
+                g.close()
+                self.sched.evicted(sid)
+            else:
+                keep.append((sid, g, last))
+        self.evicting = keep
         keep = []
         for f, last in self.retired:
             if last <= done:
@@ -351,9 +443,9 @@ class Server:
             self._admit()
             if len(self.inflight) < self.run_ahead and self._issue():
                 continue
-            if self.inflight or self.to_destroy:
+            if self.inflight or self.to_destroy or self.evicting:
                 self._retire(block=True)
-                if self.to_destroy and not self.inflight:
+                if (self.to_destroy or self.evicting) and not self.inflight:
                     self._retire(block=False)
                 continue
             if self.initializing:
@@ -369,6 +461,7 @@ class Server:
         """Kernels launched by every graph (initialisation included) and fleet so far."""
         live = sum(g.stats()["launches"] for g in self.graphs.values())
         live += sum(g.stats()["launches"] for _, g, _ in self.to_destroy)
+        live += sum(g.stats()["launches"] for _, g, _ in self.evicting)
         return self.kernels + live + (self.fleet.launches if self.fleet is not None else 0)
 
     def shutdown(self, max_seconds: float = 600.0):
@@ -388,6 +481,11 @@ class Server:
             g.close()
             self.sched.freed(sid)
         self.to_destroy = []
+        for sid, g, _ in self.evicting:
+            self.checkpoints[sid] = self._checkpoint(g)
+            g.close()
+            self.sched.evicted(sid)
+        self.evicting = []
         for g in self.graphs.values():
             g.close()
         self.graphs = {}

@@ -101,3 +101,59 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert all(np.array_equal(a, b) for a, b in zip(got[3], mine[3]))
         assert _bound_ok(got), i
         twin.close()
+
+
+def _snapshot_any(x):
+    # a released graph, or the checkpoint of a graph that closed while evicted
+    if isinstance(x, dict):
+        rp, col = x["indptr"].astype(np.int64), x["indices"]
+        rows = [np.sort(col[rp[u]:rp[u + 1]]) for u in range(len(rp) - 1)]
+        return {k: v.cpu() for k, v in x["state"].items()}, rp, col, rows
+    return _snapshot(x)
+
+
+def test_evicted_graphs_come_back_where_they_left_off():
+    # a budget for two of four graphs: idle graphs are checkpointed to host memory and freed to
+    # admit others, and restored when a request comes for them; every graph still ends exactly
+    # where its requests applied alone take it
+    from paper_2306_08967_gb300 import DamfGraph, bytes_required
+    from paper_2306_08967_gb300.serving import Server
+    rng = np.random.default_rng(19)
+    specs = [_spec(10 + i, *s) for i, s in enumerate(SPECS[:4])]
+    need = sorted(bytes_required(sp[2]) for sp in specs)
+    budget = need[-1] + need[-2]
+    final = {}
+    srv = Server(budget, max_events=128, run_ahead=2, on_release=lambda sid, g: final.update({sid: _snapshot_any(g)}))
+    for i, sp in enumerate(specs):
+        srv.open(i, *sp)
+    reqs = {i: [] for i in range(4)}
+    rid = 0
+    for rnd in range(5):                      # round robin: every graph is asked again and again
+        for i in range(4):
+            ev = _events(rng, SPECS[i][0], int(rng.integers(1, 129)))
+            reqs[i].append(ev)
+            srv.submit(rid, i, *ev)
+            rid += 1
+            srv.drain()                       # serve it before the next graph's request
+            assert srv.sched.used <= budget
+    for i in range(4):
+        srv.close(i)
+    srv.drain()
+    srv.shutdown()
+    evictions = sum(s.evictions for s in srv.sched.sessions.values())
+    assert evictions >= 4                     # graphs really left and came back
+    assert sorted(final) == [0, 1, 2, 3]
+    for i, sp in enumerate(specs):
+        twin = DamfGraph(*sp)
+        for ev in reqs[i]:
+            twin.apply_edges(*ev)
+            twin.ppr_refresh()
+        twin.check()
+        mine = _snapshot(twin)
+        got = final[i]
+        for key in ("Ub", "Vb", "PU", "PV", "sigma"):
+            assert torch.equal(got[0][key], mine[0][key]), (i, key)
+        assert np.array_equal(got[1], mine[1])
+        assert all(np.array_equal(a, b) for a, b in zip(got[3], mine[3]))
+        assert _bound_ok(got), i
+        twin.close()

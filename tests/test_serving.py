@@ -94,3 +94,59 @@ def test_a_session_closed_while_empty_is_released_without_a_step():
     assert sorted(st[1]) == [2, 3]
     s.step_done(st[0], st[1], 1.0)
     assert s.idle() and s.backlog() == 0
+
+
+def test_eviction_makes_room_with_the_least_recently_active_idle_graphs():
+    s = Scheduler(budget_bytes=100)
+    for sid in (1, 2, 3):
+        s.open(sid, 30)
+    for sid in s.admissions():
+        s.admitted(sid)
+    s.submit(_req(0, 1, t=5.0))
+    s.submit(_req(1, 2, t=1.0))
+    s.submit(_req(2, 3, t=3.0))
+    st = s.next_step()
+    s.step_done(st[0], st[1], 6.0)
+    s.open(4, 50)                          # needs 50, 10 free: two idle graphs must go
+    assert s.admissions() == []
+    assert s.plan_evictions() == [2, 3]    # least recently active first
+    s.evicting(2)
+    s.evicting(3)
+    assert s.plan_evictions() == []        # the memory on its way out is counted
+    assert s.resident() == [1]
+    s.evicted(2)
+    s.evicted(3)
+    assert s.used == 30 and s.admissions() == [4]
+    # a request for an evicted graph queues it for readmission
+    s.submit(_req(3, 2, t=7.0))
+    assert s.sessions[2].state == "waiting" and list(s.waiting) == [2]
+    assert s.sessions[2].evictions == 1
+
+
+def test_busy_or_closing_graphs_are_not_evicted():
+    s = Scheduler(budget_bytes=60)
+    s.open(1, 30)
+    s.open(2, 30)
+    for sid in s.admissions():
+        s.admitted(sid)
+    s.submit(_req(0, 1))                   # 1 has a request waiting
+    st = s.next_step()                     # and then running
+    s.close(2)                             # 2 is closing
+    s.open(3, 30)
+    assert s.plan_evictions() == []
+    s.step_done(st[0], st[1], 1.0)
+    assert s.plan_evictions() == [1]       # now idle
+
+
+def test_a_graph_that_closes_while_evicted_is_done_without_readmission():
+    s = Scheduler(budget_bytes=30)
+    s.open(1, 30)
+    for sid in s.admissions():
+        s.admitted(sid)
+    s.open(2, 30)
+    assert s.plan_evictions() == [1]
+    s.evicting(1)
+    s.evicted(1)
+    s.close(1)
+    assert s.releases() == [] and s.sessions[1].state == "freed"
+    assert s.admissions() == [2]
