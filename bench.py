@@ -849,6 +849,10 @@ def main():
     ap.add_argument("--pool", type=int, default=48, help="C5: distinct small graphs generated")
     ap.add_argument("--drain-seconds", type=float, default=60.0, help="C5: wall time allowed after the last phase")
     ap.add_argument("--share-exponent", type=float, default=0.5, help="C5: push CTAs ~ (d (n + m))^exponent")
+    ap.add_argument("--min-idle", type=float, default=3.0, help="C5: seconds without a request before a graph "
+                    "may be evicted")
+    ap.add_argument("--no-evict", dest="evict", action="store_false",
+                    help="C5: sessions wait for memory instead of evicting idle graphs to host memory")
     ap.add_argument("--mode", default="batches", choices=["batches", "node-stream"],
                     help="node-stream: ms per node event under the paper's node-arrival protocol")
     args = ap.parse_args()
@@ -978,7 +982,8 @@ def run_serving(args, sw):
     free, total = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 1e9) if args.budget_gb else int(need_big + 0.75 * sum(need_small[:sw.open_small]))
     budget = min(budget, int(free * 0.9))
-    srv = Server(budget, max_events=sw.k_hi, run_ahead=2, share_exponent=args.share_exponent)
+    srv = Server(budget, max_events=sw.k_hi, run_ahead=2, share_exponent=args.share_exponent, evict=args.evict,
+                 min_idle_s=args.min_idle)
     # sessions: the big graph for the whole run, small ones each for R requests, then replaced
     srv.open(0, *spec(big[0], big[1], big[2]))
     nxt_pool = 0
@@ -1103,7 +1108,9 @@ def run_serving(args, sw):
                 "h2d_bytes_per_step": 9 * served / max(steps, 1), "d2h_bytes_per_step": 0,
                 "note": "every request goes host -> device (pinned staging, one copy per step); completion is "
                         "observed on the host through an event"},
-        "sessions": {"opened": len(srv.sched.sessions), "admission_wait_s": {
+        "sessions": {"opened": len(srv.sched.sessions), "evict": args.evict, "min_idle_s": args.min_idle,
+                     "evictions": int(sum(x.evictions for x in srv.sched.sessions.values())),
+                     "admission_wait_s": {
             "p50": float(np.percentile(waits, 50)) if len(waits) else None,
             "p99": float(np.percentile(waits, 99)) if len(waits) else None}},
         "gpu_launches": int(srv.kernel_count()),

@@ -73,7 +73,8 @@ class Session:
 class Scheduler:
     """Admission, per-step request selection and release (no device work)."""
 
-    def __init__(self, budget_bytes: int, max_events: int = 1024):
+    def __init__(self, budget_bytes: int, max_events: int = 1024, min_idle_s: float = 0.0):
+        self.min_idle_s = float(min_idle_s)   # a graph idle for less is not evicted
         self.budget = int(budget_bytes)
         self.used = 0
         self.max_events = int(max_events)
@@ -108,10 +109,11 @@ class Scheduler:
             s.state = "waiting"
             self.waiting.append(s.sid)
 
-    def plan_evictions(self) -> List[int]:
-        """Idle resident sessions (no request waiting or in a running step, not closing) to evict,
-        least recently active first, so that the first waiting session fits; none when it fits
-        already or when evicting every idle session would not make room."""
+    def plan_evictions(self, t: float = 0.0) -> List[int]:
+        """Idle resident sessions (no request waiting or in a running step, not closing, no
+        request for min_idle_s up to time t) to evict, least recently active first, so that
+        the first waiting session fits; none when it fits already or when evicting every idle
+        session would not make room."""
         if not self.waiting:
             return []
         on_the_way = sum(s.nbytes for s in self.sessions.values() if s.state == "evicting")
@@ -119,7 +121,8 @@ class Scheduler:
         if need <= 0:
             return []
         idle = sorted((s for s in self.sessions.values()
-                       if s.state == "resident" and not s.closing and not s.queue and s.last_step <= self.done_upto),
+                       if s.state == "resident" and not s.closing and not s.queue and s.last_step <= self.done_upto
+                       and (self.min_idle_s <= 0.0 or t - s.t_active >= self.min_idle_s)),
                       key=lambda s: (s.t_active, s.sid))
         out, freed = [], 0
         for s in idle:
@@ -227,16 +230,17 @@ class Server:
     """Scheduler + library: graphs as DamfGraphs, steps as fleet steps on one stream."""
 
     def __init__(self, budget_bytes: int, max_events: int = 1024, run_ahead: int = 2, stream=None,
-                 on_release=None, share_exponent: float = 1.0, evict: bool = True):
+                 on_release=None, share_exponent: float = 1.0, evict: bool = True, min_idle_s: float = 0.0):
         import torch
         self.torch = torch
         self.on_release = on_release   # called (sid, graph) after a released graph's last step, or
         #                                (sid, checkpoint) for a session that closes while evicted
         self.evict = bool(evict)
         self.evicting = []         # (sid, graph, last step it took part in)
+        self.saving = {}           # sid -> future of its checkpoint (worker thread)
         self.checkpoints = {}      # sid -> checkpoint of an evicted session (host memory)
         self.share_exponent = float(share_exponent)   # push CTAs ~ (d (n + m))^exponent per graph
-        self.sched = Scheduler(budget_bytes, max_events)
+        self.sched = Scheduler(budget_bytes, max_events, min_idle_s)
         self.max_events = int(max_events)
         self.run_ahead = int(run_ahead)
         self.stream = stream if stream is not None else torch.cuda.Stream()
@@ -311,11 +315,22 @@ class Server:
         ck["state"] = {k: v.cpu().pin_memory() for k, v in ck["state"].items()}
         return ck
 
+    def _evict_job(self, g):
+        # worker thread: the checkpoint (its copies and the adjacency export wait for the device
+        # there, not in the loop) and the free; returns (checkpoint, kernels the graph launched)
+        torch = self.torch
+        with torch.cuda.stream(self.init_stream):
+            g.check()
+            ck = self._checkpoint(g)
+            kernels = g.stats()["launches"]
+            g.close()
+        return ck, kernels
+
     def _admit(self, block: bool = False):
         if self.init_stream is None:
             self.init_stream = self.torch.cuda.Stream()
         if self.evict:
-            for sid in self.sched.plan_evictions():
+            for sid in self.sched.plan_evictions(self.now()):
                 self.sched.evicting(sid)
                 # it takes part (empty batch) in every step issued so far
                 self.evicting.append((sid, self.graphs.pop(sid), self.sched.next_step_id - 1))
@@ -393,14 +408,17 @@ class Server:
         keep = []
         for sid, g, last in self.evicting:
             if last <= done:
-                g.check()
-                self.checkpoints[sid] = self._checkpoint(g)
-                self.kernels += g.stats()["launches"]
-                g.close()
-                self.sched.evicted(sid)
+                self.saving[sid] = self.init_pool.submit(self._evict_job, g)
             else:
                 keep.append((sid, g, last))
         self.evicting = keep
+        for sid, fut in list(self.saving.items()):
+            if block or fut.done():
+                ck, kernels = fut.result()
+                self.checkpoints[sid] = ck
+                self.kernels += kernels
+                del self.saving[sid]
+                self.sched.evicted(sid)
         keep = []
         for f, last in self.retired:
             if last <= done:
@@ -443,10 +461,8 @@ class Server:
             self._admit()
             if len(self.inflight) < self.run_ahead and self._issue():
                 continue
-            if self.inflight or self.to_destroy or self.evicting:
+            if self.inflight or self.to_destroy or self.evicting or self.saving:
                 self._retire(block=True)
-                if (self.to_destroy or self.evicting) and not self.inflight:
-                    self._retire(block=False)
                 continue
             if self.initializing:
                 self._admit(block=True)
@@ -486,6 +502,10 @@ class Server:
             g.close()
             self.sched.evicted(sid)
         self.evicting = []
+        for sid, fut in list(self.saving.items()):
+            self.checkpoints[sid], _ = fut.result()
+            self.sched.evicted(sid)
+        self.saving = {}
         for g in self.graphs.values():
             g.close()
         self.graphs = {}

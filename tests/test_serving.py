@@ -150,3 +150,18 @@ def test_a_graph_that_closes_while_evicted_is_done_without_readmission():
     s.close(1)
     assert s.releases() == [] and s.sessions[1].state == "freed"
     assert s.admissions() == [2]
+
+
+def test_graphs_active_lately_are_not_evicted():
+    s = Scheduler(budget_bytes=60, min_idle_s=2.0)
+    s.open(1, 30)
+    s.open(2, 30)
+    for sid in s.admissions():
+        s.admitted(sid)
+    s.submit(_req(0, 1, t=10.0))
+    s.submit(_req(1, 2, t=11.5))
+    st = s.next_step()
+    s.step_done(st[0], st[1], 11.6)
+    s.open(3, 30)
+    assert s.plan_evictions(t=11.7) == []        # both asked within the last 2 s
+    assert s.plan_evictions(t=12.5) == [1]       # 1 has been idle for 2.5 s
