@@ -256,7 +256,7 @@ class Server:
         self.steps_issued = 0
         self.kernels = 0           # kernels of graphs and fleets already closed
         self.init_pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
-        self.init_stream = None
+        self.init_stream = torch.cuda.Stream()   # initialisations, restores and checkpoints
         self.initializing = {}     # sid -> future of its DamfGraph
         self.ring = []             # staging buffers (pinned host, device), reused round robin
         self.ring_rows = 0
@@ -327,8 +327,6 @@ class Server:
         return ck, kernels
 
     def _admit(self, block: bool = False):
-        if self.init_stream is None:
-            self.init_stream = self.torch.cuda.Stream()
         if self.evict:
             for sid in self.sched.plan_evictions(self.now()):
                 self.sched.evicting(sid)
