@@ -118,7 +118,8 @@ damf_status damf_apply_edges(damf_ctx* ctx, const int32_t* src, const int32_t* d
                              int32_t k, int32_t new_nodes, void* stream);
 
 /*
- * damf_apply_edges with the event count on the device: the live events are the first
+ * damf_apply_edges (Algorithm 2; Algorithm 1 "UpdateEmbeddingE", Sec. 4.3) with the event
+ * count on the device: the live events are the first
  * *k_dev of src/dst/op (k_dev: device int32, read when the work runs, clamped to
  * [0, k_max]); the arrays hold k_max entries.  The call enqueues ceil(k_max / 64) updates;
  * an update whose events all lie beyond the live count finds no net change and leaves the
@@ -153,7 +154,8 @@ damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs
 
 /*
  * One step of many independent graphs (the batching pattern: graphs of uneven size and
- * rank, one batch each): for every entry, the batch's update (as damf_apply_edges, or
+ * rank, one batch each; per graph Algorithm 2 followed by the push of Sec. 4.4): for every
+ * entry, the batch's update (as damf_apply_edges, or
  * damf_apply_edges_counted when k_dev is set) and then its push (damf_ppr_refresh), run on
  * streams the graph's context owns, forked from `stream` after the work enqueued on it
  * before the call; `stream` then waits for every graph's update and push.  The graphs'
@@ -178,14 +180,17 @@ damf_status damf_step_multi(const damf_batch* batches, int32_t num_graphs, void*
  */
 typedef struct damf_fleet damf_fleet;
 
-/* Creates a fleet over count distinct contexts (the fleet order; the contexts stay owned by
- * the caller and must outlive the fleet).  Shares start proportional to d (n + m) (m the
+/* Creates a fleet over count distinct contexts (ctxs: host array; the fleet order; the
+ * contexts stay owned by the caller and must outlive the fleet; out receives the fleet, freed
+ * by damf_fleet_destroy).  Shares start proportional to d (n + m) (m the
  * initial adjacency entries).  Synchronous (uploads its tables).  DAMF_ERR_INVALID for
  * count < 1, a NULL, repeated or poisoned context. */
 damf_status damf_fleet_create(damf_ctx* const* ctxs, int32_t count, damf_fleet** out);
 
 /*
- * One step: batches[i] (fleet order; its ctx NULL or the fleet's i-th context) is applied to
+ * One step (per graph Algorithm 2, then the push of Sec. 4.4 for all graphs in one grouped
+ * launch): batches[i] (host array in fleet order; its ctx NULL or the fleet's i-th context;
+ * its event arrays on the device, read when the step runs) is applied to
  * graph i as by damf_apply_edges (damf_apply_edges_counted when k_dev is set), each graph's
  * update on its context's own stream, forked from `stream`; then the grouped push of every
  * graph; `stream` waits for all of it.  Capturable in one CUDA graph (join every context,
@@ -385,7 +390,9 @@ damf_status damf_get_state(damf_ctx* ctx, float* Ub, float* Vb, float* Zb, float
                            float* sigma, float* s0, void* stream);
 
 /*
- * Checkpoint and resume.  A context's full state, in buffers the caller owns: U_b, V_b, Z_b,
+ * Checkpoint and resume (no counterpart in the paper; the state is that of Sec. 4: the bases
+ * and transforms of the U-form, Sigma, and the PPR base signal's Z_b and r of Sec. 4.4).  A
+ * context's full state, in buffers the caller owns: U_b, V_b, Z_b,
  * r (device) float32[n x d]; P_U, P_V and their inverses (device) float32[d x d] (the
  * library updates the inverses incrementally, so they are saved rather than recomputed);
  * Sigma and s0 (device) float32[d]; and the host count of updates since the last fold.
