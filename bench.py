@@ -507,7 +507,7 @@ def run_fleet(args, fw, rank, world):
     import ctypes
     import torch
     from paper_2306_08967_gb300 import DamfFleet, DamfGraph, _lib, make_config, rsvd_width
-    from paper_2306_08967_gb300.api import _batch_array
+    from paper_2306_08967_gb300.api import batch_array
     from paper_2306_08967_gb300.autotune import DEFAULT_DIRECT_CHUNKS, DEFAULT_EXPONENTS, tune_shares
     from synth import fleet_inputs, gaussian_test_matrix
 
@@ -553,7 +553,7 @@ def run_fleet(args, fw, rank, world):
     b_op, b_cnt = torch.zeros((G, KMAX), dtype=torch.int8, device=dev), torch.zeros(G, dtype=torch.int32, device=dev)
     sig = torch.zeros((G, 128), dtype=torch.float32, device=dev)
     batches = [(g, b_src[i], b_dst[i], b_op[i], 0, b_cnt[i:i + 1]) for i, g in enumerate(graphs)]
-    arr = _batch_array(batches)
+    arr = batch_array(batches)
     lib = _lib.load()
     fs = torch.cuda.Stream(device=dev)
     fptr = ctypes.c_void_p(fs.cuda_stream)

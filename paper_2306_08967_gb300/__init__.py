@@ -5,5 +5,5 @@ package only marshals arguments.  Importing it does not load the library; the fi
 DamfGraph does, and raises ImportError when the library has not been built.
 """
 
-from .api import (DamfError, DamfFleet, DamfGraph, apply_edges_multi, bytes_required, core_svd, make_config,  # noqa: F401
-                  rsvd_width, step_multi)
+from .api import (DamfError, DamfFleet, DamfGraph, apply_edges_multi, batch_array, bytes_required,  # noqa: F401
+                  core_svd, make_config, plan_slots, rsvd_width, step_multi)

@@ -79,7 +79,7 @@ def core_svd(sigma, L, R, stream=None):
     return E, H, th
 
 
-def _batch_array(batches):
+def batch_array(batches):
     """damf_batch[] for a list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]]); with a k_dev
     (device int32 tensor of one element) the arrays hold k_max events of which *k_dev are live."""
     arr = (_lib.Batch * max(len(batches), 1))()
@@ -99,7 +99,7 @@ def _batch_array(batches):
 def apply_edges_multi(batches, stream=None):
     """One batch per graph through damf_apply_edges_multi, in order on one stream: batches is a
     list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]])."""
-    st = _lib.load().damf_apply_edges_multi(_batch_array(batches), len(batches), _stream_ptr(stream))
+    st = _lib.load().damf_apply_edges_multi(batch_array(batches), len(batches), _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "apply_edges_multi")
 
@@ -107,7 +107,7 @@ def apply_edges_multi(batches, stream=None):
 def step_multi(batches, stream=None):
     """One step of many graphs through damf_step_multi: each graph's update and push on its own
     streams, joined back to `stream`. batches as for apply_edges_multi."""
-    st = _lib.load().damf_step_multi(_batch_array(batches), len(batches), _stream_ptr(stream))
+    st = _lib.load().damf_step_multi(batch_array(batches), len(batches), _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "step_multi")
 
@@ -145,12 +145,12 @@ class DamfFleet:
 
     def step(self, batches, stream=None):
         """batches: one (src, dst, op[, new_nodes[, k_dev]]) per graph, fleet order."""
-        arr = _batch_array([(g, *b) for g, b in zip(self.graphs, batches)])
+        arr = batch_array([(g, *b) for g, b in zip(self.graphs, batches)])
         self._keep = arr
         self._check(self.lib.damf_fleet_step(self.h, arr, _stream_ptr(stream)))
 
     def step_array(self, arr, stream=None):
-        """A prepared damf_batch array (api._batch_array), e.g. for a captured step."""
+        """A prepared damf_batch array (api.batch_array), e.g. for a captured step."""
         self._check(self.lib.damf_fleet_step(self.h, arr, _stream_ptr(stream)))
 
     def set_shares(self, blocks=None, exponent: float = 1.0):

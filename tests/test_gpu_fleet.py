@@ -143,7 +143,7 @@ def test_captured_step_multi_replays_like_direct_calls():
     # one CUDA graph holds the whole damf_step_multi step (every graph's update and push);
     # replays with new events and new counts written into fixed buffers equal direct calls
     from paper_2306_08967_gb300 import _lib
-    from paper_2306_08967_gb300.api import _batch_array
+    from paper_2306_08967_gb300.api import batch_array
     rng = np.random.default_rng(33)
     gs, twins = _fleet(SPECS, SEED + 70)
     for g, blocks in zip(gs, [8, 8, 32, 8, 16]):
@@ -154,7 +154,7 @@ def test_captured_step_multi_replays_like_direct_calls():
             for _ in gs]
     stream = torch.cuda.Stream()
     lib = _lib.load()
-    arr = _batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
+    arr = batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
     import ctypes
     sptr = ctypes.c_void_p(stream.cuda_stream)
     with torch.cuda.stream(stream):
@@ -311,7 +311,7 @@ def test_captured_fleet_step_replays_like_direct_calls():
     # the whole fleet step (updates and the grouped push) as one CUDA graph; each replay reads
     # new events and counts from fixed buffers
     from paper_2306_08967_gb300 import DamfFleet
-    from paper_2306_08967_gb300.api import _batch_array
+    from paper_2306_08967_gb300.api import batch_array
     rng = np.random.default_rng(43)
     gs, twins = _fleet(SPECS, SEED + 150)
     fleet = DamfFleet(gs)
@@ -319,7 +319,7 @@ def test_captured_fleet_step_replays_like_direct_calls():
     bufs = [(torch.zeros(kmax, dtype=torch.int32, device="cuda"), torch.zeros(kmax, dtype=torch.int32, device="cuda"),
              torch.zeros(kmax, dtype=torch.int8, device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"))
             for _ in gs]
-    arr = _batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
+    arr = batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for g in gs:
@@ -358,14 +358,14 @@ def test_captured_step_after_new_shares_reports_instead_of_running():
     # a captured grouped push carries its plan; after the shares change it must not run on the
     # new tables: every CTA returns at once and the contexts report DAMF_ERR_INVALID
     from paper_2306_08967_gb300 import DamfFleet
-    from paper_2306_08967_gb300.api import _batch_array
+    from paper_2306_08967_gb300.api import batch_array
     gs, twins = _fleet(SPECS[:3], SEED + 170)
     fleet = DamfFleet(gs)
     kmax = 64
     bufs = [(torch.zeros(kmax, dtype=torch.int32, device="cuda"), torch.zeros(kmax, dtype=torch.int32, device="cuda"),
              torch.zeros(kmax, dtype=torch.int8, device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"))
             for _ in gs]
-    arr = _batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
+    arr = batch_array([(g, b[0], b[1], b[2], 0, b[3]) for g, b in zip(gs, bufs)])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for g in gs:
