@@ -23,7 +23,9 @@
 namespace damf {
 
 constexpr int kTopSlab = 64;       // candidate rows per scan step
-constexpr int kTopThreads = 256;
+constexpr int kTopThreads = 512;   // 16 warps: the tiles' shared memory allows one CTA per SM
+constexpr int kTopQPT = kTopSlab * kTopQ / kTopThreads;   // queries per thread in the score tile
+static_assert(kTopQPT == 4, "the score tile reads one float4 of queries per k");
 constexpr int kMergeThreads = 1024;
 constexpr int kMergeKeys = 16384;  // per query: scan CTAs x k keys at most
 
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_scan(int nq, int n, int K,
   }
   if (tid < kTopQ) qs[tid] = tid < nq ? qid[tid] : -1;
   const float4 one4 = make_float4(1.f, 1.f, 1.f, 1.f);
-  // score tile: thread -> one slab row ti, 8 queries jb .. jb + 7
-  const int ti = tid >> 2, jb = (tid & 3) * 8;
+  // score tile: thread -> one slab row ti, 4 queries jb .. jb + 3
+  const int ti = tid >> 3, jb = (tid & 7) * kTopQPT;
   const long long nslab = ((long long)n + kTopSlab - 1) / kTopSlab;
   for (long long sl = blockIdx.x; sl < nslab; sl += gridDim.x) {
     const long long v0 = sl * kTopSlab;
@@ -209,20 +211,17 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_scan(int nq, int n, int K,
       if (symmetric) reinterpret_cast<float4*>(Ls + i * LD)[c4] = y;
     }
     __syncthreads();
-    float s1[8], s2[8];
+    float s1[kTopQPT], s2[kTopQPT];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) s1[t] = s2[t] = 0.f;
+    for (int t = 0; t < kTopQPT; ++t) s1[t] = s2[t] = 0.f;
     for (int k4 = 0; k4 < D / 4; ++k4) {
       const float4 v4 = reinterpret_cast<const float4*>(Vs + ti * LD)[k4];
       const float vk[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const float4 qa = reinterpret_cast<const float4*>(Lqt + (4 * k4 + c) * kTopQ + jb)[0];
-        const float4 qb = reinterpret_cast<const float4*>(Lqt + (4 * k4 + c) * kTopQ + jb)[1];
         s1[0] = fmaf(vk[c], qa.x, s1[0]); s1[1] = fmaf(vk[c], qa.y, s1[1]);
         s1[2] = fmaf(vk[c], qa.z, s1[2]); s1[3] = fmaf(vk[c], qa.w, s1[3]);
-        s1[4] = fmaf(vk[c], qb.x, s1[4]); s1[5] = fmaf(vk[c], qb.y, s1[5]);
-        s1[6] = fmaf(vk[c], qb.z, s1[6]); s1[7] = fmaf(vk[c], qb.w, s1[7]);
       }
       if (symmetric) {
         const float4 l4 = reinterpret_cast<const float4*>(Ls + ti * LD)[k4];
@@ -230,16 +229,13 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_scan(int nq, int n, int K,
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const float4 ra = reinterpret_cast<const float4*>(Rqt + (4 * k4 + c) * kTopQ + jb)[0];
-          const float4 rb = reinterpret_cast<const float4*>(Rqt + (4 * k4 + c) * kTopQ + jb)[1];
           s2[0] = fmaf(lk[c], ra.x, s2[0]); s2[1] = fmaf(lk[c], ra.y, s2[1]);
           s2[2] = fmaf(lk[c], ra.z, s2[2]); s2[3] = fmaf(lk[c], ra.w, s2[3]);
-          s2[4] = fmaf(lk[c], rb.x, s2[4]); s2[5] = fmaf(lk[c], rb.y, s2[5]);
-          s2[6] = fmaf(lk[c], rb.z, s2[6]); s2[7] = fmaf(lk[c], rb.w, s2[7]);
         }
       }
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) S[ti * (kTopQ + 1) + jb + t] = symmetric ? fmaxf(s1[t], s2[t]) : s1[t];
+    for (int t = 0; t < kTopQPT; ++t) S[ti * (kTopQ + 1) + jb + t] = symmetric ? fmaxf(s1[t], s2[t]) : s1[t];
     __syncthreads();
     // merge: warp w owns queries w, w + 8, ...; lane l holds slab rows l and l + 32
     for (int j = warp; j < nq; j += kTopThreads / 32) {
