@@ -402,6 +402,15 @@ def run_ours(args, c, rank, world):
     lat_ms = np.array([ev_start[j].elapsed_time(ev_done[j]) for j in range(K)])
     elapsed_ms = float(ev_start[0].elapsed_time(ev_done[K - 1]))
     step_ms = np.diff(np.array([0.0] + [ev_start[0].elapsed_time(ev_done[j]) for j in range(K)]))
+    if args.log_jsonl and rank == 0:
+        # one line per timed batch, from the events recorded in the timed region (nothing is
+        # read from the device per step)
+        with open(args.log_jsonl, "w") as f:
+            for j in range(K):
+                b = batches[W + j]
+                f.write(json.dumps({"step": j, "edges": b.k, "new_nodes": b.new_nodes,
+                                    "deletions": int((b.op < 0).sum()), "latency_ms": float(lat_ms[j]),
+                                    "interval_ms": float(step_ms[j])}) + "\n")
     stage = g.timing()
     g.set_timing(False)
     s1 = g.stats()
@@ -836,6 +845,7 @@ def main():
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
+    ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here")
     ap.add_argument("--push-blocks", type=int, default=0, help="push CTAs (0: two per SM)")
     ap.add_argument("--push-chunks", type=int, default=-1,
                     help="in-edge chunks a row task scatters itself before its row becomes hub items (-1: 8)")
@@ -905,6 +915,7 @@ def main():
         a2 = copy.copy(args)
         a2.precision = "fp32" if args.precision == "mixed" else "mixed"
         a2.e2e_steps = 0
+        a2.log_jsonl = None
         o2 = run_ours(a2, c, rank, world)
         sig_b = np.array(o2.pop("_sigma"))
         out["precision_compare"] = {

@@ -236,6 +236,14 @@ damf_status damf_fleet_get_shares(const damf_fleet* fleet, int32_t* blocks, int3
 int64_t damf_fleet_launches(const damf_fleet* fleet);
 
 /*
+ * Fault injection on the host (a test hook): the device allocation number `after` from now
+ * on (0 = the next) made by damf_init_factorize / damf_restore fails as cudaMalloc out of
+ * memory does; the call then returns DAMF_ERR_CAPACITY having freed what it had allocated.
+ * One failure per arming; after < 0 disarms.  Not thread-safe (process-wide).
+ */
+void damf_debug_fail_allocations(int32_t after);
+
+/*
  * Failure detection without a GPU fault: runs one of the push's bounded waits against a
  * condition that never comes true, with an iteration limit of `limit` (1 .. the library's own
  * limit; each iteration sleeps up to about a microsecond), and writes the device status the

@@ -64,6 +64,7 @@ SIGNATURES = {
     "damf_fleet_launches": (c_i64, [c_vp]),
     "damf_plan_slots": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp]),
     "damf_selftest_wait": (c_i32, [c_i32, c_i64, c_vp, c_vp]),
+    "damf_debug_fail_allocations": (None, [c_i32]),
     "damf_fleet_set_timing": (c_i32, [c_vp, c_i32]),
     "damf_fleet_get_timing": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "damf_fleet_last_error": (ctypes.c_char_p, [c_vp]),

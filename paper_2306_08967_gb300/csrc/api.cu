@@ -180,6 +180,22 @@ damf_status reject(Ctx* c, const char* what) {
   return DAMF_ERR_INVALID;
 }
 
+// Device allocations of a context go through here: the test hook damf_debug_fail_allocations
+// can make the n-th one fail as cudaMalloc out of memory does (fault injection on the host).
+int g_fail_alloc_after = -1;
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  if (g_fail_alloc_after == 0) {
+    g_fail_alloc_after = -1;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  if (g_fail_alloc_after > 0) --g_fail_alloc_after;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();   // not sticky: clear it
+  return e;
+}
+
 // Makes `s` wait for the most recent push. Under stream capture: a push captured in the same
 // capture is waited for through its own event; a push from before the capture is the caller's
 // to join before capturing (so nothing is added). Outside a capture: the last push recorded
@@ -554,11 +570,11 @@ static damf_status ctx_open(const damf_config* cfg, const int32_t* row_ptr, cons
   Plan p = plan_of(cfg);
   void* ptr[64];
   for (int i = 0; i < p.count; ++i) {
-    cudaError_t e = cudaMalloc(&ptr[i], p.sz[i]);
+    cudaError_t e = dev_alloc(&ptr[i], p.sz[i]);
     if (e != cudaSuccess) {
       free_all(c);
       free(x);
-      return DAMF_ERR_CUDA;
+      return e == cudaErrorMemoryAllocation ? DAMF_ERR_CAPACITY : DAMF_ERR_CUDA;
     }
     c->allocs[c->nallocs++] = ptr[i];
     cudaMemsetAsync(ptr[i], 0, p.sz[i], s);
@@ -1099,6 +1115,8 @@ void damf_destroy(damf_ctx* x) {
   free_all(&x->c);
   free(x);
 }
+
+void damf_debug_fail_allocations(int32_t after) { g_fail_alloc_after = after < 0 ? -1 : after; }
 
 damf_status damf_selftest_wait(int32_t which, int64_t limit, int32_t* status_out, void* stream) {
   if (!status_out || (which != 0 && which != 1) || limit < 1 || limit > (int64_t)kSpinLimit) return DAMF_ERR_INVALID;

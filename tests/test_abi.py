@@ -73,3 +73,17 @@ def test_wait_selftest_rejects_bad_arguments_without_gpu_work():
     assert lib.damf_selftest_wait(0, 1 << 40, ctypes.byref(st), None) == 1  # above the library's limit
     assert lib.damf_selftest_wait(0, 1000, None, None) == 1
     assert st.value == -1
+
+
+def test_injected_allocation_failure_is_reported_and_cleaned_up_without_gpu_work():
+    # fault injection on the host: the first device allocation of an init fails as cudaMalloc
+    # out of memory does; init returns DAMF_ERR_CAPACITY, creates nothing, and the hook disarms
+    from paper_2306_08967_gb300 import _lib, make_config
+    lib = _lib.load()
+    cfg = make_config(100, 16, 0.15, 1e-4, nnz=400)
+    h = ctypes.c_void_p()
+    lib.damf_debug_fail_allocations(0)
+    st = lib.damf_init_factorize(ctypes.byref(cfg), ctypes.c_void_p(8), ctypes.c_void_p(8), 400, ctypes.c_void_p(8),
+                                 None, ctypes.byref(h))
+    assert st == 2 and not h.value                   # DAMF_ERR_CAPACITY, nothing created
+    lib.damf_debug_fail_allocations(-1)

@@ -31,3 +31,27 @@ def test_bounded_waits_give_up_and_report(which):
     g.ppr_refresh()
     g.check()
     g.close()
+
+
+@pytest.mark.parametrize("after", [0, 1, 7, 30])
+def test_allocation_failure_at_any_point_frees_everything(after):
+    # fault injection on the host: the after-th device allocation of an initialisation fails;
+    # the call reports DAMF_ERR_CAPACITY, frees what it had taken (device memory back to where
+    # it was) and the next initialisation works
+    import torch
+    from paper_2306_08967_gb300 import DamfError, _lib
+    lib = _lib.load()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    lib.damf_debug_fail_allocations(after)
+    try:
+        with pytest.raises(DamfError) as ex:
+            make_pair(500, 6.0, 2.5, 32, 0.15, 1e-4, 0xDA3F0000 + 610, oracle=False)
+        assert ex.value.code == 2
+    finally:
+        lib.damf_debug_fail_allocations(-1)
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+    g, _, _ = make_pair(500, 6.0, 2.5, 32, 0.15, 1e-4, 0xDA3F0000 + 611, oracle=False)
+    g.check()
+    g.close()
