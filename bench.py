@@ -681,8 +681,8 @@ def run_fleet(args, fw, rank, world):
         return list((cur - prev) / max(pos[0] - p0, 1))
 
     t0 = time.perf_counter()
-    tune = tune_shares(fleet, graphs, measure, push_times=push_times,
-                       rebalance_rounds=rebalance_rounds) if T >= 2 else None
+    tune = tune_shares(fleet, graphs, measure, push_times=push_times, rebalance_rounds=rebalance_rounds,
+                       cache=args.tune_cache) if T >= 2 else None
     tune_s = time.perf_counter() - t0
     cg = capture()
     run_captured(cg, 1)
@@ -852,6 +852,7 @@ def main():
     ap.add_argument("--graphs", type=int, default=0, help="C4: the first this many graphs of the fleet (0: all)")
     ap.add_argument("--compare-steps", type=int, default=5, help="C4: steps of each comparison launch form")
     ap.add_argument("--tune-steps", type=int, default=3, help="C4: steps per autotuner candidate (< 2: no tuning)")
+    ap.add_argument("--tune-cache", default=None, help="C4: JSON file of tuned push shapes, reused for the same fleet")
     ap.add_argument("--rates", default="25,100,400", help="C5: request rates (req/s) of the phases")
     ap.add_argument("--phase-seconds", type=float, default=10.0, help="C5: seconds per rate phase")
     ap.add_argument("--budget-gb", type=float, default=0.0, help="C5: HBM budget (0: the big graph and 3/4 of "

@@ -10,7 +10,9 @@ graph owns a share of the resident CTAs. How the CTAs are best split depends on 
 * under that rule it then tries the hub threshold (push_direct_chunks: how many in-edge
   chunks a row task scatters itself before its row is split into items);
 * then it measures each graph's push time in the grouped launch and re-plans the shares in
-  proportion to the measured work (time x CTAs), for a few rounds, keeping the fastest.
+  proportion to the measured work (time x CTAs), for a few rounds, keeping the fastest;
+* the result can be kept in a JSON cache file keyed by the fleet's graphs, so that the same
+  fleet is not measured again.
 
 For graphs pushed one launch each (damf_step_multi), tune_grids picks the push grid per graph
 by a rows-per-CTA rule instead. Tuning changes only launch shapes: every result stays within
@@ -19,7 +21,10 @@ the push bound.
 
 from __future__ import annotations
 
+import hashlib
+import json
 import math
+import os
 from typing import Callable, Dict, Iterable, List, Sequence, Tuple
 
 DEFAULT_ROWS_PER_CTA = (0, 32768, 8192, 2048, 512)
@@ -101,10 +106,34 @@ def measured_weights(push_ns: Sequence[float], blocks: Sequence[int]) -> List[fl
     return [max(x, floor) for x in w]
 
 
+def fleet_signature(graphs) -> str:
+    """Key of a fleet in a tuning cache: its graphs' rows and ranks in fleet order."""
+    desc = [[int(g.n), int(getattr(g, "d", 0))] for g in graphs]
+    return hashlib.sha1(json.dumps(desc).encode()).hexdigest()
+
+
+def _load_cache(path: str) -> Dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _apply(fleet, graphs, entry: Dict):
+    for g in graphs:
+        g.set_tuning(0, int(entry["push_direct_chunks"]))
+    if entry.get("weights"):
+        fleet.set_weights(entry["weights"])
+    else:
+        fleet.set_shares(exponent=float(entry["exponent"]))
+
+
 def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
                 exponents: Sequence[float] = DEFAULT_EXPONENTS,
                 direct_chunks: Sequence[int] = DEFAULT_DIRECT_CHUNKS, repeats: int = 1,
-                push_times: Callable[[], Sequence[float]] = None, rebalance_rounds: int = 3) -> Dict:
+                push_times: Callable[[], Sequence[float]] = None, rebalance_rounds: int = 3,
+                cache: str = None) -> Dict:
     """Tunes a fleet's grouped push by timing fleet steps.
 
     fleet: .set_shares(blocks=None, exponent=p), .set_weights(w) and .shares() (DamfFleet).
@@ -115,8 +144,17 @@ def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
     and hub-threshold searches, `rebalance_rounds` rounds set the shares from the measured
     work (push time x CTAs) of the previous round. Leaves the fastest shape seen set and
     returns {"exponent", "push_direct_chunks", "table_exponents", "table_chunks",
-    "rebalance_ms", "chosen", "ms_per_step", "shares"}."""
+    "rebalance_ms", "chosen", "ms_per_step", "shares"}. With `cache` (a JSON file), a fleet of
+    the same signature (fleet_signature) tuned before gets that shape without measuring
+    ("cached": True); a new result is added to the file."""
     graphs = list(graphs)
+    sig = fleet_signature(graphs)
+    if cache:
+        entry = _load_cache(cache).get(sig)
+        if entry:
+            _apply(fleet, graphs, entry)
+            blocks, launches = fleet.shares()
+            return dict(entry, cached=True, shares={"min": min(blocks), "max": max(blocks), "launches": launches})
     for g in graphs:
         g.set_tuning(0, -1)
 
@@ -153,7 +191,16 @@ def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
         else:
             fleet.set_weights(best_w)
     blocks, launches = fleet.shares()
-    return {"exponent": p, "push_direct_chunks": c, "table_exponents": {str(k): v for k, v in t_exp.items()},
-            "table_chunks": {str(k): v for k, v in t_chunks.items()}, "rebalance_ms": reb, "chosen": chosen,
-            "ms_per_step": best_ms,
-            "shares": {"min": min(blocks), "max": max(blocks), "launches": launches}}
+    out = {"exponent": p, "push_direct_chunks": c, "table_exponents": {str(k): v for k, v in t_exp.items()},
+           "table_chunks": {str(k): v for k, v in t_chunks.items()}, "rebalance_ms": reb, "chosen": chosen,
+           "ms_per_step": best_ms, "cached": False,
+           "shares": {"min": min(blocks), "max": max(blocks), "launches": launches}}
+    if cache:
+        entries = _load_cache(cache)
+        entries[sig] = {"exponent": p, "push_direct_chunks": c, "weights": list(best_w) if best_w else None,
+                        "chosen": chosen, "ms_per_step": best_ms}
+        tmp = cache + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(entries, f)
+        os.replace(tmp, cache)
+    return out

@@ -137,3 +137,25 @@ def test_tune_shares_rebalances_on_measured_work():
     b = fleet.shares()[0]
     assert abs(b[0] / b[2] - 900.0 / 3000.0) < 0.05
     assert res["ms_per_step"] < min(res["table_exponents"].values())
+
+
+def test_tuning_cache_skips_measuring_the_same_fleet(tmp_path):
+    graphs = [FakeGraph(n, 304) for n in (1000, 20_000, 400_000)]
+    fleet = FakeFleet(graphs)
+    calls = []
+
+    def step_ms():
+        calls.append(1)
+        return abs(fleet.p - 0.75) * 10 + {-1: 1.0, 4: 0.0, 16: 2.0}[fleet.snap[0]]
+
+    cache = str(tmp_path / "tune.json")
+    first = tune_shares(fleet, graphs, step_ms, cache=cache)
+    assert first["cached"] is False and len(calls) > 0
+    n_calls = len(calls)
+    fleet2 = FakeFleet([FakeGraph(n, 304) for n in (1000, 20_000, 400_000)])
+    again = tune_shares(fleet2, fleet2.graphs, step_ms, cache=cache)
+    assert again["cached"] is True and len(calls) == n_calls          # nothing measured
+    assert fleet2.p == 0.75 and fleet2.snap == [4, 4, 4]               # the cached shape applied
+    other = FakeFleet([FakeGraph(n, 304) for n in (1000, 30_000)])      # another fleet: measured
+    third = tune_shares(other, other.graphs, step_ms, cache=cache)
+    assert third["cached"] is False and len(calls) > n_calls
