@@ -43,7 +43,10 @@ typedef enum {
   DAMF_ERR_CUDA = 3,           /* a CUDA runtime call failed; damf_last_error() has the text */
   DAMF_ERR_NUMERIC = 4,        /* non-finite value in Sigma, a transform or a residual factor */
   DAMF_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
-  DAMF_ERR_NOT_CONVERGED = 6   /* the PPR push hit max_push_rounds phases before every residual was <= eps */
+  DAMF_ERR_NOT_CONVERGED = 6,  /* the PPR push hit max_push_rounds phases before every residual was <= eps */
+  DAMF_ERR_BOUNDS = 7          /* a device bounds check failed (only in a library built with DAMF_CHECK: row ids
+                                  below the node capacity, adjacency offsets inside m_capacity, queue items
+                                  inside their arrays); the access was skipped */
 } damf_status;
 
 typedef struct {

@@ -4,12 +4,13 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdamf.so")
+# DAMF_LIB_VARIANT=check loads the build with device bounds checks (build.build(check=True))
+LIB_PATH = os.path.join(HERE, "libdamf_check.so" if os.environ.get("DAMF_LIB_VARIANT") == "check" else "libdamf.so")
 
 c_i32, c_i64, c_f64, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
 STATUS_NAMES = {0: "DAMF_OK", 1: "DAMF_ERR_INVALID", 2: "DAMF_ERR_CAPACITY", 3: "DAMF_ERR_CUDA",
-                4: "DAMF_ERR_NUMERIC", 5: "DAMF_ERR_TIMEOUT", 6: "DAMF_ERR_NOT_CONVERGED"}
+                4: "DAMF_ERR_NUMERIC", 5: "DAMF_ERR_TIMEOUT", 6: "DAMF_ERR_NOT_CONVERGED", 7: "DAMF_ERR_BOUNDS"}
 
 
 class Config(ctypes.Structure):

@@ -183,6 +183,15 @@ __device__ __forceinline__ void set_status(DevHeader* h, int code) {
   atomicCAS(&h->status, 0, code);
 }
 
+// Device bounds checks of a DAMF_CHECK build: true when cond holds; otherwise the status
+// becomes DAMF_ERR_BOUNDS and the caller skips the access. Compiled out (always true) in the
+// default build.
+#ifdef DAMF_CHECK
+#define DAMF_DCHECK(h, cond) ((cond) ? true : (set_status((h), DAMF_ERR_BOUNDS), false))
+#else
+#define DAMF_DCHECK(h, cond) true
+#endif
+
 // Bounded sense-free grid barrier: every block must call it the same number of times.
 // Returns false (and records DAMF_ERR_TIMEOUT) when a wait runs out.
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, DevHeader* h, unsigned int nblocks,
@@ -245,7 +254,7 @@ struct PushArgs {
   int max_phases;
   int direct_max;          // in-edges a row task scatters itself
   int d;
-  int pad;
+  int ncap;                // node capacity: every row id is below it (checked in DAMF_CHECK builds)
 };
 PushArgs push_args(const Ctx* c, int direct_chunks);
 int push_group_max_blocks(int scaled);

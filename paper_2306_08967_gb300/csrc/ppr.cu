@@ -214,7 +214,7 @@ __device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, co
                                               const int32_t* __restrict__ outdeg, float* r, float beta, float eps,
                                               WarpQ& wq, DevHeader* h, uint32_t* inq, int32_t* queue, long long qcap,
                                               int lane, int sub, int q, bool enq = true, bool pre0 = false,
-                                              int w_pre = 0, int d_pre = 1) {
+                                              int w_pre = 0, int d_pre = 1, int ncap = 0x7fffffff) {
   constexpr int LPR = PushShape<D>::LPR;
   constexpr int RPW = PushShape<D>::RPW;
   constexpr int CHL = PushShape<D>::CHL;
@@ -230,8 +230,12 @@ __device__ __forceinline__ void scatter_edges(const float4 v, int st, int ne, co
       if (lane < nb) c_own = beta / (float)d_own;
     } else if (lane < nb) {
       w_own = __ldg(col + st + b0 + lane);
-      d_own = __ldg(outdeg + w_own);
-      c_own = beta / (float)d_own;
+      if (DAMF_DCHECK(h, (unsigned)w_own < (unsigned)ncap)) {
+        d_own = __ldg(outdeg + w_own);
+        c_own = beta / (float)d_own;
+      } else {
+        w_own = 0;   // an add of zero to row 0 in place of the bad neighbour
+      }
     }
     for (int c0 = 0; c0 < nb; c0 += EPC) {   // warp-uniform; the chunk's in-edges are lanes c0 ..
       const int ncur = min(EPC, nb - c0);
@@ -355,6 +359,11 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         break;
       }
     }
+    // a dequeued id outside its array (DAMF_CHECK builds): the task is dropped (counted done)
+    if (!(e >= 0 ? DAMF_DCHECK(h, e < a.ncap) : DAMF_DCHECK(h, (long long)(-e - 2) < ws.work_cap))) {
+      wq.done += 1;
+      continue;
+    }
     if (e >= 0) {
       if (lane == 0) ++my_rows;
       // row task. The flag is cleared first; the removal of v below is ordered after the
@@ -370,6 +379,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         deg = __ldg(in.len + u);
         aux = SCALED ? __ldg(outdeg + u) : 1;
       }
+      if (!DAMF_DCHECK(h, st >= 0 && deg >= 0 && (long long)st + deg <= in.m_cap)) deg = 0;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (sub == 0) v = f4_ldcg(r + (size_t)u * D + 4 * q);
       // the first 32 in-edges and their out-degrees are requested beside the row, so that they
@@ -383,7 +393,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         v.z = __shfl_sync(kFull, v.z, q);
         v.w = __shfl_sync(kFull, v.w, q);
       }
-      if (pre0 && lane < min(deg, 32)) d0 = __ldg(outdeg + w0);
+      if (pre0 && lane < min(deg, 32) && DAMF_DCHECK(h, (unsigned)w0 < (unsigned)a.ncap)) d0 = __ldg(outdeg + w0);
       const int dout = aux;
       const float thr_u = threshold<SCALED>(eps, dout);
       bool go = group_max<LPR>(max_abs4(v)) > thr_u;   // the same in every group: warp-uniform
@@ -442,7 +452,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         }
         if (direct)
           scatter_edges<D, SCALED>(v, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
-                                   true, pre0, w0, d0);
+                                   true, pre0, w0, d0, a.ncap);
         // u itself: adds that reached r[u] between the read of v and its removal are still there
         lm = __shfl_sync(kFull, group_max<LPR>(lm), 0);
         enqueue_rows(lane == 0 && lm > thr_u, u, wq, h, inq, queue, qcap, lane);
@@ -456,12 +466,17 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         deg = wi.z;
         aux = wi.x;
       }
+      if (!DAMF_DCHECK(h, aux >= 0 && (long long)aux < ws.rho_cap && st >= 0 && deg >= 0 && deg <= kItemEdges &&
+                              (long long)st + deg <= in.m_cap)) {
+        deg = 0;
+        aux = 0;
+      }
       const float4 rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
       int w0 = 0, d0 = 1;
       if (lane < deg) w0 = __ldg(in.col + st + lane);
-      if (lane < deg) d0 = __ldg(outdeg + w0);
+      if (lane < deg && DAMF_DCHECK(h, (unsigned)w0 < (unsigned)a.ncap)) d0 = __ldg(outdeg + w0);
       scatter_edges<D, SCALED>(rv, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
-                               q, true, true, w0, d0);
+                               q, true, true, w0, d0, a.ncap);
     }
     wq.done += 1;
     }
@@ -551,9 +566,11 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
       const int novf = *reinterpret_cast<volatile int*>(&h->ovf_count);
       for (long long i = gwarp; i < novf; i += nwarps) {
         const int4 wi = __ldcg(ws.work + __ldcg(ws.ovf + i));
-        const float4 rv = f4_ldcg(ws.rho + (size_t)wi.x * D + 4 * q);
-        scatter_edges<D, SCALED>(rv, wi.y, wi.z, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub, q,
-                                 false);
+        const bool ok = DAMF_DCHECK(h, wi.x >= 0 && (long long)wi.x < ws.rho_cap && wi.y >= 0 && wi.z >= 0 &&
+                                           (long long)wi.y + wi.z <= in.m_cap);
+        const float4 rv = f4_ldcg(ws.rho + (size_t)(ok ? wi.x : 0) * D + 4 * q);
+        scatter_edges<D, SCALED>(rv, wi.y, ok ? wi.z : 0, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane,
+                                 sub, q, false, false, 0, 1, a.ncap);
       }
     }
     for (long long u = (long long)blk * blockDim.x + threadIdx.x; u < n; u += (long long)nblocks * blockDim.x)
@@ -770,6 +787,7 @@ PushArgs push_args(const Ctx* c, int direct_chunks) {
   a.eps = (float)c->cfg.eps;
   a.max_phases = c->cfg.max_push_rounds;
   a.d = c->d;
+  a.ncap = c->cfg.n_capacity;
   const int epc = c->d == 128 ? PushShape<128>::EPC : c->d == 64 ? PushShape<64>::EPC
                 : c->d == 32 ? PushShape<32>::EPC : PushShape<16>::EPC;
   a.direct_max = (direct_chunks >= 0 ? direct_chunks : kPushDirectChunks) * epc;

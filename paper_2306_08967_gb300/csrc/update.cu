@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(256) k_gather(DevHeader* h, Workspace ws, cons
   for (int i = tid; i < 16 * D / 4; i += 256) {
     const int rr = i / (D / 4), q = i % (D / 4);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r0 + rr < nrows) v = reinterpret_cast<const float4*>(base + (size_t)idx[r0 + rr] * D)[q];
+    if (r0 + rr < nrows && DAMF_DCHECK(h, idx[r0 + rr] >= 0 && idx[r0 + rr] < h->n_nodes))
+      v = reinterpret_cast<const float4*>(base + (size_t)idx[r0 + rr] * D)[q];
     reinterpret_cast<float4*>(A)[i] = v;
   }
   __syncthreads();
@@ -505,12 +506,14 @@ __global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, flo
     float s = 0.f;
 #pragma unroll 8
     for (int k = 0; k < D; ++k) s = fmaf(A[rr * D + k], P[k * D + j], s);
+    const int u = side == 0 ? ws.S[r0 + rr] : ws.T[r0 + rr];
+    if (!DAMF_DCHECK(h, u >= 0 && u < h->n_nodes)) continue;
     if (side == 0) {
-      const size_t row = (size_t)ws.S[r0 + rr] * D;
+      const size_t row = (size_t)u * D;
       Ub[row + j] += s;
       r[row + j] += s * s0[j];
     } else {
-      Vb[(size_t)ws.T[r0 + rr] * D + j] += s;
+      Vb[(size_t)u * D + j] += s;
     }
   }
 }

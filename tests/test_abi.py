@@ -87,3 +87,15 @@ def test_injected_allocation_failure_is_reported_and_cleaned_up_without_gpu_work
                                  None, ctypes.byref(h))
     assert st == 2 and not h.value                   # DAMF_ERR_CAPACITY, nothing created
     lib.damf_debug_fail_allocations(-1)
+
+
+def test_checked_sources_compile():
+    # the DAMF_CHECK variant (device bounds checks) of the kernels that carry checks compiles
+    import subprocess
+    import tempfile
+    from paper_2306_08967_gb300 import build as b
+    with tempfile.TemporaryDirectory() as td:
+        for src in ("ppr.cu", "update.cu"):
+            cmd = [b.NVCC] + b.ARCH + b.FLAGS + ["-DDAMF_CHECK", "-c", os.path.join(b.CSRC, src), "-o",
+                                                os.path.join(td, src + ".o")]
+            subprocess.run(cmd, check=True, timeout=600)

@@ -55,3 +55,20 @@ def test_allocation_failure_at_any_point_frees_everything(after):
     g, _, _ = make_pair(500, 6.0, 2.5, 32, 0.15, 1e-4, 0xDA3F0000 + 611, oracle=False)
     g.check()
     g.close()
+
+
+def test_checked_build_runs_the_parity_cases_clean():
+    # the DAMF_CHECK build (device bounds checks that set DAMF_ERR_BOUNDS and skip the access)
+    # must pass the push-heavy parity cases: no check fires on correct work
+    import os
+    import subprocess
+    import sys
+    from tests.conftest import ROOT
+    subprocess.run([sys.executable, "-c", "from paper_2306_08967_gb300 import build; build.build(check=True)"],
+                   check=True, cwd=ROOT, timeout=900)
+    env = dict(os.environ, DAMF_LIB_VARIANT="check")
+    out = subprocess.run([sys.executable, "-m", "pytest", "tests/test_gpu_parity.py", "-q", "-x", "-p",
+                          "no:cacheprovider", "-k", "ppr or hub or overflow or multi or deletion or bruteforce or captured"],
+                         env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-3000:]
+    assert " passed" in out.stdout
