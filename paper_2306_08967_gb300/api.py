@@ -7,6 +7,8 @@ the stated dtype; numpy arrays are copied to the device first.
 from __future__ import annotations
 
 import ctypes
+import functools
+import inspect
 
 import numpy as np
 import torch
@@ -24,6 +26,23 @@ class DamfError(RuntimeError):
 def _stream_ptr(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _on_stream(fn):
+    """Runs fn with its `stream` argument (when one is given) as torch's current stream, so that
+    the inputs it copies to the device, the outputs it allocates and the library's work are all
+    ordered on that one stream; the caching allocator then hands those blocks to a later
+    allocation only after that stream's work that used them."""
+    pos = list(inspect.signature(fn).parameters).index("stream")
+
+    @functools.wraps(fn)
+    def run(*args, **kwargs):
+        s = kwargs["stream"] if "stream" in kwargs else (args[pos] if len(args) > pos else None)
+        if s is None:
+            return fn(*args, **kwargs)
+        with torch.cuda.stream(s):
+            return fn(*args, **kwargs)
+    return run
 
 
 def _dev(x, dtype):
@@ -58,6 +77,7 @@ def bytes_required(cfg: Config) -> int:
     return int(_lib.load().damf_bytes_required(ctypes.byref(cfg)))
 
 
+@_on_stream
 def core_svd(sigma, L, R, stream=None):
     """Top-d SVD of diag(sigma, 0) + L R^T through damf_core_svd (Step 2 of an update).
     Returns (E, H, theta) CUDA tensors."""
@@ -79,9 +99,12 @@ def core_svd(sigma, L, R, stream=None):
     return E, H, th
 
 
-def batch_array(batches):
+@_on_stream
+def batch_array(batches, stream=None):
     """damf_batch[] for a list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]]); with a k_dev
-    (device int32 tensor of one element) the arrays hold k_max events of which *k_dev are live."""
+    (device int32 tensor of one element) the arrays hold k_max events of which *k_dev are live.
+    Host arrays are copied to the device on `stream` (default: the current stream), the one
+    the batches are then stepped on."""
     arr = (_lib.Batch * max(len(batches), 1))()
     for i, b in enumerate(batches):
         g, src, dst, op = b[:4]
@@ -96,18 +119,20 @@ def batch_array(batches):
     return arr
 
 
+@_on_stream
 def apply_edges_multi(batches, stream=None):
     """One batch per graph through damf_apply_edges_multi, in order on one stream: batches is a
     list of (DamfGraph, src, dst, op[, new_nodes[, k_dev]])."""
-    st = _lib.load().damf_apply_edges_multi(batch_array(batches), len(batches), _stream_ptr(stream))
+    st = _lib.load().damf_apply_edges_multi(batch_array(batches, stream), len(batches), _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "apply_edges_multi")
 
 
+@_on_stream
 def step_multi(batches, stream=None):
     """One step of many graphs through damf_step_multi: each graph's update and push on its own
     streams, joined back to `stream`. batches as for apply_edges_multi."""
-    st = _lib.load().damf_step_multi(batch_array(batches), len(batches), _stream_ptr(stream))
+    st = _lib.load().damf_step_multi(batch_array(batches, stream), len(batches), _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "step_multi")
 
@@ -143,9 +168,10 @@ class DamfFleet:
         if st != 0:
             raise DamfError(st, self.lib.damf_fleet_last_error(self.h).decode())
 
+    @_on_stream
     def step(self, batches, stream=None):
         """batches: one (src, dst, op[, new_nodes[, k_dev]]) per graph, fleet order."""
-        arr = batch_array([(g, *b) for g, b in zip(self.graphs, batches)])
+        arr = batch_array([(g, *b) for g, b in zip(self.graphs, batches)], stream)
         self._keep = arr
         self._check(self.lib.damf_fleet_step(self.h, arr, _stream_ptr(stream)))
 
@@ -205,6 +231,7 @@ class DamfFleet:
 class DamfGraph:
     """One graph's DAMF state on the current CUDA device (a damf_ctx)."""
 
+    @_on_stream
     def __init__(self, indptr, indices, cfg: Config, omega, stream=None):
         self.lib = _lib.load()
         self.cfg = cfg
@@ -228,6 +255,7 @@ class DamfGraph:
         if st != 0:
             raise DamfError(st, self.lib.damf_last_error(self.h).decode())
 
+    @_on_stream
     def save(self, stream=None) -> dict:
         """A checkpoint: the full state (CUDA tensors), the out-adjacency (host CSR) and the
         config; DamfGraph.restore(checkpoint) continues from it."""
@@ -245,6 +273,7 @@ class DamfGraph:
                 "indices": col.copy(), "cfg": cfg}
 
     @classmethod
+    @_on_stream
     def restore(cls, ckpt: dict, stream=None) -> "DamfGraph":
         """A new context continuing a checkpoint from DamfGraph.save (damf_restore)."""
         self = cls.__new__(cls)
@@ -272,6 +301,7 @@ class DamfGraph:
     def n(self) -> int:
         return int(self.lib.damf_num_nodes(self.h))
 
+    @_on_stream
     def apply_edges(self, src, dst, op, new_nodes: int = 0, stream=None):
         """Device-resident events (int32 src/dst, int8 op)."""
         s, t, o = _dev(src, torch.int32), _dev(dst, torch.int32), _dev(op, torch.int8)
@@ -280,6 +310,7 @@ class DamfGraph:
                                               ctypes.c_void_p(o.data_ptr()), int(s.numel()), int(new_nodes),
                                               _stream_ptr(stream)))
 
+    @_on_stream
     def apply_edges_counted(self, src, dst, op, k_dev, new_nodes: int = 0, stream=None):
         """Device events of which the first k_dev[0] (a CUDA int32 tensor, read when the work
         runs) are live; src/dst/op hold k_max events."""
@@ -330,6 +361,7 @@ class DamfGraph:
         """Records a torch.cuda.Event on the push stream after the most recent push."""
         self._check(self.lib.damf_record_event(self.h, ctypes.c_void_p(event.cuda_event)))
 
+    @_on_stream
     def embeddings(self, rows=None, want=("X", "Y", "Z", "sigma"), stream=None):
         """Returns a dict of CUDA tensors: X, Y, Z (count x d) and sigma (d)."""
         if rows is None:
@@ -354,6 +386,7 @@ class DamfGraph:
                                                  _stream_ptr(stream)))
         return out
 
+    @_on_stream
     def score_pairs(self, src, dst, context="Z", symmetric=None, stream=None):
         """Link-prediction scores context(src[i]) . Y[dst[i]] (context "Z" enhanced or "X");
         symmetric (default: the graph is undirected) takes the larger of both directions."""
@@ -369,6 +402,7 @@ class DamfGraph:
                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
+    @_on_stream
     def topk(self, rows, k, context="Z", symmetric=None, stream=None):
         """The k best-scoring nodes v != u for each query u in rows: (ids int32, scores float32),
         each count x k, decreasing score, equal scores by increasing id (-1 / -inf padding)."""
@@ -382,6 +416,7 @@ class DamfGraph:
                                        _stream_ptr(stream)))
         return idx, sc
 
+    @_on_stream
     def state(self, stream=None) -> dict:
         """Base state: Ub, Vb, Zb, r (n x d), PU, PV (d x d), sigma, s0 (d) as CUDA tensors."""
         n, d = self.n, self.d

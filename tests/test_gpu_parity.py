@@ -629,3 +629,31 @@ def test_factor_reads_do_not_depend_on_the_push():
         assert torch.allclose(late["Z"].double(), Z, rtol=1e-4, atol=1e-6)
     g.check()
     g.close()
+
+
+def test_inputs_are_staged_on_the_given_stream():
+    # host events handed over with stream=s are copied to the device on s: a long kernel queued
+    # on torch's current stream must not hold the copies back past the library's reads on s,
+    # and a twin stepped on the current stream ends with bit-identical factors
+    rng = np.random.default_rng(71)
+    a, _, _ = make_pair(2000, 8.0, 2.2, 32, 0.15, 1e-5, SEED + 150, oracle=False)
+    b, _, _ = make_pair(2000, 8.0, 2.2, 32, 0.15, 1e-5, SEED + 150, oracle=False)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(5):
+        ev = _events(rng, a.n, 50)
+        torch.cuda._sleep(20_000_000)         # about 10 ms of spinning on the current stream
+        a.apply_edges(*ev, stream=s)
+        a.ppr_refresh(stream=s)
+        b.apply_edges(*ev)
+        b.ppr_refresh()
+    ea = a.embeddings(want=("X", "Y", "sigma"), stream=s)
+    s.synchronize()
+    eb = b.embeddings(want=("X", "Y", "sigma"))
+    torch.cuda.synchronize()
+    for k in ("X", "Y", "sigma"):
+        assert torch.equal(ea[k], eb[k]), k
+    a.check()
+    b.check()
+    a.close()
+    b.close()
