@@ -150,8 +150,10 @@ typedef struct {
  * graphs of uneven size per call), in order, on `stream`: each entry is exactly
  * damf_apply_edges(batches[i].ctx, ...), so every graph's result is the same as when its
  * batch is applied alone. Each graph's push still runs on its own context's stream
- * (damf_ppr_refresh). Returns the first non-OK status (the remaining batches are not
- * applied); DAMF_ERR_INVALID for num_graphs < 0 or a NULL batches array / context.
+ * (damf_ppr_refresh). Every batch's host-side checks (arguments, node capacity) are taken
+ * before any work is enqueued: a batch they reject poisons its own context and no graph of
+ * the call gets new work. Otherwise returns the first non-OK status (the remaining batches
+ * are not applied); DAMF_ERR_INVALID for num_graphs < 0 or a NULL batches array / context.
  */
 damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
 
@@ -165,8 +167,10 @@ damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs
  * kernels overlap on the device, and each graph's result equals its result when its batch
  * is applied and pushed alone.  Capturable in one CUDA graph (join each context, damf_join,
  * before the capture starts); a replay then runs the whole step as one launch.  A context
- * may appear once per call (DAMF_ERR_INVALID otherwise, nothing enqueued).  Returns the
- * first non-OK status; the graphs before it have been enqueued.
+ * may appear once per call (DAMF_ERR_INVALID otherwise, nothing enqueued).  A batch that the
+ * host-side checks (arguments, node capacity) reject poisons its own context and nothing is
+ * enqueued for any graph; after a later failure (a CUDA call) the graphs before it have been
+ * enqueued.  Returns the first non-OK status.
  */
 damf_status damf_step_multi(const damf_batch* batches, int32_t num_graphs, void* stream);
 
@@ -199,7 +203,8 @@ damf_status damf_fleet_create(damf_ctx* const* ctxs, int32_t count, damf_fleet**
  * graph; `stream` waits for all of it.  Capturable in one CUDA graph (join every context,
  * damf_join, before the capture starts; new_nodes = 0 and refold_every = 0 keep the host
  * bookkeeping of a captured step the same at every replay).  Afterwards each context reads
- * and joins like after damf_ppr_refresh.
+ * and joins like after damf_ppr_refresh.  A batch that the host-side checks (arguments, node
+ * capacity) reject poisons its own context, and nothing is enqueued for any graph.
  */
 damf_status damf_fleet_step(damf_fleet* fleet, const damf_batch* batches, void* stream);
 

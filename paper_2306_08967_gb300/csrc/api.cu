@@ -725,13 +725,34 @@ damf_status damf_save_state(damf_ctx* x, damf_state* st, void* stream) {
 // Events src/dst/op[0 .. k), or the first *kdev of them (clamped to [0, k]) when kdev is
 // given: ceil(k / 64) updates are enqueued either way, and an update whose events are all
 // beyond the live count finds no net change and leaves every state untouched.
-static damf_status apply_impl(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
-                              const int32_t* kdev, int32_t new_nodes, cudaStream_t s) {
+// The host-side checks of one batch (arguments, node capacity), taken before any of its work
+// is enqueued; a failed one poisons that context only.
+static damf_status batch_args_ok(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                                 int32_t new_nodes) {
   if (!x) return DAMF_ERR_INVALID;
   Ctx* c = &x->c;
   if (c->sticky) return (damf_status)c->sticky;
   if (k < 0 || new_nodes < 0 || (k > 0 && (!src || !dst || !op))) return fail(c, DAMF_ERR_INVALID, "arguments", cudaSuccess);
   if ((long long)c->n + new_nodes > c->cfg.n_capacity) return fail(c, DAMF_ERR_CAPACITY, "node capacity", cudaSuccess);
+  return DAMF_OK;
+}
+
+// The same checks for every batch of a multi-graph call (ctxs[i], or batches[i].ctx when ctxs
+// is null), so that a rejected batch leaves every graph of the call without new work.
+static damf_status batches_args_ok(const damf_batch* batches, int32_t count, damf_ctx* const* ctxs) {
+  for (int32_t i = 0; i < count; ++i) {
+    const damf_batch& b = batches[i];
+    const damf_status st = batch_args_ok(ctxs ? ctxs[i] : b.ctx, b.src, b.dst, b.op, b.k, b.new_nodes);
+    if (st != DAMF_OK) return st;
+  }
+  return DAMF_OK;
+}
+
+static damf_status apply_impl(damf_ctx* x, const int32_t* src, const int32_t* dst, const int8_t* op, int32_t k,
+                              const int32_t* kdev, int32_t new_nodes, cudaStream_t s) {
+  const damf_status ok = batch_args_ok(x, src, dst, op, k, new_nodes);
+  if (ok != DAMF_OK) return ok;
+  Ctx* c = &x->c;
   const int n_after = c->n + new_nodes;
   DAMF_CUDA(launch_validate(c, src, dst, op, k, kdev, n_after, s), "validate");
   c->launches += 1;
@@ -819,9 +840,12 @@ damf_status damf_delete_nodes(damf_ctx* x, const int32_t* nodes, int32_t count, 
 
 damf_status damf_apply_edges_multi(const damf_batch* batches, int32_t num_graphs, void* stream) {
   if (num_graphs < 0 || (num_graphs > 0 && !batches)) return DAMF_ERR_INVALID;
+  for (int32_t i = 0; i < num_graphs; ++i)
+    if (!batches[i].ctx) return DAMF_ERR_INVALID;
+  const damf_status ok = batches_args_ok(batches, num_graphs, nullptr);
+  if (ok != DAMF_OK) return ok;
   for (int32_t i = 0; i < num_graphs; ++i) {
     const damf_batch& b = batches[i];
-    if (!b.ctx) return DAMF_ERR_INVALID;
     const damf_status st = apply_impl(b.ctx, b.src, b.dst, b.op, b.k, b.k_dev, b.new_nodes, (cudaStream_t)stream);
     if (st != DAMF_OK) return st;
   }
@@ -836,6 +860,8 @@ damf_status damf_step_multi(const damf_batch* batches, int32_t num_graphs, void*
     for (int32_t j = 0; j < i; ++j)
       if (batches[j].ctx == batches[i].ctx) return reject(&batches[i].ctx->c, "step_multi: a graph appears twice");
   }
+  const damf_status ok = batches_args_ok(batches, num_graphs, nullptr);
+  if (ok != DAMF_OK) return ok;
   cudaStream_t caller = (cudaStream_t)stream;
   for (int32_t i = 0; i < num_graphs; ++i) {
     const damf_batch& b = batches[i];
@@ -1215,6 +1241,8 @@ damf_status damf_fleet_step(damf_fleet* f, const damf_batch* batches, void* stre
     if (batches[i].ctx && batches[i].ctx != f->ctxs[i]) return fleet_fail(f, DAMF_ERR_INVALID, "fleet: batch order");
     if (f->ctxs[i]->c.sticky) return (damf_status)f->ctxs[i]->c.sticky;
   }
+  const damf_status ok = batches_args_ok(batches, G, f->ctxs.data());
+  if (ok != DAMF_OK) return ok;
   cudaStream_t caller = (cudaStream_t)stream;
   f->stepped = 1;
   cudaError_t e = fleet_mark(f, caller);

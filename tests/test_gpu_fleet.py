@@ -302,6 +302,24 @@ def test_fleet_shares_are_validated():
     for g, t in zip(gs, twins):
         _same_factors(g, t)
         _push_bound(g, 0.15, 1e-5)
+    # a step whose second batch the host checks reject (node capacity) enqueues nothing for
+    # any graph: the others stay where their twins are and go on alone; the second is poisoned
+    evs = [_events(rng, g.n, 40) for g in gs]
+    evs[1] = evs[1] + (10 ** 6,)
+    with pytest.raises(DamfError):
+        fleet.step(evs)
+    torch.cuda.synchronize()
+    for i in (0, 2):
+        _same_factors(gs[i], twins[i])
+        gs[i].apply_edges(*evs[i])
+        gs[i].ppr_refresh()
+        twins[i].apply_edges(*evs[i])
+        twins[i].ppr_refresh()
+        gs[i].check()
+        _same_factors(gs[i], twins[i])
+        _push_bound(gs[i], 0.15, 1e-5)
+    with pytest.raises(DamfError):
+        gs[1].check()
     fleet.close()
     for g in gs + twins:
         g.close()
