@@ -94,8 +94,11 @@ def test_checked_sources_compile():
     import subprocess
     import tempfile
     from paper_2306_08967_gb300 import build as b
+    import concurrent.futures
     with tempfile.TemporaryDirectory() as td:
-        for src in ("ppr.cu", "update.cu"):
+        def compile_one(src):
             cmd = [b.NVCC] + b.ARCH + b.FLAGS + ["-DDAMF_CHECK", "-c", os.path.join(b.CSRC, src), "-o",
                                                 os.path.join(td, src + ".o")]
             subprocess.run(cmd, check=True, timeout=600)
+        with concurrent.futures.ThreadPoolExecutor(2) as ex:
+            list(ex.map(compile_one, ("ppr.cu", "update.cu")))
