@@ -102,3 +102,46 @@ def test_checked_sources_compile():
             subprocess.run(cmd, check=True, timeout=600)
         with concurrent.futures.ThreadPoolExecutor(2) as ex:
             list(ex.map(compile_one, ("ppr.cu", "update.cu")))
+
+
+def test_every_entry_point_turns_away_null_handles_without_gpu_work():
+    # each call given NULL handles / pointers and zero sizes returns its documented answer on
+    # the host (no CUDA call is reached; there is no GPU here): DAMF_ERR_INVALID for a status,
+    # 0 or -1 for a count, a message for an error text; an empty multi-graph call is a no-op
+    import subprocess
+    import sys
+    code = r'''
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2306_08967_gb300 import _lib
+lib = _lib.load()
+out = {}
+for name, (res, args) in sorted(_lib.SIGNATURES.items()):
+    if name == "damf_debug_fail_allocations":
+        continue
+    vals = [0 if a in (ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double) else None for a in args]
+    r = getattr(lib, name)(*vals)
+    out[name] = r.decode() if isinstance(r, bytes) else r
+print(json.dumps(out))
+'''
+    # a separate process: a NULL dereference fails this test instead of ending the session
+    p = subprocess.run([sys.executable, "-c", code, ROOT], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, p.stderr[-2000:]
+    import json
+    out = json.loads(p.stdout.strip().splitlines()[-1])
+    from paper_2306_08967_gb300 import _lib
+    assert set(out) == set(_lib.SIGNATURES) - {"damf_debug_fail_allocations"}
+    counts = {"damf_bytes_required": 0, "damf_rsvd_width": 0, "damf_core_svd_workspace_size": 0,
+              "damf_num_nodes": 0, "damf_fleet_launches": 0, "damf_plan_slots": -1}
+    empty_ok = {"damf_apply_edges_multi", "damf_step_multi"}      # zero graphs: nothing to do
+    for name, r in out.items():
+        if name in counts:
+            assert r == counts[name], name
+        elif name in empty_ok:
+            assert r == 0, name
+        elif name in ("damf_destroy", "damf_fleet_destroy"):
+            assert r is None, name
+        elif name in ("damf_last_error", "damf_fleet_last_error"):
+            assert isinstance(r, str) and r, name
+        else:
+            assert r == 1, (name, r)                              # DAMF_ERR_INVALID
