@@ -27,10 +27,24 @@ import json
 import os
 import sys
 
+
+
+def _oracle_threads(argv):
+    # --oracle-threads N: BLAS threads of the oracle (default 1), read before numpy loads
+    for i, a in enumerate(argv):
+        if a == "--oracle-threads" and i + 1 < len(argv):
+            return max(1, int(argv[i + 1]))
+        if a.startswith("--oracle-threads="):
+            return max(1, int(a.split("=", 1)[1]))
+    return 1
+
+
+ORACLE_THREADS = _oracle_threads(sys.argv)
+
 if "--impl" in sys.argv and "reference" in sys.argv or "--oracle-worker" in sys.argv:
-    # the oracle runs single-threaded: pin BLAS pools before numpy loads
+    # pin the oracle's BLAS pools before numpy loads (one thread unless --oracle-threads)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"
+        os.environ[var] = str(ORACLE_THREADS)
 
 import subprocess
 import time
@@ -89,18 +103,21 @@ def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
         n = orc.n
         np.savez(save_path, X=orc.X()[:n], Y=orc.Y()[:n], Z=orc.Z()[:n], sigma=orc.sigma,
                  batches=warmup + len(lat))
-    return {"value": edges / total, "unit": UNIT, "cores": 1, "kind": "oracle", "batches": len(lat),
+    threads = ("1 thread" if ORACLE_THREADS == 1 else
+               "%d BLAS threads (its push, in C, on one)" % ORACLE_THREADS)
+    return {"value": edges / total, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle", "batches": len(lat),
             "edges": edges, "seconds": total, "init_s": init_s,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "sample": "first %d batches of the %s stream after %d warm-up batches (%d edges), FP64 oracle, "
-                      "1 thread" % (len(lat), c.name, warmup, edges)}
+                      "%s" % (len(lat), c.name, warmup, edges, threads)}
 
 
 def oracle_subprocess(c, steps, budget, save_path=None):
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", c.name, "--steps", str(steps),
-           "--budget", str(budget)] + (["--save-state", save_path] if save_path else [])
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+           "--budget", str(budget), "--oracle-threads", str(ORACLE_THREADS)] + (
+        ["--save-state", save_path] if save_path else [])
+    nt = str(ORACLE_THREADS)
+    env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
     for line in out.stdout.splitlines()[::-1]:
         if line.startswith("{"):
@@ -843,6 +860,8 @@ def main():
                     help="skip the link-prediction query timing (score_pairs, topk) after the run")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=1,
+                    help="BLAS threads of the timed oracle (cpu_baseline and --impl reference); default 1")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
     ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here")
