@@ -144,3 +144,23 @@ def test_node_arrivals_rebuild_the_graph(directed):
                 got.add((t, s))
     want = set(zip(*[x.tolist() for x in _edges(ip, ix)]))
     assert got == want
+
+
+def test_serving_workload_sessions_and_arrivals():
+    from synth import SERVING
+    sw = SERVING["C5"]
+    big = sw.big()
+    assert big.directed and big.n == sw.big_n and big.d == 128
+    smalls = [sw.small(i) for i in range(400)]
+    n = np.array([s.n for s in smalls])
+    assert n.min() >= sw.small_lo and n.max() <= sw.small_hi and all(s.directed for s in smalls)
+    # log-uniform sizes: the median near the geometric mean of the ends
+    assert abs(np.log(np.median(n)) - 0.5 * (np.log(sw.small_lo) + np.log(sw.small_hi))) < 0.15
+    assert [sw.small(i).n for i in range(5)] == list(n[:5]) and len({s.seed for s in smalls}) == 400
+    # Poisson arrivals: increasing times in [0, T), count and mean gap as the rate says
+    rate, T = 200.0, 50.0
+    t = sw.arrivals(rate, T, seed=3)
+    assert np.all(np.diff(t) > 0) and t.min() >= 0 and t.max() < T
+    assert abs(len(t) - rate * T) < 4 * np.sqrt(rate * T)
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 1 / rate) < 0.05 / rate and abs(gaps.std() / gaps.mean() - 1.0) < 0.05
