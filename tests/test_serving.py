@@ -165,3 +165,100 @@ def test_graphs_active_lately_are_not_evicted():
     s.open(3, 30)
     assert s.plan_evictions(t=11.7) == []        # both asked within the last 2 s
     assert s.plan_evictions(t=12.5) == [1]       # 1 has been idle for 2.5 s
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_traffic_keeps_the_scheduler_invariants(seed):
+    # the Server's loop with the device replaced by delays: sessions open, ask and close at
+    # random; steps finish in order after random delays, admissions and evictions take time.
+    # Throughout: memory within the budget and equal to what the sessions on the device hold;
+    # admissions first come; a step holds one request per resident graph; only idle graphs
+    # are evicted; and in the end every request was served once, in its session's order.
+    rng = np.random.default_rng(seed)
+    budget = 100
+    s = Scheduler(budget_bytes=budget, max_events=8, min_idle_s=float(rng.choice([0.0, 2.0])))
+    on_device = ("admitting", "resident", "evicting", "released")
+    submitted, served = {}, {}
+    inflight, admitting, evicting, releasing = [], {}, [], []
+    rid = nsid = 0
+    admitted_order, waiting_order = [], []
+
+    def check():
+        assert 0 <= s.used <= budget
+        assert s.used == sum(x.nbytes for x in s.sessions.values() if x.state in on_device)
+
+    def turn(t, arrivals):
+        nonlocal rid, nsid
+        if arrivals:
+            if rng.random() < 0.15 and nsid < 40:
+                s.open(nsid, int(rng.integers(10, 61)), t)
+                submitted[nsid] = []
+                nsid += 1
+            open_ = [x.sid for x in s.sessions.values() if not x.closing]
+            for _ in range(int(rng.integers(0, 4))):
+                if open_:
+                    sid = int(rng.choice(open_))
+                    s.submit(_req(rid, sid, k=int(rng.integers(1, 9)), t=t))
+                    submitted[sid].append(rid)
+                    rid += 1
+            if open_ and rng.random() < 0.05:
+                s.close(int(rng.choice(open_)))
+        # steps finish in issue order
+        while inflight and rng.random() < 0.6:
+            st, reqs = inflight.pop(0)
+            s.step_done(st, reqs, t)
+        for sid in s.releases():
+            releasing.append((sid, s.next_step_id - 1))
+        for sid, last in list(releasing):
+            if last <= s.done_upto:
+                s.freed(sid)
+                releasing.remove((sid, last))
+        for sid, last in list(evicting):
+            if last <= s.done_upto and rng.random() < 0.5:
+                s.evicted(sid)
+                evicting.remove((sid, last))
+        for sid in s.plan_evictions(t):
+            x = s.sessions[sid]
+            assert x.state == "resident" and not x.queue and not x.closing and x.last_step <= s.done_upto
+            s.evicting(sid)
+            evicting.append((sid, s.next_step_id - 1))
+        before = list(s.waiting)
+        got = s.admissions(t)
+        assert got == before[:len(got)]                 # first come, first admitted
+        admitted_order.extend(got)
+        waiting_order.extend(before[:len(got)])
+        for sid in got:
+            admitting[sid] = int(rng.integers(0, 3))
+        for sid in list(admitting):
+            if admitting[sid] == 0:
+                s.admitted(sid)
+                del admitting[sid]
+            else:
+                admitting[sid] -= 1
+        if len(inflight) < 2:
+            nxt = s.next_step(t)
+            if nxt is not None:
+                st, reqs = nxt
+                for sid, r in reqs.items():
+                    assert s.sessions[sid].state == "resident" and r.sid == sid
+                    served.setdefault(sid, []).append(r.rid)
+                inflight.append((st, reqs))
+        check()
+
+    t = 0.0
+    for _ in range(600):
+        t += float(rng.exponential(0.3))
+        turn(t, arrivals=True)
+    for sid in list(s.sessions):
+        if not s.sessions[sid].closing:
+            s.close(sid)
+    for _ in range(5000):
+        if all(x.state == "freed" for x in s.sessions.values()):
+            break
+        t += 0.3
+        turn(t, arrivals=False)
+    assert all(x.state == "freed" for x in s.sessions.values())
+    assert s.used == 0 and not s.waiting and s.backlog() == 0
+    for sid, rids in submitted.items():
+        assert served.get(sid, []) == rids, sid         # each once, in arrival order
+    assert sum(x.evictions for x in s.sessions.values()) > 0    # the traffic did make graphs leave
