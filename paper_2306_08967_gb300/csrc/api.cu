@@ -384,16 +384,13 @@ struct Slot {
   std::vector<int> graphs;   // fleet indices
 };
 
-// Slots of one threshold mode's graphs (idx) over at most maxb CTAs. With `given`, one slot per
-// graph with those CTAs. Otherwise graph j's fair share is x_j = maxb w_j / sum(w), w_j =
-// (d (n + m))^exponent: a graph with x_j >= cap owns floor(x_j) CTAs (at least one), the rest are
-// packed first-fit-decreasing into one-CTA bins of total share <= cap, and CTAs left over go
-// to the owners by largest remainders; cap starts at 1 and grows until the slots fit.
 // Slots of `w.size()` graphs with work weights w over at most maxb CTAs (Slot.graphs holds
 // positions in w): graph j's fair share is x_j = maxb w_j / sum(w); a graph with x_j >= cap
 // owns floor(x_j) CTAs (at least one), the rest are packed first-fit-decreasing into one-CTA
 // bins of total share <= cap, and CTAs left over go to the owners by largest remainders; cap
-// starts at 1 and grows until the slots fit.
+// starts at 1 and grows until the slots fit. When no graph owns CTAs (more graphs than CTAs),
+// nobody could take the CTAs the last growth step left over, so cap is then narrowed by
+// bisection towards the smallest one that fits, keeping the plan with the most bins.
 void pack_slots(const std::vector<double>& w, int maxb, std::vector<Slot>* out) {
   const int cnt = (int)w.size();
   std::vector<double> x(cnt);
@@ -403,9 +400,14 @@ void pack_slots(const std::vector<double>& w, int maxb, std::vector<Slot>* out) 
   std::vector<int> by_x(cnt);
   for (int j = 0; j < cnt; ++j) by_x[j] = j;
   std::sort(by_x.begin(), by_x.end(), [&](int a, int b) { return x[a] > x[b] || (x[a] == x[b] && a < b); });
-  for (double cap = 1.0;; cap *= 1.25) {
-    std::vector<Slot> owners, bins;
-    std::vector<double> bin_load, rem;
+  std::vector<Slot> owners, bins;
+  std::vector<double> rem;
+  // the slots for one cap; returns the CTAs they take
+  auto attempt = [&](double cap) -> long long {
+    owners.clear();
+    bins.clear();
+    rem.clear();
+    std::vector<double> bin_load;
     for (int j : by_x) {
       if (x[j] >= cap) {
         owners.push_back(Slot{std::max(1, (int)std::floor(x[j])), {j}});
@@ -423,7 +425,35 @@ void pack_slots(const std::vector<double>& w, int maxb, std::vector<Slot>* out) 
     }
     long long used = (long long)bins.size();
     for (const Slot& o : owners) used += o.blocks;
-    if (used > maxb) continue;   // cap >= maxb leaves one bin, so this ends
+    return used;
+  };
+  double lo = 0.0;   // the largest cap seen that did not fit
+  for (double cap = 1.0;; cap *= 1.25) {
+    long long used = attempt(cap);
+    if (used > maxb) {   // cap >= maxb leaves one bin, so this ends
+      lo = cap;
+      continue;
+    }
+    if (owners.empty() && used < maxb && lo > 0.0) {
+      std::vector<Slot> best = bins;
+      long long best_used = used;
+      double hi = cap;
+      for (int it = 0; it < 40 && best_used < maxb; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const long long u = attempt(mid);
+        if (u > maxb) {
+          lo = mid;
+        } else {
+          hi = mid;
+          if (u > best_used && owners.empty()) {
+            best = bins;
+            best_used = u;
+          }
+        }
+      }
+      *out = best;
+      return;
+    }
     std::vector<int> order(owners.size());
     for (size_t k = 0; k < owners.size(); ++k) order[k] = (int)k;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return rem[a] > rem[b] || (rem[a] == rem[b] && a < b); });

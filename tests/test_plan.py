@@ -68,3 +68,15 @@ def test_deterministic_and_validated():
 def test_one_graph_gets_everything():
     slot_of, ctas, _ = _check([7.0], 608)
     assert list(ctas) == [608]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_random_fleets_keep_the_plan_invariants(seed):
+    rng = np.random.default_rng(seed)
+    g = int(rng.integers(1, 700))
+    maxb = int(rng.choice([1, 2, 7, 152, 304, 608]))
+    w = np.exp(rng.uniform(0.0, float(rng.choice([0.1, 3.0, 12.0])), size=g))
+    slot_of, ctas, x = _check(w, maxb)
+    # every CTA of the budget goes to some slot unless there are fewer graphs than CTAs to give
+    assert ctas.sum() == maxb or len(ctas) == g
+    assert len(ctas) <= maxb
