@@ -145,3 +145,17 @@ print(json.dumps(out))
             assert isinstance(r, str) and r, name
         else:
             assert r == 1, (name, r)                              # DAMF_ERR_INVALID
+
+
+def test_bytes_required_grows_with_every_size():
+    # admission control counts the state (four n_cap x d tables), the adjacency (m_cap entries)
+    # and the workspaces: more rows, entries or rank never need fewer bytes
+    from paper_2306_08967_gb300 import _lib, bytes_required, make_config
+    _lib.load()
+    base = dict(n=50_000, d=64, alpha=0.15, eps=1e-5, n_capacity=60_000, m_capacity=2_000_000)
+    b0 = bytes_required(make_config(**base))
+    assert b0 > 4 * 60_000 * 64 * 4 + 2_000_000 * 4       # at least the state and the entries
+    for key, more in (("n_capacity", 120_000), ("m_capacity", 8_000_000), ("d", 128)):
+        assert bytes_required(make_config(**dict(base, **{key: more}))) > b0, key
+    assert bytes_required(make_config(**dict(base, directed=True))) > b0   # the reverse adjacency too
+    assert bytes_required(make_config(**dict(base, n_capacity=40_000))) == 0   # capacity below n
