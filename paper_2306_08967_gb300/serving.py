@@ -312,7 +312,11 @@ class Server:
     def _checkpoint(self, g):
         """The graph's checkpoint with its tensors in pinned host memory."""
         ck = g.save()
-        ck["state"] = {k: v.cpu().pin_memory() for k, v in ck["state"].items()}
+        torch = self.torch
+        # one device-to-host copy per tensor, straight into pinned memory (ordered after the
+        # save on the current stream; a copy into host memory returns when it is done)
+        ck["state"] = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True).copy_(v)
+                       for k, v in ck["state"].items()}
         return ck
 
     def _evict_job(self, g):
