@@ -285,7 +285,7 @@ class DamfGraph:
         ip = _dev(ckpt["indptr"], torch.int32)
         ix = _dev(ckpt["indices"], torch.int32) if len(ckpt["indices"]) else torch.zeros(1, dtype=torch.int32,
                                                                                          device="cuda")
-        t = ckpt["state"]
+        t = {k: _dev(v, torch.float32) for k, v in ckpt["state"].items()}   # host tensors are copied over
         st = _lib.State(**{k: v.data_ptr() for k, v in t.items()},
                         updates_since_fold=int(ckpt["updates_since_fold"]))
         h = ctypes.c_void_p()
@@ -296,6 +296,20 @@ class DamfGraph:
             raise DamfError(code, "restore")
         self.h = h
         return self
+
+    @_on_stream
+    def save_file(self, path: str, stream=None) -> int:
+        """Writes a checkpoint (save()) to a file (paper_2306_08967_gb300.checkpoint); returns
+        its size in bytes."""
+        from .checkpoint import write_checkpoint
+        return write_checkpoint(path, self.save(stream))
+
+    @classmethod
+    @_on_stream
+    def load_file(cls, path: str, stream=None) -> "DamfGraph":
+        """A new context continuing the checkpoint file at `path` (checked before any device work)."""
+        from .checkpoint import read_checkpoint
+        return cls.restore(read_checkpoint(path), stream)
 
     @property
     def n(self) -> int:
