@@ -864,7 +864,8 @@ def main():
                     help="BLAS threads of the timed oracle (cpu_baseline and --impl reference); default 1")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
-    ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here")
+    ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here; "
+                    "C5: one per server step (issue and completion time, requests, edges, graphs)")
     ap.add_argument("--push-blocks", type=int, default=0, help="push CTAs (0: two per SM)")
     ap.add_argument("--push-chunks", type=int, default=-1,
                     help="in-edge chunks a row task scatters itself before its row becomes hub items (-1: 8)")
@@ -979,6 +980,26 @@ def serving_inputs(sw, n_pool, big_batches, small_batches):
     small = fleet_inputs([sw.small(i) for i in range(n_pool)], small_batches, log_sizes=True)
     big = fleet_inputs([sw.big()], big_batches, workers=1, log_sizes=True)[0]
     return big, small
+
+
+def serving_timeline(reqs):
+    """The serving loop's timeline, one record per server step, from the requests it served
+    ((Request, phase) pairs): issue and completion time (s on the arrival clock), requests, edge
+    events, the graphs that had a request in it and the earliest arrival among them."""
+    steps = {}
+    for r, ph in reqs:
+        if r.step is None or r.t_done is None:
+            continue
+        e = steps.setdefault(r.step, {"step": int(r.step), "t_issue_s": r.t_issue, "t_done_s": r.t_done,
+                                      "requests": 0, "edges": 0, "graphs": [], "first_arrival_s": r.t_arrive,
+                                      "phase": ph})
+        e["requests"] += 1
+        e["edges"] += r.k
+        e["graphs"].append(int(r.sid))
+        e["first_arrival_s"] = min(e["first_arrival_s"], r.t_arrive)
+    for e in steps.values():
+        e["graphs"].sort()
+    return [steps[k] for k in sorted(steps)]
 
 
 def run_serving(args, sw):
@@ -1096,6 +1117,10 @@ def run_serving(args, sw):
         progress("drained" if drained else "drain cut short")
     t_end = srv.now()
     reqs = [(r, p) for r, p in reqs if r.t_done is not None]
+    if args.log_jsonl:   # the loop's timeline: one line per server step
+        with open(args.log_jsonl, "w") as f:
+            for rec in serving_timeline(reqs):
+                f.write(json.dumps(rec) + "\n")
     for g in list(srv.graphs.values()):
         g.check()
     def pct(rs):

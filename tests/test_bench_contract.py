@@ -35,3 +35,25 @@ def test_reference_arm_reports_the_threads_it_used():
     assert out.returncode == 0, out.stderr[-500:]
     d = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
     assert d["cpu_baseline"]["cores"] == 2 and "2 BLAS threads" in d["cpu_baseline"]["sample"]
+
+
+def test_serving_timeline_has_one_record_per_step():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2306_08967_gb300.serving import Request
+
+    def req(rid, sid, k, t_arr, step, t_issue, t_done):
+        z = np.zeros(k, np.int32)
+        r = Request(rid, sid, z, z, np.ones(k, np.int8), t_arr)
+        r.step, r.t_issue, r.t_done = step, t_issue, t_done
+        return r
+
+    reqs = [(req(0, 3, 5, 0.10, 0, 0.11, 0.20), 0), (req(1, 1, 2, 0.05, 0, 0.11, 0.20), 0),
+            (req(2, 3, 7, 0.15, 1, 0.21, 0.30), 1), (req(3, 2, 1, 0.40, None, None, None), 1)]
+    tl = bench.serving_timeline(reqs)
+    assert [e["step"] for e in tl] == [0, 1]
+    assert tl[0]["requests"] == 2 and tl[0]["edges"] == 7 and tl[0]["graphs"] == [1, 3]
+    assert tl[0]["first_arrival_s"] == 0.05 and tl[0]["t_issue_s"] == 0.11 and tl[0]["t_done_s"] == 0.20
+    assert tl[1]["requests"] == 1 and tl[1]["edges"] == 7 and tl[1]["phase"] == 1
+    json.dumps(tl)                                   # JSON-ready
