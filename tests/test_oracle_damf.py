@@ -110,3 +110,30 @@ def test_node_arrival_matches_theorem_1():
     got = orc.X() @ orc.Y().T
     assert rel_fro(got[:n0, :], target) < 1e-10
     assert np.abs(got[n0, :]).max() < 1e-12          # the new row stays zero
+
+
+def test_residual_factor_of_a_block_partly_in_the_span():
+    # Prop. 1 for a block: the residual (I - U U^T) B factors as Q R with R^T R = B^T B - W^T W,
+    # W = U^T B. Columns inside span(U) add nothing to the residual: two of three columns in the
+    # span leave R with one row, all three in the span leave R empty (R_B = 0, the
+    # rank-deficient branch), and the factor's pseudo-inverse inverts it on its row space.
+    from oracle.damf import _sqrt_factor
+    rng = np.random.default_rng(17)
+    n, d = 60, 6
+    U, _ = np.linalg.qr(rng.standard_normal((n, d)))
+    inside = U @ rng.standard_normal((d, 2))
+    outside = rng.standard_normal((n, 1))
+    for B, rank in ((np.hstack([inside, outside]), 1), (np.hstack([inside, U[:, :1]]), 0),
+                    (rng.standard_normal((n, 3)), 3)):
+        W = U.T @ B
+        R, Rp = _sqrt_factor(B.T @ B - W.T @ W)
+        assert R.shape == (rank, B.shape[1]) and Rp.shape == (B.shape[1], rank)
+        np.testing.assert_allclose(R.T @ R, B.T @ B - W.T @ W, atol=1e-10)
+        np.testing.assert_allclose(R @ Rp, np.eye(rank), atol=1e-10)
+        resid = B - U @ W
+        if rank:
+            Q = resid @ Rp                              # orthonormal residual directions
+            np.testing.assert_allclose(Q.T @ Q, np.eye(rank), atol=1e-10)
+            np.testing.assert_allclose(Q @ R, resid, atol=1e-10)
+        else:
+            assert np.abs(resid).max() < 1e-12
