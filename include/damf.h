@@ -91,8 +91,10 @@ int32_t damf_rsvd_width(const damf_config* cfg);
  *   omega (device) float32[n x l], l = damf_rsvd_width(cfg): standard normal test
  *     matrix (the caller draws it so that results are reproducible across devices).
  *   out: receives the context; *out is NULL on failure.
- * Returns DAMF_ERR_INVALID for a bad cfg, DAMF_ERR_CUDA when allocation fails.
- * Synchronises `stream` before returning (setup path, not the per-update path).
+ * Returns DAMF_ERR_INVALID for a bad cfg, DAMF_ERR_CAPACITY when a device allocation
+ * fails for want of memory (everything allocated so far is freed), DAMF_ERR_CUDA when
+ * another CUDA call fails.  Synchronises `stream` before returning (setup path, not the
+ * per-update path).
  */
 damf_status damf_init_factorize(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx,
                                 int64_t m, const float* omega, void* stream, damf_ctx** out);
@@ -440,7 +442,8 @@ damf_status damf_save_state(damf_ctx* ctx, damf_state* st, void* stream);
  * bit-identical factors and adjacency (the push, whose add order depends on timing, keeps its
  * eps bound); the next push starts from every row.  A directed graph's in-adjacency is rebuilt
  * from the out-adjacency.  Synchronises `stream`.  DAMF_ERR_INVALID for a bad cfg or a NULL
- * buffer.
+ * buffer; DAMF_ERR_CAPACITY when a device allocation fails for want of memory (nothing is
+ * left allocated), DAMF_ERR_CUDA when another CUDA call fails.
  */
 damf_status damf_restore(const damf_config* cfg, const int32_t* row_ptr, const int32_t* col_idx, int64_t m,
                          const damf_state* saved, void* stream, damf_ctx** out);
