@@ -113,11 +113,23 @@ def fleet_signature(graphs) -> str:
 
 
 def _load_cache(path: str) -> Dict:
+    """The cache file's entries; an absent, unreadable or malformed file counts as empty."""
     try:
         with open(path) as f:
-            return json.load(f)
+            data = json.load(f)
     except (OSError, ValueError):
         return {}
+    return data if isinstance(data, dict) else {}
+
+
+def _usable(entry, ngraphs: int) -> bool:
+    """A cache entry that _apply can set on a fleet of ngraphs graphs."""
+    if not isinstance(entry, dict) or not isinstance(entry.get("push_direct_chunks"), int):
+        return False
+    w = entry.get("weights")
+    if w:
+        return isinstance(w, list) and len(w) == ngraphs and all(isinstance(x, (int, float)) and x > 0 for x in w)
+    return isinstance(entry.get("exponent"), (int, float))
 
 
 def _apply(fleet, graphs, entry: Dict):
@@ -151,7 +163,7 @@ def tune_shares(fleet, graphs, measure_step_ms: Callable[[], float],
     sig = fleet_signature(graphs)
     if cache:
         entry = _load_cache(cache).get(sig)
-        if entry:
+        if _usable(entry, len(graphs)):   # otherwise (damaged or foreign) the fleet is tuned afresh
             _apply(fleet, graphs, entry)
             blocks, launches = fleet.shares()
             return dict(entry, cached=True, shares={"min": min(blocks), "max": max(blocks), "launches": launches})

@@ -1,11 +1,13 @@
 """Host logic of the push-shape autotuner and of the many-graph workload (no GPU)."""
 
+import json
 import math
 
 import numpy as np
 import pytest
 
-from paper_2306_08967_gb300.autotune import blocks_for, choose, measured_weights, plan, tune_grids, tune_shares
+from paper_2306_08967_gb300.autotune import (blocks_for, choose, fleet_signature, measured_weights, plan, tune_grids,
+                                             tune_shares)
 from synth import FLEETS
 
 
@@ -159,3 +161,27 @@ def test_tuning_cache_skips_measuring_the_same_fleet(tmp_path):
     other = FakeFleet([FakeGraph(n, 304) for n in (1000, 30_000)])      # another fleet: measured
     third = tune_shares(other, other.graphs, step_ms, cache=cache)
     assert third["cached"] is False and len(calls) > n_calls
+
+
+def test_a_damaged_tuning_cache_means_tuning_afresh(tmp_path):
+    graphs = [FakeGraph(n, 304) for n in (1000, 20_000, 400_000)]
+    calls = []
+
+    def step_ms():
+        calls.append(1)
+        return abs(fleet.p - 0.75) * 10 + {-1: 1.0, 4: 0.0, 16: 2.0}[fleet.snap[0]]
+
+    sig = fleet_signature(graphs)
+    for content in ("not json", "[1, 2, 3]", json.dumps({sig: {"exponent": 0.5}}),
+                    json.dumps({sig: {"push_direct_chunks": 4, "weights": [1.0, -2.0, 3.0]}}),
+                    json.dumps({sig: {"push_direct_chunks": 4, "weights": [1.0, 2.0]}})):
+        cache = tmp_path / "tune.json"
+        cache.write_text(content)
+        fleet = FakeFleet(graphs)
+        calls.clear()
+        out = tune_shares(fleet, graphs, step_ms, cache=str(cache))
+        assert out["cached"] is False and calls, content
+        assert fleet.p == 0.75
+        # and the file now holds a usable entry for this fleet
+        again = tune_shares(FakeFleet(graphs), graphs, step_ms, cache=str(cache))
+        assert again["cached"] is True
