@@ -57,3 +57,18 @@ def test_serving_timeline_has_one_record_per_step():
     assert tl[0]["first_arrival_s"] == 0.05 and tl[0]["t_issue_s"] == 0.11 and tl[0]["t_done_s"] == 0.20
     assert tl[1]["requests"] == 1 and tl[1]["edges"] == 7 and tl[1]["phase"] == 1
     json.dumps(tl)                                   # JSON-ready
+
+
+def test_cpu_baseline_leg_runs_the_oracle_in_a_subprocess(tmp_path):
+    # the default bench's cpu_baseline and error legs: the oracle in its own process (BLAS
+    # threads pinned), its timing as JSON and its final state saved for the error comparison
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from synth import CONFIGS
+    state = str(tmp_path / "oracle_state.npz")
+    r = bench.oracle_subprocess(CONFIGS["C1"], 4, 5.0, state)
+    assert "error" not in r, r
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0 and r["batches"] >= 1
+    z = np.load(state)
+    assert int(z["batches"]) == 2 + r["batches"] and z["X"].shape[1] == CONFIGS["C1"].d
