@@ -72,3 +72,28 @@ def test_cpu_baseline_leg_runs_the_oracle_in_a_subprocess(tmp_path):
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0 and r["batches"] >= 1
     z = np.load(state)
     assert int(z["batches"]) == 2 + r["batches"] and z["X"].shape[1] == CONFIGS["C1"].d
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi prints three samples (one under a power cap) and waits to be stopped
+    sys.path.insert(0, ROOT)
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 1010.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    import time
+    with bench.ClockSampler(0) as clk:
+        time.sleep(0.5)
+    s = clk.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    # no nvidia-smi at all: the run goes on and says so
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    with bench.ClockSampler(0) as clk:
+        pass
+    assert clk.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
