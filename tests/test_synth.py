@@ -164,3 +164,18 @@ def test_serving_workload_sessions_and_arrivals():
     assert abs(len(t) - rate * T) < 4 * np.sqrt(rate * T)
     gaps = np.diff(t)
     assert abs(gaps.mean() - 1 / rate) < 0.05 / rate and abs(gaps.std() / gaps.mean() - 1.0) < 0.05
+
+
+def test_fleet_inputs_in_spawned_workers_equal_the_inputs_made_here():
+    # the many-graph inputs are generated in spawned processes (safe beside a GPU context);
+    # each graph's inputs must not depend on where they were made
+    import dataclasses
+    from synth import FLEETS
+    from synth.configs import fleet_inputs
+    members = [dataclasses.replace(m, n=min(m.n, 3000)) for m in FLEETS["C4"].members()[:3]]
+    here = fleet_inputs(members, 5, workers=1)
+    there = fleet_inputs(members, 5, workers=2)
+    for (c1, ip1, ix1, st1), (c2, ip2, ix2, st2) in zip(here, there):
+        assert c1 == c2 and np.array_equal(ip1, ip2) and np.array_equal(ix1, ix2)
+        assert all(np.array_equal(a.src, b.src) and np.array_equal(a.dst, b.dst) and np.array_equal(a.op, b.op)
+                   for a, b in zip(st1.batches, st2.batches))
