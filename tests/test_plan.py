@@ -80,3 +80,13 @@ def test_random_fleets_keep_the_plan_invariants(seed):
     # every CTA of the budget goes to some slot unless there are fewer graphs than CTAs to give
     assert ctas.sum() == maxb or len(ctas) == g
     assert len(ctas) <= maxb
+
+
+def test_a_large_fleet_plans_quickly():
+    import time
+    rng = np.random.default_rng(9)
+    w = np.exp(rng.uniform(0.0, 6.0, size=5000))
+    t = time.perf_counter()
+    slot_of, ctas, _ = _check(w, 608)
+    assert time.perf_counter() - t < 5.0
+    assert ctas.sum() == 608 and len(ctas) <= 608
