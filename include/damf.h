@@ -287,9 +287,12 @@ void damf_fleet_destroy(damf_fleet* fleet);
 /* Launch shape of a context's PPR push (damf_set_tuning, damf_get_tuning). */
 typedef struct {
   int32_t push_blocks;        /* CTAs of the persistent push, 256 threads each; 0 = the most that
-                                 stay resident beside the factor chain (two per SM); larger
-                                 values are clamped to it.  Graphs that share the GPU
-                                 (damf_step_multi) take fewer, so that their pushes overlap. */
+                                 stay resident beside the factor chain (two per SM).  Larger
+                                 values (up to the push's own occupancy, four per SM) give the
+                                 push more warps, but then the next update's factor chain no
+                                 longer runs beside it; values above the occupancy are clamped
+                                 to it.  Graphs that share the GPU (damf_step_multi) take fewer,
+                                 so that their pushes overlap. */
   int32_t push_direct_chunks; /* a row with more in-edges than this many chunks (a chunk is 8,
                                  16, 32, 32 in-edges for d = 128, 64, 32, 16) is pushed as hub
                                  items of 8 in-edges spread over warps; -1 = 8 chunks */
@@ -468,19 +471,26 @@ damf_status damf_get_last_touched(damf_ctx* ctx, int32_t* S, int32_t* nS, int32_
  * Step 2 of an update on its own (Sec. 4.5 "Rediagonalization", Eq. "svd_small_edge"):
  * the top-d SVD  E Theta H^T  of the (d + r) x (d + r) core
  *     M = [[diag(sigma), 0], [0, 0]] + L R^T,
- * computed by the kernels of the update path (one-CTA one-sided Jacobi).  No context.
+ * computed by the kernels of the update path (one-sided block Jacobi on an 8-CTA thread-block
+ * cluster, then H = M^T E Theta^{-1}).  No context.
  *   sigma (device) float32[d]; L, R (device) float32[(d+r) x r] row-major (L = [W_B; R_B],
  *   R = [W_C; R_C] in the paper's notation); d in {16, 32, 64, 128}, 1 <= r <= 128.
  *   E, H (device) float32[(d+r) x d] row-major: column k is the k-th left / right
  *   singular vector (non-increasing singular values); theta (device) float32[d].
  *   workspace (device): at least damf_core_svd_workspace_size(d, r) bytes, 256-byte
  *   aligned, owned by the caller; it holds a status word and a copy of M.
- * DAMF_ERR_INVALID for bad sizes or NULL pointers, DAMF_ERR_CAPACITY for a short
- * workspace.  Asynchronous on `stream`.
+ *   status (device) int32, optional (NULL: not written): when the call's stream work is
+ *   done it holds the device status of the computation: DAMF_OK, DAMF_ERR_NUMERIC (a
+ *   non-finite singular value or vector) or DAMF_ERR_NOT_CONVERGED (the Jacobi sweeps ran
+ *   out; the results are then only approximate).  Read it after synchronising the stream.
+ * Returns DAMF_ERR_INVALID for bad sizes or NULL pointers, DAMF_ERR_CAPACITY for a short
+ * workspace, DAMF_ERR_CUDA when a launch fails; DAMF_OK covers the enqueue only (device
+ * errors arrive through `status`).  Asynchronous on `stream`.
  */
 size_t damf_core_svd_workspace_size(int32_t d, int32_t r);
 damf_status damf_core_svd(const float* sigma, const float* L, const float* R, int32_t d, int32_t r, float* E,
-                          float* H, float* theta, void* workspace, size_t workspace_bytes, void* stream);
+                          float* H, float* theta, void* workspace, size_t workspace_bytes, int32_t* status,
+                          void* stream);
 
 /*
  * damf_core_svd without a workspace, for callers that cannot allocate device memory:
@@ -488,20 +498,23 @@ damf_status damf_core_svd(const float* sigma, const float* L, const float* R, in
  * framework whose allocator owns all device memory, or code on a latency-critical path
  * that must not call cudaMalloc (it can synchronise the device).  The paper has no
  * counterpart; this is a deployment variant of Step 2.
- *   Arguments and results are those of damf_core_svd.  The caller still provides and
- *   owns every input and output.  Nothing is allocated: the scratch (a status word and
- *   the assembled core) is one static device array of 262,656 bytes compiled into the
- *   library, which every GPU that loads the library holds until the process exits.
+ *   Arguments and results are those of damf_core_svd, `status` included (the status word
+ *   itself lives in the library's array, which the caller cannot read, so pass `status` to
+ *   learn of a device error).  The caller still provides and owns every input and output.
+ *   Nothing is allocated: the scratch (a status word and the assembled core) is one static
+ *   device array of 262,656 bytes compiled into the library, which every GPU that loads the
+ *   library holds until the process exits.
  *   Limit: d + r <= 256 (d in {16, 32, 64, 128}, 1 <= r <= 128); a larger r returns
  *   DAMF_ERR_CAPACITY, bad d or NULL pointers DAMF_ERR_INVALID.
- *   The first call on each device looks up the array's device address (with that device
- *   current); make that first call before any stream capture.
+ *   Every call looks the array's device address up with the caller's device current (so the
+ *   address stays right after a device reset); the first call on a device also loads the
+ *   library's device code there: make that first call before any stream capture.
  *   All calls on a device share the one array and each call overwrites it (the status
  *   word is cleared at the start of every call): calls that overlap on the GPU (other
  *   streams or threads) race and give undefined results; serialise them.
  */
 damf_status damf_core_svd_noalloc(const float* sigma, const float* L, const float* R, int32_t d, int32_t r,
-                                  float* E, float* H, float* theta, void* stream);
+                                  float* E, float* H, float* theta, int32_t* status, void* stream);
 
 /* Current node count as known to the host (initial n plus all node arrivals). */
 int32_t damf_num_nodes(const damf_ctx* ctx);
@@ -536,8 +549,8 @@ enum {
   DAMF_STAGE_FIXUP = 1,      /* PPR residual change of changed out-rows */
   DAMF_STAGE_GATHER = 2,     /* U[S] = Ub[S] PU, V[T] = Vb[T] PV */
   DAMF_STAGE_CHOL = 3,       /* residual Grams and Cholesky factors */
-  DAMF_STAGE_CORE = 4,       /* core assembly and one-CTA Jacobi SVD */
-  DAMF_STAGE_TRANSFORMS = 5, /* H, R^{-1} E[d:], K, K^{-1}, transform products */
+  DAMF_STAGE_CORE = 4,       /* core assembly and block Jacobi SVD (8-CTA cluster) */
+  DAMF_STAGE_TRANSFORMS = 5, /* H, re-orthonormalised E and H, Theta, R^{-1} E[d:], K, K^{-1}, transform products */
   DAMF_STAGE_SCATTER = 6,    /* base-row rewrite and PPR signal change */
   DAMF_STAGE_PUSH = 7,       /* persistent PPR push */
   DAMF_STAGE_FOLD = 8,       /* periodic fold of the transforms into the bases */

@@ -51,8 +51,15 @@ def _sqrt_factor(G: np.ndarray, tol: float = 1e-12):
 class DamfOracle:
     def __init__(self, indptr, indices, d: int, alpha: float, eps: float, n_cap: int = None,
                  directed: bool = False, Omega: np.ndarray = None, power_iters: int = 4,
-                 exact_init: bool = False, propagate: bool = True, degree_scaled: bool = False):
+                 exact_init: bool = False, propagate: bool = True, degree_scaled: bool = False,
+                 edges_per_update: int = 64):
+        """edges_per_update: a call's events are applied as consecutive updates of at most this
+        many events each (the batched reading of Algorithm 2: one rank-r update per group of
+        events; 1 gives the paper's one event per update)."""
         n = int(len(indptr) - 1)
+        self.edges_per_update = int(edges_per_update)
+        self.stats_updates = 0          # non-empty updates applied
+        self.last_core_sv = None        # full spectrum of the most recent update's core M
         n_cap = n if n_cap is None else n_cap
         self.d, self.alpha, self.eps, self.directed = d, alpha, eps, directed
         self.degree_scaled = degree_scaled
@@ -101,7 +108,7 @@ class DamfOracle:
         self.graph.validate(src, dst, op, new_nodes)
         self.graph.add_nodes(new_nodes)
         changes = []
-        for lo, hi in split_updates(len(src)):
+        for lo, hi in split_updates(len(src), self.edges_per_update):
             changes.append(self.apply_update(src[lo:hi], dst[lo:hi], op[lo:hi]))
         return changes
 
@@ -113,7 +120,9 @@ class DamfOracle:
         rows_old = {u: self.graph.out.row(u) for u in touched}
         ch = self.graph.apply(src, dst, op)
         if ch.empty:
+            self.last_core_sv = None
             return ch
+        self.stats_updates += 1
         rows_new = {int(u): self.graph.out.row(int(u)) for u in ch.S}
         rows_old = {int(u): rows_old[int(u)] for u in ch.S}
         dXb_S = self._factor_update(ch)
@@ -142,6 +151,7 @@ class DamfOracle:
         M[:d, :d] = np.diag(sig)
         M += np.vstack([W_B, R_B]) @ np.vstack([W_C, R_C]).T
         E, theta, Ht = np.linalg.svd(M, full_matrices=False)
+        self.last_core_sv = theta.copy()
         E, theta, H = E[:, :d], theta[:d], Ht[:d].T
         # Step 3: space projection
         sq2 = np.sqrt(theta)

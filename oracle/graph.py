@@ -17,9 +17,6 @@ import numpy as np
 
 from .build import build
 
-# A call's edges are applied as consecutive updates of at most this many edges each.
-EDGES_PER_UPDATE = 64
-
 _lib = None
 
 
@@ -200,6 +197,9 @@ class DynGraph:
         return SparseChange(S, T, N, entries)
 
 
-def split_updates(k: int) -> List[Tuple[int, int]]:
-    """Edge ranges [lo, hi) of the consecutive updates one call is applied as."""
-    return [(lo, min(lo + EDGES_PER_UPDATE, k)) for lo in range(0, k, EDGES_PER_UPDATE)]
+def split_updates(k: int, per_update: int) -> List[Tuple[int, int]]:
+    """Edge ranges [lo, hi) of the consecutive updates one call of k events is applied as,
+    at most per_update events each."""
+    if per_update < 1:
+        raise ValueError("per_update must be >= 1")
+    return [(lo, min(lo + per_update, k)) for lo in range(0, k, per_update)]

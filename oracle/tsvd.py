@@ -53,9 +53,3 @@ def randomized_tsvd(A, Omega: np.ndarray, d: int, power_iters: int):
     V = Vbt[:d].T
     return U, s[:d], V
 
-
-def principal_angles_cos(A: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """Cosines of the principal angles between span(A) and span(B)."""
-    Qa = _orth(A)
-    Qb = _orth(B)
-    return np.clip(np.linalg.svd(Qa.T @ Qb, compute_uv=False), 0.0, 1.0)

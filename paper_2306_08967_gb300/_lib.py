@@ -80,8 +80,8 @@ SIGNATURES = {
     "damf_topk": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "damf_num_nodes": (c_i32, [c_vp]),
     "damf_core_svd_workspace_size": (c_sz, [c_i32, c_i32]),
-    "damf_core_svd": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
-    "damf_core_svd_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "damf_core_svd": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    "damf_core_svd_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "damf_set_timing": (c_i32, [c_vp, c_i32]),
     "damf_get_timing": (c_i32, [c_vp, c_vp, c_vp]),
     "damf_get_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

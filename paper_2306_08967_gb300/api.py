@@ -78,9 +78,10 @@ def bytes_required(cfg: Config) -> int:
 
 
 @_on_stream
-def core_svd(sigma, L, R, stream=None):
+def core_svd(sigma, L, R, status=None, stream=None):
     """Top-d SVD of diag(sigma, 0) + L R^T through damf_core_svd (Step 2 of an update).
-    Returns (E, H, theta) CUDA tensors."""
+    Returns (E, H, theta) CUDA tensors; `status` (a CUDA int32 tensor of one element, optional)
+    receives the device status of the computation once the stream's work is done."""
     lib = _lib.load()
     sigma, L, R = _dev(sigma, torch.float32), _dev(L, torch.float32), _dev(R, torch.float32)
     d, r = int(sigma.numel()), int(L.shape[1])
@@ -93,7 +94,8 @@ def core_svd(sigma, L, R, stream=None):
         raise DamfError(1, "core_svd sizes")
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     p = lambda t: ctypes.c_void_p(t.data_ptr())
-    st = lib.damf_core_svd(p(sigma), p(L), p(R), d, r, p(E), p(H), p(th), p(ws), nbytes, _stream_ptr(stream))
+    stp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    st = lib.damf_core_svd(p(sigma), p(L), p(R), d, r, p(E), p(H), p(th), p(ws), nbytes, stp, _stream_ptr(stream))
     if st != 0:
         raise DamfError(st, "core_svd")
     return E, H, th

@@ -62,8 +62,8 @@ void timer_end(Ctx* c, int i, int stage, int launches, cudaStream_t s) {
     timer_end(c, ti_, stage, nl, s);              \
   } while (0)
 // kernels per update: prepare, gather, wct, chol, assemble, jacobi, hmat, ns_gram, ns_apply,
-// trans, inverse, products, commit, edit, fixup, scatter
-constexpr int kLaunchesPerUpdate = 16;
+// theta, trans, inverse, products, commit, edit, fixup, scatter
+constexpr int kLaunchesPerUpdate = 17;
 // fold: 2 x (gram part + reduce), 2 x (congruence + chol), core, jacobi, hmat, 4 small_mm,
 // finish, 4 tall GEMMs
 constexpr int kLaunchesPerFold = 4 + 4 + 1 + 2 + 4 + 1 + 4;
@@ -316,7 +316,7 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
     if ((e = spmm(in, n, Q, l, Y, s)) != cudaSuccess) goto done;  // Bt = A^T Q
     if ((e = orth(Y, Q2, R2)) != cudaSuccess) goto done;         // Bt = Q2 R2
     // R2 row-major == (R2^T) column-major: the Jacobi input is R2^T
-    if ((e = jacobi_svd_dense(R2, l, d, c->ws.E, c->ws.H, c->ws.theta, nullptr, c->hdr, s)) != cudaSuccess) goto done;
+    if ((e = jacobi_svd_dense(R2, l, d, c->ws.E, c->ws.H, c->ws.theta, 0, c->hdr, s)) != cudaSuccess) goto done;
     if ((e = gemm_ctx(c, Q, l, n, c->ws.E, l, d, c->Ub, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
     if ((e = gemm_ctx(c, Q2, l, n, c->ws.H, l, d, c->Vb, d, nullptr, nullptr, s)) != cudaSuccess) goto done;
     if ((e = cudaMemcpyAsync(c->sigma, c->ws.theta, sizeof(float) * d, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -796,7 +796,7 @@ static damf_status apply_impl(damf_ctx* x, const int32_t* src, const int32_t* ds
     DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
     DAMF_STAGE(DAMF_STAGE_CHOL, 2, launch_chol(c, s), "chol");
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
-    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 7, launch_transforms(c, s), "transforms");
+    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 8, launch_transforms(c, s), "transforms");
     // writes to the adjacency, Zb and r follow the push
     DAMF_CUDA(wait_push(c, s), "join push");
     DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_edit(c, s), "edit");
@@ -923,7 +923,8 @@ damf_status damf_set_tuning(damf_ctx* x, const damf_tuning* t) {
 damf_status damf_get_tuning(const damf_ctx* x, damf_tuning* t) {
   if (!x || !t) return DAMF_ERR_INVALID;
   const Ctx* c = &x->c;
-  t->push_blocks = (c->push_blocks > 0 && c->push_blocks < c->push_max) ? c->push_blocks : c->push_max;
+  t->push_blocks = c->push_blocks > 0 ? (c->push_occ > 0 && c->push_blocks > c->push_occ ? c->push_occ : c->push_blocks)
+                                      : c->push_max;
   t->push_direct_chunks = c->push_direct_chunks >= 0 ? c->push_direct_chunks : push_default_direct_chunks();
   return DAMF_OK;
 }

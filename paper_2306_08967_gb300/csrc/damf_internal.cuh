@@ -143,6 +143,7 @@ struct Ctx {
   long long m_init;      // adjacency entries of the initial graph (a size hint for shares)
   int push_blocks;       // requested persistent push grid size (0: push_max)
   int push_max;          // co-resident push CTAs on the device, at most two per SM (0: not yet known)
+  int push_occ;          // co-resident push CTAs when the push takes the whole occupancy
   int push_direct_chunks;  // in-edge chunks a row task scatters itself (-1: default)
   // damf_step_multi runs this graph's update on its own stream, forked from the caller's
   cudaStream_t own_stream;
@@ -293,8 +294,9 @@ cudaError_t gemm_tall(const float* A, int lda, long long n, const float* B, int 
 cudaError_t gram_tall(Ctx* c, const float* A, int lda, long long n, int K, float* out, cudaStream_t s);
 // one-CTA Cholesky (lower, G = L L^T) and inverse of L^T; out Linvt[K x K] with A * Linvt orthonormal
 cudaError_t chol_inv_upper(const float* G, int K, float* Rinv, DevHeader* h, cudaStream_t s);
-// dense one-CTA one-sided Jacobi SVD of an m x m column-major matrix: top-d (E, theta, H)
-cudaError_t jacobi_svd_dense(const float* Min, int m, int d, float* E, float* H, float* theta, float* work_M,
+// dense one-sided block Jacobi SVD (8-CTA cluster) of an m x m column-major matrix: top-d
+// (E, theta, H); report_nc = 1 records DAMF_ERR_NOT_CONVERGED in h when the sweeps run out
+cudaError_t jacobi_svd_dense(const float* Min, int m, int d, float* E, float* H, float* theta, int report_nc,
                              DevHeader* h, cudaStream_t s);
 
 }  // namespace damf

@@ -175,7 +175,7 @@ cudaError_t launch_fold(Ctx* c, cudaStream_t s) {
   if ((e = chol_inv_upper2(T1, d, RV, RVi, c->hdr, s)) != cudaSuccess) return e;
   k_fold_core<<<(int)((dd + 255) / 256), 256, 0, s>>>(RU, RV, c->sigma, c->ws.M, d);
   // E', theta, H' of the d x d core
-  if ((e = jacobi_svd_dense(c->ws.M, d, d, c->ws.E, c->ws.H, c->ws.theta, nullptr, c->hdr, s)) != cudaSuccess) return e;
+  if ((e = jacobi_svd_dense(c->ws.M, d, d, c->ws.E, c->ws.H, c->ws.theta, 0, c->hdr, s)) != cudaSuccess) return e;
   // T_U = PU RUi E', T_V = PV RVi H'
   if ((e = small_mm(c->PU, RUi, T1, d, s)) != cudaSuccess) return e;
   if ((e = small_mm(T1, c->ws.E, TU, d, s)) != cudaSuccess) return e;

@@ -162,8 +162,10 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
   __shared__ int s_rot;
   __shared__ int s_flags[kClP];
   // the same header values for every CTA of the cluster (written by earlier kernels)
-  const int m = use_hdr ? D + h->nS : m_host;
-  if (use_hdr && h->nS == 0) return;
+  // use_hdr: 1 = the update's core (m from the header, counters recorded), 0 = a dense
+  // matrix of m_host columns, 2 = the same and non-convergence recorded as a status
+  const int m = use_hdr == 1 ? D + h->nS : m_host;
+  if (use_hdr == 1 && h->nS == 0) return;
   const int mp = (m + 31) & ~31;
   const int ne = mp / 32;
   const bool two = mp > 128;       // rows 128.. present: a lane holds two float4 of a column
@@ -264,7 +266,7 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
     if (!full && any && sweep + 1 >= kClTopOnlySweeps) {
       // the top set keeps changing (values straddling the cut are close): every pair from here on
       full = true;
-      if (use_hdr && c == 0 && tid == 0) h->jacobi_full += 1;
+      if (use_hdr == 1 && c == 0 && tid == 0) h->jacobi_full += 1;
     }
     if (!any) {
       if (full) break;
@@ -281,17 +283,19 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
       }
       if (bmax * bsum < 0.98f * topmin) break;
       full = true;
-      if (use_hdr && c == 0 && tid == 0) {
+      if (use_hdr == 1 && c == 0 && tid == 0) {
         h->jacobi_gersh += 1;
         h->jacobi_full += 1;
       }
     }
   }
-  if (use_hdr && c == 0 && tid == 0) {
+  if (use_hdr == 1 && c == 0 && tid == 0) {
     const int done = sweep < max_sweeps ? sweep + 1 : sweep;
     h->last_sweeps = done;
     h->jacobi_sweeps += done;
   }
+  // a dense call that asked for it learns that the sweeps ran out before convergence
+  if (use_hdr == 2 && c == 0 && tid == 0 && sweep >= max_sweeps) set_status(h, DAMF_ERR_NOT_CONVERGED);
   // exact norms, order by decreasing norm (ties by index), write the top D as E and Theta
   cl.sync();   // every CTA is done reading the shared norms of the last sweep
   for (int j = warp; j < 2 * bs; j += nw) {
@@ -342,13 +346,15 @@ cudaError_t launch_core_svd(Ctx* c, cudaStream_t s) {
 }
 
 // Top-d SVD of a dense m x m column-major matrix (m <= kMaxM): E (m x d row-major), theta.
-cudaError_t cluster_svd_dense(const float* Min, int m, int d, float* E, float* theta, DevHeader* h, cudaStream_t s) {
+cudaError_t cluster_svd_dense(const float* Min, int m, int d, float* E, float* theta, DevHeader* h, int report_nc,
+                              cudaStream_t s) {
   if (m > kMaxM || m < d) return cudaErrorInvalidValue;
+  const int mode = report_nc ? 2 : 0;
   switch (d) {
-    case 16: return cl_launch<16>(h, Min, m, 0, E, theta, 30, s);
-    case 32: return cl_launch<32>(h, Min, m, 0, E, theta, 30, s);
-    case 64: return cl_launch<64>(h, Min, m, 0, E, theta, 30, s);
-    default: return cl_launch<128>(h, Min, m, 0, E, theta, 30, s);
+    case 16: return cl_launch<16>(h, Min, m, mode, E, theta, 30, s);
+    case 32: return cl_launch<32>(h, Min, m, mode, E, theta, 30, s);
+    case 64: return cl_launch<64>(h, Min, m, mode, E, theta, 30, s);
+    default: return cl_launch<128>(h, Min, m, mode, E, theta, 30, s);
   }
 }
 

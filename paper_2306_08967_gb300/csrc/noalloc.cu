@@ -7,13 +7,11 @@
 // (which may synchronise the device) is not allowed.  This entry point keeps its scratch
 // (a status word and the assembled core M) in one file-scope device array of fixed size,
 // so it allocates nothing.  Limits and sharing rules are stated in include/damf.h.
-#include <mutex>
-
 #include "damf_internal.cuh"
 
 namespace damf {
 cudaError_t core_svd_into(const float* sigma, const float* L, const float* R, int d, int r, float* E, float* H,
-                          float* theta, DevHeader* h, float* M, cudaStream_t s);
+                          float* theta, DevHeader* h, float* M, int32_t* status, cudaStream_t s);
 }  // namespace damf
 
 using namespace damf;
@@ -28,35 +26,24 @@ constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxM * kMaxM * sizeof(f
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_core_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices];   // device address of g_core_scratch, per device
-std::mutex g_scratch_mu;
-
 }  // namespace
 
 extern "C" damf_status damf_core_svd_noalloc(const float* sigma, const float* L, const float* R, int32_t d,
-                                             int32_t r, float* E, float* H, float* theta, void* stream) {
+                                             int32_t r, float* E, float* H, float* theta, int32_t* status,
+                                             void* stream) {
   if (!(d == 16 || d == 32 || d == 64 || d == 128) || !sigma || !L || !R || !E || !H || !theta)
     return DAMF_ERR_INVALID;
   if (r < 1 || r > kMaxR) return DAMF_ERR_CAPACITY;   // the scratch holds cores up to (128 + 128)^2
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DAMF_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return DAMF_ERR_INVALID;
+  // The host-side name of the array is not a device address: look the address up, with the
+  // caller's device current.  The first lookup on a device loads the library's device code
+  // there (set-up; make that first call before any stream capture); later lookups only read
+  // it back, and looking it up on every call keeps the address right after a device reset
+  // (which unloads the code and may place the array elsewhere when it is loaded again).
   void* base = nullptr;
-  {
-    // set-up, once per device, with that device current: the host-side name of the array
-    // is not a device address, so look the address up
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_core_scratch) != cudaSuccess || p == nullptr) return DAMF_ERR_CUDA;
-      g_scratch_addr[dev] = p;
-    }
-    base = g_scratch_addr[dev];
-  }
+  if (cudaGetSymbolAddress(&base, g_core_scratch) != cudaSuccess || base == nullptr) return DAMF_ERR_CUDA;
   DevHeader* h = (DevHeader*)base;
   float* M = (float*)((char*)base + kHeaderBytes);
   // core_svd_into clears the status word before use; M is fully overwritten by the assembly
-  const cudaError_t e = core_svd_into(sigma, L, R, d, r, E, H, theta, h, M, (cudaStream_t)stream);
+  const cudaError_t e = core_svd_into(sigma, L, R, d, r, E, H, theta, h, M, status, (cudaStream_t)stream);
   return e == cudaSuccess ? DAMF_OK : DAMF_ERR_CUDA;
 }

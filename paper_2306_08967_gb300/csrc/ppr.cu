@@ -833,11 +833,12 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D, SCALED>, 256, 0);
-    if (per_sm > kPushBlocksPerSM) per_sm = kPushBlocksPerSM;
-    c->push_max = sms * (per_sm < 1 ? 1 : per_sm);
+    if (per_sm < 1) per_sm = 1;
+    c->push_occ = sms * per_sm;
+    c->push_max = sms * (per_sm > kPushBlocksPerSM ? kPushBlocksPerSM : per_sm);
   }
   // a cooperative grid must fit on the device at once
-  const int blocks = (c->push_blocks > 0 && c->push_blocks < c->push_max) ? c->push_blocks : c->push_max;
+  const int blocks = c->push_blocks > 0 ? (c->push_blocks < c->push_occ ? c->push_blocks : c->push_occ) : c->push_max;
   const int chunks = c->push_direct_chunks;
   // qstate, q_head, overflow, rho_tail, item_tail, ovf_count, help_open, helpers
   cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 7 * sizeof(int), s);

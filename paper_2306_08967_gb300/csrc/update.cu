@@ -272,6 +272,60 @@ __global__ void __launch_bounds__(256) k_ns_apply(DevHeader* h, Workspace ws) {
   }
 }
 
+// ---- Theta from the core itself: theta_k = e_k^T M h_k (after the Newton-Schulz step) ----
+// The Jacobi values are norms of columns that took hundreds of plane rotations; read in FP32
+// each is off by about 1e-6 relative, a drift that adds up over updates. The Rayleigh quotient
+// of the orthonormalised vectors with the original core errs only to second order in the
+// vectors' error. With M = diag(sigma, 0) + L R^T, L = [W_B; R_B], R = [W_C; R_C]:
+//   theta_k = sum_{i<d} sigma_i E[i,k] H[i,k] + sum_a (L^T e_k)_a (R^T h_k)_a,
+// summed in Acc: double in mixed precision (the products of FP32 operands are exact in
+// FP64), float in plain FP32. One CTA per k, one thread per residual column a.
+template <int D, typename Acc>
+__global__ void __launch_bounds__(128) k_theta(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
+  __shared__ float ev[kMaxM], hv[kMaxM];
+  __shared__ Acc part[4];
+  if (h->status != 0 || h->nS == 0) return;
+  const int nS = h->nS, m = D + nS;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) {
+    ev[i] = ws.E[i * D + k];
+    hv[i] = ws.H[i * D + k];
+  }
+  __syncthreads();
+  Acc acc = 0;
+  for (int i = tid; i < D; i += blockDim.x) acc = fma((Acc)sigma[i] * (Acc)ev[i], (Acc)hv[i], acc);
+  if (tid < nS) {
+    const int a = tid;
+    Acc p = 0, q = 0;
+    const float4* ur = reinterpret_cast<const float4*>(ws.UST + (size_t)a * D);
+    const float4* wr = reinterpret_cast<const float4*>(ws.WCt + (size_t)a * D);
+#pragma unroll 4
+    for (int i4 = 0; i4 < D / 4; ++i4) {
+      const float4 u = ur[i4], w = wr[i4];
+      const int i = 4 * i4;
+      p = fma((Acc)ev[i], (Acc)u.x, p);
+      p = fma((Acc)ev[i + 1], (Acc)u.y, p);
+      p = fma((Acc)ev[i + 2], (Acc)u.z, p);
+      p = fma((Acc)ev[i + 3], (Acc)u.w, p);
+      q = fma((Acc)hv[i], (Acc)w.x, q);
+      q = fma((Acc)hv[i + 1], (Acc)w.y, q);
+      q = fma((Acc)hv[i + 2], (Acc)w.z, q);
+      q = fma((Acc)hv[i + 3], (Acc)w.w, q);
+    }
+    // R_B and R_C are upper triangular: column a has rows 0 .. a
+    for (int b = 0; b <= a; ++b) {
+      p = fma((Acc)ev[D + b], (Acc)ws.RB[b * kMaxR + a], p);
+      q = fma((Acc)hv[D + b], (Acc)ws.RC[b * kMaxR + a], q);
+    }
+    acc = fma(p, q, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) part[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) ws.theta[k] = (float)(part[0] + part[1] + part[2] + part[3]);
+}
+
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
 template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace ws) {
@@ -553,6 +607,11 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
     k_ns_apply<D><<<dim3(kMaxM / 16, 2), 256, sma, s>>>(c->hdr, c->ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (c->cfg.precision == 1)
+    k_theta<D, double><<<D, 128, 0, s>>>(c->hdr, c->ws, c->sigma);
+  else
+    k_theta<D, float><<<D, 128, 0, s>>>(c->hdr, c->ws, c->sigma);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t sm = (size_t)(kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);

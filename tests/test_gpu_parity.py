@@ -547,8 +547,10 @@ def test_core_svd_against_numpy(d, r):
     M[:d, :d] = np.diag(sigma)
     M += L @ R.T
     U, s, Vt = np.linalg.svd(M)
-    E, H, th = core_svd(sigma.astype(np.float32), L.astype(np.float32), R.astype(np.float32))
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    E, H, th = core_svd(sigma.astype(np.float32), L.astype(np.float32), R.astype(np.float32), status=status)
     E, H, th = E.double().cpu().numpy(), H.double().cpu().numpy(), th.double().cpu().numpy()
+    assert int(status.item()) == 0          # converged, finite
     np.testing.assert_allclose(th, s[:d], rtol=1e-4, atol=1e-5 * s[0])
     top = (U[:, :d] * s[:d]) @ Vt[:d]
     assert rel_fro((E * th) @ H.T, top) < 1e-4

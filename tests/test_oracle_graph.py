@@ -3,7 +3,7 @@
 import numpy as np
 import pytest
 
-from oracle.graph import EDGES_PER_UPDATE, DynGraph, split_updates
+from oracle.graph import DynGraph, split_updates
 from tests.helpers import csr_of_dense, random_graph_dense
 
 
@@ -58,7 +58,10 @@ def test_validation_rejects_bad_events():
 
 
 def test_split_updates():
-    assert split_updates(0) == []
-    assert split_updates(5) == [(0, 5)]
-    assert split_updates(EDGES_PER_UPDATE) == [(0, EDGES_PER_UPDATE)]
-    assert split_updates(EDGES_PER_UPDATE + 1) == [(0, EDGES_PER_UPDATE), (EDGES_PER_UPDATE, EDGES_PER_UPDATE + 1)]
+    assert split_updates(0, 64) == []
+    assert split_updates(5, 64) == [(0, 5)]
+    assert split_updates(64, 64) == [(0, 64)]
+    assert split_updates(65, 64) == [(0, 64), (64, 65)]
+    assert split_updates(3, 1) == [(0, 1), (1, 2), (2, 3)]
+    with pytest.raises(ValueError):
+        split_updates(3, 0)
