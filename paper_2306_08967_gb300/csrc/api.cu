@@ -62,8 +62,8 @@ void timer_end(Ctx* c, int i, int stage, int launches, cudaStream_t s) {
     timer_end(c, ti_, stage, nl, s);              \
   } while (0)
 // kernels per update: prepare, gather, wct, chol, assemble, jacobi, hmat, ns_gram, ns_apply,
-// theta, trans, inverse, products, commit, edit, fixup, scatter
-constexpr int kLaunchesPerUpdate = 17;
+// fo_pq, fo_t, fo_apply, fo_norm_theta, trans, inverse, products, commit, edit, fixup, scatter
+constexpr int kLaunchesPerUpdate = 20;
 // fold: 2 x (gram part + reduce), 2 x (congruence + chol), core, jacobi, hmat, 4 small_mm,
 // finish, 4 tall GEMMs
 constexpr int kLaunchesPerFold = 4 + 4 + 1 + 2 + 4 + 1 + 4;
@@ -151,6 +151,7 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = (size_t)kMaxM * kMaxM * 4;                        // M
   s[k++] = (size_t)kMaxM * d * 4; s[k++] = (size_t)kMaxM * d * 4;  // E H
   s[k++] = d * 4;                                            // theta
+  s[k++] = (2 * (size_t)kMaxR * d + d * d) * sizeof(float);   // foP foQ foT
   s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // YB YC
   s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;        // KU KV KUi KVi
   s[k++] = 4 * dd;                                           // tmp
@@ -630,6 +631,9 @@ static damf_status ctx_open(const damf_config* cfg, const int32_t* row_ptr, cons
   w.UST = (float*)ptr[k++]; w.VT = (float*)ptr[k++]; w.WCt = (float*)ptr[k++];
   w.RB = (float*)ptr[k++]; w.RC = (float*)ptr[k++]; w.M = (float*)ptr[k++];
   w.E = (float*)ptr[k++]; w.H = (float*)ptr[k++]; w.theta = (float*)ptr[k++];
+  w.foP = (float*)ptr[k++];
+  w.foQ = w.foP + (size_t)kMaxR * cfg->d;
+  w.foT = w.foQ + (size_t)kMaxR * cfg->d;
   w.YB = (float*)ptr[k++]; w.YC = (float*)ptr[k++];
   w.KU = (float*)ptr[k++]; w.KV = (float*)ptr[k++]; w.KUi = (float*)ptr[k++]; w.KVi = (float*)ptr[k++];
   w.tmp = (float*)ptr[k++];
@@ -796,7 +800,7 @@ static damf_status apply_impl(damf_ctx* x, const int32_t* src, const int32_t* ds
     DAMF_STAGE(DAMF_STAGE_GATHER, 1, launch_gather(c, s), "gather");
     DAMF_STAGE(DAMF_STAGE_CHOL, 2, launch_chol(c, s), "chol");
     DAMF_STAGE(DAMF_STAGE_CORE, 2, launch_core(c, s), "core");
-    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 8, launch_transforms(c, s), "transforms");
+    DAMF_STAGE(DAMF_STAGE_TRANSFORMS, 11, launch_transforms(c, s), "transforms");
     // writes to the adjacency, Zb and r follow the push
     DAMF_CUDA(wait_push(c, s), "join push");
     DAMF_STAGE(DAMF_STAGE_PREPARE, 1, launch_edit(c, s), "edit");

@@ -99,6 +99,10 @@ struct Workspace {
   float* E;          // [kMaxM x d] left singular vectors (column k = k-th largest)
   float* H;          // [kMaxM x d]
   float* theta;      // [d]
+  // refinement of the core SVD (update.cu): P = E^T L, Q = H^T R, T = E^T M H
+  float* foP;        // [d x kMaxR]
+  float* foQ;        // [d x kMaxR]
+  float* foT;        // [d x d]
   float* YB;         // [kMaxR x d]  R_B^{-1} E[d:]
   float* YC;         // [kMaxR x d]  R_C^{-1} H[d:]
   float* KU;         // [d x d]

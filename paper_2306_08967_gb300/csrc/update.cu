@@ -272,18 +272,57 @@ __global__ void __launch_bounds__(256) k_ns_apply(DevHeader* h, Workspace ws) {
   }
 }
 
-// ---- Theta from the core itself: theta_k = e_k^T M h_k (after the Newton-Schulz step) ----
-// The Jacobi values are norms of columns that took hundreds of plane rotations; read in FP32
-// each is off by about 1e-6 relative, a drift that adds up over updates. The Rayleigh quotient
-// of the orthonormalised vectors with the original core errs only to second order in the
-// vectors' error. With M = diag(sigma, 0) + L R^T, L = [W_B; R_B], R = [W_C; R_C]:
-//   theta_k = sum_{i<d} sigma_i E[i,k] H[i,k] + sum_a (L^T e_k)_a (R^T h_k)_a,
-// summed in Acc: double in mixed precision (the products of FP32 operands are exact in
-// FP64), float in plain FP32. One CTA per k, one thread per residual column a.
+// ---- Step 2 refinement: consistent singular pairs, exact norms, Theta from the core itself ----
+// One-sided Jacobi leaves the columns orthogonal only to its tolerance; E (normalised columns)
+// and H = M^T E Theta^{-1}, each made orthonormal by Newton-Schulz, then pair up with a first-
+// order error of that size (~1e-6 relative in E Theta H^T per update at d = 128), and in FP32
+// the normalised columns keep a norm bias of a few 1e-8 that the bases inherit update after
+// update; the largest singular value drifted up by ~3e-7 per update. So after Newton-Schulz:
+//   (1) T = E^T M H (d x d, nearly diagonal), with M = diag(sigma, 0) + L R^T,
+//       L = [W_B; R_B], R = [W_C; R_C]:  T = E[:d]^T diag(sigma) H[:d] + P Q^T,
+//       P = E^T L, Q = H^T R (d x r);
+//   (2) the first-order SVD of T = (I + A) Theta' (I + B)^T with A, B skew:
+//       A_jk = (t_k F_jk + t_j F_kj) / (t_k^2 - t_j^2), B_jk = (t_j F_jk + t_k F_kj) / (t_k^2 - t_j^2)
+//       for the off-diagonal part F of T and t = diag(T) (pairs too close to separate, or whose
+//       correction would not be small, are left as they are); E <- E (I + A), H <- H (I + B);
+//   (3) every column of E and H scaled to unit norm, the norm summed in FP64 and each element
+//       scaled in FP64 and rounded once;
+//   (4) theta_k = e_k^T M h_k, the Rayleigh quotient with the original core, summed in FP64
+//       (the products of FP32 operands are exact in FP64; FP32 sums of these dot products were
+//       measured biased by ~4e-7 relative, which the update would accumulate).
+// (1)-(2) are FP32; (3)-(4) take (d + r) d FP64 products per update.
+
+// (a) P[k][a] = (L^T e_k)_a and Q[k][a] = (R^T h_k)_a: one CTA per k, one thread per column a.
 template <int D, typename Acc>
-__global__ void __launch_bounds__(128) k_theta(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
+__device__ __forceinline__ void fo_pq_col(const Workspace& ws, int nS, const float* ev, const float* hv, int a,
+                                          Acc& p, Acc& q) {
+  p = 0;
+  q = 0;
+  const float4* ur = reinterpret_cast<const float4*>(ws.UST + (size_t)a * D);
+  const float4* wr = reinterpret_cast<const float4*>(ws.WCt + (size_t)a * D);
+#pragma unroll 4
+  for (int i4 = 0; i4 < D / 4; ++i4) {
+    const float4 u = ur[i4], w = wr[i4];
+    const int i = 4 * i4;
+    p = fma((Acc)ev[i], (Acc)u.x, p);
+    p = fma((Acc)ev[i + 1], (Acc)u.y, p);
+    p = fma((Acc)ev[i + 2], (Acc)u.z, p);
+    p = fma((Acc)ev[i + 3], (Acc)u.w, p);
+    q = fma((Acc)hv[i], (Acc)w.x, q);
+    q = fma((Acc)hv[i + 1], (Acc)w.y, q);
+    q = fma((Acc)hv[i + 2], (Acc)w.z, q);
+    q = fma((Acc)hv[i + 3], (Acc)w.w, q);
+  }
+  // R_B and R_C are upper triangular: column a has rows 0 .. a
+  for (int b = 0; b <= a; ++b) {
+    p = fma((Acc)ev[D + b], (Acc)ws.RB[b * kMaxR + a], p);
+    q = fma((Acc)hv[D + b], (Acc)ws.RC[b * kMaxR + a], q);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_fo_pq(DevHeader* h, Workspace ws) {
   __shared__ float ev[kMaxM], hv[kMaxM];
-  __shared__ Acc part[4];
   if (h->status != 0 || h->nS == 0) return;
   const int nS = h->nS, m = D + nS;
   const int k = blockIdx.x, tid = threadIdx.x;
@@ -292,38 +331,140 @@ __global__ void __launch_bounds__(128) k_theta(DevHeader* h, Workspace ws, const
     hv[i] = ws.H[i * D + k];
   }
   __syncthreads();
+  if (tid < nS) {
+    float p, q;
+    fo_pq_col<D, float>(ws, nS, ev, hv, tid, p, q);
+    ws.foP[(size_t)k * kMaxR + tid] = p;
+    ws.foQ[(size_t)k * kMaxR + tid] = q;
+  }
+}
+
+// (b) T = E[:d]^T diag(sigma) H[:d] + P Q^T in TS x TS output tiles (256 threads).
+template <int D>
+__global__ void __launch_bounds__(256) k_fo_t(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
+  constexpr int TS = D < 32 ? D : 32;
+  extern __shared__ __align__(16) float fo_smem[];
+  float* Ps = fo_smem;               // TS x (kMaxR + 1)
+  float* Qs = Ps + TS * (kMaxR + 1);  // TS x (kMaxR + 1)
+  float* Es = Qs + TS * (kMaxR + 1);  // D x TS
+  float* Hs = Es + D * TS;            // D x TS
+  if (h->status != 0 || h->nS == 0) return;
+  const int nS = h->nS;
+  const int j0 = blockIdx.x * TS, k0 = blockIdx.y * TS, tid = threadIdx.x;
+  for (int o = tid; o < TS * nS; o += blockDim.x) {
+    const int t = o / nS, a = o % nS;
+    Ps[t * (kMaxR + 1) + a] = ws.foP[(size_t)(j0 + t) * kMaxR + a];
+    Qs[t * (kMaxR + 1) + a] = ws.foQ[(size_t)(k0 + t) * kMaxR + a];
+  }
+  for (int o = tid; o < D * TS; o += blockDim.x) {
+    const int i = o / TS, t = o % TS;
+    Es[o] = ws.E[i * D + j0 + t];
+    Hs[o] = ws.H[i * D + k0 + t];
+  }
+  __syncthreads();
+  for (int o = tid; o < TS * TS; o += blockDim.x) {
+    const int tj = o / TS, tk = o % TS;
+    float s = 0.f;
+    for (int i = 0; i < D; ++i) s = fmaf(sigma[i] * Es[i * TS + tj], Hs[i * TS + tk], s);
+    float s2 = 0.f;
+    for (int a = 0; a < nS; ++a) s2 = fmaf(Ps[tj * (kMaxR + 1) + a], Qs[tk * (kMaxR + 1) + a], s2);
+    ws.foT[(size_t)(j0 + tj) * D + k0 + tk] = s + s2;
+  }
+}
+
+// (c) X <- X (I + A) for E (blockIdx.y = 0) and X <- X (I + B) for H (blockIdx.y = 1), 16 rows per
+// CTA (rows are owned by one CTA, so the update is in place); the small terms are summed first.
+template <int D>
+__global__ void __launch_bounds__(256) k_fo_apply(DevHeader* h, Workspace ws) {
+  extern __shared__ float smem[];
+  float* Gs = smem;            // D x D: A or B
+  float* Xs = smem + D * D;    // 16 x D
+  if (h->status != 0 || h->nS == 0) return;
+  const int m = D + h->nS;
+  const int r0 = blockIdx.x * 16;
+  if (r0 >= m) return;
+  const int side = blockIdx.y;
+  float* X = side == 0 ? ws.E : ws.H;
+  const float* T = ws.foT;
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
+    const int j = o / D, k = o % D;
+    float g = 0.0f;
+    if (j != k) {
+      const double tj = T[j * D + j], tk = T[k * D + k];
+      const double fjk = T[j * D + k], fkj = T[k * D + j];
+      const double den = tk * tk - tj * tj;
+      if (fabs(den) >= 1e-4 * (tj * tj + tk * tk) && den != 0.0) {
+        const double a = (tk * fjk + tj * fkj) / den;
+        const double b = (tj * fjk + tk * fkj) / den;
+        if (fabs(a) <= 1e-2 && fabs(b) <= 1e-2) g = (float)(side == 0 ? a : b);
+      }
+    }
+    Gs[o] = g;
+  }
+  for (int i = threadIdx.x; i < 16 * D; i += blockDim.x) {
+    const int rr = i / D;
+    Xs[i] = (r0 + rr < m) ? X[(r0 + rr) * D + i % D] : 0.0f;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 16 * D; o += blockDim.x) {
+    const int rr = o / D, k = o % D;
+    if (r0 + rr >= m) continue;
+    float s = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < D; ++j) s = fmaf(Xs[rr * D + j], Gs[j * D + k], s);
+    X[(r0 + rr) * D + k] = Xs[rr * D + k] + s;
+  }
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc block_sum128(Acc v, Acc* part) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();   // part may still be read from an earlier sum
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return part[0] + part[1] + part[2] + part[3];
+}
+
+// (d) unit columns (norms summed in FP64, each element scaled in FP64 and rounded once) and
+// theta_k = e_k^T M h_k in FP64. One CTA of 128 threads per k.
+template <int D>
+__global__ void __launch_bounds__(128) k_fo_norm_theta(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
+  using Acc = double;
+  __shared__ float ev[kMaxM], hv[kMaxM];
+  __shared__ Acc part[4];
+  if (h->status != 0 || h->nS == 0) return;
+  const int nS = h->nS, m = D + nS;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  Acc se = 0, sh = 0;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const float e = ws.E[i * D + k], f = ws.H[i * D + k];
+    ev[i] = e;
+    hv[i] = f;
+    se = fma((Acc)e, (Acc)e, se);
+    sh = fma((Acc)f, (Acc)f, sh);
+  }
+  se = block_sum128<Acc>(se, part);
+  sh = block_sum128<Acc>(sh, part);
+  const Acc ie = se > 0 ? (Acc)1 / sqrt(se) : (Acc)0;
+  const Acc ih = sh > 0 ? (Acc)1 / sqrt(sh) : (Acc)0;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const float e = (float)((Acc)ev[i] * ie), f = (float)((Acc)hv[i] * ih);
+    ev[i] = e;
+    hv[i] = f;
+    ws.E[i * D + k] = e;
+    ws.H[i * D + k] = f;
+  }
+  __syncthreads();
   Acc acc = 0;
   for (int i = tid; i < D; i += blockDim.x) acc = fma((Acc)sigma[i] * (Acc)ev[i], (Acc)hv[i], acc);
   if (tid < nS) {
-    const int a = tid;
-    Acc p = 0, q = 0;
-    const float4* ur = reinterpret_cast<const float4*>(ws.UST + (size_t)a * D);
-    const float4* wr = reinterpret_cast<const float4*>(ws.WCt + (size_t)a * D);
-#pragma unroll 4
-    for (int i4 = 0; i4 < D / 4; ++i4) {
-      const float4 u = ur[i4], w = wr[i4];
-      const int i = 4 * i4;
-      p = fma((Acc)ev[i], (Acc)u.x, p);
-      p = fma((Acc)ev[i + 1], (Acc)u.y, p);
-      p = fma((Acc)ev[i + 2], (Acc)u.z, p);
-      p = fma((Acc)ev[i + 3], (Acc)u.w, p);
-      q = fma((Acc)hv[i], (Acc)w.x, q);
-      q = fma((Acc)hv[i + 1], (Acc)w.y, q);
-      q = fma((Acc)hv[i + 2], (Acc)w.z, q);
-      q = fma((Acc)hv[i + 3], (Acc)w.w, q);
-    }
-    // R_B and R_C are upper triangular: column a has rows 0 .. a
-    for (int b = 0; b <= a; ++b) {
-      p = fma((Acc)ev[D + b], (Acc)ws.RB[b * kMaxR + a], p);
-      q = fma((Acc)hv[D + b], (Acc)ws.RC[b * kMaxR + a], q);
-    }
+    Acc p, q;
+    fo_pq_col<D, Acc>(ws, nS, ev, hv, tid, p, q);
     acc = fma(p, q, acc);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((tid & 31) == 0) part[tid >> 5] = acc;
-  __syncthreads();
-  if (tid == 0) ws.theta[k] = (float)(part[0] + part[1] + part[2] + part[3]);
+  acc = block_sum128<Acc>(acc, part);
+  if (tid == 0) ws.theta[k] = (float)acc;
 }
 
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
@@ -594,6 +735,24 @@ static cudaError_t chol_impl(Ctx* c, cudaStream_t s) {
 }
 
 template <int D>
+static cudaError_t refine_core(Ctx* c, cudaStream_t s) {
+  cudaError_t e;
+  k_fo_pq<D><<<D, 128, 0, s>>>(c->hdr, c->ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  constexpr int TS = D < 32 ? D : 32;
+  const size_t smt = ((size_t)2 * TS * (kMaxR + 1) + (size_t)2 * D * TS) * sizeof(float);
+  cudaFuncSetAttribute(k_fo_t<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+  k_fo_t<D><<<dim3(D / TS, D / TS), 256, smt, s>>>(c->hdr, c->ws, c->sigma);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t sma = (size_t)(D * D + 16 * D) * sizeof(float);
+  cudaFuncSetAttribute(k_fo_apply<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
+  k_fo_apply<D><<<dim3(kMaxM / 16, 2), 256, sma, s>>>(c->hdr, c->ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_fo_norm_theta<D><<<D, 128, 0, s>>>(c->hdr, c->ws, c->sigma);
+  return cudaGetLastError();
+}
+
+template <int D>
 static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
   cudaError_t e;
   k_hmat<D><<<kMaxM, 128, 0, s>>>(c->hdr, c->ws);
@@ -607,11 +766,7 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
     k_ns_apply<D><<<dim3(kMaxM / 16, 2), 256, sma, s>>>(c->hdr, c->ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (c->cfg.precision == 1)
-    k_theta<D, double><<<D, 128, 0, s>>>(c->hdr, c->ws, c->sigma);
-  else
-    k_theta<D, float><<<D, 128, 0, s>>>(c->hdr, c->ws, c->sigma);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = refine_core<D>(c, s)) != cudaSuccess) return e;
   const size_t sm = (size_t)(kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
