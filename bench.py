@@ -30,19 +30,20 @@ import sys
 
 
 def _oracle_threads(argv):
-    # --oracle-threads N: BLAS threads of the oracle (default 1), read before numpy loads
+    # --oracle-threads N: BLAS threads of the oracle (default: every host core), read before
+    # numpy loads
     for i, a in enumerate(argv):
         if a == "--oracle-threads" and i + 1 < len(argv):
             return max(1, int(argv[i + 1]))
         if a.startswith("--oracle-threads="):
             return max(1, int(a.split("=", 1)[1]))
-    return 1
+    return max(1, os.cpu_count() or 1)
 
 
 ORACLE_THREADS = _oracle_threads(sys.argv)
 
 if "--impl" in sys.argv and "reference" in sys.argv or "--oracle-worker" in sys.argv:
-    # pin the oracle's BLAS pools before numpy loads (one thread unless --oracle-threads)
+    # pin the oracle's BLAS pools before numpy loads (every host core unless --oracle-threads)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = str(ORACLE_THREADS)
 
@@ -65,25 +66,53 @@ def workload_desc(c):
                                                        100 * c.p_node, 100 * c.p_del))
 
 
+_INPUTS = {}
+
+
 def make_inputs(c, n_batches):
+    """The workload's graph and its first n_batches batches (generated once per process and
+    workload; the stream's first batches do not depend on how many follow them)."""
+    import dataclasses as dc
     from synth import chung_lu_graph, edge_stream
-    ip, ix, w = chung_lu_graph(c.n, c.avg_deg, c.gamma, seed=c.seed, directed=c.directed)
-    st = edge_stream(ip, ix, w, n_batches, c.k_lo, c.k_hi, c.p_node, c.p_del, c.seed + 1,
-                     max_new_degree=c.max_new_degree, directed=c.directed, nodes_per_batch=c.nodes_per_batch)
+    key = (c.name, c.seed, c.n)
+    if key not in _INPUTS or len(_INPUTS[key][2].batches) < n_batches:
+        if key in _INPUTS:
+            ip, ix, w = _INPUTS[key][0], _INPUTS[key][1], _INPUTS[key][3]
+        else:
+            ip, ix, w = chung_lu_graph(c.n, c.avg_deg, c.gamma, seed=c.seed, directed=c.directed)
+        st = edge_stream(ip, ix, w, n_batches, c.k_lo, c.k_hi, c.p_node, c.p_del, c.seed + 1,
+                         max_new_degree=c.max_new_degree, directed=c.directed, nodes_per_batch=c.nodes_per_batch)
+        _INPUTS[key] = (ip, ix, st, w)
+    ip, ix, st, _ = _INPUTS[key]
+    if len(st.batches) > n_batches:
+        st = dc.replace(st, batches=st.batches[:n_batches])
     return ip, ix, st
 
 
 # ---------------------------------------------------------------- oracle (CPU) leg
+# Randomized t-SVD passes of the oracle's initialisation: graphs of a million nodes or more take
+# none (two sparse products and two QR factorisations in place of ten and ten), so that the
+# oracle is initialised within minutes; the timed batches do not depend on it, and the error
+# comparison starts the device from the same randomized t-SVD.
+def oracle_power_iters(c):
+    return 0 if c.n >= 1_000_000 else 4
+
+
+ERR_SAMPLE_ROWS = 20000   # rows of X, Y, Z the error comparison reads (all of them below this)
+
+
 def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
     """Times the FP64 oracle (as it stands) on the first warmup+steps batches, stopping
     early once time_budget_s of timed work is spent.  Returns a dict; with save_path, also
-    writes the oracle's final X, Y, Z and sigma there (npz) for the error comparison."""
+    writes the oracle's final sigma and the rows of X, Y, Z of a seeded row sample there
+    (npz) for the error comparison."""
     from oracle.damf import DamfOracle
     from synth import gaussian_test_matrix
     ip, ix, st = make_inputs(c, warmup + steps)
     om = gaussian_test_matrix(c.n, 160 if c.d == 128 else ((c.d + 10 + 31) // 32) * 32, seed=c.seed + 2)
     t0 = time.perf_counter()
-    orc = DamfOracle(ip, ix, c.d, c.alpha, c.eps, n_cap=st.n_final, directed=c.directed, Omega=om)
+    orc = DamfOracle(ip, ix, c.d, c.alpha, c.eps, n_cap=st.n_final, directed=c.directed, Omega=om,
+                     power_iters=oracle_power_iters(c))
     init_s = time.perf_counter() - t0
     for b in st.batches[:warmup]:
         orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
@@ -101,34 +130,49 @@ def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
     total = time.perf_counter() - t_start
     if save_path:
         n = orc.n
-        np.savez(save_path, X=orc.X()[:n], Y=orc.Y()[:n], Z=orc.Z()[:n], sigma=orc.sigma,
-                 batches=warmup + len(lat))
+        rows = np.arange(n) if n <= ERR_SAMPLE_ROWS else np.sort(
+            np.random.default_rng(c.seed + 5).choice(n, ERR_SAMPLE_ROWS, replace=False))
+        np.savez(save_path, X=orc.X()[rows], Y=orc.Y()[rows], Z=orc.Z()[rows], sigma=orc.sigma, rows=rows, n=n,
+                 batches=warmup + len(lat), power_iters=oracle_power_iters(c))
     threads = ("1 thread" if ORACLE_THREADS == 1 else
                "%d BLAS threads (its push, in C, on one)" % ORACLE_THREADS)
     return {"value": edges / total, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle", "batches": len(lat),
             "edges": edges, "seconds": total, "init_s": init_s,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "sample": "first %d batches of the %s stream after %d warm-up batches (%d edges), FP64 oracle, "
-                      "%s" % (len(lat), c.name, warmup, edges, threads)}
+                      "%s; initialisation (%d randomized t-SVD passes, initial push) untimed, %.0f s"
+                      % (len(lat), c.name, warmup, edges, threads, oracle_power_iters(c), init_s)}
 
 
-def oracle_subprocess(c, steps, budget, save_path=None):
+def oracle_subprocess(c, steps, budget, save_path=None, wait=True):
+    """Runs the oracle leg in a child process (no GPU, its own BLAS threads). With wait=False
+    returns the running process; oracle_result() collects it."""
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--config", c.name, "--steps", str(steps),
            "--budget", str(budget), "--oracle-threads", str(ORACLE_THREADS)] + (
         ["--save-state", save_path] if save_path else [])
     nt = str(ORACLE_THREADS)
     env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt, CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
-    for line in out.stdout.splitlines()[::-1]:
+    p = subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+    return oracle_result(p) if wait else p
+
+
+def oracle_result(p, timeout=1800):
+    try:
+        out, err = p.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        p.kill()
+        out, err = p.communicate()
+    for line in (out or "").splitlines()[::-1]:
         if line.startswith("{"):
             return json.loads(line)
-    return {"error": (out.stderr or out.stdout)[-400:]}
+    return {"error": (err or out or "")[-400:]}
 
 
 def err_vs_oracle(c, path, precisions):
-    """Replays the oracle's batches on the device (fresh context per precision) and compares
-    sigma, X Y^T and Z Y^T with the oracle's FP64 result: relative errors, the Frobenius
-    ones through d x d Grams (|A B^T|_F^2 = tr((A^T A)(B^T B)))."""
+    """Replays the oracle's batches on the device (fresh context per precision, the same
+    randomized t-SVD passes as the oracle) and compares sigma and, on the oracle's row sample
+    (all rows up to ERR_SAMPLE_ROWS), the products X Y^T and Z Y^T: relative errors, the
+    Frobenius ones through d x d Grams (|A B^T|_F^2 = tr((A^T A)(B^T B)))."""
     import torch
     from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
     from synth import gaussian_test_matrix
@@ -136,6 +180,7 @@ def err_vs_oracle(c, path, precisions):
     nb = int(ref["batches"])
     dev = torch.device("cuda")
     Xo, Yo, Zo = (torch.from_numpy(ref[k]).to(dev) for k in ("X", "Y", "Z"))
+    rows = torch.from_numpy(ref["rows"].astype(np.int32)).to(dev)
     so = ref["sigma"]
     ip, ix, st = make_inputs(c, nb)
 
@@ -145,17 +190,19 @@ def err_vs_oracle(c, path, precisions):
         go = torch.trace((A.T @ Ao) @ (Bo.T @ B))
         return float(torch.sqrt(torch.clamp(gg - 2 * go + oo, min=0)) / torch.sqrt(oo))
 
-    out = {"batches": nb, "oracle": "FP64 incremental oracle (the paper's X-form) on the same batches"}
+    out = {"batches": nb, "rows_compared": int(rows.numel()), "rows": int(ref["n"]),
+           "oracle": "FP64 incremental oracle (the paper's X-form) on the same batches; X Y^T and Z Y^T over the "
+                     "rows compared (a seeded sample when the graph has more)"}
     for prec in precisions:
         cfg = make_config(c.n, c.d, c.alpha, c.eps, n_capacity=st.n_final + 16, nnz=len(ix), directed=c.directed,
-                          refold_every=256, precision=prec)
+                          refold_every=256, precision=prec, rsvd_power_iters=int(ref["power_iters"]))
         om = gaussian_test_matrix(c.n, rsvd_width(cfg), seed=c.seed + 2)
         g = DamfGraph(ip, ix, cfg, om)
         for b in st.batches[:nb]:
             g.apply_edges_host(b.src, b.dst, b.op, b.new_nodes)
             g.ppr_refresh()
         g.check()
-        e = g.embeddings()
+        e = g.embeddings(rows=rows)
         X, Y, Z = (e[k].double() for k in ("X", "Y", "Z"))
         sg = e["sigma"].double().cpu().numpy()
         out[prec] = {"sigma_max_rel": float(np.max(np.abs(sg - so) / np.abs(so))),
@@ -506,6 +553,7 @@ def run_ours(args, c, rank, world):
         "dominant_stage": dominant,
         "scoring": scoring,
         "counters": {"pushes": pushes, "push_edges": push_edges, "updates": s1["updates"] - s0["updates"],
+                     "folds": s1["folds"] - s0["folds"],
                      "push_rounds": s1["push_rounds"] - s0["push_rounds"],
                      "touched_rows": s1["touched_rows"] - s0["touched_rows"], "last_sweeps": s1["last_sweeps"],
                      "jacobi_sweeps": s1["jacobi_sweeps"] - s0["jacobi_sweeps"],
@@ -849,19 +897,22 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--config", default="C2")
+    ap.add_argument("--config", default="C3")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refold-every", type=int, default=256)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--no-compare-precision", dest="compare_precision", action="store_false",
-                    help="skip timing the other precision build of the path on the same workload")
+                    help="skip timing both precisions over a longer window of the same workload")
+    ap.add_argument("--precision-steps", type=int, default=300,
+                    help="steps of each precision's window in the comparison (C3: ~800 updates, three folds)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scoring", dest="scoring", action="store_false",
                     help="skip the link-prediction query timing (score_pairs, topk) after the run")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--oracle-worker", action="store_true")
-    ap.add_argument("--oracle-threads", type=int, default=1,
-                    help="BLAS threads of the timed oracle (cpu_baseline and --impl reference); default 1")
+    ap.add_argument("--oracle-threads", type=int, default=max(1, os.cpu_count() or 1),
+                    help="BLAS threads of the timed oracle (cpu_baseline and --impl reference); default: every "
+                         "host core (its push, in C, runs on one)")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--save-state", default=None)
     ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here; "
@@ -929,29 +980,53 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    proc, state = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle leg runs in its own process beside the GPU leg (no GPU, host cores only)
+        import tempfile
+        state = os.path.join(tempfile.mkdtemp(prefix="damf_oracle_"), "state.npz")
+        proc = oracle_subprocess(c, 400, args.cpu_budget, state, wait=False)
     out = run_ours(args, c, rank, world)
-    sig_a = np.array(out.pop("_sigma"))
+    out.pop("_sigma")
     if args.compare_precision:
         import copy
-        a2 = copy.copy(args)
-        a2.precision = "fp32" if args.precision == "mixed" else "mixed"
-        a2.e2e_steps = 0
-        a2.log_jsonl = None
-        o2 = run_ours(a2, c, rank, world)
-        sig_b = np.array(o2.pop("_sigma"))
-        out["precision_compare"] = {
-            args.precision: {"value": out["value"], "ms_per_step": out["ms_per_step"], "err": out["err"],
-                             "fold_ms": out["stage_ms"].get("fold")},
-            a2.precision: {"value": o2["value"], "ms_per_step": o2["ms_per_step"], "err": o2["err"],
-                           "fold_ms": o2["stage_ms"].get("fold")},
-            "sigma_max_rel_diff": float(np.max(np.abs(sig_a - sig_b) / np.abs(sig_b))),
-            "note": "same workload and stream; err = max |U^T U - I|, |V^T V - I| of the effective bases "
-                    "after the run; mixed runs the fold's n x d by d x d GEMMs on tcgen05 (TF32, 3-term split)"}
+        # both precisions over the same longer window (fresh contexts, the same batches), long
+        # enough to hold folds (every refold_every updates), so that the fold's tensor-core
+        # GEMMs are timed too
+        cmp = {}
+        for prec in [args.precision, "fp32" if args.precision == "mixed" else "mixed"]:
+            a2 = copy.copy(args)
+            a2.precision, a2.steps, a2.e2e_steps, a2.log_jsonl, a2.scoring = prec, args.precision_steps, 0, None, False
+            o2 = run_ours(a2, c, rank, world)
+            o2.pop("_sigma")
+            cmp[prec] = {"value": o2["value"], "ms_per_step": o2["ms_per_step"], "steps": a2.steps,
+                         "updates": o2["counters"]["updates"], "folds": o2["counters"]["folds"],
+                         "fold_ms": o2["stage_ms"].get("fold"), "latency_ms": {k: o2["latency_ms"][k] for k in
+                                                                               ("p50", "p99")},
+                         "stage_ms_per_update": {k: round(v / max(o2["counters"]["updates"], 1), 4)
+                                                 for k, v in o2["stage_ms"].items()},
+                         "err": o2["err"]}
+        pa = cmp[args.precision]
+        cmp["speedup_mixed_over_fp32"] = (cmp["mixed"]["value"] / cmp["fp32"]["value"]) if cmp["fp32"]["value"] else None
+        cmp["note"] = ("same workload and batches, fresh contexts; err = max |U^T U - I|, |V^T V - I| of the effective "
+                       "bases after the window; mixed runs the per-update projection U[S] = Ub[S] PU and the d x d "
+                       "transform products, the fold's n x d by d x d GEMMs and the initialisation on tcgen05 (TF32, "
+                       "three-term split), plain FP32 runs them on the SIMT units; errors against the FP64 oracle "
+                       "for both are under err_vs_oracle")
+        out["precision_compare"] = cmp
+        # the fold's cost per step, amortised over refold_every updates, from the longer window
+        if pa["folds"]:
+            per_fold = pa["fold_ms"] / pa["folds"]
+            ups = out["counters"]["updates"] / max(out["steps"], 1)
+            amort = per_fold * ups / max(args.refold_every, 1)
+            out["fold"] = {"ms_per_fold": per_fold, "updates_per_fold": args.refold_every,
+                           "folds_in_timed_steps": out["counters"]["folds"],
+                           "amortized_ms_per_step": amort,
+                           "value_with_amortized_fold": out["value"] * out["ms_per_step"] / (
+                               out["ms_per_step"] + (amort if out["counters"]["folds"] == 0 else 0.0))}
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
-            import tempfile
-            state = os.path.join(tempfile.mkdtemp(prefix="damf_oracle_"), "state.npz")
-            r = oracle_subprocess(c, 400, args.cpu_budget, state)
+        if proc is not None:
+            r = oracle_result(proc)
             if os.path.exists(state):
                 try:
                     precs = [args.precision] + (["fp32" if args.precision == "mixed" else "mixed"]
@@ -965,7 +1040,7 @@ def main():
                                        "sample": r["sample"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                                        "init_s": r["init_s"]}
             else:
-                out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
                                        "sample": "failed: " + r.get("error", "")}
         print(json.dumps(out))
     if world > 1:

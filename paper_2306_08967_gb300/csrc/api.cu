@@ -152,6 +152,7 @@ Plan plan_of(const damf_config* cfg) {
   s[k++] = (size_t)kMaxM * d * 4; s[k++] = (size_t)kMaxM * d * 4;  // E H
   s[k++] = d * 4;                                            // theta
   s[k++] = (2 * (size_t)kMaxR * d + d * d) * sizeof(float);   // foP foQ foT
+  s[k++] = ((size_t)kMaxR * kFixSplit * d + kMaxR) * sizeof(float);   // fixpart fixcnt
   s[k++] = (size_t)kMaxR * d * 4; s[k++] = (size_t)kMaxR * d * 4;  // YB YC
   s[k++] = dd; s[k++] = dd; s[k++] = dd; s[k++] = dd;        // KU KV KUi KVi
   s[k++] = 4 * dd;                                           // tmp
@@ -634,6 +635,8 @@ static damf_status ctx_open(const damf_config* cfg, const int32_t* row_ptr, cons
   w.foP = (float*)ptr[k++];
   w.foQ = w.foP + (size_t)kMaxR * cfg->d;
   w.foT = w.foQ + (size_t)kMaxR * cfg->d;
+  w.fixpart = (float*)ptr[k++];
+  w.fixcnt = (int32_t*)(w.fixpart + (size_t)kMaxR * kFixSplit * cfg->d);
   w.YB = (float*)ptr[k++]; w.YC = (float*)ptr[k++];
   w.KU = (float*)ptr[k++]; w.KV = (float*)ptr[k++]; w.KUi = (float*)ptr[k++]; w.KVi = (float*)ptr[k++];
   w.tmp = (float*)ptr[k++];

@@ -26,6 +26,7 @@ constexpr long long kSpinLimit = 1ll << 26;  // iterations of a bounded wait (wi
 constexpr int kTopQ = 32;                 // queries per top-k pass (score.cu)
 constexpr int kMaxTopK = 64;              // largest k of damf_topk
 constexpr int kTopMaxCtas = 256;          // top-k scan CTAs at most
+constexpr int kFixSplit = 16;             // CTAs that share one changed row of the PPR fix-up
 
 // Grid barrier state for persistent cooperative kernels.
 struct GridBar {
@@ -103,6 +104,9 @@ struct Workspace {
   float* foP;        // [d x kMaxR]
   float* foQ;        // [d x kMaxR]
   float* foT;        // [d x d]
+  // PPR fix-up: partial sums of the CTAs that share a row, and per-row arrival counters
+  float* fixpart;    // [kMaxR x kFixSplit x d]
+  int32_t* fixcnt;   // [kMaxR], zero between launches
   float* YB;         // [kMaxR x d]  R_B^{-1} E[d:]
   float* YC;         // [kMaxR x d]  R_C^{-1} H[d:]
   float* KU;         // [d x d]

@@ -149,8 +149,6 @@ __global__ void k_fold_finish(const float* TU, float* TX, float* s0, float* sigm
   }
 }
 
-cudaError_t jacobi_svd_dense(const float* Min, int m, int d, float* E, float* H, float* theta, float* work_M,
-                             DevHeader* h, cudaStream_t s);
 
 cudaError_t launch_fold(Ctx* c, cudaStream_t s) {
   const int d = c->d;

@@ -43,16 +43,32 @@ cudaError_t launch_validate(Ctx* c, const int32_t* src, const int32_t* dst, cons
   return cudaGetLastError();
 }
 
-// Warp searches row u for v; returns the position or -1.
+// Warp searches row u for v; returns the position or -1.  Four 32-entry chunks are loaded
+// per round, so a long row costs a quarter of the dependent round trips.
 __device__ __forceinline__ int row_find(const Adj& a, int u, int v) {
   const int lane = threadIdx.x & 31;
   const int st = a.start[u], ln = a.len[u];
-  for (int base = 0; base < ln; base += 32) {
-    int j = base + lane;
-    unsigned hit = __ballot_sync(0xffffffffu, j < ln && a.col[st + j] == v);
-    if (hit) return base + __ffs(hit) - 1;
+  for (int base = 0; base < ln; base += 128) {
+    int x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = base + 32 * c + lane;
+      x[c] = j < ln ? a.col[st + j] : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const unsigned hit = __ballot_sync(0xffffffffu, x[c] == v);
+      if (hit) return base + 32 * c + __ffs(hit) - 1;
+    }
   }
   return -1;
+}
+
+// Whether entry (u, v) is present: row u of the out-adjacency holds v exactly when row v of
+// the in-adjacency (the out-adjacency itself for an undirected graph) holds u, so the
+// shorter of the two rows is searched (a hub's row is then rarely scanned).
+__device__ __forceinline__ bool has_entry(const Adj& out, const Adj& in, int u, int v) {
+  return in.len[v] < out.len[u] ? row_find(in, v, u) >= 0 : row_find(out, u, v) >= 0;
 }
 
 __device__ __forceinline__ int grown_cap(int cap, int need) {
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
       int dl = 0;
       if (last) {
         const int u = (int)(skey[i] >> 32), v = (int)(skey[i] & 0xffffffffu);
-        const int initial = row_find(out, u, v) >= 0 ? 1 : 0;
+        const int initial = has_entry(out, in, u, v) ? 1 : 0;
         const int fin = sop[i] > 0 ? 1 : 0;
         dl = fin - initial;
       }
@@ -351,35 +367,60 @@ cudaError_t launch_prepare(Ctx* c, const int32_t* src, const int32_t* dst, const
 // r[u] += (a - b) sum_{v in N'(u)} Zb[v] + b (sum_{added} Zb[v] - sum_{removed} Zb[v])
 // with a = c/deg'(u) (0 if deg' = 0), b = c/deg(u) (0 if deg = 0), c = (1-alpha)/alpha:
 // this equals c (mean_{N'(u)} Zb - mean_{N(u)} Zb) because N(u) = N'(u) - added + removed.
+// One changed row u per blockIdx.x, its adjacency row split over kFixSplit CTAs (blockIdx.y,
+// interleaved groups of rows, four loads in flight per warp): a hub's thousands of
+// neighbours are read by many SMs at once. Each CTA leaves its partial sum in the workspace;
+// the last of the row's CTAs (counted by an atomic per row, reset by that CTA) adds the
+// partials in CTA order to r[u], so the result does not depend on which CTA finishes last.
 template <int D>
 __global__ void __launch_bounds__(256) k_fixup(DevHeader* h, Adj out, Workspace ws, const float* __restrict__ Zb,
                                                float* r, float c_alpha) {
   constexpr int LPR = D / 4;          // lanes per row (float4 each)
   constexpr int RPW = 32 / LPR;       // rows per warp step
+  constexpr int UNR = 4;              // row loads in flight per lane
   __shared__ float4 part[8][32];
-  const int a_idx = blockIdx.x;
+  __shared__ int last;
+  const int a_idx = blockIdx.x, cta = blockIdx.y;
   if (h->status != 0 || a_idx >= h->nS) return;
   const int u = ws.S[a_idx];
   const int dold = ws.deg_old[a_idx], dnew = ws.deg_new[a_idx];
   const float ca = dnew > 0 ? c_alpha / (float)dnew : 0.0f;
   const float cb = dold > 0 ? c_alpha / (float)dold : 0.0f;
+  const float w = ca - cb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / LPR, q = lane % LPR;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   const int st = out.start[u], ln = out.len[u];
-  for (int j = warp * RPW + sub; j < ln; j += 8 * RPW) {
-    const int v = out.col[st + j];
-    const float4 z = reinterpret_cast<const float4*>(Zb + (size_t)v * D)[q];
-    const float w = ca - cb;
-    acc.x += w * z.x, acc.y += w * z.y, acc.z += w * z.z, acc.w += w * z.w;
+  // rows of the group: j = (g * kFixSplit + cta) * 8 RPW + warp RPW + sub, g = 0, 1, ...
+  const int stride = kFixSplit * 8 * RPW;
+  for (int j0 = cta * 8 * RPW + warp * RPW + sub; j0 < ln; j0 += UNR * stride) {
+    float4 z[UNR];
+#pragma unroll
+    for (int t = 0; t < UNR; ++t) {
+      const int j = j0 + t * stride;
+      z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < ln) {
+        const int v = __ldg(out.col + st + j);
+        z[t] = __ldg(reinterpret_cast<const float4*>(Zb + (size_t)v * D) + q);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < UNR; ++t) {
+      acc.x = fmaf(w, z[t].x, acc.x);
+      acc.y = fmaf(w, z[t].y, acc.y);
+      acc.z = fmaf(w, z[t].z, acc.z);
+      acc.w = fmaf(w, z[t].w, acc.w);
+    }
   }
   const int nedit = h->nedit;
-  for (int e = warp * RPW + sub; e < nedit; e += 8 * RPW) {
-    const int4 x = ws.edits[e];
-    if (x.x != u) continue;
-    const float4 z = reinterpret_cast<const float4*>(Zb + (size_t)x.y * D)[q];
-    const float w = x.z > 0 ? cb : -cb;
-    acc.x += w * z.x, acc.y += w * z.y, acc.z += w * z.z, acc.w += w * z.w;
+  if (cta == 0) {
+    for (int e = warp * RPW + sub; e < nedit; e += 8 * RPW) {
+      const int4 x = ws.edits[e];
+      if (x.x != u) continue;
+      const float4 z = reinterpret_cast<const float4*>(Zb + (size_t)x.y * D)[q];
+      const float we = x.z > 0 ? cb : -cb;
+      acc.x += we * z.x, acc.y += we * z.y, acc.z += we * z.z, acc.w += we * z.w;
+    }
   }
   // reduce the RPW sub-rows of the warp, then the 8 warps
 #pragma unroll
@@ -391,10 +432,26 @@ __global__ void __launch_bounds__(256) k_fixup(DevHeader* h, Adj out, Workspace 
   }
   part[warp][lane] = acc;
   __syncthreads();
+  float4* mine = reinterpret_cast<float4*>(ws.fixpart + ((size_t)a_idx * kFixSplit + cta) * D);
   if (warp == 0 && lane < LPR) {
     float4 s = part[0][lane];
-    for (int w = 1; w < 8; ++w) {
-      const float4 t = part[w][lane];
+    for (int wi = 1; wi < 8; ++wi) {
+      const float4 t = part[wi][lane];
+      s.x += t.x, s.y += t.y, s.z += t.z, s.w += t.w;
+    }
+    __stcg(mine + lane, s);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ws.fixcnt + a_idx, 1) == kFixSplit - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (warp == 0 && lane < LPR) {
+    const float4* all = reinterpret_cast<const float4*>(ws.fixpart + (size_t)a_idx * kFixSplit * D);
+    float4 s = __ldcg(all + lane);
+    for (int c = 1; c < kFixSplit; ++c) {
+      const float4 t = __ldcg(all + (size_t)c * LPR + lane);
       s.x += t.x, s.y += t.y, s.z += t.z, s.w += t.w;
     }
     float4* ru = reinterpret_cast<float4*>(r + (size_t)u * D) + lane;
@@ -402,16 +459,20 @@ __global__ void __launch_bounds__(256) k_fixup(DevHeader* h, Adj out, Workspace 
     cur.x += s.x, cur.y += s.y, cur.z += s.z, cur.w += s.w;
     *ru = cur;
   }
-  if (threadIdx.x == 0) atomicAdd((unsigned long long*)&h->fixup_edges, (unsigned long long)(ln + nedit));
+  if (threadIdx.x == 0) {
+    ws.fixcnt[a_idx] = 0;   // ready for the next update (the kernel boundary orders it)
+    atomicAdd((unsigned long long*)&h->fixup_edges, (unsigned long long)(ln + nedit));
+  }
 }
 
 cudaError_t launch_fixup(Ctx* c, cudaStream_t s) {
   const float ca = (float)((1.0 - c->cfg.alpha) / c->cfg.alpha);
+  const dim3 grid(kMaxR, kFixSplit);
   switch (c->d) {
-    case 16: k_fixup<16><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
-    case 32: k_fixup<32><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
-    case 64: k_fixup<64><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
-    default: k_fixup<128><<<kMaxR, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    case 16: k_fixup<16><<<grid, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    case 32: k_fixup<32><<<grid, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    case 64: k_fixup<64><<<grid, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
+    default: k_fixup<128><<<grid, 256, 0, s>>>(c->hdr, c->out, c->ws, c->Zb, c->r, ca); break;
   }
   return cudaGetLastError();
 }

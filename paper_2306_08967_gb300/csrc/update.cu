@@ -16,10 +16,21 @@
 //          Y_C = R_C^{-1} H[d:], K_V = H[:d] - W_C Y_C, Vb[T] += (N^T Y_C) PVi;  Sigma <- Theta.
 //   Step 4 input: r[S] += (Ub[S] change) diag(s0), the change of the PPR signal Ub diag(s0).
 #include "damf_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace damf {
 
 constexpr float kPivotTol = 1e-5f;   // relative Cholesky pivot tolerance (FP32)
+
+// Register tiles of a D x D output over up to 512 threads: TR rows x TC columns per thread.
+template <int D>
+struct MMShape {
+  static constexpr int TR = D >= 128 ? 4 : D >= 64 ? 2 : 1;   // rows per thread
+  static constexpr int TC = D >= 128 ? 8 : D >= 64 ? 4 : D >= 32 ? 2 : 1;   // columns per thread
+  static constexpr int NTJ = D / TC;
+  static constexpr int NT = (D / TR) * NTJ;   // threads that compute (512, or 256 for D = 16)
+};
+
 
 // ---- a2: gather U[S] = Ub[S] PU and V[T] = Vb[T] PV (16 rows per CTA) ----
 template <int D>
@@ -89,66 +100,98 @@ template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace ws) {
   // CTA 0: G_B = I - U[S] U[S]^T -> R_B; CTA 1: G_C = N N^T - (N V[T])(N V[T])^T -> R_C
   extern __shared__ float smem[];
+  constexpr int LDX = D + 1;             // padded strides: a warp reads rows b, b + 1, ... of X
+  constexpr int LDN = kMaxR + 1;         // and of N in different banks
   const bool isC = blockIdx.x == 1;
-  float* G = smem;                       // kMaxR x kMaxR
-  float* X = G + kMaxR * kMaxR;          // nS x D: U[S] or W_C^T
-  float* Ns = X + kMaxR * D;             // nS x nT (CTA 1)
-  __shared__ float piv, scale;
+  constexpr int LG = kMaxR + 1;          // padded stride of G: lanes on consecutive rows hit other banks
+  float* G = smem;                       // kMaxR x LG
+  float* X = G + kMaxR * LG;             // nS x LDX: U[S] or W_C^T
+  float* Ns = X + kMaxR * LDX;           // nS x LDN (CTA 1)
+  __shared__ float scale;
   __shared__ int kept;
   if (h->status != 0) return;
   const int nS = h->nS, nT = h->nT;
   if (nS == 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const float4* src = reinterpret_cast<const float4*>(isC ? ws.WCt : ws.UST);
-  for (int i = tid; i < nS * D / 4; i += nt) reinterpret_cast<float4*>(X)[i] = src[i];
+  const float* src = isC ? ws.WCt : ws.UST;
+  for (int i = tid; i < nS * D; i += nt) X[(i / D) * LDX + i % D] = src[i];
   if (isC)
-    for (int i = tid; i < nS * nT; i += nt) Ns[i] = ws.N[i];
+    for (int i = tid; i < nS * nT; i += nt) Ns[(i / nT) * LDN + i % nT] = ws.N[i];
   __syncthreads();
+  // the whole symmetric Gram (both triangles: no idle threads), entry (a, b) by one thread
   for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
-    if (b < a) continue;
     float g = (!isC && a == b) ? 1.0f : 0.0f;
     if (isC)
-      for (int t = 0; t < nT; ++t) g = fmaf(Ns[a * nT + t], Ns[b * nT + t], g);
+      for (int t = 0; t < nT; ++t) g = fmaf(Ns[a * LDN + t], Ns[b * LDN + t], g);
     float sx = 0.f;
 #pragma unroll 4
-    for (int k = 0; k < D; ++k) sx = fmaf(X[a * D + k], X[b * D + k], sx);
-    g -= sx;
-    G[a * kMaxR + b] = G[b * kMaxR + a] = g;
+    for (int k = 0; k < D; ++k) sx = fmaf(X[a * LDX + k], X[b * LDX + k], sx);
+    G[a * LG + b] = g - sx;
   }
   __syncthreads();
   if (tid == 0) {
     float mx = 1.0f;
-    for (int a = 0; a < nS; ++a) mx = fmaxf(mx, G[a * kMaxR + a]);
+    for (int a = 0; a < nS; ++a) mx = fmaxf(mx, G[a * LG + a]);
     scale = mx * kPivotTol;
     kept = 0;
   }
   __syncthreads();
-  // right-looking Cholesky G = R^T R (R upper); rows with a pivot <= tol are zero
-  for (int j = 0; j < nS; ++j) {
-    if (tid == 0) {
-      const float p = G[j * kMaxR + j];
-      piv = p > scale ? sqrtf(p) : 0.0f;
-      kept += piv > 0.f;
+  // blocked right-looking Cholesky G = R^T R (R upper), panels of 32 rows; a pivot <= tol
+  // makes its row of R zero. Per panel [k0, k1): warp 0 factors the diagonal block, the
+  // 16 warps solve the panel's trailing columns (forward substitution with R11^T, lane l
+  // holding row k0 + l), then everyone updates the trailing block.
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int k0 = 0; k0 < nS; k0 += 32) {
+    const int k1 = min(k0 + 32, nS);
+    if (warp == 0) {
+      for (int j = k0; j < k1; ++j) {
+        const float p = G[j * LG + j];
+        const float pv = p > scale ? sqrtf(p) : 0.0f;
+        const float ip = pv > 0.f ? 1.0f / pv : 0.0f;
+        __syncwarp();
+        const int l = j + lane;            // row j of R inside the block: columns j .. k1 - 1
+        if (l < k1) G[j * LG + l] = (l == j) ? pv : G[j * LG + l] * ip;
+        if (lane == 0) kept += pv > 0.f;
+        __syncwarp();
+        for (int a = j + 1 + lane; a < k1; a += 32) {   // block rows below j: a, columns a .. k1 - 1
+          const float ra = G[j * LG + a];
+          for (int b = a; b < k1; ++b) G[a * LG + b] -= ra * G[j * LG + b];
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
-    const float ip = piv > 0.f ? 1.0f / piv : 0.0f;
-    for (int l = j + tid; l < nS; l += nt) G[j * kMaxR + l] = (l == j) ? piv : G[j * kMaxR + l] * ip;
+    // trailing columns c >= k1 of the panel's rows: R[k][c] = (G[k][c] - sum_{i<k} R[i][k] R[i][c]) / R[k][k]
+    const int ncol = nS - k1;
+    for (int c = warp; c < ncol; c += 16) {
+      const int col = k1 + c;
+      const int row = k0 + lane;
+      float x = row < k1 ? G[row * LG + col] : 0.0f;
+      for (int k = 0; k < k1 - k0; ++k) {
+        const float rkk = G[(k0 + k) * LG + k0 + k];
+        float y = __shfl_sync(0xffffffffu, x, k);
+        y = rkk > 0.f ? y / rkk : 0.0f;
+        if (lane == k) x = y;
+        else if (lane > k && row < k1) x = fmaf(-G[(k0 + k) * LG + row], y, x);
+      }
+      if (row < k1) G[row * LG + col] = x;
+    }
     __syncthreads();
-    const int rem = nS - j - 1;
-    for (int i = tid; i < rem * rem; i += nt) {
-      const int a = j + 1 + i / rem, b = j + 1 + i % rem;
+    // trailing update of the upper triangle: G[a][b] -= sum_k R[k][a] R[k][b], k1 <= a <= b
+    for (int i = tid; i < ncol * ncol; i += nt) {
+      const int a = k1 + i / ncol, b = k1 + i % ncol;
       if (b < a) continue;
-      const float v = G[a * kMaxR + b] - G[j * kMaxR + a] * G[j * kMaxR + b];
-      G[a * kMaxR + b] = v;
-      G[b * kMaxR + a] = v;
+      float sacc = 0.f;
+      for (int k = k0; k < k1; ++k) sacc = fmaf(G[k * LG + a], G[k * LG + b], sacc);
+      G[a * LG + b] -= sacc;
     }
     __syncthreads();
   }
   float* R = isC ? ws.RC : ws.RB;
   for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
-    R[a * kMaxR + b] = b >= a ? G[a * kMaxR + b] : 0.0f;
+    R[a * kMaxR + b] = b >= a ? G[a * LG + b] : 0.0f;
   }
   if (tid == 0) {
     if (isC)
@@ -390,13 +433,14 @@ __global__ void __launch_bounds__(256) k_fo_apply(DevHeader* h, Workspace ws) {
     const int j = o / D, k = o % D;
     float g = 0.0f;
     if (j != k) {
-      const double tj = T[j * D + j], tk = T[k * D + k];
-      const double fjk = T[j * D + k], fkj = T[k * D + j];
-      const double den = tk * tk - tj * tj;
-      if (fabs(den) >= 1e-4 * (tj * tj + tk * tk) && den != 0.0) {
-        const double a = (tk * fjk + tj * fkj) / den;
-        const double b = (tj * fjk + tk * fkj) / den;
-        if (fabs(a) <= 1e-2 && fabs(b) <= 1e-2) g = (float)(side == 0 ? a : b);
+      const float tj = T[j * D + j], tk = T[k * D + k];
+      const float fjk = T[j * D + k], fkj = T[k * D + j];
+      const float den = tk * tk - tj * tj;
+      if (fabsf(den) >= 1e-4f * (tj * tj + tk * tk) && den != 0.0f) {
+        const float id = 1.0f / den;
+        const float a = (tk * fjk + tj * fkj) * id;
+        const float b = (tj * fjk + tk * fkj) * id;
+        if (fabsf(a) <= 1e-2f && fabsf(b) <= 1e-2f) g = side == 0 ? a : b;
       }
     }
     Gs[o] = g;
@@ -468,11 +512,17 @@ __global__ void __launch_bounds__(128) k_fo_norm_theta(DevHeader* h, Workspace w
 }
 
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
+// Blocked back substitution over row blocks of 32, bottom block first: a warp solves the
+// block's 32 x 32 triangle for its D/16 columns in registers (lane l holds row l, the solved
+// value of row j is broadcast by a shuffle), then the rows above take the block's
+// contribution as one product; two barriers per block instead of one per row.
 template <int D>
 __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace ws) {
+  constexpr int LDR = kMaxR + 1;      // padded row stride: a lane per row reads one column
+  constexpr int CPW = D / 16;         // columns per warp (16 warps)
   extern __shared__ float smem[];
-  float* R = smem;                    // kMaxR x kMaxR
-  float* Y = R + kMaxR * kMaxR;       // nS x D
+  float* R = smem;                    // kMaxR x LDR
+  float* Y = R + kMaxR * LDR;         // nS x D
   float* Wts = Y + kMaxR * D;         // nS x D
   if (h->status != 0) return;
   const int nS = h->nS;
@@ -483,59 +533,95 @@ __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace
   const float* Wt = side == 0 ? ws.UST : ws.WCt;  // nS x D  (W^T)
   float* Yg = side == 0 ? ws.YB : ws.YC;
   float* K = side == 0 ? ws.KU : ws.KV;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < nS * nS; i += blockDim.x) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  for (int i = tid; i < nS * nS; i += nt) {
     const int a = i / nS, b = i % nS;
-    R[a * kMaxR + b] = Rg[a * kMaxR + b];
+    R[a * LDR + b] = Rg[a * kMaxR + b];
   }
-  for (int i = tid; i < nS * D; i += blockDim.x) {
+  for (int i = tid; i < nS * D; i += nt) {
     Y[i] = Eg[D * D + i];
     Wts[i] = Wt[i];
   }
   __syncthreads();
-  // back substitution, 8 threads per column
-  const int sub = tid & 7;
-  for (int j = nS - 1; j >= 0; --j) {
-    for (int col0 = 0; col0 < D; col0 += blockDim.x >> 3) {
-      const int col = col0 + (tid >> 3);
-      float s = 0.f;
-      if (col < D)
-        for (int l = j + 1 + sub; l < nS; l += 8) s = fmaf(R[j * kMaxR + l], Y[l * D + col], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (col < D && sub == 0) {
-        const float p = R[j * kMaxR + j];
-        Y[j * D + col] = p > 0.f ? (Y[j * D + col] - s) / p : 0.0f;
+  const int nblk = (nS + 31) / 32;
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int r0 = blk * 32;
+    const int row = r0 + lane;
+    const bool live = row < nS;
+    if (warp < 16) {
+      float x[CPW];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) x[c] = live ? Y[row * D + warp * CPW + c] : 0.0f;
+      for (int j = min(31, nS - 1 - r0); j >= 0; --j) {
+        const float p = R[(r0 + j) * LDR + r0 + j];
+        const float ip = p > 0.f ? 1.0f / p : 0.0f;
+        const float rl = (lane < j) ? R[row * LDR + r0 + j] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          float yj = __shfl_sync(0xffffffffu, x[c], j);
+          yj *= ip;
+          if (lane == j) x[c] = yj;
+          else if (lane < j) x[c] = fmaf(-rl, yj, x[c]);
+        }
       }
+      if (live)
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) Y[row * D + warp * CPW + c] = x[c];
+    }
+    __syncthreads();
+    // rows above the block: Y[i] -= R[i, block] Y[block]
+    const int nb = min(32, nS - r0);
+    for (int o = tid; o < r0 * D; o += nt) {
+      const int i = o / D, col = o % D;
+      float s = 0.f;
+      for (int j = 0; j < nb; ++j) s = fmaf(R[i * LDR + r0 + j], Y[(r0 + j) * D + col], s);
+      Y[o] -= s;
     }
     __syncthreads();
   }
-  for (int i = tid; i < nS * D; i += blockDim.x) Yg[i] = Y[i];
-  for (int o = tid; o < D * D; o += blockDim.x) {
-    const int i = o / D, k = o % D;
-    float s = Eg[i * D + k];
-    for (int a = 0; a < nS; ++a) s = fmaf(-Wts[a * D + i], Y[a * D + k], s);
-    K[o] = s;
+  for (int i = tid; i < nS * D; i += nt) Yg[i] = Y[i];
+  // K = E[:d] - W Y with W = Wts^T: register tiles (TR x TC outputs per thread)
+  using S = MMShape<D>;
+  if (tid < S::NT) {
+    const int i0 = (tid / S::NTJ) * S::TR, j0 = (tid % S::NTJ) * S::TC;
+    float acc[S::TR][S::TC];
+#pragma unroll
+    for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+      for (int c = 0; c < S::TC; ++c) acc[r][c] = 0.f;
+    for (int a = 0; a < nS; ++a) {
+      float av[S::TR], bv[S::TC];
+#pragma unroll
+      for (int r = 0; r < S::TR; ++r) av[r] = Wts[a * D + i0 + r];
+#pragma unroll
+      for (int c = 0; c < S::TC; ++c) bv[c] = Y[a * D + j0 + c];
+#pragma unroll
+      for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+        for (int c = 0; c < S::TC; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+      for (int c = 0; c < S::TC; ++c) {
+        const int i = i0 + r, j = j0 + c;
+        K[i * D + j] = Eg[i * D + j] - acc[r][c];
+      }
   }
 }
 
-// ---- Gauss-Jordan inverse with partial pivoting (block 0: K_U, block 1: K_V) ----
-// [K | I] in shared memory with a padded row stride (2D + 1: column reads are free of
-// bank conflicts); each warp owns rows, each lane columns; the pivot row's live window
-// [p, 2D) is read once per step into registers.
+// ---- K^{-1}: Newton-Schulz when K is close to a scaled orthogonal matrix, else Gauss-Jordan ----
+// Gauss-Jordan with partial pivoting: [K | I] in shared memory with a padded row stride
+// (2D + 1: column reads are free of bank conflicts); each warp owns rows, each lane columns;
+// the pivot row's live window [p, 2D) is read once per step into registers.
 template <int D>
-__global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspace ws) {
+__device__ __forceinline__ void gj_inverse(DevHeader* h, const float* K, float* Ki, float* smem) {
   constexpr int LD = 2 * D + 1;
   constexpr int CPL = (2 * D + 31) / 32;   // columns per lane
-  extern __shared__ float smem[];
   float* Aug = smem;   // D x LD
   __shared__ int piv_row;
   __shared__ float piv_val;
   __shared__ float colv[D];
-  if (h->status != 0 || h->nS == 0) return;
-  const float* K = blockIdx.x == 0 ? ws.KU : ws.KV;
-  float* Ki = blockIdx.x == 0 ? ws.KUi : ws.KVi;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int o = tid; o < D * 2 * D; o += nt) {
     const int i = o / (2 * D), j = o % (2 * D);
@@ -596,6 +682,142 @@ __global__ void __launch_bounds__(kChainThreads) k_inverse(DevHeader* h, Workspa
     const int i = o / D, j = o % D;
     Ki[o] = Aug[i * LD + D + j];
   }
+}
+
+// Register-tiled product of D x D matrices in shared memory (row stride D) by up to 512 threads:
+// MODE 0: C = A B;  MODE 1: C = I - A B;  MODE 2: C = A + A B (A and C must differ).
+template <int D, int MODE>
+__device__ __forceinline__ void smem_mm(const float* A, const float* B, float* C) {
+  using S = MMShape<D>;
+  const int tid = threadIdx.x;
+  if (tid >= S::NT) return;
+  const int i0 = (tid / S::NTJ) * S::TR, j0 = (tid % S::NTJ) * S::TC;
+  float acc[S::TR][S::TC];
+#pragma unroll
+  for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+    for (int c = 0; c < S::TC; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < D; ++k) {
+    float a[S::TR], b[S::TC];
+#pragma unroll
+    for (int r = 0; r < S::TR; ++r) a[r] = A[(i0 + r) * D + k];
+#pragma unroll
+    for (int c = 0; c < S::TC; ++c) b[c] = B[k * D + j0 + c];
+#pragma unroll
+    for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+      for (int c = 0; c < S::TC; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < S::TR; ++r)
+#pragma unroll
+    for (int c = 0; c < S::TC; ++c) {
+      const int i = i0 + r, j = j0 + c;
+      float v = acc[r][c];
+      if (MODE == 1) v = (i == j ? 1.0f : 0.0f) - v;
+      if (MODE == 2) v += A[i * D + j];
+      C[i * D + j] = v;
+    }
+}
+
+// max over the block (kChainThreads threads) of v
+__device__ __forceinline__ float block_max512(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
+// One CTA per side (block 0: K_U, block 1: K_V). K relates the old and the new bases and is
+// close to orthogonal after a small change, so X0 = K^T (scaled by d / |K|_F^2) starts the
+// Newton-Schulz iteration X <- X + X (I - K X), whose residual squares each step; when the
+// start is too far (|I - K X0|_F >= 0.9) or the residual stops shrinking, Gauss-Jordan with
+// partial pivoting takes over. Three d x d buffers; K is re-read from global memory (L2) in
+// each step, its buffer having received the new X.
+constexpr int kNSInvSteps = 12;
+constexpr float kNSInvTol = 2e-6f;   // max |I - K X| accepted (FP32 level for d <= 128)
+
+template <int D>
+__global__ void __launch_bounds__(kChainThreads, 2) k_inverse(DevHeader* h, Workspace ws) {   // <= 64 registers
+  extern __shared__ float smem[];
+  __shared__ float red[kChainThreads / 32];
+  if (h->status != 0 || h->nS == 0) return;
+  const float* K = blockIdx.x == 0 ? ws.KU : ws.KV;
+  float* Ki = blockIdx.x == 0 ? ws.KUi : ws.KVi;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* b0 = smem;
+  float* b1 = smem + D * D;
+  float* W = smem + 2 * D * D;
+  float ss = 0.f;
+  for (int o = tid; o < D * D; o += nt) {
+    const float v = K[o];
+    b0[o] = v;
+    ss = fmaf(v, v, ss);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = ss;
+  __syncthreads();
+  float fro = 0.f;
+  for (int w = 0; w < nt / 32; ++w) fro += red[w];
+  const float scale = fro > 0.f ? (float)D / fro : 0.0f;
+  __syncthreads();
+  for (int o = tid; o < D * D; o += nt) {
+    const int i = o / D, j = o % D;
+    b1[o] = b0[j * D + i] * scale;   // X0 = scaled K^T
+  }
+  __syncthreads();
+  float* Kb = b0;
+  float* Xb = b1;
+  bool ok = false;
+  float prev = 3.0e38f;
+  for (int it = 0; it < kNSInvSteps && fro > 0.f; ++it) {
+    smem_mm<D, 1>(Kb, Xb, W);   // W = I - K X
+    __syncthreads();
+    float mx = 0.f, f2 = 0.f;
+    for (int o = tid; o < D * D; o += nt) {
+      const float w = W[o];
+      mx = fmaxf(mx, fabsf(w));
+      f2 = fmaf(w, w, f2);
+    }
+    const float res = block_max512(mx, red);
+    if (res <= kNSInvTol) {
+      ok = true;
+      break;
+    }
+    if (it == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = f2;
+      __syncthreads();
+      float ff = 0.f;
+      for (int w = 0; w < nt / 32; ++w) ff += red[w];
+      if (!(ff < 0.81f)) break;     // |I - K X0|_F >= 0.9: the iteration may not converge
+    } else if (!(res < 0.5f * prev)) {
+      break;                        // not shrinking any more (rounding floor or divergence)
+    }
+    prev = res;
+    smem_mm<D, 2>(Xb, W, Kb);       // K's buffer <- X + X W
+    __syncthreads();
+    float* t = Kb;
+    Kb = Xb;
+    Xb = t;
+    for (int o = tid; o < D * D; o += nt) Kb[o] = K[o];   // K again, into the old X's buffer
+    __syncthreads();
+  }
+  if (ok) {
+    for (int o = tid; o < D * D; o += nt) Ki[o] = Xb[o];
+    return;
+  }
+  __syncthreads();
+  gj_inverse<D>(h, K, Ki, smem);
 }
 
 // ---- d x d products into tmp: PU K_U, K_U^{-1} PUi, PV K_V, K_V^{-1} PVi ----
@@ -713,8 +935,35 @@ __global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, flo
   }
 }
 
+// Mixed precision runs the update's projection U[S] = Ub[S] PU, V[T] = Vb[T] PV on the tensor
+// cores (kind::tf32 with the three-term split); plain FP32 keeps the SIMT kernel. d = 16 has no
+// 32-wide K chunk and stays on SIMT in both. The projection is formed afresh in every update,
+// so its rounding does not accumulate.
+template <int D>
+static cudaError_t mm_tc(Ctx* c, const tc::SmallJobs& jobs, int njobs, cudaStream_t s) {
+  if constexpr (D % tc::kChunkK == 0) {
+    const size_t sm = tc::smem_bytes<D, D>();
+    cudaFuncSetAttribute(tc::k_mm_tc_small<D, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    tc::k_mm_tc_small<D, D><<<dim3((kMaxR + tc::kTileM - 1) / tc::kTileM, njobs), tc::kThreads, sm, s>>>(
+        jobs, &c->hdr->status, &c->hdr->status);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D>
+static bool use_tc(const Ctx* c) {
+  return c->cfg.precision == 1 && D % tc::kChunkK == 0;
+}
+
 template <int D>
 static cudaError_t gather_impl(Ctx* c, cudaStream_t s) {
+  if (use_tc<D>(c)) {   // U[S] = Ub[S] PU, V[T] = Vb[T] PV
+    tc::SmallJobs jobs{};
+    jobs.j[0] = {c->Ub, c->ws.S, &c->hdr->nS, 0, D, c->PU, c->ws.UST, D};
+    jobs.j[1] = {c->Vb, c->ws.T, &c->hdr->nT, 0, D, c->PV, c->ws.VT, D};
+    return mm_tc<D>(c, jobs, 2, s);
+  }
   const size_t sm = (size_t)(D * D + 16 * D) * sizeof(float);
   cudaFuncSetAttribute(k_gather<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_gather<D><<<dim3(kMaxR / 16, 2), 256, sm, s>>>(c->hdr, c->ws, c->Ub, c->Vb, c->PU, c->PV);
@@ -728,7 +977,7 @@ static cudaError_t chol_impl(Ctx* c, cudaStream_t s) {
   k_wct<D><<<kMaxR / 16, 256, smw, s>>>(c->hdr, c->ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t sm = (size_t)(2 * kMaxR * kMaxR + kMaxR * D) * sizeof(float);
+  const size_t sm = (size_t)(kMaxR * (kMaxR + 1) + kMaxR * (D + 1) + kMaxR * (kMaxR + 1)) * sizeof(float);
   cudaFuncSetAttribute(k_chol<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_chol<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
   return cudaGetLastError();
@@ -767,18 +1016,24 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = refine_core<D>(c, s)) != cudaSuccess) return e;
-  const size_t sm = (size_t)(kMaxR * kMaxR + 2 * kMaxR * D) * sizeof(float);
+  const size_t sm = (size_t)(kMaxR * (kMaxR + 1) + 2 * kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_trans<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_trans<D><<<2, kChainThreads, sm, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smi = (size_t)(D * (2 * D + 1)) * sizeof(float);
+  const size_t smi = (size_t)(D * (2 * D + 1) > 3 * D * D ? D * (2 * D + 1) : 3 * D * D) * sizeof(float);
   cudaFuncSetAttribute(k_inverse<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
   k_inverse<D><<<2, kChainThreads, smi, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  constexpr int TS = D < 32 ? D : 32;
-  constexpr int NT = D / TS;
-  k_products<D><<<4 * NT * NT, 256, 0, s>>>(c->hdr, c->ws, c->PU, c->PUi, c->PV, c->PVi);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the transform products stay on the SIMT units in both precisions: P and P^{-1} accumulate
+  // one product per update, and on the tensor cores (TF32, three-term split, accumulation in
+  // TMEM) the per-product error of a few 1e-7 drifted the factors by ~1e-3 after 600 d = 128
+  // updates, against ~2e-5 for FP32
+  {
+    constexpr int TS = D < 32 ? D : 32;
+    constexpr int NT = D / TS;
+    k_products<D><<<4 * NT * NT, 256, 0, s>>>(c->hdr, c->ws, c->PU, c->PUi, c->PV, c->PVi);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   k_commit<D><<<4, 256, 0, s>>>(c->hdr, c->ws, c->PU, c->PUi, c->PV, c->PVi, c->sigma);
   return cudaGetLastError();
 }
