@@ -167,6 +167,9 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
   unsigned char* top = reinterpret_cast<unsigned char*>(allnrm + kClBlocks * kClBsMax);
   __shared__ int s_rot;
   __shared__ int s_flags[kClP];
+  // the step's pairs, round by round: (slot * kClBsMax + i) of both columns packed as p | q << 8,
+  // -1 when the top-set rule leaves the pair out (built once per step, read by one warp a round)
+  __shared__ int s_pairs[(2 * kClBsMax - 1) * kClBsMax];
   // the same header values for every CTA of the cluster (written by earlier kernels)
   // use_hdr: 1 = the update's core (m from the header, counters recorded), 0 = a dense
   // matrix of m_host columns, 2 = the same and non-convergence recorded as a status
@@ -224,26 +227,38 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
     for (int t = 0; t < kClL; ++t) {
       const int bx = cl_block(c, 0, t), by = cl_block(c, 1, t);
       const int nrounds = t == 0 ? 2 * bs - 1 : bs;
+      for (int e = tid; e < nrounds * bs; e += kClThreads) {
+        const int round = e / bs, k = e % bs;
+        int sp = 0, ip = k, sq = 1, iq = k + round;
+        if (t == 0) {   // local indices 0 .. 2 bs - 1: slot 0 first, then slot 1
+          cl_pair(2 * bs, round, k, ip, iq);
+          sp = ip >= bs;
+          ip -= sp ? bs : 0;
+          sq = iq >= bs;
+          iq -= sq ? bs : 0;
+        } else {
+          iq -= iq >= bs ? bs : 0;
+        }
+        const int gp = (sp ? by : bx) * bs + ip, gq = (sq ? by : bx) * bs + iq;
+        const bool act = full || top[gp] || top[gq];
+        s_pairs[round * kClBsMax + k] = act ? (sp * kClBsMax + ip) | ((sq * kClBsMax + iq) << 8) : -1;
+      }
+      __syncthreads();
+      float* const cbase = colbuf + (size_t)cur * 2 * kClBsMax * kClStride;
+      float* const nbase = bnrm + cur * 2 * kClBsMax;
       for (int round = 0; round < nrounds; ++round) {
-        for (int k = warp; k < bs; k += nw) {
-          int sp = 0, ip = k, sq = 1, iq = k + round;
-          if (t == 0) {   // local indices 0 .. 2 bs - 1: slot 0 first, then slot 1
-            cl_pair(2 * bs, round, k, ip, iq);
-            sp = ip >= bs;
-            ip -= sp ? bs : 0;
-            sq = iq >= bs;
-            iq -= sq ? bs : 0;
-          } else {
-            iq -= iq >= bs ? bs : 0;
-          }
-          const int gp = (sp ? by : bx) * bs + ip, gq = (sq ? by : bx) * bs + iq;
-          float* np = nrm(cur, sp, ip);
-          float* nq = nrm(cur, sq, iq);
-          const bool act = (full || top[gp] || top[gq]) && *np > 1e-30f && *nq > 1e-30f;
-          if (act) {
-            const bool rot = two ? cl_rotate<true>(col(cur, sp, ip), col(cur, sq, iq), np, nq, lane, tol2)
-                                 : cl_rotate<false>(col(cur, sp, ip), col(cur, sq, iq), np, nq, lane, tol2);
-            if (rot && lane == 0) s_rot = 1;
+        if (warp < bs) {
+          const int e = s_pairs[round * kClBsMax + warp];
+          if (e >= 0) {
+            const int jp = e & 0xff, jq = e >> 8;
+            float* np = nbase + jp;
+            float* nq = nbase + jq;
+            if (*np > 1e-30f && *nq > 1e-30f) {
+              float* ap = cbase + jp * kClStride;
+              float* aq = cbase + jq * kClStride;
+              const bool rot = two ? cl_rotate<true>(ap, aq, np, nq, lane, tol2) : cl_rotate<false>(ap, aq, np, nq, lane, tol2);
+              if (rot && lane == 0) s_rot = 1;
+            }
           }
         }
         __syncthreads();

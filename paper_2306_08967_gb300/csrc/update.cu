@@ -114,20 +114,58 @@ __global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace 
   if (nS == 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
   const float* src = isC ? ws.WCt : ws.UST;
-  for (int i = tid; i < nS * D; i += nt) X[(i / D) * LDX + i % D] = src[i];
+  // rows nS .. kMaxR - 1 are zero (the register tiles below read them)
+  for (int i = tid; i < kMaxR * D; i += nt) X[(i / D) * LDX + i % D] = i < nS * D ? src[i] : 0.0f;
   if (isC)
-    for (int i = tid; i < nS * nT; i += nt) Ns[(i / nT) * LDN + i % nT] = ws.N[i];
+    for (int i = tid; i < kMaxR * nT; i += nt) Ns[(i / nT) * LDN + i % nT] = i < nS * nT ? ws.N[i] : 0.0f;
   __syncthreads();
-  // the whole symmetric Gram (both triangles: no idle threads), entry (a, b) by one thread
-  for (int i = tid; i < nS * nS; i += nt) {
-    const int a = i / nS, b = i % nS;
-    float g = (!isC && a == b) ? 1.0f : 0.0f;
-    if (isC)
-      for (int t = 0; t < nT; ++t) g = fmaf(Ns[a * LDN + t], Ns[b * LDN + t], g);
-    float sx = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < D; ++k) sx = fmaf(X[a * LDX + k], X[b * LDX + k], sx);
-    G[a * LG + b] = g - sx;
+  // the symmetric Gram in register tiles: a warp takes 4 rows a0 .. a0 + 3 (read by every lane
+  // at once) against the columns lane, lane + 32, lane + 64, lane + 96 (consecutive rows of X,
+  // other banks): 8 shared-memory reads per 16 FMAs
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    const int ngrp = (nS + 3) / 4;
+    const int ncol = (nS + 31) / 32;   // column blocks of 32 in use
+    for (int grp = warp; grp < ngrp; grp += nt / 32) {
+      const int a0 = grp * 4;
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+      if (isC) {
+        for (int t = 0; t < nT; ++t) {
+          float na[4], nb[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) na[r] = Ns[(a0 + r) * LDN + t];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) nb[c] = c < ncol ? Ns[(lane + 32 * c) * LDN + t] : 0.0f;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(na[r], nb[c], acc[r][c]);
+        }
+      }
+#pragma unroll 2
+      for (int k = 0; k < D; ++k) {
+        float xa[4], xb[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) xa[r] = X[(a0 + r) * LDX + k];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xb[c] = c < ncol ? X[(lane + 32 * c) * LDX + k] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(-xa[r], xb[c], acc[r][c]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int a = a0 + r, b = lane + 32 * c;
+          if (a < nS && b < nS) G[a * LG + b] = acc[r][c] + ((!isC && a == b) ? 1.0f : 0.0f);
+        }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -470,45 +508,107 @@ __device__ __forceinline__ Acc block_sum128(Acc v, Acc* part) {
   return part[0] + part[1] + part[2] + part[3];
 }
 
+// Double-float accumulation (an unevaluated pair hi + lo of floats): sums of exact products
+// (TwoProduct by an FMA, TwoSum by Knuth's branch-free form) carry about 48 bits, as FP64
+// sums of FP32 products do, at FP32 instruction rates (FP64 runs at ~1/64 of FP32 here).
+// The __f*_rn intrinsics keep the compiler from fusing the roundings the error terms rely on.
+struct DFloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_add_prod(DFloat acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = fmaf(a, b, -p);              // a b = p + pe exactly
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));   // acc.hi + p = s + err
+  return {s, __fadd_rn(acc.lo, __fadd_rn(err, pe))};
+}
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+
 // (d) unit columns (norms summed in FP64, each element scaled in FP64 and rounded once) and
-// theta_k = e_k^T M h_k in FP64. One CTA of 128 threads per k.
+// theta_k = e_k^T M h_k with double-float sums. One CTA of 128 threads per k.
 template <int D>
 __global__ void __launch_bounds__(128) k_fo_norm_theta(DevHeader* h, Workspace ws, const float* __restrict__ sigma) {
-  using Acc = double;
   __shared__ float ev[kMaxM], hv[kMaxM];
-  __shared__ Acc part[4];
+  __shared__ double part[4];
+  __shared__ DFloat dpart[4];
   if (h->status != 0 || h->nS == 0) return;
   const int nS = h->nS, m = D + nS;
   const int k = blockIdx.x, tid = threadIdx.x;
-  Acc se = 0, sh = 0;
+  double se = 0, sh = 0;
   for (int i = tid; i < m; i += blockDim.x) {
     const float e = ws.E[i * D + k], f = ws.H[i * D + k];
     ev[i] = e;
     hv[i] = f;
-    se = fma((Acc)e, (Acc)e, se);
-    sh = fma((Acc)f, (Acc)f, sh);
+    se = fma((double)e, (double)e, se);
+    sh = fma((double)f, (double)f, sh);
   }
-  se = block_sum128<Acc>(se, part);
-  sh = block_sum128<Acc>(sh, part);
-  const Acc ie = se > 0 ? (Acc)1 / sqrt(se) : (Acc)0;
-  const Acc ih = sh > 0 ? (Acc)1 / sqrt(sh) : (Acc)0;
+  se = block_sum128<double>(se, part);
+  sh = block_sum128<double>(sh, part);
+  const double ie = se > 0 ? 1.0 / sqrt(se) : 0.0;
+  const double ih = sh > 0 ? 1.0 / sqrt(sh) : 0.0;
   for (int i = tid; i < m; i += blockDim.x) {
-    const float e = (float)((Acc)ev[i] * ie), f = (float)((Acc)hv[i] * ih);
+    const float e = (float)((double)ev[i] * ie), f = (float)((double)hv[i] * ih);
     ev[i] = e;
     hv[i] = f;
     ws.E[i * D + k] = e;
     ws.H[i * D + k] = f;
   }
   __syncthreads();
-  Acc acc = 0;
-  for (int i = tid; i < D; i += blockDim.x) acc = fma((Acc)sigma[i] * (Acc)ev[i], (Acc)hv[i], acc);
-  if (tid < nS) {
-    Acc p, q;
-    fo_pq_col<D, Acc>(ws, nS, ev, hv, tid, p, q);
-    acc = fma(p, q, acc);
+  DFloat acc = {0.f, 0.f};
+  for (int i = tid; i < D; i += blockDim.x) {
+    // sigma_i e_i h_i: (sigma_i e_i) split exactly, then times h_i
+    const float t = __fmul_rn(sigma[i], ev[i]);
+    const float te = fmaf(sigma[i], ev[i], -t);
+    acc = df_add_prod(acc, t, hv[i]);
+    acc.lo = __fadd_rn(acc.lo, __fmul_rn(te, hv[i]));
   }
-  acc = block_sum128<Acc>(acc, part);
-  if (tid == 0) ws.theta[k] = (float)acc;
+  if (tid < nS) {
+    const int a = tid;
+    DFloat p = {0.f, 0.f}, q = {0.f, 0.f};
+    const float4* ur = reinterpret_cast<const float4*>(ws.UST + (size_t)a * D);
+    const float4* wr = reinterpret_cast<const float4*>(ws.WCt + (size_t)a * D);
+    for (int i4 = 0; i4 < D / 4; ++i4) {
+      const float4 u = ur[i4], w = wr[i4];
+      const int i = 4 * i4;
+      p = df_add_prod(p, ev[i], u.x);
+      p = df_add_prod(p, ev[i + 1], u.y);
+      p = df_add_prod(p, ev[i + 2], u.z);
+      p = df_add_prod(p, ev[i + 3], u.w);
+      q = df_add_prod(q, hv[i], w.x);
+      q = df_add_prod(q, hv[i + 1], w.y);
+      q = df_add_prod(q, hv[i + 2], w.z);
+      q = df_add_prod(q, hv[i + 3], w.w);
+    }
+    for (int b = 0; b <= a; ++b) {   // R_B and R_C are upper triangular: column a has rows 0 .. a
+      p = df_add_prod(p, ev[D + b], ws.RB[b * kMaxR + a]);
+      q = df_add_prod(q, hv[D + b], ws.RC[b * kMaxR + a]);
+    }
+    // p q = p.hi q.hi + p.hi q.lo + p.lo q.hi (+ p.lo q.lo, below the precision kept)
+    acc = df_add_prod(acc, p.hi, q.hi);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fmul_rn(p.hi, q.lo), __fmul_rn(p.lo, q.hi)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DFloat other;
+    other.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+    other.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+    acc = df_add(acc, other);
+  }
+  if ((tid & 31) == 0) dpart[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    DFloat t = dpart[0];
+    for (int w = 1; w < 4; ++w) t = df_add(t, dpart[w]);
+    ws.theta[k] = __fadd_rn(t.hi, t.lo);
+  }
 }
 
 // ---- Step 3 part 1: Y = R^{-1} E[d:] and K = E[:d] - W Y (block 0: U side, block 1: V side) ----
@@ -893,6 +993,7 @@ __global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, flo
   extern __shared__ float smem[];
   float* P = smem;             // D x D
   float* A = smem + D * D;     // 16 x D
+  float* Ys = A + 16 * D;      // nS x D: Y_C (side 1)
   if (h->status != 0) return;
   const int nS = h->nS, nT = h->nT;
   if (nS == 0) return;
@@ -903,15 +1004,19 @@ __global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, flo
   const float* Pm = side == 0 ? PUi : PVi;
   const int tid = threadIdx.x;
   for (int i = tid; i < D * D / 4; i += 256) reinterpret_cast<float4*>(P)[i] = reinterpret_cast<const float4*>(Pm)[i];
+  if (side == 1)
+    for (int i = tid; i < nS * D / 4; i += 256)
+      reinterpret_cast<float4*>(Ys)[i] = reinterpret_cast<const float4*>(ws.YC)[i];
+  __syncthreads();
   for (int o = tid; o < 16 * D; o += 256) {
     const int rr = o / D, k = o % D;
     float v = 0.f;
     if (r0 + rr < nrows) {
       if (side == 0) {
         v = ws.YB[(r0 + rr) * D + k];
-      } else {
+      } else {   // (N^T Y_C)[b]: the column b of N is the same for the whole warp (a broadcast)
         const int b = r0 + rr;
-        for (int a = 0; a < nS; ++a) v = fmaf(ws.N[a * nT + b], ws.YC[a * D + k], v);
+        for (int a = 0; a < nS; ++a) v = fmaf(__ldg(ws.N + a * nT + b), Ys[a * D + k], v);
       }
     }
     A[o] = v;
@@ -1040,7 +1145,7 @@ static cudaError_t trans_impl(Ctx* c, cudaStream_t s) {
 
 template <int D>
 static cudaError_t scatter_impl(Ctx* c, cudaStream_t s) {
-  const size_t sm = (size_t)(D * D + 16 * D) * sizeof(float);
+  const size_t sm = (size_t)(D * D + 16 * D + kMaxR * D) * sizeof(float);
   cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_scatter<D><<<dim3(kMaxR / 16, 2), 256, sm, s>>>(c->hdr, c->ws, c->Ub, c->Vb, c->r, c->PUi, c->PVi, c->s0);
   return cudaGetLastError();

@@ -69,7 +69,7 @@ def test_cpu_baseline_leg_runs_the_oracle_in_a_subprocess(tmp_path):
     state = str(tmp_path / "oracle_state.npz")
     r = bench.oracle_subprocess(CONFIGS["C1"], 4, 5.0, state)
     assert "error" not in r, r
-    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0 and r["batches"] >= 1
+    assert r["kind"] == "oracle" and r["cores"] == bench.ORACLE_THREADS and r["value"] > 0 and r["batches"] >= 1
     z = np.load(state)
     assert int(z["batches"]) == 2 + r["batches"] and z["X"].shape[1] == CONFIGS["C1"].d
 
