@@ -106,9 +106,33 @@ def oracle_power_iters(c):
 
 
 ERR_SAMPLE_ROWS = 20000   # rows of X, Y, Z the error comparison reads (all of them below this)
+ORACLE_ALT_THREADS = 8    # the second thread count the oracle leg is timed at (when the host has more)
 
 
-def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
+def _blas_thread_setter():
+    """The OpenBLAS thread-count setter of the BLAS numpy loaded (found through the process's
+    mapped libraries, as threadpoolctl does), or None."""
+    import ctypes
+    try:
+        paths = sorted({ln.split()[-1] for ln in open("/proc/self/maps") if "openblas" in ln.lower()
+                        and ln.split()[-1].startswith("/")})
+    except OSError:
+        return None
+    for path in paths:
+        try:
+            h = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for name in ("scipy_openblas_set_num_threads64_", "scipy_openblas_set_num_threads",
+                     "openblas_set_num_threads64_", "openblas_set_num_threads"):
+            fn = getattr(h, name, None)
+            if fn is not None:
+                fn.argtypes, fn.restype = [ctypes.c_int], None
+                return fn
+    return None
+
+
+def oracle_run(c, steps, warmup, time_budget_s, save_path=None, alt_threads=0):
     """Times the FP64 oracle (as it stands) on the first warmup+steps batches, stopping
     early once time_budget_s of timed work is spent.  Returns a dict; with save_path, also
     writes the oracle's final sigma and the rows of X, Y, Z of a seeded row sample there
@@ -127,17 +151,29 @@ def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
     for b in st.batches[:warmup]:
         orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
         orc.ppr_refresh()
-    lat, edges = [], 0
+    # with alternate threads, odd batches run with ORACLE_ALT_THREADS BLAS threads: both thread
+    # counts are timed on interleaved batches of the same stream within one budget
+    setter = _blas_thread_setter() if alt_threads and alt_threads < ORACLE_THREADS else None
+    lat, edges, alt_lat, alt_edges = [], 0, [], 0
     t_start = time.perf_counter()
-    for b in st.batches[warmup:warmup + steps]:
+    for i, b in enumerate(st.batches[warmup:warmup + steps]):
+        alt = setter is not None and i % 2 == 1
+        if setter is not None:
+            setter(alt_threads if alt else ORACLE_THREADS)
         t = time.perf_counter()
         orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
         orc.ppr_refresh()
-        lat.append(time.perf_counter() - t)
-        edges += b.k
+        if alt:
+            alt_lat.append(time.perf_counter() - t)
+            alt_edges += b.k
+        else:
+            lat.append(time.perf_counter() - t)
+            edges += b.k
         if time.perf_counter() - t_start > time_budget_s:
             break
-    total = time.perf_counter() - t_start
+    if setter is not None:
+        setter(ORACLE_THREADS)
+    total = float(np.sum(lat))
     if save_path:
         n = orc.n
         rows = np.arange(n) if n <= ERR_SAMPLE_ROWS else np.sort(
@@ -147,13 +183,24 @@ def oracle_run(c, steps, warmup, time_budget_s, save_path=None):
                  pushes=orc.pushes - pushes0)
     threads = ("1 thread" if ORACLE_THREADS == 1 else
                "%d BLAS threads (its push, in C, on one)" % ORACLE_THREADS)
-    return {"value": edges / total, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle", "batches": len(lat),
-            "edges": edges, "seconds": total, "init_s": init_s, "pushes": int(orc.pushes - pushes0),
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "sample": "first %d batches of the %s stream after %d warm-up batches (%d edges), FP64 oracle, "
-                      "%s; initialisation untimed (%.0f s): %d randomized t-SVD power passes, %s"
-                      % (len(lat), c.name, warmup, edges, threads, init_s, oracle_power_iters(c),
-                         "initial PPR propagation skipped (Z_b = r = 0)" if oracle_big(c) else "initial push")}
+    out = {"value": edges / total, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle", "batches": len(lat),
+           "edges": edges, "seconds": total, "init_s": init_s, "pushes": int(orc.pushes - pushes0),
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "sample": "%s%d batches of the %s stream after %d warm-up batches (%d edges), FP64 oracle, "
+                     "%s; initialisation untimed (%.0f s): %d randomized t-SVD power passes, %s"
+                     % ("the even ones of the first " if alt_lat else "first ", len(lat) + len(alt_lat), c.name,
+                        warmup, edges, threads, init_s, oracle_power_iters(c),
+                        "initial PPR propagation skipped (Z_b = r = 0)" if oracle_big(c) else "initial push")}
+    if alt_lat:
+        out["alt_threads"] = {"cores": alt_threads, "value": alt_edges / float(np.sum(alt_lat)),
+                              "batches": len(alt_lat), "edges": alt_edges,
+                              "p50_ms": 1e3 * float(np.percentile(alt_lat, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(alt_lat, 99)),
+                              "sample": "the odd batches of the same window, %d BLAS threads" % alt_threads}
+    elif alt_threads and alt_threads < ORACLE_THREADS:
+        out["alt_threads"] = {"cores": alt_threads, "value": None,
+                              "sample": "not timed: no OpenBLAS thread setter found in the process"}
+    return out
 
 
 def oracle_subprocess(c, steps, budget, save_path=None, wait=True):
@@ -929,7 +976,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scoring", dest="scoring", action="store_false",
                     help="skip the link-prediction query timing (score_pairs, topk) after the run")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=30.0,
+                    help="seconds of timed oracle work in the cpu_baseline leg (both thread counts)")
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--oracle-threads", type=int, default=max(1, os.cpu_count() or 1),
                     help="BLAS threads of the timed oracle (cpu_baseline and --impl reference); default: every "
@@ -973,7 +1021,7 @@ def main():
     else:
         c = CONFIGS[args.config]
     if args.oracle_worker:
-        print(json.dumps(oracle_run(c, args.steps, 2, args.budget, args.save_state)))
+        print(json.dumps(oracle_run(c, args.steps, 2, args.budget, args.save_state, alt_threads=ORACLE_ALT_THREADS)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -1060,6 +1108,8 @@ def main():
                 out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                                        "sample": r["sample"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                                        "init_s": r["init_s"]}
+                if "alt_threads" in r:
+                    out["cpu_baseline"]["alt_threads"] = r["alt_threads"]
             else:
                 out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
                                        "sample": "failed: " + r.get("error", "")}

@@ -76,6 +76,19 @@ static cudaError_t gemm_tall_kn(const float* A, int lda, long long n, const floa
 template <int K, int N>
 static cudaError_t gemm_tc_kn(const float* A, int lda, long long n, const float* B, float* C, int ldc,
                               const float* as, const float* cs, int* err, cudaStream_t s) {
+  if constexpr (tc::pipe_smem_bytes<K, N>() <= 227 * 1024) {
+    // the pipelined kernel: B split once per CTA, two A stages, one CTA per SM
+    const size_t smp = tc::pipe_smem_bytes<K, N>();
+    cudaFuncSetAttribute(tc::k_gemm_tc_pipe<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (n + tc::kTileM - 1) / tc::kTileM;
+    int grid = (int)(tiles < sms ? tiles : sms);
+    if (grid < 1) grid = 1;
+    tc::k_gemm_tc_pipe<K, N><<<grid, tc::kThreads, smp, s>>>(A, lda, n, B, C, ldc, as, cs, err);
+    return cudaGetLastError();
+  }
   const size_t sm = tc::smem_bytes<K, N>();
   cudaFuncSetAttribute(tc::k_gemm_tc<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int dev = 0, sms = 0;

@@ -417,3 +417,226 @@ __global__ void __launch_bounds__(kThreads) k_mm_tc_small(SmallJobs jobs, const 
 
 }  // namespace tc
 }  // namespace damf
+
+namespace damf {
+namespace tc {
+
+// Pipelined variant of k_gemm_tc for the fold and full-table queries (K, N <= 160, 2 K N 4 B of
+// shared memory for B): the right factor B is split into hi/lo tiles once per CTA for all of K,
+// and the rows of A go through two shared-memory stages, so that the threads load and split
+// chunk c + 1 of a tile while the tensor core runs the MMAs of chunk c (each stage's MMAs are
+// committed to their own mbarrier, which is waited on, bounded, before the stage is refilled).
+// One CTA per SM, grid-stride over 128-row tiles; the accumulator is read out per tile as in
+// k_gemm_tc. In-place use (C == A) is allowed (a tile's rows of A are read before its rows of
+// C are written, and no other CTA touches them).
+template <int K, int N>
+constexpr size_t pipe_smem_bytes() {
+  return (size_t)2 * K * N * 4 + (size_t)2 * 2 * kTileM * kChunkK * 4;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase) {
+  long long it = 0;
+  uint32_t done = 0;
+  while (!done) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(smem_u32(mbar)), "r"(phase));
+    if (!done && ++it > kWaitLimit) return false;
+  }
+  return true;
+}
+
+template <int K, int N>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc_pipe(const float* __restrict__ A, int lda, long long n,
+                                                             const float* __restrict__ B, float* C, int ldc,
+                                                             const float* __restrict__ ascale,
+                                                             const float* __restrict__ cscale, int* err) {
+  static_assert(K % kChunkK == 0 && N % 16 == 0 && N >= 16 && N <= 256, "shape");
+  constexpr int NC = K / kChunkK;
+  constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  constexpr uint32_t A_BYTES = kTileM * kChunkK * 4;
+  constexpr uint32_t B_BYTES = N * kChunkK * 4;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* b_hi = smem;                        // NC chunks of N x 32
+  unsigned char* b_lo = b_hi + NC * B_BYTES;
+  unsigned char* a_st = b_lo + NC * B_BYTES;         // stage s: hi at a_st + 2 s A_BYTES, lo after it
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+    failed = 0;
+  }
+  // B^T for all of K: row = output column j
+  for (int j = tid; j < N; j += kThreads) {
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int q = 0; q < kChunkK / 4; ++q) {
+        const int k = c * kChunkK + 4 * q;
+        const float4 v = make_float4(B[(size_t)k * N + j], B[(size_t)(k + 1) * N + j], B[(size_t)(k + 2) * N + j],
+                                     B[(size_t)(k + 3) * N + j]);
+        const float4 hh = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+        const float4 ll = make_float4(v.x - hh.x, v.y - hh.y, v.z - hh.z, v.w - hh.w);
+        const uint32_t off = (uint32_t)c * B_BYTES + tile_off(j, 4 * q);
+        *reinterpret_cast<float4*>(b_hi + off) = hh;
+        *reinterpret_cast<float4*>(b_lo + off) = ll;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_tf32(kTileM, N);
+  // pend: a commit of stage 0 / 1 not waited for yet; thread 0 waits (bounded), the others learn
+  // the outcome at the barrier that follows, so every thread takes the same path
+  __shared__ int s_ok;
+  int pend0 = 0, pend1 = 0;
+  uint32_t ph0 = 0, ph1 = 0;
+  bool ok = true;
+  long long it = 0;
+  for (long long r0 = (long long)blockIdx.x * kTileM; r0 < n && ok; r0 += (long long)gridDim.x * kTileM) {
+    const long long gr = r0 + tid;
+    for (int c = 0; c < NC && ok; ++c, ++it) {
+      const int s = (int)(it & 1);
+      // the MMAs that last read this stage are done before it is refilled
+      if ((s == 0 && pend0) || (s == 1 && pend1)) {
+        if (tid == 0) s_ok = mbar_wait_bounded(&mbar[s], s == 0 ? ph0 : ph1) ? 1 : 0;
+        __syncthreads();
+        ok = s_ok != 0;
+        if (ok && s == 0) {
+          ph0 ^= 1u;
+          pend0 = 0;
+        } else if (ok) {
+          ph1 ^= 1u;
+          pend1 = 0;
+        }
+        __syncthreads();   // s_ok is read by everyone before it is written again
+      }
+      if (!ok) break;
+      unsigned char* ahi = a_st + (uint32_t)s * 2 * A_BYTES;
+      unsigned char* alo = ahi + A_BYTES;
+      const int kc = c * kChunkK;
+#pragma unroll
+      for (int q = 0; q < kChunkK / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gr < n) v = *reinterpret_cast<const float4*>(A + gr * lda + kc + 4 * q);
+        if (ascale) {
+          v.x *= ascale[kc + 4 * q];
+          v.y *= ascale[kc + 4 * q + 1];
+          v.z *= ascale[kc + 4 * q + 2];
+          v.w *= ascale[kc + 4 * q + 3];
+        }
+        const float4 hh = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+        const float4 ll = make_float4(v.x - hh.x, v.y - hh.y, v.z - hh.z, v.w - hh.w);
+        const uint32_t off = tile_off(tid, 4 * q);
+        *reinterpret_cast<float4*>(ahi + off) = hh;
+        *reinterpret_cast<float4*>(alo + off) = ll;
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const uint32_t koff = (uint32_t)ks * 2 * kLBO;
+          const uint32_t boff = (uint32_t)c * B_BYTES + koff;
+          const uint64_t dah = smem_desc(smem_u32(ahi) + koff, kLBO, kSBO);
+          const uint64_t dal = smem_desc(smem_u32(alo) + koff, kLBO, kSBO);
+          const uint64_t dbh = smem_desc(smem_u32(b_hi) + boff, kLBO, kSBO);
+          const uint64_t dbl = smem_desc(smem_u32(b_lo) + boff, kLBO, kSBO);
+          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+              :: "r"(tmem), "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+              :: "r"(tmem), "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+              :: "r"(tmem), "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(&mbar[s])));
+      }
+      if (s == 0) pend0 = 1;
+      else pend1 = 1;
+    }
+    // the tile's MMAs are done: both stages' commits waited for, then the accumulator read out
+    if (ok) {
+      if (tid == 0) {
+        int w = 3;   // bit 0: stage 0 done (or not pending), bit 1: stage 1
+        if (pend0 && !mbar_wait_bounded(&mbar[0], ph0)) w &= ~1;
+        if ((w & 1) && pend1 && !mbar_wait_bounded(&mbar[1], ph1)) w &= ~2;
+        if (!(w & 1)) w &= ~2;   // stage 1 not waited for
+        s_ok = w;
+      }
+      __syncthreads();
+      const int w = s_ok;
+      ok = w == 3;
+      if (pend0 && (w & 1)) {
+        ph0 ^= 1u;
+        pend0 = 0;
+      }
+      if (pend1 && (w & 2)) {
+        ph1 ^= 1u;
+        pend1 = 0;
+      }
+      __syncthreads();
+    }
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const long long row = r0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row < n) {
+#pragma unroll
+        for (int e = 0; e < 16; e += 4) {
+          float4 o = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                                 __uint_as_float(v[e + 3]));
+          if (cscale) {
+            o.x *= cscale[c0 + e];
+            o.y *= cscale[c0 + e + 1];
+            o.z *= cscale[c0 + e + 2];
+            o.w *= cscale[c0 + e + 3];
+          }
+          *reinterpret_cast<float4*>(C + row * ldc + c0 + e) = o;
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok && tid == 0) {
+    failed = 1;
+    // a wait ran out: wait again (bounded) for the commits still pending before freeing TMEM
+    if (pend0) mbar_wait_bounded(&mbar[0], ph0);
+    if (pend1) mbar_wait_bounded(&mbar[1], ph1);
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
+  if (tid == 0 && failed && err) atomicCAS(err, 0, 5);
+}
+
+}  // namespace tc
+}  // namespace damf

@@ -5,7 +5,9 @@ Tolerances (from the FP32 device arithmetic: unit roundoff 6e-8 grown over the d
   * one update vs the brute-force t-SVD of (previous product + dA) (Theorem 2):
     sigma rel 2e-4, X Y^T rel Frobenius 2e-4
   * PPR: |Zb - Pi Xb|_max <= eps (1 + 1e-3) + 2e-6 |Xb|_max  (push bound plus FP32 rounding)
-  * whole-stream runs vs the FP64 oracle: sigma rel 1e-3, X Y^T rel Frobenius 1e-3
+  * whole-stream runs vs the FP64 oracle: sigma rel 1e-4, X Y^T rel Frobenius 1e-4 (the FP32
+    tolerance after 1,000 updates; these streams are shorter); Z Y^T rel Frobenius 1e-3, since
+    Z is PPR(X) only within the push's eps and two push orders land at different points of it
 """
 
 import numpy as np
@@ -20,6 +22,15 @@ from tests.gpu_util import dense_adj, gpu_xy, make_pair, rel_fro
 pytestmark = pytest.mark.gpu
 
 SEED = 0xDA3F0000 + 200
+STREAM_TOL = 1e-4
+
+
+def _stream_close(tag, sg, Xg, Yg, orc):
+    es = float(np.max(np.abs(sg - orc.sigma) / orc.sigma))
+    ex = rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T)
+    print("%s: sigma rel %.2e, X Y^T rel %.2e" % (tag, es, ex))
+    assert es <= STREAM_TOL, (tag, es)
+    assert ex <= STREAM_TOL, (tag, ex)
 
 
 def _events(rng, n, k, p_del=0.25):
@@ -380,8 +391,7 @@ def test_c1_stream_against_oracle():
         orc.ppr_refresh()
     g.check()
     Xg, Yg, sg = gpu_xy(g)
-    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
-    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    _stream_close("C1 stream", sg, Xg, Yg, orc)
     # Z is PPR(X); columns of X, Y, Z carry a common sign (or rotation within a repeated
     # singular value), so compare the invariant product Z Y^T = PPR(X Y^T)
     Zg = g.embeddings()["Z"].double().cpu().numpy()
@@ -413,8 +423,7 @@ def test_node_arrival_stream_against_oracle(directed):
     g.check()
     assert g.n == n
     Xg, Yg, sg = gpu_xy(g)
-    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
-    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    _stream_close("node arrivals, directed=%s" % directed, sg, Xg, Yg, orc)
     Zg = g.embeddings()["Z"].double().cpu().numpy()
     assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
     # the final graph is the full graph
@@ -445,8 +454,7 @@ def test_c3_shaped_stream_against_oracle():
     g.check()
     assert g.stats()["updates"] > len(st.batches)     # calls above 64 events took several updates
     Xg, Yg, sg = gpu_xy(g)
-    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
-    assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+    _stream_close("C3 shape", sg, Xg, Yg, orc)
     Zg = g.embeddings()["Z"].double().cpu().numpy()
     assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
     g.close()
@@ -482,8 +490,7 @@ def test_c4_shaped_graphs_in_one_call_against_oracles():
     for g, orc, _ in graphs:
         g.check()
         Xg, Yg, sg = gpu_xy(g)
-        np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
-        assert rel_fro(Xg @ Yg.T, orc.X() @ orc.Y().T) < 1e-3
+        _stream_close("C4 shape, n=%d d=%d" % (g.n, g.d), sg, Xg, Yg, orc)
         Zg = g.embeddings()["Z"].double().cpu().numpy()
         assert rel_fro(Zg @ Yg.T, orc.Z() @ orc.Y().T) < 1e-3
         g.close()
@@ -596,8 +603,7 @@ def test_fold_preserves_the_factorisation():
                      propagate=False)
     for b in st.batches:
         orc.apply_edges(b.src, b.dst, b.op, b.new_nodes)
-    np.testing.assert_allclose(s1, orc.sigma, rtol=1e-3)
-    assert rel_fro(X1 @ Y1.T, orc.X() @ orc.Y().T) < 1e-3
+    _stream_close("folded stream", s1, X1, Y1, orc)
 
 
 def test_mixed_precision_matches_plain_fp32():
@@ -659,3 +665,18 @@ def test_inputs_are_staged_on_the_given_stream():
     b.check()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("d,n", [(64, 1000), (128, 1300)])
+def test_full_table_query_on_tensor_cores_matches_row_query(d, n):
+    # mixed precision answers a full-table query (rows = NULL) with the pipelined tcgen05 GEMM
+    # (three-term TF32 split) and a row list with the SIMT kernel: the two must agree to FP32
+    # accuracy, n not a multiple of the 128-row tile
+    g, _, _ = make_pair(n, 10.0, 2.5, d, 0.15, 1e-4, SEED + 500 + d, oracle=False)
+    full = g.embeddings()
+    rows = g.embeddings(rows=np.arange(g.n, dtype=np.int32))
+    for k in ("X", "Y", "Z"):
+        a, b = full[k].double().cpu().numpy(), rows[k].double().cpu().numpy()
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= 2e-6 * scale, (k, np.abs(a - b).max() / scale)
+    g.close()
