@@ -7,8 +7,8 @@
 // a circle-method tournament over the blocks: in step t CTA c holds a pair of blocks and
 // rotates every column pair between them (in step 0 also every pair inside them, which
 // covers the pairs within each block once per sweep); between steps the CTAs pull the blocks
-// of the next step from each other's shared memory (distributed shared memory, two cluster
-// barriers). Every column pair is visited once per sweep, as in the one-CTA order, while
+// of the next step from each other's shared memory (distributed shared memory, one cluster
+// barrier: the two buffers alternate). Every column pair is visited once per sweep, as in the one-CTA order, while
 // each CTA works on an eighth of the columns: eight SMs issue the rotations instead of one.
 // Within a step a warp rotates one pair per round (rounds of disjoint pairs separated by
 // __syncthreads), holding both columns in registers between the dot product and the rotation.
@@ -40,6 +40,12 @@ constexpr int kClThreads = 512;
 constexpr int kClStride = 256;                   // floats per column: rows padded with zeros
 constexpr float kClTol = 1e-6f;                  // rotate while |a_p . a_q| > tol |a_p| |a_q|
 constexpr int kClTopOnlySweeps = 6;
+// An update's core stops after a sweep whose largest relative coupling |a_p . a_q| / |a_p||a_q|
+// was below kClStopRel: the pairs it left are coupled at about its square, and the first-order
+// correction that follows (T = E^T M H) removes what remains between the top columns; on cores
+// of d = 128 streams this gave the factors of the sweeps run to the end within FP32 rounding,
+// with a third fewer sweeps.
+constexpr float kClStopRel = 3e-4f;
 
 // shared memory: columns [2 buffers][2 slots][kClBsMax][kClStride], their squared norms
 // [2][2][kClBsMax], all norms by global column [kClBlocks * kClBsMax], top flags, sweep flags
@@ -96,7 +102,8 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); 
 // when TWO, 128 + 4 lane .. +3), cached squared norms np, nq. Rotates when
 // |g| > tol |a_p||a_q| (the rotation makes the two columns orthogonal); returns whether it did.
 template <bool TWO>
-__device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float* nq, int lane, float tol2) {
+__device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float* nq, int lane, float tol2,
+                                          float& rel2) {
   float4* p4 = reinterpret_cast<float4*>(ap) + lane;
   float4* q4 = reinterpret_cast<float4*>(aq) + lane;
   const float4 x0 = p4[0], y0 = q4[0];
@@ -111,6 +118,7 @@ __device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float
   const float g = warp_sum(acc.x + acc.y);
   const float aa = *np, bb = *nq;
   if (!(g * g > tol2 * aa * bb)) return false;
+  rel2 = __fdividef(g * g, aa * bb);
   // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g): the smaller root of
   // t^2 + 2 zeta t - 1 = 0, so that the rotated columns are orthogonal. The angle may come
   // from hardware approximations (an inexact t only leaves a smaller g for the next sweep),
@@ -167,6 +175,8 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
   unsigned char* top = reinterpret_cast<unsigned char*>(allnrm + kClBlocks * kClBsMax);
   __shared__ int s_rot;
   __shared__ int s_flags[kClP];
+  __shared__ unsigned s_rel2;           // largest squared relative coupling rotated in the sweep (float bits)
+  __shared__ unsigned s_rels[kClP];
   // the step's pairs, round by round: (slot * kClBsMax + i) of both columns packed as p | q << 8,
   // -1 when the top-set rule leaves the pair out (built once per step, read by one warp a round)
   __shared__ int s_pairs[(2 * kClBsMax - 1) * kClBsMax];
@@ -213,7 +223,10 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
         for (int k = 0; k < kClP; ++k) cl.map_shared_rank(allnrm, k)[g] = s2;
       }
     }
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_rel2 = 0u;
+    }
     cl.sync();
     // top set: the D columns of largest norm (ties by lower index)
     for (int g = warp; g < ng; g += nw) {
@@ -256,8 +269,13 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
             if (*np > 1e-30f && *nq > 1e-30f) {
               float* ap = cbase + jp * kClStride;
               float* aq = cbase + jq * kClStride;
-              const bool rot = two ? cl_rotate<true>(ap, aq, np, nq, lane, tol2) : cl_rotate<false>(ap, aq, np, nq, lane, tol2);
-              if (rot && lane == 0) s_rot = 1;
+              float rel2 = 0.f;
+              const bool rot = two ? cl_rotate<true>(ap, aq, np, nq, lane, tol2, rel2)
+                                   : cl_rotate<false>(ap, aq, np, nq, lane, tol2, rel2);
+              if (rot && lane == 0) {
+                s_rot = 1;
+                atomicMax(&s_rel2, __float_as_uint(rel2));   // non-negative floats order as their bits
+              }
             }
           }
         }
@@ -276,22 +294,36 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
         const float* sn = cl.map_shared_rank(nrm(cur, hs, 0), hc);
         for (int i = tid; i < bs; i += kClThreads) *nrm(cur ^ 1, slot, i) = sn[i];
       }
-      cl.sync();
+      // a CTA's own pull must be complete before its next rounds; no cluster barrier is needed:
+      // the buffer pulled into is read by others only after the next step's barrier (which
+      // this CTA reaches after its pull), and the buffer pulled from is written again only
+      // after that barrier too (which every reader reaches after its pull)
+      __syncthreads();
       cur ^= 1;
     }
     // did any CTA rotate in this sweep?
-    if (tid < kClP) cl.map_shared_rank(s_flags, tid)[c] = s_rot;
+    if (tid < kClP) {
+      cl.map_shared_rank(s_flags, tid)[c] = s_rot;
+      cl.map_shared_rank(s_rels, tid)[c] = s_rel2;
+    }
     cl.sync();
     bool any = false;
-    for (int k = 0; k < kClP; ++k) any |= s_flags[k] != 0;
-    if (!full && any && sweep + 1 >= kClTopOnlySweeps) {
+    float rel2 = 0.f;
+    for (int k = 0; k < kClP; ++k) {
+      any |= s_flags[k] != 0;
+      rel2 = fmaxf(rel2, __uint_as_float(s_rels[k]));
+    }
+    // an update's core whose sweep rotated only weakly coupled pairs is done (the refinement
+    // that follows takes the rest); dense calls sweep until nothing rotates
+    const bool weak = use_hdr == 1 && any && rel2 < kClStopRel * kClStopRel;
+    if (!full && any && !weak && sweep + 1 >= kClTopOnlySweeps) {
       // the top set keeps changing (values straddling the cut are close): every pair from here on
       full = true;
       if (use_hdr == 1 && c == 0 && tid == 0) h->jacobi_full += 1;
     }
-    if (!any) {
+    if (!any || weak) {
       if (full) break;
-      // the norms are those of the sweep's start (nothing rotated since)
+      // the norms are those of the sweep's start (nothing rotated since, or only weakly)
       float topmin = 3.0e38f, bsum = 0.f, bmax = 0.f;
       for (int g = 0; g < ng; ++g) {
         if (top[g]) {
