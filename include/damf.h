@@ -502,7 +502,7 @@ damf_status damf_core_svd(const float* sigma, const float* L, const float* R, in
  *   itself lives in the library's array, which the caller cannot read, so pass `status` to
  *   learn of a device error).  The caller still provides and owns every input and output.
  *   Nothing is allocated: the scratch (a status word and the assembled core) is one static
- *   device array of 262,656 bytes compiled into the library, which every GPU that loads the
+ *   device array of 263,168 bytes compiled into the library, which every GPU that loads the
  *   library holds until the process exits.
  *   Limit: d + r <= 256 (d in {16, 32, 64, 128}, 1 <= r <= 128); a larger r returns
  *   DAMF_ERR_CAPACITY, bad d or NULL pointers DAMF_ERR_INVALID.

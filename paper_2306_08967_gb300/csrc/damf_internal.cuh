@@ -56,9 +56,11 @@ struct DevHeader {
   unsigned long long push_ns[4];   // block 0 of the push: seeding, task loop, barriers; [3] mean idle (ns)
   // push work queue (ppr.cu), zeroed before each launch: qstate = (tasks not finished << 32) |
   // queue tail; q_head = next queue position to claim; bump counters of rho slots and items
-  unsigned long long qstate;
-  int q_head;
-  int overflow;
+  // Each word every warp of the push hits (qstate at each publication, q_head at each claim)
+  // sits on its own 128-byte line, so that their atomics queue at different L2 slices.
+  alignas(128) unsigned long long qstate;
+  alignas(128) int q_head;
+  alignas(128) int overflow;
   int rho_tail;
   int item_tail;
   int ovf_count;    // hub items that found the queue full (processed at the end of the phase)
@@ -66,7 +68,7 @@ struct DevHeader {
   // (between the seeding barrier and the end of the loop); helpers counts those inside
   int help_open;
   int helpers;
-  GridBar bar;
+  alignas(128) GridBar bar;
 };
 
 struct Adj {

@@ -18,9 +18,9 @@ using namespace damf;
 
 namespace {
 
-constexpr size_t kHeaderBytes = 512;
+constexpr size_t kHeaderBytes = 1024;
 static_assert(sizeof(DevHeader) <= kHeaderBytes, "status area too small");
-// status word area + the largest core (d + r <= 256) in FP32: 262,656 bytes
+// status word area + the largest core (d + r <= 256) in FP32: 263,168 bytes
 constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxM * kMaxM * sizeof(float);
 
 // Held by every GPU that loads the library, until the process exits.

@@ -23,8 +23,10 @@
 // counted before it is published and uncounted in the same atomic that counts the tasks it
 // queued (or later), so the count reaches 0 only when no task is queued or running. A warp
 // claims kClaim positions at a time (q_head), keeps the tasks it queues in a shared-memory
-// buffer, and publishes them (one atomic, release stores) after each claim and before it
-// waits for an empty slot; it leaves when the count is 0.
+// buffer, and publishes them (one atomic, release stores) once 16 are buffered and before it
+// waits for an empty slot; it leaves when the count is 0. The queue words sit on their own
+// cache lines (every warp hits them); a claim's hub items read their in-edges in one pass and
+// share the hub's row through a per-warp shared-memory slot.
 // The queue does not wrap within a phase. When it is full, rows stay flagged and unqueued and
 // the overflow flag is set; after the phase every row is cleared and checked again.
 // Every wait is bounded (kSpinLimit with __nanosleep; DAMF_ERR_TIMEOUT).
@@ -83,8 +85,10 @@ template <int D>
 struct PushShape {
   static constexpr int LPR = D / 4;
   static constexpr int RPW = 32 / LPR;
-  static constexpr int CHL = RPW <= 4 ? 8 : 4;
-  static constexpr int EPC = RPW * CHL;   // 8, 16, 32, 32 for D = 128, 64, 32, 16
+  // atomics in flight per lane: four (returns in 16 registers) measured as fast as eight,
+  // which pushed the task loop past 64 registers into local-memory spills
+  static constexpr int CHL = 4;
+  static constexpr int EPC = RPW * CHL;   // 4, 8, 16, 32 for D = 128, 64, 32, 16
 };
 
 // maximum over the LPR lanes of a row group (every lane of the warp takes part)
@@ -113,9 +117,18 @@ __device__ __forceinline__ void st_release(int32_t* p, int v) {
 constexpr int kQBuf = 256;    // per-warp buffer of tasks to publish (shared memory)
 constexpr int kClaim = 4;     // queue positions a warp claims at a time
 
+// A warp's counters, kept by its lane 0 in shared memory (registers are the push's scarce
+// resource: what does not fit in 64 per thread spills to local memory, whose reloads miss L1).
+struct WarpStats {
+  long long pushes, edges;   // rows pushed, in-edges scattered
+  unsigned long long wait;   // ns spent waiting for a queue slot
+  int rows, items;           // row and item tasks taken
+};
+
 // A warp's tasks to publish and the count of its finished tasks not yet uncounted.
 struct WarpQ {
   int32_t* buf;   // [kQBuf] in shared memory
+  float* rho;     // [128] in shared memory: the hub row of the claim's items
   int n;          // buffered entries (warp-uniform)
   int done;       // finished tasks (warp-uniform)
   int32_t* ovf;   // list of hub items that found the queue full
@@ -297,8 +310,7 @@ __device__ __forceinline__ int wait_slot(DevHeader* h, int32_t* queue, long long
 // Owners call it between the grid barriers of a phase; in a grouped push, warps whose own
 // graphs are done call it on another graph's queue while that graph's loop is open.
 template <int D, bool SCALED>
-__device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long long& my_pushes, long long& my_edges,
-                                          int& my_rows, int& my_items, unsigned long long& my_wait) {
+__device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, WarpStats& st_w) {
   DevHeader* const h = a.h;
   const Adj in = a.in;
   const int32_t* __restrict__ outdeg = a.outdeg;
@@ -341,6 +353,21 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         m2 = wi.x;
       }
     }
+    // the in-edges of every claimed hub item and their out-degrees, two loads for the whole
+    // claim instead of two per item: lane kItemEdges b + j holds in-edge j of entry b
+    int iw = 0, idg = 1;
+    if constexpr (kClaim * kItemEdges == 32) {
+      const int bb = lane / kItemEdges, j = lane % kItemEdges;
+      const int e_b = __shfl_sync(kFull, eb, bb);
+      const int st_b = __shfl_sync(kFull, m0, bb), n_b = __shfl_sync(kFull, m1, bb);
+      const bool want = e_b < -1 && j < n_b &&
+                        DAMF_DCHECK(h, st_b >= 0 && n_b <= kItemEdges && (long long)st_b + n_b <= in.m_cap);
+      if (want) iw = __ldg(in.col + st_b + j);
+      if (want && DAMF_DCHECK(h, (unsigned)iw < (unsigned)a.ncap)) idg = __ldg(outdeg + iw);
+      else iw = 0;
+    }
+    // consecutive items of one hub share its rho row: read once per claim
+    int rho_slot = -1;
     for (int b = 0; b < kClaim; ++b) {
     const long long p = p0 + b;
     int e = __shfl_sync(kFull, eb, b);
@@ -351,7 +378,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
       if (lane == 0) {
         const unsigned long long t0 = gtimer();
         e = wait_slot(h, queue, p, qcap);
-        my_wait += gtimer() - t0;
+        st_w.wait += gtimer() - t0;
       }
       e = __shfl_sync(kFull, e, 0);
       if (e == -1) {
@@ -365,7 +392,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
       continue;
     }
     if (e >= 0) {
-      if (lane == 0) ++my_rows;
+      if (lane == 0) ++st_w.rows;
       // row task. The flag is cleared first; the removal of v below is ordered after the
       // clear (fence), so an add that lands after the removal finds the flag clear and queues
       // u again, while an add between the read of v and the removal shows in `left`.
@@ -424,8 +451,8 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
                     make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w));
         }
         if (lane == 0) {
-          my_pushes += 1;
-          my_edges += deg;
+          st_w.pushes += 1;
+          st_w.edges += deg;
         }
         bool direct = true;
         if (deg > direct_max) {
@@ -459,7 +486,7 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
       }
     } else {
       // item task: one chunk of a hub's in-edges
-      if (lane == 0) ++my_items;
+      if (lane == 0) ++st_w.items;
       if (!pre) {
         const int4 wi = __ldcg(ws.work + (-e - 2));
         st = wi.y;
@@ -471,17 +498,34 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
         deg = 0;
         aux = 0;
       }
-      const float4 rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
+      float4 rv;
+      if (aux != rho_slot) {   // warp-uniform; the row is kept in the warp's shared slot, not in registers
+        rv = f4_ldcg(ws.rho + (size_t)aux * D + 4 * q);
+        if (sub == 0) reinterpret_cast<float4*>(wq.rho)[q] = rv;
+        __syncwarp();
+        rho_slot = aux;
+      } else {
+        rv = reinterpret_cast<const float4*>(wq.rho)[q];
+      }
       int w0 = 0, d0 = 1;
-      if (lane < deg) w0 = __ldg(in.col + st + lane);
-      if (lane < deg && DAMF_DCHECK(h, (unsigned)w0 < (unsigned)a.ncap)) d0 = __ldg(outdeg + w0);
+      if (pre && kClaim * kItemEdges == 32) {   // the claim's pass loaded them: in-edge `lane` of this entry sits in lane kItemEdges b + lane
+        const int src = min(b * kItemEdges + lane, 31);
+        w0 = __shfl_sync(kFull, iw, src);
+        d0 = __shfl_sync(kFull, idg, src);
+      } else {
+        if (lane < deg) w0 = __ldg(in.col + st + lane);
+        if (lane < deg && DAMF_DCHECK(h, (unsigned)w0 < (unsigned)a.ncap)) d0 = __ldg(outdeg + w0);
+      }
       scatter_edges<D, SCALED>(rv, st, deg, in.col, outdeg, r, beta, eps, wq, h, inq, queue, qcap, lane, sub,
                                q, true, true, w0, d0, a.ncap);
     }
     wq.done += 1;
     }
-    flush(wq, h, queue, qcap, lane, ws.ovf);
+    // publish once enough is buffered (and always before waiting, above): fewer atomics on
+    // the queue word, which every warp of the push shares
+    if (wq.n >= 16) flush(wq, h, queue, qcap, lane, ws.ovf);
   }
+  flush(wq, h, queue, qcap, lane, ws.ovf);
 }
 
 // The push of one graph by `nblocks` CTAs of 256 threads (this one is CTA `blk` of them): the
@@ -489,7 +533,8 @@ __device__ __forceinline__ void task_loop(const PushArgs& a, WarpQ& wq, long lon
 // s_t (5 words) and s_buf (8 warps x kQBuf) are the CTA's shared timers and warp queue buffers.
 template <int D, bool SCALED>
 __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_all, unsigned blk, unsigned nblocks,
-                                          unsigned long long* s_t, int32_t (*s_buf)[kQBuf]) {
+                                          unsigned long long* s_t, int32_t (*s_buf)[kQBuf], float (*s_rho)[kMaxD],
+                                          WarpStats* s_ws) {
   DevHeader* const h = a.h;
   const Adj in = a.in;
   const int32_t* __restrict__ outdeg = a.outdeg;
@@ -508,9 +553,8 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
   const long long qcap = ws.qcap;
   int32_t* queue = ws.queue;
   uint32_t* inq = ws.stamp;
-  long long my_pushes = 0, my_edges = 0;
-  int my_rows = 0, my_items = 0;   // tasks taken by this warp (lane 0)
-  unsigned long long my_wait = 0;  // ns this warp waited for a queue slot (lane 0)
+  WarpStats& st_w = s_ws[threadIdx.x >> 5];   // this warp's counters (lane 0 keeps them)
+  if (lane == 0) st_w = WarpStats{0, 0, 0ull, 0, 0};
   const int npend = h->pending;
   // block 0's view of where the time goes (ns): seeding, task loop, barriers; [4] is the last
   // mark. Kept in shared memory, where it costs no registers.
@@ -519,7 +563,7 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
     s_t[0] = s_t[1] = s_t[2] = s_t[3] = 0ull;
     s_t[4] = gtimer();
   }
-  WarpQ wq{s_buf[threadIdx.x >> 5], 0, 0, ws.ovf, ws.stamp};
+  WarpQ wq{s_buf[threadIdx.x >> 5], s_rho[threadIdx.x >> 5], 0, 0, ws.ovf, ws.stamp};
   int phase = 0;
   for (;; ++phase) {
     if (phase >= max_phases) {
@@ -549,7 +593,7 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
     if (blk == 0 && threadIdx.x == 0) atomicExch(&h->help_open, 1);   // the queue is seeded
 
     // ---- task loop ----
-    task_loop<D, SCALED>(a, wq, my_pushes, my_edges, my_rows, my_items, my_wait);
+    task_loop<D, SCALED>(a, wq, st_w);
     if (timer) time_mark(s_t, 1);
     if (!grid_barrier(&h->bar, h, nblocks)) return;   // every warp has left the task loop
     if (blk == 0 && threadIdx.x == 0) atomicExch(&h->help_open, 0);   // no task is left to help with
@@ -602,18 +646,17 @@ __device__ __forceinline__ void push_body(const PushArgs& a, int n, int check_al
   if (timer)
     for (int i = 0; i < 3; ++i) h->push_ns[i] += s_t[i];
   // counters and bookkeeping (block 0 after the last barrier; everyone has left the loop)
-  for (int o = 16; o > 0; o >>= 1) {
-    my_pushes += __shfl_xor_sync(kFull, my_pushes, o);
-    my_edges += __shfl_xor_sync(kFull, my_edges, o);
-  }
-  if (lane == 0 && (my_pushes || my_edges)) {
-    atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)my_pushes);
-    atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)my_edges);
-  }
-  if (lane == 0 && my_wait) atomicAdd(&h->push_ns[3], my_wait / (unsigned long long)nwarps);
-  if (lane == 0 && (my_rows || my_items)) {
-    atomicAdd((unsigned long long*)&h->push_tasks, (unsigned long long)my_rows);
-    atomicAdd((unsigned long long*)&h->push_items, (unsigned long long)my_items);
+  if (lane == 0) {
+    const WarpStats w = st_w;
+    if (w.pushes || w.edges) {
+      atomicAdd((unsigned long long*)&h->pushes, (unsigned long long)w.pushes);
+      atomicAdd((unsigned long long*)&h->push_edges, (unsigned long long)w.edges);
+    }
+    if (w.wait) atomicAdd(&h->push_ns[3], w.wait / (unsigned long long)nwarps);
+    if (w.rows || w.items) {
+      atomicAdd((unsigned long long*)&h->push_tasks, (unsigned long long)w.rows);
+      atomicAdd((unsigned long long*)&h->push_items, (unsigned long long)w.items);
+    }
   }
   if (blk == 0 && threadIdx.x == 0) {
     h->push_rounds += phase;
@@ -629,7 +672,9 @@ template <int D, bool SCALED>
 __global__ void __launch_bounds__(256, 4) k_push(PushArgs a, int n, int check_all) {
   __shared__ unsigned long long s_t[5];
   __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
-  push_body<D, SCALED>(a, n, check_all, blockIdx.x, gridDim.x, s_t, s_buf);
+  __shared__ __align__(16) float s_rho[8][kMaxD];
+  __shared__ WarpStats s_ws[8];
+  push_body<D, SCALED>(a, n, check_all, blockIdx.x, gridDim.x, s_t, s_buf, s_rho, s_ws);
 }
 
 // Zeroes the work-queue words of every graph of a grouped push (one thread per graph).
@@ -655,7 +700,8 @@ constexpr int kHelpRounds = 256;    // graphs one warp may help in turn
 // then checks the gate, so that a graph that closes its gate and then finds helpers == 0 has no
 // warp of another graph left in its loop; its tasks' counters go to that graph's header.
 template <bool SCALED>
-__device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, int ngraphs, int32_t* buf) {
+__device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, int ngraphs, int32_t* buf,
+                                            float* rho, WarpStats& st_w) {
   const int lane = threadIdx.x & 31;
   for (int round = 0; round < kHelpRounds; ++round) {
     unsigned best = 0;
@@ -688,24 +734,23 @@ __device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, 
       if (!ok) atomicSub(&a.h->helpers, 1);
     }
     if (!__shfl_sync(kFull, ok, 0)) continue;
-    WarpQ wq{buf, 0, 0, a.ws.ovf, a.ws.stamp};
-    long long pushes = 0, edges = 0;
-    int rows = 0, items = 0;
-    unsigned long long wait = 0;
+    WarpQ wq{buf, rho, 0, 0, a.ws.ovf, a.ws.stamp};
+    if (lane == 0) st_w = WarpStats{0, 0, 0ull, 0, 0};
     switch (a.d) {
-      case 16: task_loop<16, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
-      case 32: task_loop<32, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
-      case 64: task_loop<64, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
-      default: task_loop<128, SCALED>(a, wq, pushes, edges, rows, items, wait); break;
+      case 16: task_loop<16, SCALED>(a, wq, st_w); break;
+      case 32: task_loop<32, SCALED>(a, wq, st_w); break;
+      case 64: task_loop<64, SCALED>(a, wq, st_w); break;
+      default: task_loop<128, SCALED>(a, wq, st_w); break;
     }
     if (lane == 0) {
-      if (pushes || edges) {
-        atomicAdd((unsigned long long*)&a.h->pushes, (unsigned long long)pushes);
-        atomicAdd((unsigned long long*)&a.h->push_edges, (unsigned long long)edges);
+      const WarpStats w = st_w;
+      if (w.pushes || w.edges) {
+        atomicAdd((unsigned long long*)&a.h->pushes, (unsigned long long)w.pushes);
+        atomicAdd((unsigned long long*)&a.h->push_edges, (unsigned long long)w.edges);
       }
-      if (rows || items) {
-        atomicAdd((unsigned long long*)&a.h->push_tasks, (unsigned long long)rows);
-        atomicAdd((unsigned long long*)&a.h->push_items, (unsigned long long)items);
+      if (w.rows || w.items) {
+        atomicAdd((unsigned long long*)&a.h->push_tasks, (unsigned long long)w.rows);
+        atomicAdd((unsigned long long*)&a.h->push_items, (unsigned long long)w.items);
       }
       __threadfence();
       atomicSub(&a.h->helpers, 1);
@@ -727,6 +772,8 @@ __global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restric
   __shared__ int s_s, s_n, s_all;
   __shared__ unsigned long long s_t[5];
   __shared__ int32_t s_buf[8][kQBuf];   // 256 threads: 8 warps
+  __shared__ __align__(16) float s_rho[8][kMaxD];
+  __shared__ WarpStats s_ws[8];
   // a launch captured under an earlier plan of the fleet must not run on this plan's tables:
   // every CTA returns before any barrier and the graphs' status reports it
   if (table[0] != nslots || table[1] != (int)gridDim.x || table[2] != plan) {
@@ -764,14 +811,14 @@ __global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restric
     }
     __syncthreads();
     switch (sa.d) {
-      case 16: push_body<16, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
-      case 32: push_body<32, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
-      case 64: push_body<64, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
-      default: push_body<128, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf); break;
+      case 16: push_body<16, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf, s_rho, s_ws); break;
+      case 32: push_body<32, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf, s_rho, s_ws); break;
+      case 64: push_body<64, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf, s_rho, s_ws); break;
+      default: push_body<128, SCALED>(sa, s_n, s_all, blk, nb, s_t, s_buf, s_rho, s_ws); break;
     }
   }
   // this CTA's graphs are pushed: its warps help the graphs still running
-  help_others<SCALED>(descs, gfirst[nslots], s_buf[threadIdx.x >> 5]);
+  help_others<SCALED>(descs, gfirst[nslots], s_buf[threadIdx.x >> 5], s_rho[threadIdx.x >> 5], s_ws[threadIdx.x >> 5]);
 }
 
 PushArgs push_args(const Ctx* c, int direct_chunks) {
@@ -840,8 +887,10 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
   // a cooperative grid must fit on the device at once
   const int blocks = c->push_blocks > 0 ? (c->push_blocks < c->push_occ ? c->push_blocks : c->push_occ) : c->push_max;
   const int chunks = c->push_direct_chunks;
-  // qstate, q_head, overflow, rho_tail, item_tail, ovf_count, help_open, helpers
-  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, sizeof(unsigned long long) + 7 * sizeof(int), s);
+  // qstate .. helpers (the queue words, on their own cache lines, and the padding between them)
+  static_assert(offsetof(DevHeader, helpers) > offsetof(DevHeader, qstate), "queue words in header order");
+  const size_t qbytes = offsetof(DevHeader, helpers) + sizeof(int) - offsetof(DevHeader, qstate);
+  cudaError_t e = cudaMemsetAsync(&c->hdr->qstate, 0, qbytes, s);
   if (e != cudaSuccess) return e;
   PushArgs a = push_args(c, chunks);
   int n = c->n;
