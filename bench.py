@@ -935,6 +935,7 @@ def run_fleet(args, fw, rank, world):
         "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": G * KMAX * 9 + 4 * G, "d2h_bytes_per_step": G * 128 * 4, "steps": E},
         "gpu_launches": int(launches),
+        "kernel_nodes_per_captured_step": int(cg.kernels),
         "gpu_launches_note": "kernels per captured step (counted while capturing) x timed steps",
         "roofline": {"bound": "hbm", "kernel": "k_push_group", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,

@@ -2,10 +2,44 @@
 // Gram matrices, Cholesky with triangular inverse, and the adjacency SpMM.  Used by the
 // randomized t-SVD initialisation (Appendix A, Algorithm 3; Halko et al.), the query
 // (Sec. 4.6) and the periodic fold of the transforms into the bases.
+#include <cudaTypedefs.h>
+
 #include "damf_internal.cuh"
 #include "tc_gemm.cuh"
 
 namespace damf {
+
+// cuTensorMapEncodeTiled from the driver (the library links only the runtime), or null.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The 4-D view of A (n x K, row-major, lda floats per row) that k_gemm_tc_tma loads from:
+// [n / 8 row groups][K / 4 column groups][8 rows][4 floats], strides 8 lda, 16 bytes and lda
+// floats, box 16 x 4 x 8 x 4 = one 128-row by 16-column chunk in the MMA's canonical layout.
+// False when A does not meet the tensor map's alignment rules or the encoder is missing.
+static bool gemm_tensor_map(CUtensorMap* m, const float* A, int lda, long long n, int K) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || n < 8 || (reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda & 3) != 0 || K % tc::kTmaChunk != 0)
+    return false;
+  const cuuint64_t dims[4] = {4, 8, (cuuint64_t)(K / 4), (cuuint64_t)(n / 8)};
+  const cuuint64_t strides[3] = {(cuuint64_t)lda * 4, 16, (cuuint64_t)lda * 4 * 8};
+  const cuuint32_t box[4] = {4, 8, (cuuint32_t)(tc::kTmaChunk / 4), (cuuint32_t)(tc::kTileM / 8)};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(A), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // C[n x N] = A[n x K] B[K x N]; 64-row tiles, 16 x 16 threads, each a 4 x (N/16) micro-tile.
 // Optional per-column scalings: A's column k by ascale[k] (before), C's column j by cscale[j].
@@ -76,6 +110,21 @@ static cudaError_t gemm_tall_kn(const float* A, int lda, long long n, const floa
 template <int K, int N>
 static cudaError_t gemm_tc_kn(const float* A, int lda, long long n, const float* B, float* C, int ldc,
                               const float* as, const float* cs, int* err, cudaStream_t s) {
+  if constexpr (tc::tma_stages<K, N>() >= 2) {
+    // TMA-fed kernel: B split once per CTA, A chunks copied by the tensor-memory accelerator
+    CUtensorMap m;
+    if (gemm_tensor_map(&m, A, lda, n, K)) {
+      const size_t smt = tc::tma_smem_bytes<K, N>();
+      cudaFuncSetAttribute(tc::k_gemm_tc_tma<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const long long tiles = (n + tc::kTileM - 1) / tc::kTileM;
+      const int grid = (int)(tiles < sms ? tiles : sms);
+      tc::k_gemm_tc_tma<K, N><<<grid, tc::kThreads, smt, s>>>(m, A, lda, n, B, C, ldc, as, cs, err);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (tc::pipe_smem_bytes<K, N>() <= 227 * 1024) {
     // the pipelined kernel: B split once per CTA, two A stages, one CTA per SM
     const size_t smp = tc::pipe_smem_bytes<K, N>();
