@@ -19,6 +19,8 @@ Other workloads (not the default line):
   --config C5 [--rates a,b,c]     serving: sessions admitted by device memory, Poisson requests
                                   in phases of rising rate, continuous batching of fleet steps
   --mode node-stream              the paper's node-arrival protocol, ms per node event
+  --mode init-scale               the randomized t-SVD initialisation at the serving workload's
+                                  stated size (n = 50M, m = 1B, directed), then update requests
 """
 
 import argparse
@@ -960,6 +962,194 @@ def run_fleet(args, fw, rank, world):
     return out
 
 
+def gpu_chung_lu_directed(n, m, gamma, seed):
+    """A directed Chung-Lu graph generated on the device (torch), for sizes whose host
+    generation would take tens of minutes: node i has expected out- and in-degree proportional
+    to (i + 1)^(-1 / (gamma - 1)) (in-weights on a seeded random permutation of the nodes),
+    m distinct edges without self-loops (endpoint pairs drawn by inverse-CDF sampling, then
+    deduplicated and, if more than m remain, a seeded uniform subset of m kept). Returns the
+    CSR (row_ptr int32[n + 1], col int32[m]) on the device, rows sorted."""
+    import torch
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    w = torch.arange(1, n + 1, device=dev, dtype=torch.float64).pow_(-1.0 / (gamma - 1.0))
+    cdf = torch.cumsum(w, 0)
+    cdf /= cdf[-1].clone()
+    del w
+    perm = torch.randperm(n, device=dev, generator=gen)
+    keys = []
+    drawn = int(m * 1.10)
+    chunk = 1 << 27
+    for lo in range(0, drawn, chunk):
+        k = min(chunk, drawn - lo)
+        u = torch.searchsorted(cdf, torch.rand(k, device=dev, dtype=torch.float64, generator=gen))
+        iv = torch.searchsorted(cdf, torch.rand(k, device=dev, dtype=torch.float64, generator=gen))
+        v = perm[iv.clamp_(max=n - 1)]
+        del iv
+        u.clamp_(max=n - 1)
+        keep = u != v
+        keys.append(u[keep] * n + v[keep])
+        del u, v, keep
+    del cdf, perm
+    keys = torch.cat(keys)
+    keys, _ = torch.sort(keys)
+    keys = torch.unique_consecutive(keys)
+    if keys.numel() > m:
+        pick = torch.randperm(keys.numel(), device=dev, generator=gen)[:m]
+        pick, _ = torch.sort(pick)
+        keys = keys[pick]
+        del pick
+    rows = keys // n
+    col = (keys - rows * n).to(torch.int32)
+    del keys
+    counts = torch.bincount(rows, minlength=n)
+    del rows
+    row_ptr = torch.zeros(n + 1, device=dev, dtype=torch.int64)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    del counts
+    torch.cuda.empty_cache()
+    return row_ptr.to(torch.int32), col
+
+
+def run_init_scale(args):
+    """The randomized t-SVD initialisation (Algorithm 3) at the serving workload's stated size
+    (one directed Chung-Lu graph of --nodes nodes and --edges edges, d = 128), then a short
+    stream of update requests of 1-1024 events (10% deletions of present edges) on that graph,
+    each followed by its push. The graph and the Gaussian test matrix are drawn on the device
+    (seeded). Too large for the FP64 oracle (its initialisation's parity is pinned at small n
+    by the GPU tests), so the factors are checked by properties that hold at any size: the
+    orthonormality of U and V and the relative residuals |A v_i - sigma_i u_i| / sigma_i of
+    the leading singular triplets (A the out-adjacency, FP32 sparse products)."""
+    import torch
+    from paper_2306_08967_gb300 import DamfGraph, bytes_required, make_config, rsvd_width
+    dev = torch.device("cuda")
+    n, m, d = int(args.nodes), int(args.edges), 128
+    t0 = time.perf_counter()
+    row_ptr, col = gpu_chung_lu_directed(n, m, args.gamma, args.seed)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    m_real = int(col.numel())
+    extra = 64
+    cfg = make_config(n, d, 0.15, 1e-5, n_capacity=n + extra, nnz=m_real,
+                      m_capacity=int(1.15 * m_real) + 8 * (n + extra), directed=True, refold_every=256,
+                      precision=args.precision)
+    need = bytes_required(cfg)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed + 2)
+    om = torch.randn((n, rsvd_width(cfg)), device=dev, dtype=torch.float32, generator=gen)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0, total = torch.cuda.mem_get_info()
+    t1 = time.perf_counter()
+    g = DamfGraph(row_ptr, col, cfg, om)
+    g.check()
+    init_s = time.perf_counter() - t1
+    del om
+    torch.cuda.empty_cache()
+    free1, _ = torch.cuda.mem_get_info()
+    st0 = g.stats()
+    # properties of the initial factors
+    e = g.embeddings(want=("X", "Y", "sigma"))
+    sig = e["sigma"].double()
+    rs = torch.rsqrt(e["sigma"].clamp_min(1e-30))
+    GU = torch.zeros((d, d), dtype=torch.float64, device=dev)
+    GV = torch.zeros((d, d), dtype=torch.float64, device=dev)
+    step = 1 << 22
+    for lo in range(0, n, step):
+        Uc = (e["X"][lo:lo + step] * rs).double()
+        Vc = (e["Y"][lo:lo + step] * rs).double()
+        GU += Uc.T @ Uc
+        GV += Vc.T @ Vc
+        del Uc, Vc
+    eye = torch.eye(d, dtype=torch.float64, device=dev)
+    orth = (float((GU - eye).abs().max()), float((GV - eye).abs().max()))
+    k = 8
+    A = torch.sparse_csr_tensor(row_ptr, col, torch.ones(m_real, device=dev, dtype=torch.float32), size=(n, n))
+    Vk = (e["Y"][:, :k] * rs[:k]).contiguous()
+    AV = A @ Vk
+    Uk = e["X"][:, :k] * rs[:k]
+    res = [float(torch.linalg.vector_norm((AV[:, i] - e["sigma"][i] * Uk[:, i]).double()) / sig[i]) for i in range(k)]
+    av_norm = [float(torch.linalg.vector_norm(AV[:, i].double())) for i in range(k)]
+    del A, Vk, AV, Uk, e
+    torch.cuda.empty_cache()
+    # a stream of update requests on the big graph: U[1, 1024] events, 10% deletions of present
+    # edges, insertions with endpoints drawn by the generator's weight law (host, seeded)
+    rng = np.random.default_rng(args.seed + 3)
+    w = np.arange(1, n + 1, dtype=np.float64) ** (-1.0 / (args.gamma - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    del w
+    K, W = int(args.steps), int(args.warmup)
+    reqs = []
+    rp64 = row_ptr.long()
+    for _ in range(K + W):
+        kk = int(rng.integers(1, 1025))
+        nd = int(rng.binomial(kk, 0.10))
+        ni = kk - nd
+        su = np.minimum(np.searchsorted(cdf, rng.random(ni)), n - 1)
+        sv = np.minimum(np.searchsorted(cdf, rng.random(ni)), n - 1)
+        sv = np.where(sv == su, (sv + 1) % n, sv)
+        pos = torch.from_numpy(rng.integers(0, m_real, nd)).to(dev)
+        du = (torch.searchsorted(rp64, pos, right=True) - 1).cpu().numpy()
+        dv = col[pos].long().cpu().numpy()
+        src = np.concatenate([su, du]).astype(np.int32)
+        dst = np.concatenate([sv, dv]).astype(np.int32)
+        op = np.concatenate([np.ones(ni, np.int8), -np.ones(nd, np.int8)])
+        reqs.append((src, dst, op))
+    del cdf, rp64
+    stream = torch.cuda.current_stream()
+    for i in range(W):
+        g.apply_edges(*reqs[i])
+        g.ppr_refresh()
+    g.check()
+    s1 = g.stats()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for e1 in ev1:
+        e1.record(stream)   # creates the events the library records into
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        for j in range(K):
+            ev0[j].record(stream)
+            g.apply_edges(*reqs[W + j])
+            g.ppr_refresh()
+            g.record_event(ev1[j])
+        torch.cuda.synchronize()
+    g.check()
+    s2 = g.stats()
+    lat = np.array([ev0[j].elapsed_time(ev1[j]) for j in range(K)])
+    total_ms = float(ev0[0].elapsed_time(ev1[K - 1]))
+    edges = int(sum(len(r[0]) for r in reqs[W:]))
+    out = {"metric": "randomized t-SVD initialisation time at the serving workload's size, then update latency",
+           "value": init_s, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f32",
+           "data": "synthetic (directed Chung-Lu graph and Gaussian test matrix drawn on the device, seeded)",
+           "config": {"workload": "directed Chung-Lu gamma=%.1f n=%d m=%d (requested %d); d=128 alpha=0.15 "
+                                  "eps=1e-5; %d randomized t-SVD power passes" % (args.gamma, n, m_real, m,
+                                                                                  cfg.rsvd_power_iters),
+                      "precision": args.precision},
+           "generate_s": gen_s, "init_s": init_s,
+           "init_pushes": int(st0["pushes"]), "init_push_edges": int(st0["push_edges"]),
+           "device_bytes_required": int(need), "device_bytes_used_by_context": int(free0 - free1),
+           "device_total_bytes": int(total),
+           "checks": {"U_orth_max": orth[0], "V_orth_max": orth[1],
+                      "sigma_top": [float(x) for x in sig[:k].tolist()],
+                      "residual_rel_top": res, "norm_Av_top": av_norm,
+                      "note": "|A v_i - sigma_i u_i| / sigma_i for the leading singular triplets (A the "
+                              "out-adjacency, FP32 sparse product) and max |U^T U - I|, |V^T V - I| (FP64 "
+                              "sums); the initialisation's parity with the FP64 oracle is pinned at small n "
+                              "by tests/test_gpu_parity.py::test_init_matches_oracle"},
+           "updates": {"requests": K, "warmup": W, "edges": edges, "edge_updates_per_s": edges / (total_ms / 1e3),
+                       "ms_per_request": total_ms / K,
+                       "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                       "updates": int(s2["updates"] - s1["updates"]), "pushes": int(s2["pushes"] - s1["pushes"]),
+                       "definition": "requests of U[1, 1024] events back to back on one stream; latency from an "
+                                     "event before the apply to an event after the push"},
+           "clocks": clk.summary()}
+    g.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1005,10 +1195,17 @@ def main():
                     "may be evicted")
     ap.add_argument("--no-evict", dest="evict", action="store_false",
                     help="C5: sessions wait for memory instead of evicting idle graphs to host memory")
-    ap.add_argument("--mode", default="batches", choices=["batches", "node-stream"],
+    ap.add_argument("--nodes", type=int, default=50_000_000, help="init-scale: nodes of the generated graph")
+    ap.add_argument("--edges", type=int, default=1_000_000_000, help="init-scale: edges of the generated graph")
+    ap.add_argument("--gamma", type=float, default=2.2, help="init-scale: power-law exponent")
+    ap.add_argument("--seed", type=int, default=0xDA3F0500, help="init-scale: generator seed")
+    ap.add_argument("--mode", default="batches", choices=["batches", "node-stream", "init-scale"],
                     help="node-stream: ms per node event under the paper's node-arrival protocol")
     args = ap.parse_args()
     from synth import CONFIGS, FLEETS, SERVING
+    if args.mode == "init-scale":
+        print(json.dumps(run_init_scale(args)))
+        return
     if args.config in SERVING:
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
         print(json.dumps(run_serving(args, SERVING[args.config])))
