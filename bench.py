@@ -341,9 +341,10 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one k_push launch of the C2 workload, from the ncu capture
-# summarised in profiles/k_push_C2.md; None once k_push changes until it is captured again
-PUSH_DRAM_BYTES = 482.82e6
+# DRAM bytes (read + write) per k_push launch by workload, from the ncu capture summarised in
+# profiles/k_push_<workload>.md; a workload is left out once k_push changes until it is
+# captured again
+PUSH_DRAM_BYTES = {}
 
 # ---------------------------------------------------------------- ranks
 def reduce_over_ranks(elapsed_ms, edges, world):
@@ -595,9 +596,9 @@ def run_ours(args, c, rank, world):
     push_ms_per = stage_ms["push"] / max(push_launches, 1)
     achieved = (push_bytes / max(push_launches, 1)) / (push_ms_per * 1e-3) / 1e9 if push_launches else 0.0
     roof = {"bound": "hbm", "kernel": "k_push", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": PUSH_DRAM_BYTES if c.name == "C2" else None,
-            "traffic_note": "dram read + write of one captured launch of the current k_push (ncu, "
-                            "profiles/k_push_C2.md); most of the algorithmic bytes are L2 atomics",
+            "frac": round(achieved / hbm_peak, 4), "traffic": PUSH_DRAM_BYTES.get(c.name),
+            "traffic_note": "dram read + write per launch of the current k_push from an ncu capture "
+                            "(profiles/k_push_%s.md), null when none was taken of it" % c.name,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_launch": push_bytes / max(push_launches, 1), "ms_per_launch": push_ms_per}
     launches = s1["launches"] - s0["launches"]

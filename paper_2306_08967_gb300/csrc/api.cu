@@ -12,7 +12,6 @@
 #include "damf_internal.cuh"
 
 namespace damf {
-cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, cudaStream_t s);
 cudaError_t chol_inv_upper2(const float* G, int K, float* R, float* Rinv, DevHeader* h, cudaStream_t s);
 cudaError_t small_mm(const float* A, const float* B, float* C, int K, cudaStream_t s);
 cudaError_t gemm_tall_scaled(const float* A, int lda, long long n, const float* B, int K, int N, float* C, int ldc,
@@ -293,6 +292,8 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
   cudaError_t e;
   const Adj& out = c->out;
   const Adj& in = c->cfg.directed ? c->in : c->out;
+  SpmmPlan pout, pin_;   // long rows of the out- and (directed) in-adjacency
+  const SpmmPlan* pin = c->cfg.directed ? &pin_ : &pout;
   const size_t ll = (size_t)l * l * sizeof(float);
   if ((e = cudaMalloc(&Y, nl)) != cudaSuccess) goto done;
   if ((e = cudaMalloc(&Q, nl)) != cudaSuccess) goto done;
@@ -302,6 +303,8 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
   if ((e = cudaMalloc(&Ri, ll)) != cudaSuccess) goto done;
   if ((e = cudaMalloc(&R2, ll)) != cudaSuccess) goto done;
   if ((e = cudaMalloc(&Rt, ll)) != cudaSuccess) goto done;
+  if ((e = spmm_plan(out, n, l, &pout, s)) != cudaSuccess) goto done;
+  if (c->cfg.directed && (e = spmm_plan(in, n, l, &pin_, s)) != cudaSuccess) goto done;
   {
     // orth(X) in place into dst with its triangular factor accumulated in Racc (optional)
     auto orth = [&](const float* X, float* dst, float* Racc) -> cudaError_t {
@@ -317,15 +320,15 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
       }
       return cudaSuccess;
     };
-    if ((e = spmm(out, n, omega, l, Y, s)) != cudaSuccess) goto done;
+    if ((e = spmm(out, n, omega, l, Y, &pout, s)) != cudaSuccess) goto done;
     if ((e = orth(Y, Q, nullptr)) != cudaSuccess) goto done;
     for (int it = 0; it < c->cfg.rsvd_power_iters; ++it) {
-      if ((e = spmm(in, n, Q, l, Y, s)) != cudaSuccess) goto done;
+      if ((e = spmm(in, n, Q, l, Y, pin, s)) != cudaSuccess) goto done;
       if ((e = orth(Y, Q2, nullptr)) != cudaSuccess) goto done;
-      if ((e = spmm(out, n, Q2, l, Y, s)) != cudaSuccess) goto done;
+      if ((e = spmm(out, n, Q2, l, Y, &pout, s)) != cudaSuccess) goto done;
       if ((e = orth(Y, Q, nullptr)) != cudaSuccess) goto done;
     }
-    if ((e = spmm(in, n, Q, l, Y, s)) != cudaSuccess) goto done;  // Bt = A^T Q
+    if ((e = spmm(in, n, Q, l, Y, pin, s)) != cudaSuccess) goto done;  // Bt = A^T Q
     if ((e = orth(Y, Q2, R2)) != cudaSuccess) goto done;         // Bt = Q2 R2
     // R2 row-major == (R2^T) column-major: the Jacobi input is R2^T
     if ((e = jacobi_svd_dense(R2, l, d, c->ws.E, c->ws.H, c->ws.theta, 0, c->hdr, s)) != cudaSuccess) goto done;
@@ -341,6 +344,8 @@ cudaError_t init_factorize(Ctx* c, const int32_t*, const int32_t*, int64_t, cons
   }
 done:
   cudaStreamSynchronize(s);
+  spmm_plan_free(&pout);
+  spmm_plan_free(&pin_);
   cudaFree(Y);
   cudaFree(Q);
   cudaFree(Q2);

@@ -79,6 +79,18 @@ struct Adj {
   long long m_cap;
 };
 
+// The long rows of an adjacency cut into chunks for the initialisation's SpMM (dense.cu).
+struct SpmmPlan {
+  int nlong = 0, nchunks = 0;
+  int* rows = nullptr;      // [nlong] long rows, increasing
+  int* first = nullptr;     // [nlong + 1] chunks of row i: first[i] .. first[i + 1] - 1
+  int2* chunks = nullptr;   // [nchunks] (first entry, entry count)
+  float* P = nullptr;       // [nchunks x l] partial sums
+};
+cudaError_t spmm_plan(const Adj& a, int n, int l, SpmmPlan* p, cudaStream_t s);
+void spmm_plan_free(SpmmPlan* p);
+cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, const SpmmPlan* plan, cudaStream_t s);
+
 struct Workspace {
   int32_t* S;        // [kMaxR]
   int32_t* T;        // [kMaxR]

@@ -4,6 +4,9 @@
 // (Sec. 4.6) and the periodic fold of the transforms into the bases.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "damf_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -320,13 +323,22 @@ cudaError_t chol_inv_upper(const float* G, int K, float* Rinv, DevHeader* h, cud
   return chol_inv_upper2(G, K, nullptr, Rinv, h, s);
 }
 
-// Y[u] = sum_{v in row u} X[v] over an adjacency (warp per row, float4 columns).
+// Y[u] = sum_{v in row u} X[v] over an adjacency (the randomized t-SVD's products A Omega,
+// A^T Q, A Q'). A row of at most kSpmmLong entries is one warp's (float4 columns, the sum in
+// entry order). Longer rows (the hubs of a power-law graph hold millions of entries, and one
+// warp per row left a launch waiting seconds on its largest row, its FP32 sum drifting over
+// millions of terms) are cut into chunks of kSpmmLong entries, one warp each, whose partial
+// sums are then added per row in chunk order: the result is deterministic and each row's sum
+// is a sum of short sums.
+constexpr int kSpmmLong = 1024;
+
 __global__ void k_spmm(Adj a, int n, const float* __restrict__ X, int l, float* Y) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= n) return;
   const int u = (int)wid;
   const int st = a.start[u], ln = a.len[u];
+  if (ln > kSpmmLong) return;   // the chunked pass
   const int nq = l / 4;
   for (int c = lane; c < nq; c += 32) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -339,9 +351,144 @@ __global__ void k_spmm(Adj a, int n, const float* __restrict__ X, int l, float* 
   }
 }
 
-cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, cudaStream_t s) {
+// rows longer than kSpmmLong, appended in any order (the plan sorts them)
+__global__ void k_spmm_long_rows(const int32_t* __restrict__ len, int n, int* count, int* rows, int cap) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n || len[u] <= kSpmmLong) return;
+  const int i = atomicAdd(count, 1);
+  if (i < cap) rows[i] = u;
+}
+
+// chunk k = (first entry, entry count) of a long row: its partial sum into P[k]
+__global__ void k_spmm_chunks(const int32_t* __restrict__ col, const int2* __restrict__ chunks, int nchunks,
+                              const float* __restrict__ X, int l, float* P) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= nchunks) return;
+  const int2 ch = chunks[wid];
+  const int nq = l / 4;
+  for (int c = lane; c < nq; c += 32) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < ch.y; ++j) {
+      const int v = __ldg(col + ch.x + j);
+      const float4 x = __ldg(reinterpret_cast<const float4*>(X + (size_t)v * l) + c);
+      acc.x += x.x, acc.y += x.y, acc.z += x.z, acc.w += x.w;
+    }
+    reinterpret_cast<float4*>(P + (size_t)wid * l)[c] = acc;
+  }
+}
+
+// long row i (rows[i]) = the sum of its chunks first[i] .. first[i + 1] - 1, in order
+__global__ void k_spmm_reduce(const int* __restrict__ rows, const int* __restrict__ first, int nlong,
+                              const float* __restrict__ P, int l, float* Y) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= nlong) return;
+  const int u = rows[wid], k0 = first[wid], k1 = first[wid + 1];
+  const int nq = l / 4;
+  for (int c = lane; c < nq; c += 32) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = k0; k < k1; ++k) {
+      const float4 x = reinterpret_cast<const float4*>(P + (size_t)k * l)[c];
+      acc.x += x.x, acc.y += x.y, acc.z += x.z, acc.w += x.w;
+    }
+    reinterpret_cast<float4*>(Y + (size_t)u * l)[c] = acc;
+  }
+}
+
+__global__ void k_spmm_gather_rows(const int* __restrict__ rows, int nlong, const int32_t* __restrict__ start,
+                                   const int32_t* __restrict__ len, int2* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nlong) out[i] = make_int2(start[rows[i]], len[rows[i]]);
+}
+
+void spmm_plan_free(SpmmPlan* p) {
+  cudaFree(p->rows);
+  cudaFree(p->first);
+  cudaFree(p->chunks);
+  cudaFree(p->P);
+  *p = SpmmPlan{};
+}
+
+// The chunks of an adjacency's long rows (setup path: synchronises `s`). Rows in increasing
+// order, chunks in entry order, so that the sums do not depend on the order the rows were found.
+cudaError_t spmm_plan(const Adj& a, int n, int l, SpmmPlan* p, cudaStream_t s) {
+  *p = SpmmPlan{};
+  if (n <= 0) return cudaSuccess;
+  const long long capl = a.m_cap / kSpmmLong + 1;
+  const int cap = (int)(capl < n ? capl : n);
+  int* d_count = nullptr;
+  int* d_rows = nullptr;
+  int2* d_sl = nullptr;
+  int count = 0;
+  std::vector<int> rows;
+  std::vector<int2> sl;
+  std::vector<int2> chunks;
+  std::vector<int> first;
+  cudaError_t e = cudaMalloc(&d_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rows, sizeof(int) * (size_t)cap);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_spmm_long_rows<<<(n + 255) / 256, 256, 0, s>>>(a.len, n, d_count, d_rows, cap);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && count > cap) e = cudaErrorInvalidValue;   // more long rows than entries allow
+  if (e == cudaSuccess && count > 0) {
+    rows.resize(count);
+    sl.resize(count);
+    e = cudaMemcpyAsync(rows.data(), d_rows, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      std::sort(rows.begin(), rows.end());
+      e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&d_sl, sizeof(int2) * (size_t)count);
+    if (e == cudaSuccess) {
+      k_spmm_gather_rows<<<(count + 255) / 256, 256, 0, s>>>(d_rows, count, a.start, a.len, d_sl);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.data(), d_sl, sizeof(int2) * (size_t)count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      first.push_back(0);
+      for (int i = 0; i < count; ++i) {
+        for (int j = 0; j < sl[i].y; j += kSpmmLong)
+          chunks.push_back(make_int2(sl[i].x + j, sl[i].y - j < kSpmmLong ? sl[i].y - j : kSpmmLong));
+        first.push_back((int)chunks.size());
+      }
+      p->nlong = count;
+      p->nchunks = (int)chunks.size();
+      e = cudaMalloc(&p->rows, sizeof(int) * (size_t)count);
+      if (e == cudaSuccess) e = cudaMalloc(&p->first, sizeof(int) * first.size());
+      if (e == cudaSuccess) e = cudaMalloc(&p->chunks, sizeof(int2) * chunks.size());
+      if (e == cudaSuccess) e = cudaMalloc(&p->P, sizeof(float) * chunks.size() * (size_t)l);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->rows, rows.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
+  cudaFree(d_count);
+  cudaFree(d_rows);
+  cudaFree(d_sl);
+  if (e != cudaSuccess) spmm_plan_free(p);
+  return e;
+}
+
+cudaError_t spmm(const Adj& a, int n, const float* X, int l, float* Y, const SpmmPlan* plan, cudaStream_t s) {
   const long long threads = (long long)n * 32;
   k_spmm<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, n, X, l, Y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !plan || plan->nchunks == 0) return e;
+  const long long tc = (long long)plan->nchunks * 32, tr = (long long)plan->nlong * 32;
+  k_spmm_chunks<<<(unsigned)((tc + 255) / 256), 256, 0, s>>>(a.col, plan->chunks, plan->nchunks, X, l, plan->P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_spmm_reduce<<<(unsigned)((tr + 255) / 256), 256, 0, s>>>(plan->rows, plan->first, plan->nlong, plan->P, l, Y);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cub/device/device_segmented_sort.cuh>
+
 #include "damf_internal.cuh"
 
 namespace damf {
@@ -530,23 +532,37 @@ cudaError_t launch_expand_row(Ctx* c, int u, int cnt, int incoming, int32_t* src
   return cudaGetLastError();
 }
 
-// Sorts every row of the in-adjacency by source id (insertion sort, one thread per row), so
-// the in-rows do not depend on the order in which k_in_fill's atomics ran: two contexts built
-// from the same graph hold the same adjacency, and sums over in-rows round the same way.
-__global__ void k_sort_rows(const int32_t* start, const int32_t* len, int n, int32_t* col) {
+// Every row of the in-adjacency is sorted by source id, so the in-rows do not depend on the
+// order in which k_in_fill's atomics ran: two contexts built from the same graph hold the
+// same adjacency, and sums over in-rows round the same way. The rows are the segments
+// [start[u], start[u] + len[u]) of col; a segmented sort (CUB's, setup path only) handles
+// the hub rows of millions of entries that a per-row insertion sort took minutes on.
+__global__ void k_seg_end(const int32_t* __restrict__ start, const int32_t* __restrict__ len, int n, int32_t* end) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n) return;
-  int32_t* row = col + start[u];
-  const int k = len[u];
-  for (int i = 1; i < k; ++i) {
-    const int32_t x = row[i];
-    int j = i - 1;
-    while (j >= 0 && row[j] > x) {
-      row[j + 1] = row[j];
-      --j;
-    }
-    row[j + 1] = x;
+  if (u < n) end[u] = start[u] + len[u];
+}
+
+static cudaError_t sort_rows(Adj* a, int n, long long span, cudaStream_t s) {
+  if (n <= 0 || span <= 0) return cudaSuccess;
+  int32_t* end = nullptr;
+  int32_t* tmp = nullptr;
+  void* ts = nullptr;
+  size_t tb = 0;
+  cudaError_t e = cudaMalloc(&end, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) {
+    k_seg_end<<<(n + 255) / 256, 256, 0, s>>>(a->start, a->len, n, end);
+    e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = cub::DeviceSegmentedSort::SortKeys(nullptr, tb, a->col, tmp, (int)span, n, a->start, end, s);
+  if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * (size_t)span);
+  if (e == cudaSuccess) e = cudaMalloc(&ts, tb > 0 ? tb : 16);
+  if (e == cudaSuccess) e = cub::DeviceSegmentedSort::SortKeys(ts, tb, a->col, tmp, (int)span, n, a->start, end, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(a->col, tmp, sizeof(int32_t) * (size_t)span, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(end);
+  cudaFree(tmp);
+  cudaFree(ts);
+  return e;
 }
 
 __global__ void k_cap_from_len(const int32_t* len, int n, int32_t* cap) {
@@ -591,8 +607,9 @@ cudaError_t build_adjacency(Ctx* c, Adj* a, const int32_t* row_ptr, const int32_
     int32_t* fillpos = c->ws.queue;  // >= n ints of scratch, unused until the first push
     cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * (size_t)n, s);
     k_in_fill<<<wb, 256, 0, s>>>(row_ptr, col_idx, n, a->start, fillpos, a->col);
-    k_sort_rows<<<nb, 256, 0, s>>>(a->start, a->len, n, a->col);
     cudaMemsetAsync(fillpos, 0xff, sizeof(int32_t) * (size_t)n, s);   // empty queue slots again
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = sort_rows(a, n, acc, s)) != cudaSuccess) return e;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);

@@ -55,6 +55,38 @@ def test_init_matches_oracle(d, n):
 
 
 @pytest.mark.parametrize("directed", [False, True])
+def test_init_with_rows_longer_than_a_chunk_matches_oracle(directed):
+    # hub rows of 2,500, 1,800 and 2,000 entries: the initialisation's SpMM cuts rows of more than
+    # 1,024 entries into chunks whose partial sums it adds per row; against the FP64 oracle's
+    # randomized t-SVD with the same test matrix
+    from oracle.damf import DamfOracle
+    from paper_2306_08967_gb300 import DamfGraph, make_config, rsvd_width
+    from synth import gaussian_test_matrix
+    n, d = 3000, 32
+    ip, ix, _ = chung_lu_graph(n, 8.0, 2.5, seed=SEED + 520, directed=directed)
+    rows = np.repeat(np.arange(n), np.diff(ip))
+    # out-rows of nodes 0 and 7, and the in-row of node 11 (2,000 entries)
+    hub_u = np.concatenate([np.zeros(2500, np.int64), np.full(1800, 7), np.arange(100, 2100)])
+    hub_v = np.concatenate([np.arange(1, 2501), np.arange(1000, 2800), np.full(2000, 11)])
+    u = np.concatenate([rows, hub_u] + ([] if directed else [hub_v]))
+    v = np.concatenate([ix, hub_v] + ([] if directed else [hub_u]))
+    keep = u != v
+    key = np.unique(u[keep].astype(np.int64) * n + v[keep])
+    u, v = key // n, key % n
+    ip2 = np.concatenate([[0], np.cumsum(np.bincount(u, minlength=n))]).astype(np.int32)
+    ix2 = v.astype(np.int32)
+    assert np.diff(ip2).max() > 1024
+    cfg = make_config(n, d, 0.15, 1e-4, n_capacity=n + 8, nnz=len(ix2), directed=directed)
+    om = gaussian_test_matrix(n, rsvd_width(cfg), seed=SEED + 521)
+    g = DamfGraph(ip2, ix2, cfg, om)
+    orc = DamfOracle(ip2, ix2, d, 0.15, 1e-4, n_cap=n + 8, directed=directed, Omega=om, propagate=False)
+    X, Y, sg = gpu_xy(g)
+    np.testing.assert_allclose(sg, orc.sigma, rtol=1e-3)
+    assert rel_fro(X @ Y.T, orc.X() @ orc.Y().T) < 1e-3
+    g.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
 def test_each_update_equals_bruteforce_tsvd(directed):
     rng = np.random.default_rng(7)
     n, d = 400, 16
