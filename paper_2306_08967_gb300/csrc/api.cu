@@ -113,9 +113,11 @@ long long qcap_of(const damf_config* cfg) {
   return q > 0x7fffff00ll ? 0x7fffff00ll : q;
 }
 
+// CTAs (and FP32 partial Grams) of a tall Gram: about 2,048 rows each, at most 8,192 (a part's
+// FP32 sum then spans <= 6,200 rows at n = 50M; the parts are added in FP64)
 int gram_parts_of(const damf_config* cfg) {
   long long p = (cfg->n_capacity + 2047) / 2048;
-  if (p > 1024) p = 1024;
+  if (p > 8192) p = 8192;
   if (p < 1) p = 1;
   return (int)p;
 }
