@@ -181,7 +181,7 @@ def oracle_run(c, steps, warmup, time_budget_s, save_path=None, alt_threads=0):
         rows = np.arange(n) if n <= ERR_SAMPLE_ROWS else np.sort(
             np.random.default_rng(c.seed + 5).choice(n, ERR_SAMPLE_ROWS, replace=False))
         np.savez(save_path, X=orc.X()[rows], Y=orc.Y()[rows], Z=orc.Z()[rows], sigma=orc.sigma, rows=rows, n=n,
-                 batches=warmup + len(lat), power_iters=oracle_power_iters(c), propagated=not oracle_big(c),
+                 batches=warmup + len(lat) + len(alt_lat), power_iters=oracle_power_iters(c), propagated=not oracle_big(c),
                  pushes=orc.pushes - pushes0)
     threads = ("1 thread" if ORACLE_THREADS == 1 else
                "%d BLAS threads (its push, in C, on one)" % ORACLE_THREADS)

@@ -71,7 +71,25 @@ def test_cpu_baseline_leg_runs_the_oracle_in_a_subprocess(tmp_path):
     assert "error" not in r, r
     assert r["kind"] == "oracle" and r["cores"] == bench.ORACLE_THREADS and r["value"] > 0 and r["batches"] >= 1
     z = np.load(state)
-    assert int(z["batches"]) == 2 + r["batches"] and z["X"].shape[1] == CONFIGS["C1"].d
+    alt = r.get("alt_threads", {}).get("batches") or 0
+    assert int(z["batches"]) == 2 + r["batches"] + alt and z["X"].shape[1] == CONFIGS["C1"].d
+
+
+def test_cpu_baseline_with_two_thread_counts_saves_every_batch_it_ran(tmp_path):
+    # batches alternate between the thread counts; the saved state (which the GPU replays for the
+    # error comparison) must count the batches of both
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import pytest
+    import bench
+    from synth import CONFIGS
+    if bench.ORACLE_THREADS < 2 or bench._blas_thread_setter() is None:
+        pytest.skip("needs two BLAS thread counts")
+    state = str(tmp_path / "oracle_state.npz")
+    r = bench.oracle_run(CONFIGS["C1"], 6, 2, 30.0, state, alt_threads=1)
+    assert r["alt_threads"]["cores"] == 1 and r["alt_threads"]["batches"] >= 1
+    z = np.load(state)
+    assert int(z["batches"]) == 2 + r["batches"] + r["alt_threads"]["batches"] == 8
 
 
 def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
