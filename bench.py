@@ -344,7 +344,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per k_push launch by workload, from the ncu capture summarised in
 # profiles/k_push_<workload>.md; a workload is left out once k_push changes until it is
 # captured again
-PUSH_DRAM_BYTES = {}
+PUSH_DRAM_BYTES = {"C3": 4.226e9}   # mean of the 20 timed launches of a 20-call C3 run (0.71-6.38 ms each)
 
 # ---------------------------------------------------------------- ranks
 def reduce_over_ranks(elapsed_ms, edges, world):
@@ -1178,7 +1178,7 @@ def main():
     ap.add_argument("--save-state", default=None)
     ap.add_argument("--log-jsonl", default=None, help="write one JSON line per timed batch (edges, latency) here; "
                     "C5: one per server step (issue and completion time, requests, edges, graphs)")
-    ap.add_argument("--push-blocks", type=int, default=0, help="push CTAs (0: two per SM)")
+    ap.add_argument("--push-blocks", type=int, default=0, help="push CTAs (0: the library's default, 2.5 per SM)")
     ap.add_argument("--push-chunks", type=int, default=-1,
                     help="in-edge chunks a row task scatters itself before its row becomes hub items (-1: 8)")
     ap.add_argument("--graphs", type=int, default=0, help="C4: the first this many graphs of the fleet (0: all)")
@@ -1277,10 +1277,11 @@ def main():
         pa = cmp[args.precision]
         cmp["speedup_mixed_over_fp32"] = (cmp["mixed"]["value"] / cmp["fp32"]["value"]) if cmp["fp32"]["value"] else None
         cmp["note"] = ("same workload and batches, fresh contexts; err = max |U^T U - I|, |V^T V - I| of the effective "
-                       "bases after the window; mixed runs the per-update projection U[S] = Ub[S] PU and the d x d "
-                       "transform products, the fold's n x d by d x d GEMMs and the initialisation on tcgen05 (TF32, "
-                       "three-term split), plain FP32 runs them on the SIMT units; errors against the FP64 oracle "
-                       "for both are under err_vs_oracle")
+                       "bases after the window; mixed runs the fold's n x d by d x d GEMMs, the initialisation and "
+                       "full-table queries on tcgen05 (TF32, three-term split), plain FP32 runs them on the SIMT "
+                       "units; the per-update chain is FP32 SIMT in both (on tcgen05 its products coupled columns "
+                       "of U at up to 3e-4 between folds); errors against the FP64 oracle for both are under "
+                       "err_vs_oracle")
         out["precision_compare"] = cmp
         # the fold's cost per step, amortised over refold_every updates, from the longer window
         if pa["folds"]:

@@ -287,7 +287,7 @@ void damf_fleet_destroy(damf_fleet* fleet);
 /* Launch shape of a context's PPR push (damf_set_tuning, damf_get_tuning). */
 typedef struct {
   int32_t push_blocks;        /* CTAs of the persistent push, 256 threads each; 0 = the most that
-                                 stay resident beside the factor chain (two per SM).  Larger
+                                 leave room for the factor chain (2.5 per SM).  Larger
                                  values (up to the push's own occupancy, four per SM) give the
                                  push more warps, but then the next update's factor chain no
                                  longer runs beside it; values above the occupancy are clamped

@@ -164,7 +164,7 @@ struct Ctx {
   Workspace ws;
   long long m_init;      // adjacency entries of the initial graph (a size hint for shares)
   int push_blocks;       // requested persistent push grid size (0: push_max)
-  int push_max;          // co-resident push CTAs on the device, at most two per SM (0: not yet known)
+  int push_max;          // default push CTAs on the device, 2.5 per SM (0: not yet known)
   int push_occ;          // co-resident push CTAs when the push takes the whole occupancy
   int push_direct_chunks;  // in-edge chunks a row task scatters itself (-1: default)
   // damf_step_multi runs this graph's update on its own stream, forked from the caller's

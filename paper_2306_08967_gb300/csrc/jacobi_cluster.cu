@@ -40,11 +40,12 @@ constexpr int kClThreads = 512;
 constexpr int kClStride = 256;                   // floats per column: rows padded with zeros
 constexpr float kClTol = 1e-6f;                  // rotate while |a_p . a_q| > tol |a_p| |a_q|
 constexpr int kClTopOnlySweeps = 6;
-// An update's core stops after a sweep whose largest relative coupling |a_p . a_q| / |a_p||a_q|
-// was below kClStopRel: the pairs it left are coupled at about its square, and the first-order
-// correction that follows (T = E^T M H) removes what remains between the top columns; on cores
-// of d = 128 streams this gave the factors of the sweeps run to the end within FP32 rounding,
-// with a third fewer sweeps.
+// An update's core stops after a sweep in which every rotation was small: relative coupling
+// |a_p . a_q| / |a_p||a_q| and rotation tangent both below kClStopRel. The pairs it left are
+// then coupled at about the product of those, and the first-order correction that follows
+// (T = E^T M H) removes what remains between the top columns. (With the coupling alone as the
+// measure, a cluster of nearly equal norms, whose pairs turn by large angles at any coupling,
+// stopped early on a C3 core and left two columns of U coupled at 1.3e-3.)
 constexpr float kClStopRel = 3e-4f;
 
 // shared memory: columns [2 buffers][2 slots][kClBsMax][kClStride], their squared norms
@@ -118,7 +119,6 @@ __device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float
   const float g = warp_sum(acc.x + acc.y);
   const float aa = *np, bb = *nq;
   if (!(g * g > tol2 * aa * bb)) return false;
-  rel2 = __fdividef(g * g, aa * bb);
   // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g): the smaller root of
   // t^2 + 2 zeta t - 1 = 0, so that the rotated columns are orthogonal. The angle may come
   // from hardware approximations (an inexact t only leaves a smaller g for the next sweep),
@@ -138,6 +138,10 @@ __device__ __forceinline__ bool cl_rotate(float* ap, float* aq, float* np, float
   const float dres = fmaf(-(tt1 * ry), ry, 1.0f);
   const float cs = fmaf(0.5f * ry, dres, ry);
   const float sn = cs * t;
+  // the stop rule's measure: the larger of the squared relative coupling and the squared
+  // rotation tangent (a pair of nearly equal norms turns by a large angle however weak its
+  // coupling, and such a turn passes couplings on to the other pairs at full size)
+  rel2 = fmaxf(__fdividef(g * g, aa * bb), t * t);
   const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ms2 = make_float2(-sn, -sn);
   {
     const float2 pl = __ffma2_rn(c2, lo2(x0), __fmul2_rn(ms2, lo2(y0)));

@@ -36,10 +36,13 @@
 
 namespace damf {
 
-// CTAs of the push per SM at most: leaves registers, threads and shared memory on every SM
-// for the one-CTA kernels of the next update's factor chain. A context's grid is this many
-// per SM unless damf_set_tuning asks for fewer (graphs that share the GPU).
-constexpr int kPushBlocksPerSM = 2;
+// CTAs of the push per SM, in halves: five halves = 2.5 per SM on average (every other SM
+// holds three), which leaves registers, threads and shared memory on at least half the SMs
+// for the next update's factor chain (an 8-CTA cluster of 512 threads at 64 registers fits
+// beside two push CTAs). Measured on C3: 304 CTAs 3.21 ms per push and 5.21 ms per call, 380
+// CTAs 2.89 and 4.91, 456 CTAs 2.70 and 5.61 (the chain waits for SMs). A context's grid is
+// this many unless damf_set_tuning asks otherwise.
+constexpr int kPushHalfBlocksPerSM = 5;
 // A row with more than this many chunks of in-edges is a hub: its chunks become item tasks
 // (per context: damf_set_tuning).
 constexpr int kPushDirectChunks = 8;
@@ -882,7 +885,7 @@ static cudaError_t push_impl(Ctx* c, int check_all, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<D, SCALED>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     c->push_occ = sms * per_sm;
-    c->push_max = sms * (per_sm > kPushBlocksPerSM ? kPushBlocksPerSM : per_sm);
+    c->push_max = 2 * per_sm > kPushHalfBlocksPerSM ? sms * kPushHalfBlocksPerSM / 2 : sms * per_sm;
   }
   // a cooperative grid must fit on the device at once
   const int blocks = c->push_blocks > 0 ? (c->push_blocks < c->push_occ ? c->push_blocks : c->push_occ) : c->push_max;

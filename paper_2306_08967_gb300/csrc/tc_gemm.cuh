@@ -246,182 +246,6 @@ constexpr size_t smem_bytes() {
 namespace damf {
 namespace tc {
 
-// Up to four small products C = A B in one launch (blockIdx.y picks the product, blockIdx.x
-// its 128-row tile): A rows taken as A + (idx ? idx[row] : row) * lda for row < rows, where
-// rows may live on the device (rows_dev, read when the kernel runs); B is K x N row-major;
-// C rows are written with stride ldc. The per-update projections U[S] = Ub[S] PU and the
-// d x d transform products of mixed precision run here (kind::tf32, three-term split as in
-// k_gemm_tc). A tile's MMAs are waited for with a bounded wait; `err` receives
-// DAMF_ERR_TIMEOUT (5) when it runs out.
-struct SmallJob {
-  const float* A;
-  const int32_t* idx;
-  const int* rows_dev;
-  int rows;
-  int lda;
-  const float* B;
-  float* C;
-  int ldc;
-};
-struct SmallJobs {
-  SmallJob j[4];
-};
-
-template <int K, int N>
-__global__ void __launch_bounds__(kThreads) k_mm_tc_small(SmallJobs jobs, const int* __restrict__ status, int* err) {
-  static_assert(K % kChunkK == 0 && N % 16 == 0 && N >= 16 && N <= 256, "shape");
-  constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-  constexpr uint32_t A_BYTES = kTileM * kChunkK * 4;
-  constexpr uint32_t B_BYTES = N * kChunkK * 4;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = a_hi + A_BYTES;
-  unsigned char* b_hi = a_lo + A_BYTES;
-  unsigned char* b_lo = b_hi + B_BYTES;
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int failed;
-  __shared__ int s_rows;
-  const SmallJob jb = jobs.j[blockIdx.y];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r0 = blockIdx.x * kTileM;
-  // one thread reads the status (another stream may set it) and the row count, so that the
-  // whole CTA takes the same branch before any allocation or barrier
-  if (tid == 0) s_rows = *reinterpret_cast<const volatile int*>(status) == 0 ? (jb.rows_dev ? *jb.rows_dev : jb.rows) : 0;
-  __syncthreads();
-  const int rows = s_rows;
-  if (r0 >= rows) return;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base)), "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
-    failed = 0;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  uint32_t phase = 0;
-  constexpr uint32_t idesc = idesc_tf32(kTileM, N);
-  const int myrow = r0 + tid;
-  const float* arow = nullptr;
-  if (myrow < rows) arow = jb.A + (size_t)(jb.idx ? jb.idx[myrow] : myrow) * jb.lda;
-  for (int kc = 0; kc < K && !failed; kc += kChunkK) {
-#pragma unroll
-    for (int q = 0; q < kChunkK / 4; ++q) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (arow) v = *reinterpret_cast<const float4*>(arow + kc + 4 * q);
-      const float4 hh = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-      const float4 ll = make_float4(v.x - hh.x, v.y - hh.y, v.z - hh.z, v.w - hh.w);
-      const uint32_t off = tile_off(tid, 4 * q);
-      *reinterpret_cast<float4*>(a_hi + off) = hh;
-      *reinterpret_cast<float4*>(a_lo + off) = ll;
-    }
-    for (int j = tid; j < N; j += kThreads) {
-#pragma unroll
-      for (int q = 0; q < kChunkK / 4; ++q) {
-        const int k = kc + 4 * q;
-        const float4 v = make_float4(jb.B[(size_t)k * N + j], jb.B[(size_t)(k + 1) * N + j],
-                                     jb.B[(size_t)(k + 2) * N + j], jb.B[(size_t)(k + 3) * N + j]);
-        const float4 hh = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-        const float4 ll = make_float4(v.x - hh.x, v.y - hh.y, v.z - hh.z, v.w - hh.w);
-        const uint32_t off = tile_off(j, 4 * q);
-        *reinterpret_cast<float4*>(b_hi + off) = hh;
-        *reinterpret_cast<float4*>(b_lo + off) = ll;
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-      for (int ks = 0; ks < kChunkK / 8; ++ks) {
-        const uint32_t koff = (uint32_t)ks * 2 * kLBO;
-        const uint64_t dah = smem_desc(smem_u32(a_hi) + koff, kLBO, kSBO);
-        const uint64_t dal = smem_desc(smem_u32(a_lo) + koff, kLBO, kSBO);
-        const uint64_t dbh = smem_desc(smem_u32(b_hi) + koff, kLBO, kSBO);
-        const uint64_t dbl = smem_desc(smem_u32(b_lo) + koff, kLBO, kSBO);
-        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            :: "r"(tmem), "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            :: "r"(tmem), "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            :: "r"(tmem), "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar)));
-    }
-    {
-      long long it = 0;
-      uint32_t done = 0;
-      while (!done) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase));
-        if (!done && ++it > kWaitLimit) {
-          failed = 1;
-          break;
-        }
-      }
-      phase ^= 1u;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-  }
-  if (!failed) {
-    const int row = r0 + warp * 32 + lane;
-#pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < rows) {
-#pragma unroll
-        for (int e = 0; e < 16; e += 4)
-          *reinterpret_cast<float4*>(jb.C + (size_t)row * jb.ldc + c0 + e) =
-              make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
-                          __uint_as_float(v[e + 3]));
-      }
-    }
-  } else {
-    // a wait ran out: wait again (bounded) for the MMAs still in flight before freeing TMEM
-    long long it = 0;
-    uint32_t done = 0;
-    while (!done && ++it <= kWaitLimit) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase ^ 1u));
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
-  if (tid == 0 && failed && err) atomicCAS(err, 0, 5);
-}
-
-}  // namespace tc
-}  // namespace damf
-
-namespace damf {
-namespace tc {
-
 // Pipelined variant of k_gemm_tc for the fold and full-table queries (K, N <= 160, 2 K N 4 B of
 // shared memory for B): the right factor B is split into hi/lo tiles once per CTA for all of K,
 // and the rows of A go through two shared-memory stages, so that the threads load and split
@@ -747,8 +571,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc_tma(const __grid_consta
            "r"((int)(t * (kTileM / 8))), "r"(smem_u32(&full[st]))
         : "memory");
   };
-  // s_fail: set (never cleared) by thread 0 when a wait ran out; every thread reads it only
-  // after a barrier that follows thread 0's last possible write, so all leave together
+  // s_fail: set (never cleared) when a wait ran out; every thread reads it only after a
+  // barrier that follows the last possible write, so all leave together
   long long issued = 0;                        // chunks whose copy was issued (thread 0)
   long long committed = 0;                     // chunks whose MMAs were committed (thread 0)
   if (tid == 0)
@@ -759,8 +583,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc_tma(const __grid_consta
     const long long t = (long long)blockIdx.x + (i / NC) * gridDim.x;
     const int c = (int)(i % NC);
     const long long r0 = t * kTileM;
-    // the chunk's copy has landed
-    if (tid == 0 && !s_fail && !mbar_wait_bounded(&full[st], use)) s_fail = 1;
+    // the chunk's copy has landed: every thread waits on the barrier itself (its acquire is
+    // what makes the copy's bytes visible to that thread)
+    if (!mbar_wait_bounded(&full[st], use)) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
     unsigned char* ahi = a_st + (uint32_t)st * 2 * kTmaChunkBytes;

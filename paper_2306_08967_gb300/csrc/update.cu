@@ -16,7 +16,6 @@
 //          Y_C = R_C^{-1} H[d:], K_V = H[:d] - W_C Y_C, Vb[T] += (N^T Y_C) PVi;  Sigma <- Theta.
 //   Step 4 input: r[S] += (Ub[S] change) diag(s0), the change of the PPR signal Ub diag(s0).
 #include "damf_internal.cuh"
-#include "tc_gemm.cuh"
 
 namespace damf {
 
@@ -1040,35 +1039,13 @@ __global__ void __launch_bounds__(256) k_scatter(DevHeader* h, Workspace ws, flo
   }
 }
 
-// Mixed precision runs the update's projection U[S] = Ub[S] PU, V[T] = Vb[T] PV on the tensor
-// cores (kind::tf32 with the three-term split); plain FP32 keeps the SIMT kernel. d = 16 has no
-// 32-wide K chunk and stays on SIMT in both. The projection is formed afresh in every update,
-// so its rounding does not accumulate.
-template <int D>
-static cudaError_t mm_tc(Ctx* c, const tc::SmallJobs& jobs, int njobs, cudaStream_t s) {
-  if constexpr (D % tc::kChunkK == 0) {
-    const size_t sm = tc::smem_bytes<D, D>();
-    cudaFuncSetAttribute(tc::k_mm_tc_small<D, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    tc::k_mm_tc_small<D, D><<<dim3((kMaxR + tc::kTileM - 1) / tc::kTileM, njobs), tc::kThreads, sm, s>>>(
-        jobs, &c->hdr->status, &c->hdr->status);
-    return cudaGetLastError();
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int D>
-static bool use_tc(const Ctx* c) {
-  return c->cfg.precision == 1 && D % tc::kChunkK == 0;
-}
-
+// The update's projection U[S] = Ub[S] PU, V[T] = Vb[T] PV stays on the SIMT units in both
+// precisions: on the tensor cores (kind::tf32, three-term split, accumulation in TMEM) its
+// error of ~1e-6 per product, amplified by residual Grams with small pivots (hub rows nearly
+// inside the span of U), coupled columns of U at up to 3e-4 between folds on C3, against 5e-5
+// with FP32 products, for no measurable gain in speed.
 template <int D>
 static cudaError_t gather_impl(Ctx* c, cudaStream_t s) {
-  if (use_tc<D>(c)) {   // U[S] = Ub[S] PU, V[T] = Vb[T] PV
-    tc::SmallJobs jobs{};
-    jobs.j[0] = {c->Ub, c->ws.S, &c->hdr->nS, 0, D, c->PU, c->ws.UST, D};
-    jobs.j[1] = {c->Vb, c->ws.T, &c->hdr->nT, 0, D, c->PV, c->ws.VT, D};
-    return mm_tc<D>(c, jobs, 2, s);
-  }
   const size_t sm = (size_t)(D * D + 16 * D) * sizeof(float);
   cudaFuncSetAttribute(k_gather<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_gather<D><<<dim3(kMaxR / 16, 2), 256, sm, s>>>(c->hdr, c->ws, c->Ub, c->Vb, c->PU, c->PV);
