@@ -254,9 +254,11 @@ __global__ void __launch_bounds__(256) k_assemble(DevHeader* h, Workspace ws, co
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     float s = (i == j && i < D) ? sigma[i] : 0.0f;
     if (i < D) {
-      for (int a = 0; a < nS; ++a) s = fmaf(ws.UST[a * D + i], Rj[a], s);
+#pragma unroll 8
+      for (int a = 0; a < nS; ++a) s = fmaf(ws.UST[a * D + i], Rj[a], s);   // loads of 8 rows in flight
     } else {
       const float* rb = ws.RB + (i - D) * kMaxR;
+#pragma unroll 8
       for (int a = 0; a < nS; ++a) s = fmaf(rb[a], Rj[a], s);
     }
     ws.M[(size_t)j * m + i] = s;
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(128) k_hmat(DevHeader* h, Workspace ws) {
   __syncthreads();
   for (int k = threadIdx.x; k < D; k += blockDim.x) {
     float s = 0.f;
-    for (int i = 0; i < m; ++i) s = fmaf(Mj[i], ws.E[i * D + k], s);
+#pragma unroll 8
+    for (int i = 0; i < m; ++i) s = fmaf(Mj[i], ws.E[i * D + k], s);   // eight rows' loads in flight
     const float t = ws.theta[k];
     ws.H[j * D + k] = t > 0.f ? s / t : 0.0f;
   }
@@ -393,10 +396,22 @@ __device__ __forceinline__ void fo_pq_col(const Workspace& ws, int nS, const flo
     q = fma((Acc)hv[i + 2], (Acc)w.z, q);
     q = fma((Acc)hv[i + 3], (Acc)w.w, q);
   }
-  // R_B and R_C are upper triangular: column a has rows 0 .. a
-  for (int b = 0; b <= a; ++b) {
-    p = fma((Acc)ev[D + b], (Acc)ws.RB[b * kMaxR + a], p);
-    q = fma((Acc)hv[D + b], (Acc)ws.RC[b * kMaxR + a], q);
+  // R_B and R_C are upper triangular: column a has rows 0 .. a (eight rows' loads in flight
+  // before their products, the sums in row order)
+  for (int b0 = 0; b0 <= a; b0 += 8) {
+    float rb[8], rc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      rb[j] = b0 + j <= a ? ws.RB[(b0 + j) * kMaxR + a] : 0.0f;
+      rc[j] = b0 + j <= a ? ws.RC[(b0 + j) * kMaxR + a] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (b0 + j <= a) {
+        p = fma((Acc)ev[D + b0 + j], (Acc)rb[j], p);
+        q = fma((Acc)hv[D + b0 + j], (Acc)rc[j], q);
+      }
+    }
   }
 }
 
@@ -459,6 +474,7 @@ __global__ void __launch_bounds__(256) k_fo_apply(DevHeader* h, Workspace ws) {
   extern __shared__ float smem[];
   float* Gs = smem;            // D x D: A or B
   float* Xs = smem + D * D;    // 16 x D
+  float* Ts = Xs + 16 * D;     // D x (D + 1): T, read once with coalesced loads
   if (h->status != 0 || h->nS == 0) return;
   const int m = D + h->nS;
   const int r0 = blockIdx.x * 16;
@@ -466,12 +482,14 @@ __global__ void __launch_bounds__(256) k_fo_apply(DevHeader* h, Workspace ws) {
   const int side = blockIdx.y;
   float* X = side == 0 ? ws.E : ws.H;
   const float* T = ws.foT;
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) Ts[(o / D) * (D + 1) + o % D] = T[o];
+  __syncthreads();
   for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
     const int j = o / D, k = o % D;
     float g = 0.0f;
     if (j != k) {
-      const float tj = T[j * D + j], tk = T[k * D + k];
-      const float fjk = T[j * D + k], fkj = T[k * D + j];
+      const float tj = Ts[j * (D + 1) + j], tk = Ts[k * (D + 1) + k];
+      const float fjk = Ts[j * (D + 1) + k], fkj = Ts[k * (D + 1) + j];
       const float den = tk * tk - tj * tj;
       if (fabsf(den) >= 1e-4f * (tj * tj + tk * tk) && den != 0.0f) {
         const float id = 1.0f / den;
@@ -586,9 +604,23 @@ __global__ void __launch_bounds__(128) k_fo_norm_theta(DevHeader* h, Workspace w
       q = df_add_prod(q, hv[i + 2], w.z);
       q = df_add_prod(q, hv[i + 3], w.w);
     }
-    for (int b = 0; b <= a; ++b) {   // R_B and R_C are upper triangular: column a has rows 0 .. a
-      p = df_add_prod(p, ev[D + b], ws.RB[b * kMaxR + a]);
-      q = df_add_prod(q, hv[D + b], ws.RC[b * kMaxR + a]);
+    // R_B and R_C are upper triangular: column a has rows 0 .. a; eight rows' loads are issued
+    // before their sums, so the loop does not wait on one L2 round trip per row
+    for (int b0 = 0; b0 <= a; b0 += 8) {
+      float rb[8], rc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int b = b0 + j;
+        rb[j] = b <= a ? ws.RB[b * kMaxR + a] : 0.0f;
+        rc[j] = b <= a ? ws.RC[b * kMaxR + a] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (b0 + j <= a) {
+          p = df_add_prod(p, ev[D + b0 + j], rb[j]);
+          q = df_add_prod(q, hv[D + b0 + j], rc[j]);
+        }
+      }
     }
     // p q = p.hi q.hi + p.hi q.lo + p.lo q.hi (+ p.lo q.lo, below the precision kept)
     acc = df_add_prod(acc, p.hi, q.hi);
@@ -1075,7 +1107,7 @@ static cudaError_t refine_core(Ctx* c, cudaStream_t s) {
   cudaFuncSetAttribute(k_fo_t<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
   k_fo_t<D><<<dim3(D / TS, D / TS), 256, smt, s>>>(c->hdr, c->ws, c->sigma);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t sma = (size_t)(D * D + 16 * D) * sizeof(float);
+  const size_t sma = (size_t)(D * D + 16 * D + D * (D + 1)) * sizeof(float);
   cudaFuncSetAttribute(k_fo_apply<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
   k_fo_apply<D><<<dim3(kMaxM / 16, 2), 256, sma, s>>>(c->hdr, c->ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
