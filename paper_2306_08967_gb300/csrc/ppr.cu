@@ -767,9 +767,11 @@ __device__ __forceinline__ void help_others(const PushArgs* __restrict__ descs, 
 // runs that graph's push over its CTAs (its own queue, header and grid barrier among them); a
 // slot of several graphs has one CTA, which pushes them one after another. The rank d of each
 // graph selects the row shape; node count and full seeding come from the graph's device header,
-// so one captured launch serves every step.
+// so one captured launch serves every step. Three CTAs per SM (80 registers): the kernel holds
+// the task loop for every d, and at four (64 registers) it spilled 1.9 KB per thread; on the
+// 256-graph fleet three ran the push phase in 283 ms per step against 333 ms for four.
 template <bool SCALED>
-__global__ void __launch_bounds__(256, 4) k_push_group(const PushArgs* __restrict__ descs, const int* __restrict__ table,
+__global__ void __launch_bounds__(256, 3) k_push_group(const PushArgs* __restrict__ descs, const int* __restrict__ table,
                                                        int nslots, int plan, int ngraphs) {
   __shared__ PushArgs sa;
   __shared__ int s_s, s_n, s_all;
