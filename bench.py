@@ -5,13 +5,17 @@ A step is one batch of the workload through the whole hot path: damf_apply_edges
 (adjacency edit, projection, residual CholQR, core SVD, transform update, row rewrite,
 PPR residual fix-up) followed by damf_ppr_refresh (push until every residual <= eps).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config C2] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config C3] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the same
-workload (bounded sample per step) and prints the same metric with "impl": "reference".
+The default workload is C3 (the 2M-node graph, calls of 1-256 events, the fold every 256
+updates); the line adds both precisions over a longer window (precision_compare), the FP64
+oracle timed on the host cores (cpu_baseline) and its error on the same batches
+(err_vs_oracle). Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same workload (bounded sample per step) and prints the same metric with "impl":
+"reference".
 
 Other workloads (not the default line):
-  --config C3                     the 2M-node graph, batches of 1-256 events, the fold every 256
+  --config C1, C2                 the smaller single-graph workloads
   --config C4 [--graphs G]        many graphs per step: a fleet (every graph's update on its own
                                   stream, one grouped push), each step one CUDA graph replay
                                   after the push shares are autotuned; beside it the same step
