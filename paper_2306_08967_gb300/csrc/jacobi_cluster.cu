@@ -241,6 +241,8 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
       if (lane == 0) top[g] = rk < D ? 1 : 0;
     }
     __syncthreads();
+    bool wrot = false;   // this warp rotated in the sweep; the largest rel2 it rotated (lane 0)
+    float wrel2 = 0.f;
     for (int t = 0; t < kClL; ++t) {
       const int bx = cl_block(c, 0, t), by = cl_block(c, 1, t);
       const int nrounds = t == 0 ? 2 * bs - 1 : bs;
@@ -276,9 +278,9 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
               float rel2 = 0.f;
               const bool rot = two ? cl_rotate<true>(ap, aq, np, nq, lane, tol2, rel2)
                                    : cl_rotate<false>(ap, aq, np, nq, lane, tol2, rel2);
-              if (rot && lane == 0) {
-                s_rot = 1;
-                atomicMax(&s_rel2, __float_as_uint(rel2));   // non-negative floats order as their bits
+              if (rot) {
+                wrot = true;
+                wrel2 = fmaxf(wrel2, rel2);
               }
             }
           }
@@ -305,6 +307,11 @@ __global__ void __cluster_dims__(kClP, 1, 1) __launch_bounds__(kClThreads, 2)   
       __syncthreads();
       cur ^= 1;
     }
+    if (lane == 0 && wrot) {
+      s_rot = 1;
+      atomicMax(&s_rel2, __float_as_uint(wrel2));   // non-negative floats order as their bits
+    }
+    __syncthreads();
     // did any CTA rotate in this sweep?
     if (tid < kClP) {
       cl.map_shared_rank(s_flags, tid)[c] = s_rot;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_wct(DevHeader* h, Workspace ws) {
 
 // ---- a3: residual Grams and semi-definite Cholesky (one CTA per Gram) ----
 template <int D>
-__global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace ws) {
+__global__ void __launch_bounds__(kChainThreads, 2) k_chol(DevHeader* h, Workspace ws) {   // <= 64 registers
   // CTA 0: G_B = I - U[S] U[S]^T -> R_B; CTA 1: G_C = N N^T - (N V[T])(N V[T])^T -> R_C
   extern __shared__ float smem[];
   constexpr int LDX = D + 1;             // padded strides: a warp reads rows b, b + 1, ... of X
@@ -167,61 +167,108 @@ __global__ void __launch_bounds__(kChainThreads) k_chol(DevHeader* h, Workspace 
     }
   }
   __syncthreads();
-  if (tid == 0) {
+  const int lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {   // the pivot scale: the largest diagonal entry (at least 1)
     float mx = 1.0f;
-    for (int a = 0; a < nS; ++a) mx = fmaxf(mx, G[a * LG + a]);
-    scale = mx * kPivotTol;
-    kept = 0;
+    for (int a = lane; a < nS; a += 32) mx = fmaxf(mx, G[a * LG + a]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      scale = mx * kPivotTol;
+      kept = 0;
+    }
   }
   __syncthreads();
   // blocked right-looking Cholesky G = R^T R (R upper), panels of 32 rows; a pivot <= tol
-  // makes its row of R zero. Per panel [k0, k1): warp 0 factors the diagonal block, the
-  // 16 warps solve the panel's trailing columns (forward substitution with R11^T, lane l
-  // holding row k0 + l), then everyone updates the trailing block.
-  const int lane = tid & 31, warp = tid >> 5;
+  // makes its row of R zero. Per panel [k0, k1): warp 0 factors the diagonal block in
+  // registers, the 16 warps solve the panel's trailing columns (forward substitution with
+  // R11^T, lane l holding row k0 + l), then everyone updates the trailing block. Every entry
+  // sees the same operations in the same order as in the plain column-by-column algorithm.
+  constexpr int kTrailBlocks = kMaxR / 32 - 1;   // column blocks of 32 right of a panel
   for (int k0 = 0; k0 < nS; k0 += 32) {
     const int k1 = min(k0 + 32, nS);
+    const int nb = k1 - k0;
     if (warp == 0) {
-      for (int j = k0; j < k1; ++j) {
-        const float p = G[j * LG + j];
+      // lane b holds column k0 + b of the diagonal block, rows k0 .. k0 + b; lanes past the
+      // panel hold zero columns, whose pivots (0 <= tol) are dropped and change nothing
+      float g[32];
+#pragma unroll
+      for (int a = 0; a < 32; ++a) g[a] = (a <= lane && lane < nb) ? G[(k0 + a) * LG + k0 + lane] : 0.0f;
+      int kp = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float p = __shfl_sync(0xffffffffu, g[j], j);
         const float pv = p > scale ? sqrtf(p) : 0.0f;
         const float ip = pv > 0.f ? 1.0f / pv : 0.0f;
-        __syncwarp();
-        const int l = j + lane;            // row j of R inside the block: columns j .. k1 - 1
-        if (l < k1) G[j * LG + l] = (l == j) ? pv : G[j * LG + l] * ip;
-        if (lane == 0) kept += pv > 0.f;
-        __syncwarp();
-        for (int a = j + 1 + lane; a < k1; a += 32) {   // block rows below j: a, columns a .. k1 - 1
-          const float ra = G[j * LG + a];
-          for (int b = a; b < k1; ++b) G[a * LG + b] -= ra * G[j * LG + b];
+        kp += pv > 0.f;
+        g[j] = lane == j ? pv : (lane > j ? g[j] * ip : 0.0f);   // row j of R
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {                           // G[a][b] -= R[j][a] R[j][b]
+          if (a > j) g[a] = fmaf(-__shfl_sync(0xffffffffu, g[j], a), g[j], g[a]);
+          // (fixed trip count: g stays in registers; in lanes b < a this writes the lower
+          // entry G[a][b], which is set to zero at step a before any use and never stored)
         }
-        __syncwarp();
       }
+#pragma unroll
+      for (int a = 0; a < 32; ++a)
+        if (a <= lane && lane < nb) G[(k0 + a) * LG + k0 + lane] = g[a];
+      if (lane == 0) kept += kp;
     }
     __syncthreads();
-    // trailing columns c >= k1 of the panel's rows: R[k][c] = (G[k][c] - sum_{i<k} R[i][k] R[i][c]) / R[k][k]
+    // trailing columns c >= k1 of the panel's rows, four per warp at once:
+    // R[k][c] = (G[k][c] - sum_{i<k} R[i][k] R[i][c]) / R[k][k]
     const int ncol = nS - k1;
-    for (int c = warp; c < ncol; c += 16) {
-      const int col = k1 + c;
-      const int row = k0 + lane;
-      float x = row < k1 ? G[row * LG + col] : 0.0f;
-      for (int k = 0; k < k1 - k0; ++k) {
+    const int row = k0 + lane;
+    for (int c0 = 4 * warp; c0 < ncol; c0 += 4 * (nt / 32)) {
+      float x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = (row < k1 && c0 + q < ncol) ? G[row * LG + k1 + c0 + q] : 0.0f;
+      for (int k = 0; k < nb; ++k) {
         const float rkk = G[(k0 + k) * LG + k0 + k];
-        float y = __shfl_sync(0xffffffffu, x, k);
-        y = rkk > 0.f ? y / rkk : 0.0f;
-        if (lane == k) x = y;
-        else if (lane > k && row < k1) x = fmaf(-G[(k0 + k) * LG + row], y, x);
+        const bool below = lane > k && row < k1;
+        const float rk = below ? G[(k0 + k) * LG + row] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float y = __shfl_sync(0xffffffffu, x[q], k);
+          y = rkk > 0.f ? y / rkk : 0.0f;
+          if (lane == k) x[q] = y;
+          else if (below) x[q] = fmaf(-rk, y, x[q]);
+        }
       }
-      if (row < k1) G[row * LG + col] = x;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (row < k1 && c0 + q < ncol) G[row * LG + k1 + c0 + q] = x[q];
     }
     __syncthreads();
-    // trailing update of the upper triangle: G[a][b] -= sum_k R[k][a] R[k][b], k1 <= a <= b
-    for (int i = tid; i < ncol * ncol; i += nt) {
-      const int a = k1 + i / ncol, b = k1 + i % ncol;
-      if (b < a) continue;
-      float sacc = 0.f;
-      for (int k = k0; k < k1; ++k) sacc = fmaf(G[k * LG + a], G[k * LG + b], sacc);
-      G[a * LG + b] -= sacc;
+    // trailing update of the upper triangle, G[a][b] -= sum_k R[k][a] R[k][b] (k1 <= a <= b):
+    // a warp takes rows a0 .. a0 + 3 against the columns k1 + lane + 32 c
+    for (int a0 = k1 + 4 * warp; a0 < nS; a0 += 4 * (nt / 32)) {
+      float acc[4][kTrailBlocks];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kTrailBlocks; ++c) acc[r][c] = 0.f;
+      for (int k = k0; k < k1; ++k) {
+        float ra[4], rb[kTrailBlocks];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ra[r] = a0 + r < nS ? G[k * LG + a0 + r] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < kTrailBlocks; ++c) {
+          const int b = k1 + lane + 32 * c;
+          rb[c] = b < nS ? G[k * LG + b] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < kTrailBlocks; ++c) acc[r][c] = fmaf(ra[r], rb[c], acc[r][c]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kTrailBlocks; ++c) {
+          const int a = a0 + r, b = k1 + lane + 32 * c;
+          if (a <= b && b < nS) G[a * LG + b] -= acc[r][c];
+        }
     }
     __syncthreads();
   }
@@ -817,8 +864,68 @@ __device__ __forceinline__ void gj_inverse(DevHeader* h, const float* K, float* 
 
 // Register-tiled product of D x D matrices in shared memory (row stride D) by up to 512 threads:
 // MODE 0: C = A B;  MODE 1: C = I - A B;  MODE 2: C = A + A B (A and C must differ).
+// (not inlined: the product gets the kernel's whole register budget, nothing spills in its loop)
 template <int D, int MODE>
-__device__ __forceinline__ void smem_mm(const float* A, const float* B, float* C) {
+__device__ __noinline__ void smem_mm(const float* A, const float* B, float* C) {
+  if constexpr (D == 128) {
+    // 512 threads, 4 rows x 8 columns each: rows 4 ti .. 4 ti + 3, columns 4 tj .. 4 tj + 3 and
+    // 64 + 4 tj .. 64 + 4 tj + 3 (a half-warp reads 256 contiguous bytes of a row of B, the
+    // other half-warp the same: no bank conflicts); two k at a time from one 8-byte read of
+    // each row of A, and column pairs through paired FMAs. Every output is the same
+    // sequence of FMAs in increasing k as in the generic path below.
+    const int tid = threadIdx.x;
+    if (tid >= 512) return;
+    const int i0 = (tid >> 4) * 4, j0 = (tid & 15) * 4;
+    float2 acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int k = 0; k < D; k += 2) {
+      float2 a2r[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a2r[r] = *reinterpret_cast<const float2*>(A + (i0 + r) * D + k);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const float4 bl = *reinterpret_cast<const float4*>(B + (k + kk) * D + j0);
+        const float4 bh = *reinterpret_cast<const float4*>(B + (k + kk) * D + 64 + j0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float av = kk == 0 ? a2r[r].x : a2r[r].y;
+          const float2 a2 = make_float2(av, av);
+          acc[r][0] = __ffma2_rn(a2, make_float2(bl.x, bl.y), acc[r][0]);
+          acc[r][1] = __ffma2_rn(a2, make_float2(bl.z, bl.w), acc[r][1]);
+          acc[r][2] = __ffma2_rn(a2, make_float2(bh.x, bh.y), acc[r][2]);
+          acc[r][3] = __ffma2_rn(a2, make_float2(bh.z, bh.w), acc[r][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = h * 64 + j0;
+        float4 v = make_float4(acc[r][2 * h].x, acc[r][2 * h].y, acc[r][2 * h + 1].x, acc[r][2 * h + 1].y);
+        if (MODE == 1) {
+          v.x = (i == j ? 1.0f : 0.0f) - v.x;
+          v.y = (i == j + 1 ? 1.0f : 0.0f) - v.y;
+          v.z = (i == j + 2 ? 1.0f : 0.0f) - v.z;
+          v.w = (i == j + 3 ? 1.0f : 0.0f) - v.w;
+        }
+        if (MODE == 2) {
+          const float4 a = *reinterpret_cast<const float4*>(A + i * D + j);
+          v.x += a.x;
+          v.y += a.y;
+          v.z += a.z;
+          v.w += a.w;
+        }
+        *reinterpret_cast<float4*>(C + i * D + j) = v;
+      }
+    }
+    return;
+  }
   using S = MMShape<D>;
   const int tid = threadIdx.x;
   if (tid >= S::NT) return;
