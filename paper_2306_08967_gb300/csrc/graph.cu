@@ -192,21 +192,35 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     }
   }
   __syncthreads();
-  if (tid == 0) {  // compaction and S (edits are in (u, v) order)
-    int m = 0, s = 0;
-    for (int i = 0; i < ne; ++i) {
-      if (sdelta[i] == 0) continue;
-      const int u = (int)(skey[i] >> 32), v = (int)(skey[i] & 0xffffffffu);
-      if (s == 0 || Srow[s - 1] != u) {
-        Srow[s] = u;
-        Sfirst[s] = m;
-        ++s;
+  if (tid < 32) {  // compaction and S (edits are in (u, v) order), 32 entries at a time
+    const int lane = tid;
+    const unsigned below = (1u << lane) - 1u;
+    int m = 0, s = 0, prevu = -1;   // edits and rows so far, the last edit's row
+    for (int base = 0; base < ne; base += 32) {
+      const int i = base + lane;
+      const bool live = i < ne && sdelta[i] != 0;
+      const int u = live ? (int)(skey[i] >> 32) : -1;
+      const unsigned lmask = __ballot_sync(0xffffffffu, live);
+      const unsigned lb = lmask & below;
+      const int pu = __shfl_sync(0xffffffffu, u, lb ? 31 - __clz(lb) : 0);
+      const bool head = live && (lb ? pu : prevu) != u;   // first edit of its row
+      const unsigned hmask = __ballot_sync(0xffffffffu, head);
+      const int pos = m + __popc(lb);
+      if (live) ed[pos] = make_int3(u, (int)(skey[i] & 0xffffffffu), sdelta[i]);
+      if (head) {
+        const int q = s + __popc(hmask & below);
+        Srow[q] = u;
+        Sfirst[q] = pos;
       }
-      ed[m++] = make_int3(u, v, sdelta[i]);
+      m += __popc(lmask);
+      s += __popc(hmask);
+      if (lmask) prevu = __shfl_sync(0xffffffffu, u, 31 - __clz(lmask));
     }
-    Sfirst[s] = m;
-    nedit = m;
-    nS = s;
+    if (lane == 0) {
+      Sfirst[s] = m;
+      nedit = m;
+      nS = s;
+    }
   }
   __syncthreads();
   // T: sorted unique columns; edT = edits ordered by (v, u)
@@ -220,18 +234,29 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     edT[rk] = make_int3(x.y, x.x, x.z);
   }
   __syncthreads();
-  if (tid == 0) {
-    int t = 0;
-    for (int i = 0; i < nedit; ++i) {
-      if (t == 0 || Tcol[t - 1] != edT[i].x) {
-        Tcol[t] = edT[i].x;
-        Tfirst[t] = i;
-        ++t;
+  if (tid < 32) {  // T's heads: the first edit of each column, 32 edits at a time
+    const int lane = tid;
+    const unsigned below = (1u << lane) - 1u;
+    int t = 0, prevv = -1;   // columns so far, the last edit's column
+    for (int base = 0; base < nedit; base += 32) {
+      const int i = base + lane;
+      const int v = i < nedit ? edT[i].x : -1;
+      const int pv = __shfl_up_sync(0xffffffffu, v, 1);
+      const bool head = i < nedit && (lane == 0 ? prevv : pv) != v;
+      const unsigned hmask = __ballot_sync(0xffffffffu, head);
+      if (head) {
+        const int q = t + __popc(hmask & below);
+        Tcol[q] = v;
+        Tfirst[q] = i;
       }
+      t += __popc(hmask);
+      prevv = __shfl_sync(0xffffffffu, v, 31);
     }
-    Tfirst[t] = nedit;
-    nT = t;
-    nTrow = t;
+    if (lane == 0) {
+      Tfirst[t] = nedit;
+      nT = t;
+      nTrow = t;
+    }
   }
   __syncthreads();
   // capacity check (before any write): one thread per touched row, then a prefix sum
@@ -253,28 +278,41 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    long long need = 0;
+  if (tid < 32) {   // relocation offsets: exclusive prefix sums in one warp, 32 rows at a time
+    const int lane = tid;
+    auto plan = [&](const int* rcap, long long* reloc, int cnt, long long t0) {
+      long long need = 0;
+      for (int base = 0; base < cnt; base += 32) {
+        const int q = base + lane;
+        const long long c = q < cnt ? rcap[q] : 0;
+        long long incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (q < cnt) reloc[q] = c ? t0 + need + (incl - c) : -1;
+        need += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      return need;
+    };
     const long long t0 = h->tail_out;
-    for (int q = 0; q < nS; ++q) {
-      relocS[q] = rcapS[q] ? t0 + need : -1;
-      need += rcapS[q];
-    }
-    if (t0 + need > out.m_cap) fail = 1;
+    const long long need = plan(rcapS, relocS, nS, t0);
+    bool over = t0 + need > out.m_cap;
     long long needT = 0;
     if (DIRECTED) {
       const long long t1 = h->tail_in;
-      for (int q = 0; q < nTrow; ++q) {
-        relocT[q] = rcapT[q] ? t1 + needT : -1;
-        needT += rcapT[q];
-      }
-      if (t1 + needT > in.m_cap) fail = 1;
+      needT = plan(rcapT, relocT, nTrow, t1);
+      over = over || t1 + needT > in.m_cap;
     }
-    if (fail) {
-      set_status(h, DAMF_ERR_CAPACITY);
-    } else {
-      h->tail_out = t0 + need;
-      if (DIRECTED) h->tail_in += needT;
+    if (lane == 0) {
+      if (over) {
+        fail = 1;
+        set_status(h, DAMF_ERR_CAPACITY);
+      } else {
+        h->tail_out = t0 + need;
+        if (DIRECTED) h->tail_in += needT;
+      }
     }
   }
   __syncthreads();
@@ -303,10 +341,17 @@ __global__ void __launch_bounds__(512) k_prepare(DevHeader* h, Adj out, Adj in, 
   __syncthreads();
   for (int e = tid; e < nedit; e += blockDim.x) {
     const int3 x = ed[e];
-    int a = 0;
-    while (Srow[a] != x.x) ++a;
-    int b = 0;
-    while (Tcol[b] != x.y) ++b;
+    int a = 0, b = 0;   // positions of x's row in S and column in T (both sorted, unique)
+    for (int hi = nS - 1; a < hi;) {
+      const int mid = (a + hi) >> 1;
+      if (Srow[mid] < x.x) a = mid + 1;
+      else hi = mid;
+    }
+    for (int hi = nT - 1; b < hi;) {
+      const int mid = (b + hi) >> 1;
+      if (Tcol[mid] < x.y) b = mid + 1;
+      else hi = mid;
+    }
     ws.N[a * nT + b] = (float)x.z;
     ws.edits[e] = make_int4(x.x, x.y, x.z, a);
     if (DIRECTED) ws.editsT[e] = make_int4(edT[e].x, edT[e].y, edT[e].z, 0);

@@ -95,6 +95,64 @@ __global__ void __launch_bounds__(256) k_wct(DevHeader* h, Workspace ws) {
 }
 
 // ---- a3: residual Grams and semi-definite Cholesky (one CTA per Gram) ----
+// Rows a0 .. a0 + 3 of a residual Gram (read by every lane at once) against the columns
+// lane + 32 c (consecutive rows of X, other banks), two column blocks per paired FMA. Only
+// the upper triangle is read later, so the column pairs p < P0 (blocks 2 p, 2 p + 1, all left
+// of a0) are skipped. Each entry is the same sequence of FMAs as one column at a time: the
+// N N^T terms (CTA 1) in increasing t, then the X X^T terms in increasing k.
+template <int D, int P0>
+__device__ __forceinline__ void chol_gram_rows(float* G, const float* X, const float* Ns, bool isC, int nS, int nT,
+                                               int a0, int lane) {
+  constexpr int LDX = D + 1, LDN = kMaxR + 1, LG = kMaxR + 1;
+  static_assert(kMaxR == 128, "four column blocks of 32");
+  const int ncol = (nS + 31) / 32;   // column blocks of 32 in use
+  float2 acc[4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) acc[r][q] = make_float2(0.f, 0.f);
+  if (isC) {
+    for (int t = 0; t < nT; ++t) {
+      float na[4];
+      float2 nb[2];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) na[r] = Ns[(a0 + r) * LDN + t];
+#pragma unroll
+      for (int q = P0; q < 2; ++q)
+        nb[q] = make_float2(2 * q < ncol ? Ns[(lane + 64 * q) * LDN + t] : 0.0f,
+                            2 * q + 1 < ncol ? Ns[(lane + 64 * q + 32) * LDN + t] : 0.0f);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = P0; q < 2; ++q) acc[r][q] = __ffma2_rn(make_float2(na[r], na[r]), nb[q], acc[r][q]);
+    }
+  }
+#pragma unroll 2
+  for (int k = 0; k < D; ++k) {
+    float xa[4];
+    float2 xb[2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) xa[r] = X[(a0 + r) * LDX + k];
+#pragma unroll
+    for (int q = P0; q < 2; ++q)
+      xb[q] = make_float2(2 * q < ncol ? X[(lane + 64 * q) * LDX + k] : 0.0f,
+                          2 * q + 1 < ncol ? X[(lane + 64 * q + 32) * LDX + k] : 0.0f);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = P0; q < 2; ++q) acc[r][q] = __ffma2_rn(make_float2(-xa[r], -xa[r]), xb[q], acc[r][q]);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = P0; q < 2; ++q)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int a = a0 + r, b = lane + 64 * q + 32 * hh;
+        if (a < nS && b < nS) G[a * LG + b] = (hh ? acc[r][q].y : acc[r][q].x) + ((!isC && a == b) ? 1.0f : 0.0f);
+      }
+}
+
 template <int D>
 __global__ void __launch_bounds__(kChainThreads, 2) k_chol(DevHeader* h, Workspace ws) {   // <= 64 registers
   // CTA 0: G_B = I - U[S] U[S]^T -> R_B; CTA 1: G_C = N N^T - (N V[T])(N V[T])^T -> R_C
@@ -112,62 +170,33 @@ __global__ void __launch_bounds__(kChainThreads, 2) k_chol(DevHeader* h, Workspa
   const int nS = h->nS, nT = h->nT;
   if (nS == 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const float* src = isC ? ws.WCt : ws.UST;
   // rows nS .. kMaxR - 1 are zero (the register tiles below read them)
   for (int i = tid; i < kMaxR * D; i += nt) X[(i / D) * LDX + i % D] = i < nS * D ? src[i] : 0.0f;
-  if (isC)
-    for (int i = tid; i < kMaxR * nT; i += nt) Ns[(i / nT) * LDN + i % nT] = i < nS * nT ? ws.N[i] : 0.0f;
-  __syncthreads();
-  // the symmetric Gram in register tiles: a warp takes 4 rows a0 .. a0 + 3 (read by every lane
-  // at once) against the columns lane, lane + 32, lane + 64, lane + 96 (consecutive rows of X,
-  // other banks): 8 shared-memory reads per 16 FMAs
-  {
-    const int lane = tid & 31, warp = tid >> 5;
-    const int ngrp = (nS + 3) / 4;
-    const int ncol = (nS + 31) / 32;   // column blocks of 32 in use
-    for (int grp = warp; grp < ngrp; grp += nt / 32) {
-      const int a0 = grp * 4;
-      float acc[4][4];
+  if (isC)   // a warp per two rows of N, four loads per row in flight
+    for (int r0 = 2 * warp; r0 < kMaxR; r0 += 2 * (nt / 32)) {
+      float v[2][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-      if (isC) {
-        for (int t = 0; t < nT; ++t) {
-          float na[4], nb[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) na[r] = Ns[(a0 + r) * LDN + t];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) nb[c] = c < ncol ? Ns[(lane + 32 * c) * LDN + t] : 0.0f;
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(na[r], nb[c], acc[r][c]);
+        for (int q = 0; q < 4; ++q) {
+          const int t = lane + 32 * q;
+          v[rr][q] = (r0 + rr < nS && t < nT) ? ws.N[(r0 + rr) * nT + t] : 0.0f;
         }
-      }
-#pragma unroll 2
-      for (int k = 0; k < D; ++k) {
-        float xa[4], xb[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) xa[r] = X[(a0 + r) * LDX + k];
+      for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) xb[c] = c < ncol ? X[(lane + 32 * c) * LDX + k] : 0.0f;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(-xa[r], xb[c], acc[r][c]);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int a = a0 + r, b = lane + 32 * c;
-          if (a < nS && b < nS) G[a * LG + b] = acc[r][c] + ((!isC && a == b) ? 1.0f : 0.0f);
-        }
+        for (int q = 0; q < 4; ++q)
+          if (lane + 32 * q < nT) Ns[(r0 + rr) * LDN + lane + 32 * q] = v[rr][q];
     }
+  __syncthreads();
+  // the Gram's upper triangle: a warp per four rows
+  for (int a0 = 4 * warp; a0 < nS; a0 += 4 * (nt / 32)) {
+    if (a0 < 64) chol_gram_rows<D, 0>(G, X, Ns, isC, nS, nT, a0, lane);
+    else chol_gram_rows<D, 1>(G, X, Ns, isC, nS, nT, a0, lane);
   }
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {   // the pivot scale: the largest diagonal entry (at least 1)
     float mx = 1.0f;
     for (int a = lane; a < nS; a += 32) mx = fmaxf(mx, G[a * LG + a]);
@@ -749,18 +778,90 @@ __global__ void __launch_bounds__(kChainThreads) k_trans(DevHeader* h, Workspace
     __syncthreads();
     // rows above the block: Y[i] -= R[i, block] Y[block]
     const int nb = min(32, nS - r0);
-    for (int o = tid; o < r0 * D; o += nt) {
-      const int i = o / D, col = o % D;
-      float s = 0.f;
-      for (int j = 0; j < nb; ++j) s = fmaf(R[i * LDR + r0 + j], Y[(r0 + j) * D + col], s);
-      Y[o] -= s;
+    if constexpr (D == 128) {
+      // warp w takes the rows w, w + 16, ... (at most six: r0 <= kMaxR - 32), lane l the
+      // columns 4 l .. 4 l + 3: one 16-byte read of a block row serves all the rows
+      static_assert(kMaxR - 32 <= 6 * 16, "six rows per warp");
+      float4 acc[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < nb; ++j) {
+        const float4 y = *reinterpret_cast<const float4*>(Y + (r0 + j) * D + 4 * lane);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const int i = warp + 16 * q;
+          if (i < r0) {
+            const float rij = R[i * LDR + r0 + j];
+            acc[q].x = fmaf(rij, y.x, acc[q].x);
+            acc[q].y = fmaf(rij, y.y, acc[q].y);
+            acc[q].z = fmaf(rij, y.z, acc[q].z);
+            acc[q].w = fmaf(rij, y.w, acc[q].w);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int i = warp + 16 * q;
+        if (i < r0) {
+          float4* yi = reinterpret_cast<float4*>(Y + i * D + 4 * lane);
+          float4 v = *yi;
+          v.x -= acc[q].x;
+          v.y -= acc[q].y;
+          v.z -= acc[q].z;
+          v.w -= acc[q].w;
+          *yi = v;
+        }
+      }
+    } else {
+      for (int o = tid; o < r0 * D; o += nt) {
+        const int i = o / D, col = o % D;
+        float s = 0.f;
+        for (int j = 0; j < nb; ++j) s = fmaf(R[i * LDR + r0 + j], Y[(r0 + j) * D + col], s);
+        Y[o] -= s;
+      }
     }
     __syncthreads();
   }
   for (int i = tid; i < nS * D; i += nt) Yg[i] = Y[i];
   // K = E[:d] - W Y with W = Wts^T: register tiles (TR x TC outputs per thread)
   using S = MMShape<D>;
-  if (tid < S::NT) {
+  if constexpr (D == 128) {
+    // rows 4 ti .. 4 ti + 3 and columns 4 tj .. + 3, 64 + 4 tj .. + 3 (as in smem_mm): one
+    // 16-byte read of W^T and two of Y per a, paired FMAs; the same FMAs in increasing a
+    const int i0 = (tid >> 4) * 4, j0 = (tid & 15) * 4;
+    float2 acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int a = 0; a < nS; ++a) {
+      const float4 w = *reinterpret_cast<const float4*>(Wts + a * D + i0);
+      const float4 bl = *reinterpret_cast<const float4*>(Y + a * D + j0);
+      const float4 bh = *reinterpret_cast<const float4*>(Y + a * D + 64 + j0);
+      const float wr[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float2 a2 = make_float2(wr[r], wr[r]);
+        acc[r][0] = __ffma2_rn(a2, make_float2(bl.x, bl.y), acc[r][0]);
+        acc[r][1] = __ffma2_rn(a2, make_float2(bl.z, bl.w), acc[r][1]);
+        acc[r][2] = __ffma2_rn(a2, make_float2(bh.x, bh.y), acc[r][2]);
+        acc[r][3] = __ffma2_rn(a2, make_float2(bh.z, bh.w), acc[r][3]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int j = hh * 64 + j0;
+        const float4 e = *reinterpret_cast<const float4*>(Eg + i * D + j);
+        *reinterpret_cast<float4*>(K + i * D + j) =
+            make_float4(e.x - acc[r][2 * hh].x, e.y - acc[r][2 * hh].y, e.z - acc[r][2 * hh + 1].x,
+                        e.w - acc[r][2 * hh + 1].y);
+      }
+    }
+  } else if (tid < S::NT) {
     const int i0 = (tid / S::NTJ) * S::TR, j0 = (tid % S::NTJ) * S::TC;
     float acc[S::TR][S::TC];
 #pragma unroll
