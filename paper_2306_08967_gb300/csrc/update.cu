@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_wct(DevHeader* h, Workspace ws) {
 // ---- a3: residual Grams and semi-definite Cholesky (one CTA per Gram) ----
 // Rows a0 .. a0 + 3 of a residual Gram (read by every lane at once) against the columns
 // lane + 32 c (consecutive rows of X, other banks), two column blocks per paired FMA. Only
-// the upper triangle is read later, so the column pairs p < P0 (blocks 2 p, 2 p + 1, all left
+// the upper triangle is read later, so the column pairs q < P0 (blocks 2 q, 2 q + 1, all left
 // of a0) are skipped. Each entry is the same sequence of FMAs as one column at a time: the
 // N N^T terms (CTA 1) in increasing t, then the X X^T terms in increasing k.
 template <int D, int P0>
